@@ -1,0 +1,432 @@
+#!/usr/bin/env python
+"""Benchmark: forward + adjoint evaluations per second of the coded-aperture
+coherent-scatter operators on the paper-scale workload.
+
+Workload (one "step" = one penalised EM-type iteration, i.e. one forward
+model, one adjoint and the elementwise update, through caxsi_recon_step):
+object 256 (y, across the fan) x 128 (x, along the beam) voxels x 128 q bins
+(0.1-3.5 nm^-1), detector 256 x 64 pixels, 64 energy bins (20-100 keV),
+tungsten-like spectrum, Bernoulli(0.5) mask with a 2-pixel feature, 10 seeded
+phantoms (up to 8 ellipses with Bragg-peak profiles), Poisson counts with a
+peak log-uniform in [1e2, 1e4].  Steps cycle through the phantoms, whose
+states (10 x 16.8 MB) exceed the 129 MB L2 together with the operator tables.
+
+Multi-GPU: the phantoms are independent problems; ranks take disjoint
+phantoms and run without any data-path collective (weak scaling).
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "fwd+adj evals/s"
+UNIT = "evals/s"
+N_PHANTOMS = 10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--path", default="direct",
+                    choices=["direct", "table_fp32", "table_bf16", "table_fp16"])
+    ap.add_argument("--workload", choices=["paper", "tiny"], default="paper")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def geometry(name):
+    return synth.paper_geometry() if name == "paper" else synth.tiny_geometry()
+
+
+def workload_desc(g, name):
+    return (f"{'paper-scale' if name == 'paper' else 'tiny'} fan-beam coded-aperture scatter: "
+            f"object {g.J}(y) x {g.X}(x) voxels x {g.Q} q bins ({g.q_min}-{g.q_max} nm^-1), "
+            f"detector {g.N}x{g.M} pixels, {g.K} energy bins ({g.E_min:g}-{g.E_max:g} keV); "
+            f"penalised EM step (A, ratio, A^T, update) over {N_PHANTOMS} seeded phantoms")
+
+
+def mask_seed(name):
+    return synth.PAPER_MASK_SEED if name == "paper" else synth.TINY_MASK_SEED
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [s for (t, s) in self.samples if t0 <= t <= t1] or [s for _, s in self.samples]
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            parts = [p.strip() for p in r.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_query_id(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[dev] if vis else str(dev)
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def kernel_work(name, g, info, path):
+    """Algorithmic work of one launch of the named kernel (units, amount, bound)."""
+    open_pairs = info["n_open_pairs"]
+    if name in ("fwd_direct", "adj_direct"):
+        # per open (voxel, pixel) pair: K energy terms of 8 flop (tau FMA, floor,
+        # fraction, lerp FMA, accumulate FMA) plus 30 flop of scatter geometry
+        return "TFLOP/s", open_pairs * (8.0 * g.K + 30.0), "alu"
+    return None, None, None
+
+
+def traffic_for(name, path):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        ent = d.get(name)
+        if not ent:
+            return None
+        src = os.path.join(ROOT, "paper_1603_06400_gb300", "csrc", ent["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return ent["dram_bytes_per_launch"] if sha == ent["source_sha"] else None
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timings (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_eval_seconds(g, phi, mask, f, w, n_pix, n_vox, seed):
+    import oracle
+    rng = np.random.default_rng(seed)
+    pix = rng.choice(g.M * g.N, size=min(n_pix, g.M * g.N), replace=False)
+    vox = rng.choice(g.X * g.J, size=min(n_vox, g.X * g.J), replace=False)
+    t0 = time.perf_counter()
+    oracle.forward_pixels(g, phi, mask, f, pix)
+    t1 = time.perf_counter()
+    oracle.adjoint_voxels(g, phi, mask, w, vox)
+    t2 = time.perf_counter()
+    per_eval = (t1 - t0) * (g.M * g.N / len(pix)) + (t2 - t1) * (g.X * g.J / len(vox))
+    return per_eval, (t2 - t0), len(pix), len(vox)
+
+
+def cpu_inputs(g):
+    phi = synth.tungsten_spectrum(g)
+    mask = synth.random_mask(g, mask_seed("paper" if g.X == 128 else "tiny"))
+    f = synth.phantom(g, 0)
+    w = synth.uniform_random((g.M, g.N), 1)
+    return phi, mask, f, w
+
+
+def cpu_baseline(g, target_s=15.0):
+    import oracle
+    phi, mask, f, w = cpu_inputs(g)
+    # size the sample from a short probe so that it takes ~target_s seconds
+    probe, took, npx, nvx = oracle_eval_seconds(g, phi, mask, f, w, 32, 32, 99)
+    scale = max(1.0, target_s / max(took, 1e-3))
+    n_pix = int(min(g.M * g.N, 32 * scale))
+    n_vox = int(min(g.X * g.J, 32 * scale))
+    per_eval, took, npx, nvx = oracle_eval_seconds(g, phi, mask, f, w, n_pix, n_vox, 7)
+    return {"value": 1.0 / per_eval, "unit": UNIT, "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"FP64 direct-summation oracle on {npx} sampled pixels (forward) and "
+                      f"{nvx} sampled voxels (adjoint) of one phantom, {took:.1f} s wall, "
+                      f"scaled to one full forward + adjoint"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    g = geometry(args.workload)
+    phi, mask, f, w = cpu_inputs(g)
+    # per step a bounded sample (~1 s of CPU work) of one forward + adjoint
+    probe, took, _, _ = oracle_eval_seconds(g, phi, mask, f, w, 16, 16, 1)
+    scale = max(1.0, 1.0 / max(took, 1e-3))
+    n = int(min(g.M * g.N, 16 * scale))
+    times = []
+    for s in range(args.warmup + args.steps):
+        per_eval, _, npx, nvx = oracle_eval_seconds(g, phi, mask, f, w, n, n, 1000 + s)
+        if s >= args.warmup:
+            times.append(per_eval)
+    mean = float(np.mean(times))
+    value = 1.0 / mean
+    cores = oracle.max_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(g, args.workload), "path": "oracle",
+                   "l2": "host CPU"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: FP64 oracle forward on {npx} sampled pixels and "
+                                   f"adjoint on {nvx} sampled voxels, scaled to one full "
+                                   f"forward + adjoint"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1603_06400_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    from paper_1603_06400_gb300 import caxsi
+
+    g = geometry(args.workload)
+    phi = synth.tungsten_spectrum(g)
+    mask = synth.random_mask(g, mask_seed(args.workload))
+    path = caxsi.PATHS[args.path]
+    plan = caxsi.Plan(g, phi, mask)
+    info = plan.info()
+
+    # this rank's phantoms (disjoint across ranks)
+    mine = [p for p in range(N_PHANTOMS) if p % world == rank] or [rank % N_PHANTOMS]
+    states = []
+    ones = torch.ones((g.M, g.N), device=dev)
+    b1 = plan.adjoint(ones, path=path)
+    for p in mine:
+        f_true = torch.tensor(synth.phantom(g, p), dtype=torch.float32, device=dev)
+        mean = plan.forward(f_true, path=path)
+        peak = synth.log_uniform_peak(p)
+        y = torch.tensor(synth.poisson_counts((mean * (peak / mean.max())).cpu().numpy().astype(
+            np.float64), 100 + p), dtype=torch.float32, device=dev)
+        f0 = torch.full((g.X, g.J, g.Q), float(y.sum() / b1.sum()), device=dev)
+        beta = 1e-3 * float(y.sum()) / (g.X * g.J * g.Q)
+        delta = 0.01 * float(f0.max())
+        states.append((y, f0, beta, delta))
+    torch.cuda.synchronize()
+
+    def step(t):
+        y, f, beta, delta = states[t % len(states)]
+        plan.recon_step(y, f, beta=beta, delta=delta, path=path)
+
+    for t in range(args.warmup):
+        step(t)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(gpu_query_id(torch, local))
+    time.sleep(0.6)  # let the sampler start
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    plan.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    e0.record(stream)
+    for t in range(args.steps):
+        step(args.warmup + t)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall1 = time.time()
+    ms = e0.elapsed_time(e1)
+    kstats = plan.profile_read()
+    plan.profile(False)
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+
+    ms_max = ms
+    if dist:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_max = float(tt.item())
+    total_evals = args.steps * world
+    value = total_evals / (ms_max / 1e3)
+
+    # e2e through the host-buffer C calls (pinned host memory), per step one
+    # forward + one adjoint with their copies
+    e2e = None
+    if not args.no_e2e:
+        fh = torch.tensor(synth.phantom(g, mine[0]), dtype=torch.float32).pin_memory().numpy()
+        wh = torch.rand((g.M, g.N), dtype=torch.float32).pin_memory().numpy()
+        gh = torch.empty((g.M, g.N), dtype=torch.float32).pin_memory().numpy()
+        fo = torch.empty((g.X, g.J, g.Q), dtype=torch.float32).pin_memory().numpy()
+        n_e2e = max(3, min(args.steps, 50))
+        for _ in range(3):
+            plan.forward_host(fh, out=gh, path=path)
+            plan.adjoint_host(wh, out=fo, path=path)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            plan.forward_host(fh, out=gh, path=path)
+            plan.adjoint_host(wh, out=fo, path=path)
+        el = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([el], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = float(tt.item())
+        e2e = {"value": n_e2e * world / el, "unit": UNIT,
+               "h2d_bytes_per_step": int((g.f_len + g.g_len) * 4),
+               "d2h_bytes_per_step": int((g.g_len + g.f_len) * 4),
+               "api": "caxsi_forward_host + caxsi_adjoint_host (pinned host buffers)"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_kind = measured_peaks()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    kernels = {k: {"launches": n, "avg_ms": tot / max(n, 1), "total_ms": tot}
+               for k, (n, tot) in kstats.items()}
+    dom = max(kernels, key=lambda k: kernels[k]["total_ms"]) if kernels else None
+    roofline = None
+    if dom:
+        unit, work, bound = kernel_work(dom, g, info, path)
+        if work is not None:
+            avg_s = kernels[dom]["avg_ms"] / 1e3
+            if bound == "alu":
+                # FP32 FMA pipes: 128 lanes per SM x 2 flop at the maximum SM clock
+                peak = nsm * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+                peak_note = (f"FP32 SIMT: {nsm} SMs x 128 lanes x 2 flop x "
+                             f"{peaks.get('sm_max_mhz', 2070.0):g} MHz ({peak_kind} clock)")
+            achieved = work / avg_s / 1e12
+            roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
+                        "unit": unit, "frac": achieved / peak,
+                        "traffic": traffic_for(dom, path), "peak_source": peak_note,
+                        "work_per_launch": work}
+    launches = sum(n for n, _ in kstats.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(g, args.workload), "path": args.path,
+                   "l2": f"inputs larger than L2: {len(states)} phantom states of "
+                         f"{g.f_len * 4 / 1e6:.1f} MB cycled per step plus "
+                         f"{info['table_bytes'] / 1e6:.0f} MB of plan tables",
+                   "phantoms_per_rank": len(states)},
+        "roofline": roofline,
+        "cpu_baseline": None,
+        "e2e": e2e,
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                   "reasons": clocks["reasons"], "samples": clocks["samples"]},
+        "gpu_launches": launches,
+        "kernels": kernels,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g)
+    print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * caxsi.h -- C ABI of the GB300 (sm_103a) library for the fan-beam
+ * coded-aperture X-ray coherent-scatter forward model g = A f and its
+ * adjoint f = A^T w (Odinaka et al., arXiv:1603.06400).
+ *
+ * Model (Sec. II, Eq. 1-4, Appendix A).  With the source at the origin and
+ * the fan in the plane z = 0, object voxel (i, j) sits at r = (x_i, y_j, 0)
+ * and detector pixel (m, n) at r' = (X_det, y'_n, z'_m); s = r' - r.  Then
+ *
+ *   g[m][n] = C sum_{i,j} G_so(r) G_od(s) T(r, r') dtheta(s) W(r, theta),
+ *   W(r, theta) = (1 + cos^2 theta) cos(theta/2)
+ *                 * sum_k Phi_k E_k dE / hc^2 * f~(r, E_k sin(theta/2) / hc),
+ *
+ * G_so = x/(x^2+y^2)^1.5, G_od = |s_x|/|s|^3, theta the angle between r and
+ * s, dtheta the angle between the scatter vectors to the pixel's two z edges,
+ * T the binary mask value where the ray crosses the mask plane x = X_mask,
+ * E_k the midpoints of K equal energy bins on [E_min, E_max] (the energy form
+ * of Eq. 4 under Bragg's law q = E sin(theta/2)/hc), and f~ the linear
+ * interpolation of the samples f[i][j][l] at q_l = q_min + l dq,
+ * dq = (q_max - q_min)/(Q - 1), with a zero sample one step beyond each end.
+ *
+ * Layouts (all row-major, float32 on the device unless stated):
+ *   f : [X][J][Q]  voxel i along the central ray, j across the fan, q fastest
+ *       (the lexicographic voxel-by-channel order of Eq. 5).
+ *   g, w, y, r : [M][N]  detector row m (z), column n (y), n fastest.
+ *
+ * Centres: x_i = x_center + (i - (X-1)/2) dx, y_j = (j - (J-1)/2) rho_y p_y,
+ *          y'_n = (n - (N-1)/2) p_y, z'_m = (m - (M-1)/2) p_z.
+ * The object pitch along y is rho_y detector pitches (Sec. III-A translation
+ * symmetry).  Mask cell (row, col) covers
+ *   [mask_z0 + row*cell, +cell) x [mask_y0 + col*cell, +cell) on the mask plane;
+ * the transmission is 0 outside the mask array.
+ *
+ * Ownership and streams.  The caller owns every buffer passed in and the
+ * stream (a cudaStream_t passed as void*, NULL = legacy default stream).
+ * A plan owns its device tables and its scratch; entry points that take
+ * device pointers are asynchronous on the given stream unless stated.  Calls
+ * that share one plan must be ordered (same stream, or synchronised by the
+ * caller): they share the plan's scratch memory.
+ *
+ * Errors.  Every entry point returns a caxsi_status; nothing is thrown across
+ * the ABI and nothing aborts.  Null pointers, wrong lengths and invalid
+ * geometry give CAXSI_ERR_INVALID without launching anything.  A CUDA
+ * failure gives CAXSI_ERR_CUDA.
+ */
+#ifndef CAXSI_H
+#define CAXSI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct caxsi_plan caxsi_plan;
+
+typedef enum {
+    CAXSI_OK = 0,
+    CAXSI_ERR_INVALID = 1,      /* bad argument: null pointer, length, geometry */
+    CAXSI_ERR_CUDA = 2,         /* a CUDA runtime call or launch failed */
+    CAXSI_ERR_OOM = 3,          /* device allocation failed */
+    CAXSI_ERR_NONPOS_MEAN = 4,  /* a positive count met a non-positive mean A f + r */
+    CAXSI_ERR_INTERNAL = 5,     /* a device-side consistency check failed */
+    CAXSI_ERR_UNSUPPORTED = 6   /* option not available for this plan */
+} caxsi_status;
+
+/* How A and A^T are evaluated.
+ * DIRECT: the energy sum of Eq. 4 per (voxel, pixel) pair in FP32 (Alg. 1 / 3
+ *   structure, all factors computed or fetched per pair).
+ * TABLE_FP32: the same operator evaluated exactly through the piecewise-
+ *   linear structure of W in u = sin(theta/2): W(r, u) is tabulated per voxel
+ *   at every u where some energy bin crosses a q-grid node (so that linear
+ *   interpolation in u between table entries is exact), the table is a
+ *   contraction over q, and each pair interpolates it (forward) or scatters
+ *   into its transposed table (adjoint).  FP32 arithmetic throughout.
+ * TABLE_BF16 / TABLE_FP16: as TABLE_FP32 with the contraction over q on
+ *   tensor cores with bf16 / fp16 operands and FP32 accumulation (reduced
+ *   precision; the error against FP64 is measured, not bounded to 1e-5). */
+typedef enum {
+    CAXSI_PATH_DIRECT = 0,
+    CAXSI_PATH_TABLE_FP32 = 1,
+    CAXSI_PATH_TABLE_BF16 = 2,
+    CAXSI_PATH_TABLE_FP16 = 3
+} caxsi_path;
+
+/* System description; lengths in mm, energies in keV, q in nm^-1 (so that
+ * hc = 1.23984193 keV nm).  Requirements: X, J, M, N, K >= 1; Q >= 2;
+ * rho_y >= 1; K <= 1024; dx, p_y, p_z, mask_cell > 0; 0 < x_i < X_mask <
+ * X_det for every voxel; q_min < q_max; 0 < E_min < E_max; hc > 0. */
+typedef struct {
+    int32_t X, J, Q, M, N, K, rho_y, mask_rows, mask_cols;
+    double x_center, dx, p_y, p_z, X_det, X_mask;
+    double q_min, q_max, E_min, E_max, hc, C;
+    double mask_cell, mask_y0, mask_z0;
+} caxsi_geometry;
+
+/* Build a plan on the current CUDA device: validates the geometry, uploads the
+ * spectrum and mask, and builds the device tables in FP64 kernels (per-voxel
+ * position and G_so, per-offset G_od * dtheta -- one entry per scatter vector,
+ * shared by all voxel/pixel pairs related by the translation symmetry of
+ * Sec. III-A -- and the precomputed binary mask factor of every pair, as the
+ * paper precomputes its mask factors offline, Sec. III-C).
+ *   geom      host pointer, read during the call.
+ *   phi_host  host pointer to K doubles: the bin-averaged spectrum Phi_k.
+ *   mask_host host pointer to mask_rows * mask_cols bytes, 0 = opaque,
+ *             nonzero = open, row = z cell, col = y cell.
+ *   out       receives the plan; unchanged on error.
+ * Synchronous.  Errors: INVALID, OOM, CUDA. */
+caxsi_status caxsi_plan_create(const caxsi_geometry *geom, const double *phi_host,
+                               const uint8_t *mask_host, caxsi_plan **out);
+
+/* Release a plan and all device memory it owns (synchronises the device
+ * first).  NULL is ignored. */
+void caxsi_plan_destroy(caxsi_plan *plan);
+
+/* Forward model g = A f (Eq. 3 with Eq. 4; Algorithm 1's sum over object
+ * points, detector points and the spectrum).
+ *   f_dev  device, f_len = X*J*Q floats, layout [X][J][Q].
+ *   g_dev  device, g_len = M*N floats, layout [M][N]; overwritten.
+ *   path   a caxsi_path.
+ * Asynchronous on stream.  Errors: INVALID, UNSUPPORTED, CUDA, OOM. */
+caxsi_status caxsi_forward(caxsi_plan *plan, const float *f_dev, int64_t f_len,
+                           float *g_dev, int64_t g_len, int path, void *stream);
+
+/* Backward model f = A^T w (the exact transpose of caxsi_forward; Algorithm 3
+ * of Sec. IV with the spectral interpolation weights transposed onto the q
+ * bins).
+ *   w_dev  device, w_len = M*N floats.
+ *   f_dev  device, f_len = X*J*Q floats; overwritten.
+ * Asynchronous on stream.  Errors: INVALID, UNSUPPORTED, CUDA, OOM. */
+caxsi_status caxsi_adjoint(caxsi_plan *plan, const float *w_dev, int64_t w_len,
+                           float *f_dev, int64_t f_len, int path, void *stream);
+
+/* One iteration of the EM-type algorithm of Sec. VI (Algorithm 4) for the
+ * penalised Poisson likelihood of Sec. V:
+ *   z = A f + r;  b2 = A^T (y / z);  f <- positive root of
+ *   chi1 f^2 + chi2 f - chi3 = 0 (Eq. 10, Appendices B and C) with
+ *   b1 = A^T 1 (computed on first use, cached in the plan), Huber potential
+ *   psi_delta on the 4 spatial neighbours (i +- 1, j +- 1) of each voxel and
+ *   q channel, unit weights.  beta = 0 gives the MLEM update f b2 / b1.
+ *   y_dev     device, M*N counts (float, >= 0).
+ *   r_dev     device, M*N background (>= 0) or NULL for r = 0.
+ *   f_dev     device, X*J*Q, in/out (f >= 0).
+ *   nll_out   host pointer or NULL.  When non-NULL the call synchronises the
+ *             stream and stores the negative log-likelihood
+ *             L(f_in) = sum_i z_i - y_i ln z_i + ln y_i! accumulated in FP64.
+ * Edge rules: y_i = z_i = 0 contributes ratio 0 and likelihood 0; y_i > 0 with
+ * z_i <= 0 gives CAXSI_ERR_NONPOS_MEAN (detected when nll_out is non-NULL, or
+ * on the next call otherwise; f is then left unchanged by this call only if
+ * nll_out is non-NULL).  A voxel/channel with b1 = 0 and beta = 0 keeps its
+ * value.  Errors: INVALID, NONPOS_MEAN, CUDA, OOM. */
+caxsi_status caxsi_recon_step(caxsi_plan *plan, const float *y_dev, const float *r_dev,
+                              float *f_dev, int64_t f_len, float beta, float delta,
+                              int path, double *nll_out, void *stream);
+
+/* Host-buffer forms: copy the input from host memory to plan-owned device
+ * staging buffers, evaluate, copy the result back to host memory, and
+ * synchronise before returning.  Pinned host memory gives the fastest copies.
+ * Same lengths and layouts as the device forms. */
+caxsi_status caxsi_forward_host(caxsi_plan *plan, const float *f_host, int64_t f_len,
+                                float *g_host, int64_t g_len, int path);
+caxsi_status caxsi_adjoint_host(caxsi_plan *plan, const float *w_host, int64_t w_len,
+                                float *f_host, int64_t f_len, int path);
+
+/* Plan facts for callers and benchmarks: entries of the per-offset table,
+ * bytes of device tables, and the number of u breakpoints of the table paths
+ * (0 until a table path is first used). */
+typedef struct {
+    int64_t n_offsets;        /* N + rho_y (J - 1) */
+    int64_t table_bytes;      /* device bytes held by the plan */
+    int64_t n_breakpoints;    /* u breakpoints of the table paths */
+    int64_t kernel_launches;  /* kernels launched by the last forward/adjoint/recon call */
+    int64_t n_open_pairs;     /* (voxel, pixel) pairs whose mask factor T is 1 */
+} caxsi_plan_info_t;
+
+caxsi_status caxsi_plan_info(const caxsi_plan *plan, caxsi_plan_info_t *info);
+
+/* Kernel timing (tracing).  When enabled, every kernel the plan launches is
+ * bracketed by CUDA events recorded on its launch stream; caxsi_profile_read
+ * synchronises on those events, returns per-kernel launch counts and total
+ * device milliseconds (up to `capacity` distinct kernels, count in *count),
+ * and clears the record.  Enabling or disabling clears the record too.
+ * The event pairs add a few microseconds of host work per launch. */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} caxsi_kernel_stat;
+
+caxsi_status caxsi_profile_enable(caxsi_plan *plan, int enable);
+caxsi_status caxsi_profile_read(caxsi_plan *plan, caxsi_kernel_stat *out, int capacity,
+                                int *count);
+
+/* Human-readable name of a status code (static storage). */
+const char *caxsi_status_string(caxsi_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CAXSI_H */

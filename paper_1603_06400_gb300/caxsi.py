@@ -1,0 +1,224 @@
+"""Thin Python binding of libcaxsi (ctypes).  Argument marshalling only: every
+step of the forward model, the adjoint and the reconstruction update runs in
+the library's CUDA kernels.  PyTorch supplies device memory and streams.
+
+There is no fallback: if the shared library is missing or fails to load, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+PATH_DIRECT = 0
+PATH_TABLE_FP32 = 1
+PATH_TABLE_BF16 = 2
+PATH_TABLE_FP16 = 3
+PATHS = {"direct": PATH_DIRECT, "table_fp32": PATH_TABLE_FP32,
+         "table_bf16": PATH_TABLE_BF16, "table_fp16": PATH_TABLE_FP16}
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
+          4: "positive count with non-positive mean", 5: "internal check failed",
+          6: "unsupported option"}
+
+
+class CaxsiError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)} (status {status})")
+        self.status = status
+
+
+class CGeometry(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in
+                ("X", "J", "Q", "M", "N", "K", "rho_y", "mask_rows", "mask_cols")] + \
+               [(k, ctypes.c_double) for k in
+                ("x_center", "dx", "p_y", "p_z", "X_det", "X_mask", "q_min", "q_max",
+                 "E_min", "E_max", "hc", "C", "mask_cell", "mask_y0", "mask_z0")]
+
+
+class CPlanInfo(ctypes.Structure):
+    _fields_ = [("n_offsets", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
+                ("n_breakpoints", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("n_open_pairs", ctypes.c_int64)]
+
+
+class CKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libcaxsi.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with "
+                                   "paper_1603_06400_gb300.build.build()")
+            lib = ctypes.CDLL(path)
+            P = ctypes.c_void_p
+            F = ctypes.POINTER(ctypes.c_float)
+            I64 = ctypes.c_int64
+            lib.caxsi_plan_create.argtypes = [ctypes.POINTER(CGeometry),
+                                              ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_uint8),
+                                              ctypes.POINTER(P)]
+            lib.caxsi_plan_destroy.argtypes = [P]
+            lib.caxsi_plan_destroy.restype = None
+            lib.caxsi_forward.argtypes = [P, P, I64, P, I64, ctypes.c_int, P]
+            lib.caxsi_adjoint.argtypes = [P, P, I64, P, I64, ctypes.c_int, P]
+            lib.caxsi_recon_step.argtypes = [P, P, P, P, I64, ctypes.c_float, ctypes.c_float,
+                                             ctypes.c_int, ctypes.POINTER(ctypes.c_double), P]
+            lib.caxsi_forward_host.argtypes = [P, F, I64, F, I64, ctypes.c_int]
+            lib.caxsi_adjoint_host.argtypes = [P, F, I64, F, I64, ctypes.c_int]
+            lib.caxsi_plan_info.argtypes = [P, ctypes.POINTER(CPlanInfo)]
+            lib.caxsi_profile_enable.argtypes = [P, ctypes.c_int]
+            lib.caxsi_profile_read.argtypes = [P, ctypes.POINTER(CKernelStat), ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int)]
+            lib.caxsi_status_string.argtypes = [ctypes.c_int]
+            lib.caxsi_status_string.restype = ctypes.c_char_p
+            for name in ("caxsi_plan_create", "caxsi_forward", "caxsi_adjoint",
+                         "caxsi_recon_step", "caxsi_forward_host", "caxsi_adjoint_host",
+                         "caxsi_plan_info", "caxsi_profile_enable", "caxsi_profile_read"):
+                getattr(lib, name).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def geometry_struct(g) -> CGeometry:
+    d = g.as_dict() if hasattr(g, "as_dict") else dict(g)
+    return CGeometry(**{k: d[k] for k, _ in CGeometry._fields_})
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise CaxsiError(status, where)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, n, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError(f"{name} must be a CUDA float32 tensor")
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be contiguous with {n} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A device plan for one geometry, spectrum and mask (see include/caxsi.h)."""
+
+    def __init__(self, geom, phi, mask):
+        self.lib = load()
+        self.geom = geom
+        self.X, self.J, self.Q = geom.X, geom.J, geom.Q
+        self.M, self.N = geom.M, geom.N
+        self.f_len = self.X * self.J * self.Q
+        self.g_len = self.M * self.N
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        if phi.size != geom.K or mask.size != geom.mask_rows * geom.mask_cols:
+            raise ValueError("spectrum or mask has the wrong size")
+        self._g = geometry_struct(geom)
+        h = ctypes.c_void_p()
+        _check(self.lib.caxsi_plan_create(
+            ctypes.byref(self._g), phi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.byref(h)),
+            "caxsi_plan_create")
+        self.handle = h
+
+    # -- device-pointer calls -------------------------------------------------
+    def forward(self, f, out=None, path=PATH_DIRECT, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.M, self.N), device=f.device, dtype=torch.float32)
+        _check(self.lib.caxsi_forward(self.handle, _dev(f, self.f_len, "f"), self.f_len,
+                                      _dev(out, self.g_len, "g"), self.g_len, int(path),
+                                      _stream_handle(stream)), "caxsi_forward")
+        return out
+
+    def adjoint(self, w, out=None, path=PATH_DIRECT, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.X, self.J, self.Q), device=w.device, dtype=torch.float32)
+        _check(self.lib.caxsi_adjoint(self.handle, _dev(w, self.g_len, "w"), self.g_len,
+                                      _dev(out, self.f_len, "f"), self.f_len, int(path),
+                                      _stream_handle(stream)), "caxsi_adjoint")
+        return out
+
+    def recon_step(self, y, f, r=None, beta=0.0, delta=0.0, path=PATH_DIRECT,
+                   want_nll=False, stream=None):
+        nll = ctypes.c_double(0.0)
+        rp = _dev(r, self.g_len, "r") if r is not None else ctypes.c_void_p(None)
+        _check(self.lib.caxsi_recon_step(
+            self.handle, _dev(y, self.g_len, "y"), rp, _dev(f, self.f_len, "f"), self.f_len,
+            float(beta), float(delta), int(path),
+            ctypes.byref(nll) if want_nll else None, _stream_handle(stream)), "caxsi_recon_step")
+        return nll.value if want_nll else None
+
+    # -- host-buffer calls ----------------------------------------------------
+    def forward_host(self, f, out=None, path=PATH_DIRECT):
+        f = np.ascontiguousarray(f, dtype=np.float32)
+        out = np.empty((self.M, self.N), np.float32) if out is None else out
+        FP = ctypes.POINTER(ctypes.c_float)
+        _check(self.lib.caxsi_forward_host(self.handle, f.ctypes.data_as(FP), f.size,
+                                           out.ctypes.data_as(FP), out.size, int(path)),
+               "caxsi_forward_host")
+        return out
+
+    def adjoint_host(self, w, out=None, path=PATH_DIRECT):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        out = np.empty((self.X, self.J, self.Q), np.float32) if out is None else out
+        FP = ctypes.POINTER(ctypes.c_float)
+        _check(self.lib.caxsi_adjoint_host(self.handle, w.ctypes.data_as(FP), w.size,
+                                           out.ctypes.data_as(FP), out.size, int(path)),
+               "caxsi_adjoint_host")
+        return out
+
+    def info(self) -> dict:
+        i = CPlanInfo()
+        _check(self.lib.caxsi_plan_info(self.handle, ctypes.byref(i)), "caxsi_plan_info")
+        return {k: getattr(i, k) for k, _ in CPlanInfo._fields_}
+
+    def profile(self, enable: bool = True):
+        _check(self.lib.caxsi_profile_enable(self.handle, int(bool(enable))), "caxsi_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (launches, total device ms)} since the last read/enable."""
+        cap = 64
+        arr = (CKernelStat * cap)()
+        n = ctypes.c_int(0)
+        _check(self.lib.caxsi_profile_read(self.handle, arr, cap, ctypes.byref(n)),
+               "caxsi_profile_read")
+        return {arr[k].name.decode(): (arr[k].launches, arr[k].total_ms) for k in range(n.value)}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.caxsi_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,334 @@
+// C ABI entry points: validation, plan ownership, dispatch.
+#include <math.h>
+#include <new>
+#include <string.h>
+
+#include "internal.cuh"
+
+size_t direct_fwd_smem(const caxsi_plan *p);
+size_t direct_adj_smem(const caxsi_plan *p);
+
+namespace {
+
+// Makes the plan's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+caxsi_status validate(const caxsi_geometry *g) {
+    if (g->X < 1 || g->J < 1 || g->M < 1 || g->N < 1 || g->K < 1 || g->Q < 2 || g->rho_y < 1)
+        return CAXSI_ERR_INVALID;
+    if (g->K > CAXSI_MAX_K || g->mask_rows < 1 || g->mask_cols < 1) return CAXSI_ERR_INVALID;
+    if (!finite_pos(g->dx) || !finite_pos(g->p_y) || !finite_pos(g->p_z) ||
+        !finite_pos(g->mask_cell) || !finite_pos(g->hc) || !finite_pos(g->E_min))
+        return CAXSI_ERR_INVALID;
+    if (!isfinite(g->x_center) || !isfinite(g->X_det) || !isfinite(g->X_mask) ||
+        !isfinite(g->q_min) || !isfinite(g->q_max) || !isfinite(g->E_max) || !isfinite(g->C) ||
+        !isfinite(g->mask_y0) || !isfinite(g->mask_z0))
+        return CAXSI_ERR_INVALID;
+    if (!(g->q_max > g->q_min) || !(g->E_max > g->E_min)) return CAXSI_ERR_INVALID;
+    const double x_lo = g->x_center - 0.5 * (g->X - 1) * g->dx;
+    const double x_hi = g->x_center + 0.5 * (g->X - 1) * g->dx;
+    if (!(x_lo > 0.0) || !(x_hi < g->X_mask) || !(g->X_mask < g->X_det)) return CAXSI_ERR_INVALID;
+    // sizes: every table index below 2^31 per dimension product used in int arithmetic
+    const double R = (double)g->X * g->J;
+    if (R * g->Q > 2e9 || (double)g->M * g->N > 2e9 ||
+        (double)g->J * g->rho_y + g->N > 1e7 || (double)g->N > 4e6)
+        return CAXSI_ERR_INVALID;
+    return CAXSI_OK;
+}
+
+void free_plan(caxsi_plan *p) {
+    if (!p) return;
+    for (auto &r : p->prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : p->prof.pool) cudaEventDestroy(e);
+    table_destroy(p);
+    cudaFree(p->vox);
+    cudaFree(p->zrow);
+    cudaFree(p->god);
+    cudaFree(p->tbits);
+    cudaFree(p->energy);
+    cudaFree(p->fwd_part);
+    cudaFree(p->adj_part);
+    cudaFree(p->gtmp);
+    cudaFree(p->ratio);
+    cudaFree(p->ones);
+    for (int k = 0; k < 4; ++k) cudaFree(p->b1[k]);
+    cudaFree(p->b2);
+    cudaFree(p->fnew);
+    cudaFree(p->nll_part);
+    cudaFree(p->nll_dev);
+    cudaFree(p->err_flag);
+    cudaFree(p->stage_in);
+    cudaFree(p->stage_out);
+    delete p;
+}
+
+__global__ void k_fill(float *a, float v, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+
+caxsi_status alloc_scratch(caxsi_plan *p) {
+    const DevGeo &g = p->dg;
+    const int64_t npix = (int64_t)g.M * g.N, nf = (int64_t)g.R * g.Q;
+    CAXSI_CUDA_TRY(cudaMalloc(&p->fwd_part, (size_t)p->fwd_chunks * npix * sizeof(float)));
+    if (p->adj_split > 1)
+        CAXSI_CUDA_TRY(cudaMalloc(&p->adj_part, (size_t)p->adj_split * nf * sizeof(float)));
+    CAXSI_CUDA_TRY(cudaMalloc(&p->gtmp, npix * sizeof(float)));
+    CAXSI_CUDA_TRY(cudaMalloc(&p->ratio, npix * sizeof(float)));
+    CAXSI_CUDA_TRY(cudaMalloc(&p->ones, npix * sizeof(float)));
+    CAXSI_CUDA_TRY(cudaMalloc(&p->b2, nf * sizeof(float)));
+    CAXSI_CUDA_TRY(cudaMalloc(&p->fnew, nf * sizeof(float)));
+    p->nll_blocks = (int)(ceil_div64(npix, 256) < 2 * p->num_sms ? ceil_div64(npix, 256) : 2 * p->num_sms);
+    if (p->nll_blocks < 1) p->nll_blocks = 1;
+    CAXSI_CUDA_TRY(cudaMalloc(&p->nll_part, p->nll_blocks * sizeof(double)));
+    CAXSI_CUDA_TRY(cudaMalloc(&p->nll_dev, sizeof(double)));
+    CAXSI_CUDA_TRY(cudaMalloc(&p->err_flag, sizeof(int)));
+    CAXSI_CUDA_TRY(cudaMemset(p->err_flag, 0, sizeof(int)));
+    k_fill<<<(unsigned)ceil_div64(npix, 256), 256>>>(p->ones, 1.f, npix);
+    CAXSI_CUDA_TRY(cudaGetLastError());
+    CAXSI_CUDA_TRY(cudaDeviceSynchronize());
+    p->table_bytes += (int64_t)p->fwd_chunks * npix * 4 + (p->adj_split > 1 ? p->adj_split * nf * 4 : 0) +
+                      3 * npix * 4 + 2 * nf * 4;
+    return CAXSI_OK;
+}
+
+bool path_ok(int path) { return path >= CAXSI_PATH_DIRECT && path <= CAXSI_PATH_TABLE_FP16; }
+
+caxsi_status run_forward(caxsi_plan *p, const float *f, float *g, int path, cudaStream_t s) {
+    if (path == CAXSI_PATH_DIRECT) return direct_forward(p, f, g, s);
+    return table_forward(p, f, g, path, s);
+}
+
+caxsi_status run_adjoint(caxsi_plan *p, const float *w, float *f, int path, cudaStream_t s) {
+    if (path == CAXSI_PATH_DIRECT) return direct_adjoint(p, w, f, s);
+    return table_adjoint(p, w, f, path, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+caxsi_status caxsi_plan_create(const caxsi_geometry *geom, const double *phi_host,
+                               const uint8_t *mask_host, caxsi_plan **out) {
+    if (!geom || !phi_host || !mask_host || !out) return CAXSI_ERR_INVALID;
+    caxsi_status st = validate(geom);
+    if (st != CAXSI_OK) return st;
+    for (int k = 0; k < geom->K; ++k)
+        if (!isfinite(phi_host[k])) return CAXSI_ERR_INVALID;
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CAXSI_ERR_CUDA;
+    caxsi_plan *p = new (std::nothrow) caxsi_plan();
+    if (!p) return CAXSI_ERR_OOM;
+    p->g = *geom;
+    p->device = dev;
+    if (cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        delete p;
+        return CAXSI_ERR_CUDA;
+    }
+    DevGeo &d = p->dg;
+    d.X = geom->X; d.J = geom->J; d.Q = geom->Q; d.M = geom->M; d.N = geom->N; d.K = geom->K;
+    d.rho_y = geom->rho_y;
+    d.R = geom->X * geom->J;
+    d.ND = geom->N + geom->rho_y * (geom->J - 1);
+    d.d_min = -geom->rho_y * (geom->J - 1);
+    d.Nw = (geom->N + 31) / 32;
+    d.p_y = (float)geom->p_y;
+    d.Xd = (float)geom->X_det;
+    d.cN = 0.5f * (float)(geom->N - 1);
+    const double dq = (geom->q_max - geom->q_min) / (geom->Q - 1);
+    d.b = (float)(geom->q_min / dq);
+    d.Qf = (float)geom->Q;
+
+    direct_configure(p);
+    int smem_max = 0;
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if ((size_t)smem_max < direct_adj_smem(p) || (size_t)smem_max < direct_fwd_smem(p)) {
+        delete p;
+        return CAXSI_ERR_UNSUPPORTED;
+    }
+    st = plan_build_tables(p, phi_host, mask_host);
+    if (st == CAXSI_OK) st = alloc_scratch(p);
+    if (st != CAXSI_OK) {
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return CAXSI_OK;
+}
+
+void caxsi_plan_destroy(caxsi_plan *plan) {
+    if (!plan) return;
+    DeviceGuard dg(plan->device);
+    cudaDeviceSynchronize();
+    free_plan(plan);
+}
+
+caxsi_status caxsi_forward(caxsi_plan *p, const float *f_dev, int64_t f_len, float *g_dev,
+                           int64_t g_len, int path, void *stream) {
+    if (!p || !f_dev || !g_dev || !path_ok(path)) return CAXSI_ERR_INVALID;
+    if (f_len != (int64_t)p->dg.R * p->dg.Q || g_len != (int64_t)p->dg.M * p->dg.N)
+        return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return CAXSI_ERR_CUDA;
+    p->launches = 0;
+    return run_forward(p, f_dev, g_dev, path, (cudaStream_t)stream);
+}
+
+caxsi_status caxsi_adjoint(caxsi_plan *p, const float *w_dev, int64_t w_len, float *f_dev,
+                           int64_t f_len, int path, void *stream) {
+    if (!p || !f_dev || !w_dev || !path_ok(path)) return CAXSI_ERR_INVALID;
+    if (f_len != (int64_t)p->dg.R * p->dg.Q || w_len != (int64_t)p->dg.M * p->dg.N)
+        return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return CAXSI_ERR_CUDA;
+    p->launches = 0;
+    return run_adjoint(p, w_dev, f_dev, path, (cudaStream_t)stream);
+}
+
+caxsi_status caxsi_recon_step(caxsi_plan *p, const float *y_dev, const float *r_dev, float *f_dev,
+                              int64_t f_len, float beta, float delta, int path, double *nll_out,
+                              void *stream) {
+    if (!p || !y_dev || !f_dev || !path_ok(path)) return CAXSI_ERR_INVALID;
+    if (f_len != (int64_t)p->dg.R * p->dg.Q) return CAXSI_ERR_INVALID;
+    if (!isfinite(beta) || beta < 0.f || !isfinite(delta) || delta < 0.f) return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return CAXSI_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    p->launches = 0;
+    const int64_t nf = (int64_t)p->dg.R * p->dg.Q;
+    caxsi_status st;
+    if (!p->b1[path]) {
+        CAXSI_CUDA_TRY(cudaMalloc(&p->b1[path], nf * sizeof(float)));
+        p->table_bytes += nf * 4;
+        st = run_adjoint(p, p->ones, p->b1[path], path, s);
+        if (st != CAXSI_OK) return st;
+    }
+    // z = A f + r, ratio = y / z, L(f) in FP64
+    if ((st = run_forward(p, f_dev, p->gtmp, path, s)) != CAXSI_OK) return st;
+    if ((st = recon_ratio(p, y_dev, r_dev, s)) != CAXSI_OK) return st;
+    if (nll_out) {
+        int64_t keep = p->launches;
+        st = recon_nll_fetch(p, nll_out, s);
+        p->launches = keep;
+        if (st != CAXSI_OK) return st;
+    }
+    // b2 = A^T (y / z), then the closed-form update
+    if ((st = run_adjoint(p, p->ratio, p->b2, path, s)) != CAXSI_OK) return st;
+    if ((st = recon_update(p, f_dev, beta, delta, p->b1[path], s)) != CAXSI_OK) return st;
+    CAXSI_CUDA_TRY(cudaMemcpyAsync(f_dev, p->fnew, nf * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return CAXSI_OK;
+}
+
+static caxsi_status host_call(caxsi_plan *p, const float *in_host, int64_t in_len, float *out_host,
+                              int64_t out_len, int path, bool fwd) {
+    if (!p || !in_host || !out_host || !path_ok(path)) return CAXSI_ERR_INVALID;
+    const int64_t nf = (int64_t)p->dg.R * p->dg.Q, ng = (int64_t)p->dg.M * p->dg.N;
+    if (in_len != (fwd ? nf : ng) || out_len != (fwd ? ng : nf)) return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return CAXSI_ERR_CUDA;
+    const int64_t big = nf > ng ? nf : ng;
+    if (!p->stage_in) {
+        CAXSI_CUDA_TRY(cudaMalloc(&p->stage_in, big * sizeof(float)));
+        CAXSI_CUDA_TRY(cudaMalloc(&p->stage_out, big * sizeof(float)));
+        p->table_bytes += 2 * big * 4;
+    }
+    p->launches = 0;
+    cudaStream_t s = 0;
+    CAXSI_CUDA_TRY(cudaMemcpyAsync(p->stage_in, in_host, in_len * sizeof(float), cudaMemcpyHostToDevice, s));
+    caxsi_status st = fwd ? run_forward(p, p->stage_in, p->stage_out, path, s)
+                          : run_adjoint(p, p->stage_in, p->stage_out, path, s);
+    if (st != CAXSI_OK) return st;
+    CAXSI_CUDA_TRY(cudaMemcpyAsync(out_host, p->stage_out, out_len * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CAXSI_CUDA_TRY(cudaStreamSynchronize(s));
+    return CAXSI_OK;
+}
+
+caxsi_status caxsi_forward_host(caxsi_plan *p, const float *f_host, int64_t f_len, float *g_host,
+                                int64_t g_len, int path) {
+    return host_call(p, f_host, f_len, g_host, g_len, path, true);
+}
+
+caxsi_status caxsi_adjoint_host(caxsi_plan *p, const float *w_host, int64_t w_len, float *f_host,
+                                int64_t f_len, int path) {
+    return host_call(p, w_host, w_len, f_host, f_len, path, false);
+}
+
+caxsi_status caxsi_plan_info(const caxsi_plan *p, caxsi_plan_info_t *info) {
+    if (!p || !info) return CAXSI_ERR_INVALID;
+    info->n_offsets = p->dg.ND;
+    info->table_bytes = p->table_bytes;
+    info->n_breakpoints = 0;
+    info->kernel_launches = p->launches;
+    info->n_open_pairs = p->open_pairs;
+    return CAXSI_OK;
+}
+
+static void prof_clear(caxsi_plan *p) {
+    for (auto &r : p->prof.recs) {
+        cudaEventSynchronize(r.b);
+        p->prof.pool.push_back(r.a);
+        p->prof.pool.push_back(r.b);
+    }
+    p->prof.recs.clear();
+}
+
+caxsi_status caxsi_profile_enable(caxsi_plan *p, int enable) {
+    if (!p) return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    prof_clear(p);
+    p->prof.on = enable != 0;
+    return CAXSI_OK;
+}
+
+caxsi_status caxsi_profile_read(caxsi_plan *p, caxsi_kernel_stat *out, int capacity, int *count) {
+    if (!p || !count || capacity < 0 || (capacity > 0 && !out)) return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    int n = 0;
+    caxsi_status st = CAXSI_OK;
+    for (auto &r : p->prof.recs) {
+        if (cudaEventSynchronize(r.b) != cudaSuccess) { st = CAXSI_ERR_CUDA; continue; }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) { st = CAXSI_ERR_CUDA; continue; }
+        int k = 0;
+        while (k < n && strncmp(out[k].name, r.name, sizeof(out[k].name) - 1) != 0) ++k;
+        if (k == n) {
+            if (n >= capacity) continue;
+            memset(&out[n], 0, sizeof(out[n]));
+            strncpy(out[n].name, r.name, sizeof(out[n].name) - 1);
+            ++n;
+        }
+        out[k].launches += 1;
+        out[k].total_ms += ms;
+    }
+    prof_clear(p);
+    *count = n;
+    return st;
+}
+
+const char *caxsi_status_string(caxsi_status s) {
+    switch (s) {
+        case CAXSI_OK: return "ok";
+        case CAXSI_ERR_INVALID: return "invalid argument";
+        case CAXSI_ERR_CUDA: return "CUDA error";
+        case CAXSI_ERR_OOM: return "out of device memory";
+        case CAXSI_ERR_NONPOS_MEAN: return "positive count with non-positive mean";
+        case CAXSI_ERR_INTERNAL: return "internal consistency check failed";
+        case CAXSI_ERR_UNSUPPORTED: return "unsupported option";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,252 @@
+// Direct FP32 evaluation of the forward model (Eq. 3-4, Algorithm 1) and its
+// transpose (Algorithm 3): every (voxel, pixel) pair computes its scatter
+// angle and sums the K energy bins of the source spectrum.
+//
+// Forward: a block owns a tile of 8 detector rows x 32 columns (one warp per
+// row, one lane per pixel) and a chunk of voxels; the chunk's q rows are
+// staged in shared memory as (f_l, f_{l+1} - f_l) pairs so that one 8-byte
+// load gives both interpolation nodes.  Each chunk writes a private partial
+// image; a second kernel sums the partials in a fixed order (deterministic,
+// no atomics).
+//
+// Adjoint: a warp owns one voxel (optionally a range of detector rows of it);
+// lanes walk the pixels; every lane scatters its energy terms into a
+// lane-private row of Q+3 q bins in shared memory laid out [bin][lane] (bank
+// = lane, so the scatter is conflict-free), and the 32 private rows are
+// summed at the end with a rotated read (also conflict-free).  No atomics.
+#include "internal.cuh"
+#include "pairgeo.cuh"
+
+namespace {
+
+constexpr int FWD_WARPS = 8;
+constexpr int FWD_THREADS = FWD_WARPS * 32;
+constexpr int FWD_VS = 32;  // voxels staged per shared-memory round
+constexpr int ADJ_WARPS = 4;
+
+struct Tables {
+    DevGeo g;
+    const float4 *vox;
+    const float *zrow;
+    const float *god;
+    const uint32_t *tbits;
+    const float2 *energy;
+};
+
+__global__ void __launch_bounds__(FWD_THREADS)
+k_fwd_direct(Tables T, const float *__restrict__ f, float *__restrict__ part, int vc, int tiles_n) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const DevGeo &g = T.g;
+    const int QP = g.Q + 2;
+    float2 *s_en = reinterpret_cast<float2 *>(smem_raw);
+    float4 *s_vox = reinterpret_cast<float4 *>(s_en + ((g.K + 1) & ~1));
+    float2 *s_f = reinterpret_cast<float2 *>(s_vox + FWD_VS);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
+    const int m = tm * FWD_WARPS + warp, n = tn * 32 + lane;
+    const bool valid = (m < g.M) && (n < g.N);
+    const int v0 = blockIdx.y * vc;
+    const int v1 = min(v0 + vc, g.R);
+
+    for (int k = tid; k < g.K; k += FWD_THREADS) s_en[k] = T.energy[k];
+    const float Npix = (float)n - g.cN;
+    const float sz = valid ? T.zrow[m] : 0.f;
+    const int wsel = n >> 5, bsel = n & 31;
+    float acc = 0.f;
+
+    for (int vb = v0; vb < v1; vb += FWD_VS) {
+        const int nv = min(FWD_VS, v1 - vb);
+        __syncthreads();
+        for (int idx = tid; idx < nv * QP; idx += FWD_THREADS) {
+            const int vv = idx / QP, lp = idx - vv * QP;
+            const float *row = f + (int64_t)(vb + vv) * g.Q;
+            const float F0 = (lp >= 1 && lp <= g.Q) ? row[lp - 1] : 0.f;
+            const float F1 = (lp + 1 <= g.Q) ? row[lp] : 0.f;
+            s_f[idx] = make_float2(F0, F1 - F0);
+        }
+        if (tid < nv) s_vox[tid] = T.vox[vb + tid];
+        __syncthreads();
+        if (!valid) continue;
+        for (int vv = 0; vv < nv; ++vv) {
+            const int v = vb + vv;
+            const uint32_t word = T.tbits[((int64_t)v * g.M + m) * g.Nw + wsel];
+            if (!((word >> bsel) & 1u)) continue;
+            const int i = v / g.J, j = v - i * g.J;
+            const float4 vx = s_vox[vv];
+            float u, ang;
+            pair_u_angular(vx.x, vx.y, vx.w, Npix, sz, g.p_y, g.Xd, u, ang);
+            const float gd = T.god[((int64_t)i * g.M + m) * g.ND + (n - g.rho_y * j - g.d_min)];
+            const float2 *fr = s_f + vv * QP;
+            float e_acc = 0.f;
+#pragma unroll 8
+            for (int k = 0; k < g.K; ++k) {
+                const float2 ak = s_en[k];
+                float tau = fmaf(ak.x, u, -g.b);
+                tau = fminf(fmaxf(tau, -1.f), g.Qf);
+                const float fl = floorf(tau);
+                const float al = tau - fl;
+                const float2 F = fr[(int)fl + 1];
+                e_acc = fmaf(ak.y, fmaf(al, F.y, F.x), e_acc);
+            }
+            acc = fmaf(vx.z * gd * ang, e_acc, acc);
+        }
+    }
+    if (valid) part[(int64_t)blockIdx.y * g.M * g.N + (int64_t)m * g.N + n] = acc;
+}
+
+// out[idx] = sum_c part[c * stride + idx], c ascending.
+__global__ void k_sum_parts(const float *__restrict__ part, int nparts, int64_t stride,
+                            float *__restrict__ out, int64_t n) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    float s = 0.f;
+    for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * stride + idx];
+    out[idx] = s;
+}
+
+__global__ void __launch_bounds__(ADJ_WARPS * 32)
+k_adj_direct(Tables T, const float *__restrict__ w, float *__restrict__ out, int split,
+             int rows_per_split) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const DevGeo &g = T.g;
+    const int QB = g.Q + 3;  // bins l' = l + 1 in [0, Q + 2]; 1..Q are real
+    float2 *s_en = reinterpret_cast<float2 *>(smem_raw);
+    float *s_acc = reinterpret_cast<float *>(s_en + ((g.K + 1) & ~1));
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int item = blockIdx.x * ADJ_WARPS + warp;
+    const int v = item / split, sp = item - (item / split) * split;
+    for (int k = tid; k < g.K; k += blockDim.x) s_en[k] = T.energy[k];
+    float *acc = s_acc + (int64_t)warp * QB * 32;
+    for (int b = lane; b < QB * 32; b += 32) acc[b] = 0.f;
+    __syncthreads();
+    if (v >= g.R) return;
+
+    const int i = v / g.J, j = v - i * g.J;
+    const float4 vx = T.vox[v];
+    const int m0 = sp * rows_per_split, m1 = min(g.M, m0 + rows_per_split);
+    float *my = acc + lane;
+    for (int m = m0; m < m1; ++m) {
+        const float sz = T.zrow[m];
+        const uint32_t *trow = T.tbits + ((int64_t)v * g.M + m) * g.Nw;
+        const float *god_row = T.god + ((int64_t)i * g.M + m) * g.ND - g.d_min - g.rho_y * j;
+        for (int nb = 0; nb < g.N; nb += 32) {
+            const int n = nb + lane;
+            if (n >= g.N) break;
+            if (!((trow[nb >> 5] >> lane) & 1u)) continue;
+            const float wv = w[(int64_t)m * g.N + n];
+            if (wv == 0.f) continue;
+            float u, ang;
+            pair_u_angular(vx.x, vx.y, vx.w, (float)n - g.cN, sz, g.p_y, g.Xd, u, ang);
+            const float base = vx.z * god_row[n] * ang * wv;
+#pragma unroll 4
+            for (int k = 0; k < g.K; ++k) {
+                const float2 ak = s_en[k];
+                float tau = fmaf(ak.x, u, -g.b);
+                tau = fminf(fmaxf(tau, -1.f), g.Qf);
+                const float fl = floorf(tau);
+                const float al = tau - fl;
+                const int lp = (int)fl + 1;
+                const float cb = ak.y * base;
+                const float hi = cb * al;
+                my[lp * 32] += cb - hi;
+                my[(lp + 1) * 32] += hi;
+            }
+        }
+    }
+    __syncwarp();
+    float *dst = out + ((int64_t)sp * g.R + v) * g.Q;
+    for (int lp = 1 + lane; lp <= g.Q; lp += 32) {
+        const float *rowp = acc + lp * 32;
+        float s = 0.f;
+        for (int c = 0; c < 32; ++c) s += rowp[(lane + c) & 31];
+        dst[lp - 1] = s;
+    }
+}
+
+Tables tables_of(const caxsi_plan *p) {
+    Tables T;
+    T.g = p->dg;
+    T.vox = p->vox;
+    T.zrow = p->zrow;
+    T.god = p->god;
+    T.tbits = p->tbits;
+    T.energy = p->energy;
+    return T;
+}
+
+size_t fwd_smem(const DevGeo &g) {
+    return ((g.K + 1) & ~1) * sizeof(float2) + FWD_VS * sizeof(float4) +
+           (size_t)FWD_VS * (g.Q + 2) * sizeof(float2);
+}
+size_t adj_smem(const DevGeo &g) {
+    return ((g.K + 1) & ~1) * sizeof(float2) + (size_t)ADJ_WARPS * (g.Q + 3) * 32 * sizeof(float);
+}
+
+}  // namespace
+
+void direct_configure(caxsi_plan *p) {
+    const DevGeo &g = p->dg;
+    const int tiles = (int)(ceil_div64(g.M, FWD_WARPS) * ceil_div64(g.N, 32));
+    const int target = 16 * p->num_sms;
+    int chunks = (int)ceil_div64(target, tiles);
+    if (chunks > g.R) chunks = g.R;
+    int vc = (int)ceil_div64(g.R, chunks);
+    if (vc < 8) vc = 8;
+    p->fwd_vc = vc;
+    p->fwd_chunks = (int)ceil_div64(g.R, vc);
+    int split = (int)ceil_div64(16 * p->num_sms, g.R);
+    if (split > g.M) split = g.M;
+    if (split < 1) split = 1;
+    int rps = (int)ceil_div64(g.M, split);
+    p->adj_split = (int)ceil_div64(g.M, rps);
+}
+
+size_t direct_fwd_smem(const caxsi_plan *p) { return fwd_smem(p->dg); }
+size_t direct_adj_smem(const caxsi_plan *p) { return adj_smem(p->dg); }
+
+caxsi_status direct_forward(caxsi_plan *p, const float *f, float *g_out, cudaStream_t s) {
+    const DevGeo &g = p->dg;
+    const int tiles_n = (int)ceil_div64(g.N, 32);
+    const int tiles = (int)ceil_div64(g.M, FWD_WARPS) * tiles_n;
+    const size_t sm = fwd_smem(g);
+    CAXSI_CUDA_TRY(cudaFuncSetAttribute(k_fwd_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    dim3 grid(tiles, p->fwd_chunks);
+    {
+        CAXSI_PROF(p, "fwd_direct", s);
+        k_fwd_direct<<<grid, FWD_THREADS, sm, s>>>(tables_of(p), f, p->fwd_part, p->fwd_vc, tiles_n);
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    const int64_t npix = (int64_t)g.M * g.N;
+    {
+        CAXSI_PROF(p, "sum_parts", s);
+        k_sum_parts<<<(unsigned)ceil_div64(npix, 256), 256, 0, s>>>(p->fwd_part, p->fwd_chunks, npix, g_out, npix);
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    return CAXSI_OK;
+}
+
+caxsi_status direct_adjoint(caxsi_plan *p, const float *w, float *f_out, cudaStream_t s) {
+    const DevGeo &g = p->dg;
+    const size_t sm = adj_smem(g);
+    CAXSI_CUDA_TRY(cudaFuncSetAttribute(k_adj_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int split = p->adj_split;
+    const int rps = (int)ceil_div64(g.M, split);
+    const int64_t items = (int64_t)g.R * split;
+    float *dst = split > 1 ? p->adj_part : f_out;
+    {
+        CAXSI_PROF(p, "adj_direct", s);
+        k_adj_direct<<<(unsigned)ceil_div64(items, ADJ_WARPS), ADJ_WARPS * 32, sm, s>>>(tables_of(p), w, dst, split, rps);
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    if (split > 1) {
+        const int64_t nf = (int64_t)g.R * g.Q;
+        {
+            CAXSI_PROF(p, "sum_parts", s);
+            k_sum_parts<<<(unsigned)ceil_div64(nf, 256), 256, 0, s>>>(p->adj_part, split, nf, f_out, nf);
+        }
+        CAXSI_LAUNCH_CHECK(p);
+    }
+    return CAXSI_OK;
+}

@@ -1,0 +1,138 @@
+// Internal declarations of the caxsi CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "caxsi.h"
+
+#define CAXSI_MAX_K 1024
+
+// Geometry scalars needed by the kernels, derived once per plan.
+struct DevGeo {
+    int X, J, Q, M, N, K, rho_y;
+    int R;        // X * J voxels
+    int ND;       // offsets d = n - rho_y j: N + rho_y (J - 1)
+    int d_min;    // -rho_y (J - 1)
+    int Nw;       // 32-bit words per detector row of mask bits
+    float p_y;    // detector pitch along y (mm)
+    float Xd;     // detector plane x (mm)
+    float cN;     // (N - 1) / 2
+    float b;      // q_min / dq
+    float Qf;     // (float)Q
+};
+
+// Optional per-kernel timing with CUDA events recorded on the launch stream
+// around every kernel of the library (off by default).
+struct KernelProfiler {
+    bool on = false;
+    struct Rec { const char *name; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+
+// Table-path data (piecewise-linear structure of W in u); built on first use.
+struct TablePath;
+
+struct caxsi_plan {
+    caxsi_geometry g;
+    DevGeo dg;
+    int device;
+    int num_sms;
+
+    // device tables (built by FP64 kernels)
+    float4 *vox;        // [R] {x_i, Y_j = y_j/p_y, C*G_so, x_i^2 + y_j^2}
+    float *zrow;        // [M] z'_m
+    float *god;         // [X][M][ND] G_od * dtheta per scatter vector
+    uint32_t *tbits;    // [R][M][Nw] mask factor bits per pair
+    float2 *energy;     // [K] {a_k = E_k/(hc dq), c_k = Phi_k E_k dE / hc^2}
+
+    // scratch (plan-owned)
+    float *fwd_part;    // [fwd_chunks][M*N] forward partial sums
+    int fwd_chunks;
+    int fwd_vc;         // voxels per forward chunk
+    float *adj_part;    // [adj_split][R*Q] adjoint partials (adj_split > 1)
+    int adj_split;
+    float *gtmp;        // [M*N]
+    float *ratio;       // [M*N]
+    float *ones;        // [M*N]
+    float *b1[4];       // [R*Q] A^T 1 per path, lazily
+    float *b2;          // [R*Q]
+    float *fnew;        // [R*Q]
+    double *nll_part;   // [nll_blocks]
+    double *nll_dev;    // [1]
+    int nll_blocks;
+    int *err_flag;      // [1] device error word
+    float *stage_in, *stage_out;  // host-API staging, lazily
+
+    TablePath *table;
+
+    int64_t table_bytes;
+    int64_t launches;   // kernels launched by the current / last call
+    int64_t open_pairs; // (voxel, pixel) pairs with mask factor 1
+    KernelProfiler prof;
+};
+
+// ---- plan.cu -----------------------------------------------------------------
+caxsi_status plan_build_tables(caxsi_plan *p, const double *phi_host, const uint8_t *mask_host);
+
+// ---- direct.cu ---------------------------------------------------------------
+caxsi_status direct_forward(caxsi_plan *p, const float *f, float *g, cudaStream_t s);
+caxsi_status direct_adjoint(caxsi_plan *p, const float *w, float *f, cudaStream_t s);
+void direct_configure(caxsi_plan *p);
+
+// ---- table.cu ----------------------------------------------------------------
+caxsi_status table_forward(caxsi_plan *p, const float *f, float *g, int path, cudaStream_t s);
+caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f, int path, cudaStream_t s);
+void table_destroy(caxsi_plan *p);
+
+// ---- recon.cu ----------------------------------------------------------------
+caxsi_status recon_ratio(caxsi_plan *p, const float *y, const float *r, cudaStream_t s);
+caxsi_status recon_update(caxsi_plan *p, const float *f_old, float beta, float delta,
+                          const float *b1, cudaStream_t s);
+caxsi_status recon_nll_fetch(caxsi_plan *p, double *out, cudaStream_t s);
+
+// ---- helpers -----------------------------------------------------------------
+#define CAXSI_CUDA_TRY(expr)                                   \
+    do {                                                       \
+        cudaError_t _e = (expr);                               \
+        if (_e != cudaSuccess) {                               \
+            return _e == cudaErrorMemoryAllocation ? CAXSI_ERR_OOM : CAXSI_ERR_CUDA; \
+        }                                                      \
+    } while (0)
+
+#define CAXSI_LAUNCH_CHECK(p)                                  \
+    do {                                                       \
+        (p)->launches++;                                       \
+        cudaError_t _e = cudaGetLastError();                   \
+        if (_e != cudaSuccess) return CAXSI_ERR_CUDA;          \
+    } while (0)
+
+// Bracket one kernel launch with profiler events (no-op when profiling is off).
+struct ProfScope {
+    caxsi_plan *p;
+    const char *name;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    ProfScope(caxsi_plan *p_, const char *n, cudaStream_t s_) : p(p_), name(n), s(s_) {
+        if (p->prof.on) { a = p->prof.get(); cudaEventRecord(a, s); }
+    }
+    ~ProfScope() {
+        if (a) {
+            cudaEvent_t b = p->prof.get();
+            cudaEventRecord(b, s);
+            p->prof.recs.push_back({name, a, b});
+        }
+    }
+};
+#define CAXSI_PROF(p, name, s) ProfScope _prof_scope_##__LINE__((p), (name), (s))
+
+static inline int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -18,3 +18,17 @@ def tiny():
     import synth
     g = synth.tiny_geometry()
     return g, synth.tungsten_spectrum(g), synth.random_mask(g, synth.TINY_MASK_SEED)
+
+
+def pytest_collection_modifyitems(config, items):
+    try:
+        import torch
+        has_cuda = torch.cuda.is_available()
+    except Exception:
+        has_cuda = False
+    if has_cuda:
+        return
+    skip = pytest.mark.skip(reason="needs a CUDA GPU")
+    for it in items:
+        if "gpu" in it.keywords:
+            it.add_marker(skip)

@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerance: relative L2 error <= 1e-5 for FP32 paths (the target stated for the
+FP32 forward and adjoint), measured against the oracle evaluated in FP64 on the
+same float32 inputs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+REL_L2_TOL = 1e-5
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+@pytest.fixture(scope="module")
+def cx():
+    import torch
+    from paper_1603_06400_gb300 import build, caxsi
+    build.build()
+    return caxsi, torch
+
+
+def _t(torch, a):
+    return torch.tensor(np.asarray(a, np.float32), device="cuda:0")
+
+
+def _f32(a):
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
+GEOMS = {
+    "tiny": lambda: synth.tiny_geometry(),
+    # ragged: N not a multiple of 32, M not a multiple of 8, odd J, rho_y = 3
+    "ragged": lambda: synth.make_geometry(X=5, J=7, Q=37, M=9, N=45, K=13, rho_y=3,
+                                          p_y=2.5, p_z=4.0, dx=6.0),
+    "one_column": lambda: synth.make_geometry(X=3, J=1, Q=20, M=12, N=70, K=9, rho_y=1,
+                                              p_y=1.5, p_z=3.0, dx=5.0),
+    "single_pixel": lambda: synth.make_geometry(X=4, J=3, Q=2, M=1, N=1, K=1, rho_y=2,
+                                                p_y=10.0, p_z=10.0, dx=5.0),
+    "wide_rows": lambda: synth.make_geometry(X=2, J=40, Q=16, M=3, N=130, K=7, rho_y=3,
+                                             p_y=1.2, p_z=3.0, dx=7.0),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GEOMS))
+@pytest.mark.parametrize("path", ["direct"])
+def test_forward_adjoint_parity(cx, name, path):
+    caxsi, torch = cx
+    g = GEOMS[name]()
+    phi = synth.tungsten_spectrum(g)
+    mask = synth.random_mask(g, 77)
+    f = synth.phantom(g, 3, n_ellipses=3) + 0.05 * synth.uniform_random((g.X, g.J, g.Q), 4)
+    w = synth.uniform_random((g.M, g.N), 5)
+    plan = caxsi.Plan(g, phi, mask)
+    p = caxsi.PATHS[path]
+    gg = plan.forward(_t(torch, f), path=p).cpu().numpy()
+    fa = plan.adjoint(_t(torch, w), path=p).cpu().numpy()
+    ref_g = oracle.forward(g, phi, mask, _f32(f))
+    ref_f = oracle.adjoint(g, phi, mask, _f32(w))
+    assert rel_l2(gg, ref_g) <= REL_L2_TOL
+    assert rel_l2(fa, ref_f) <= REL_L2_TOL
+    # elementwise: every entry above 1e-3 of the maximum within 1e-4 relative
+    big = np.abs(ref_g) > 1e-3 * np.abs(ref_g).max()
+    assert np.all(np.abs(gg - ref_g)[big] <= 1e-4 * np.abs(ref_g)[big])
+    big = np.abs(ref_f) > 1e-3 * np.abs(ref_f).max()
+    assert np.all(np.abs(fa - ref_f)[big] <= 1e-4 * np.abs(ref_f)[big])
+    plan.close()
+
+
+def test_zero_inputs_and_closed_mask(cx):
+    caxsi, torch = cx
+    g = GEOMS["ragged"]()
+    phi = synth.tungsten_spectrum(g)
+    plan = caxsi.Plan(g, phi, synth.random_mask(g, 1))
+    assert not torch.any(plan.forward(torch.zeros(g.f_len, device="cuda:0")))
+    assert not torch.any(plan.adjoint(torch.zeros(g.g_len, device="cuda:0")))
+    plan.close()
+    closed = caxsi.Plan(g, phi, np.zeros((g.mask_rows, g.mask_cols), np.uint8))
+    assert not torch.any(closed.forward(torch.ones(g.f_len, device="cuda:0")))
+    assert not torch.any(closed.adjoint(torch.ones(g.g_len, device="cuda:0")))
+    closed.close()
+
+
+def test_adjoint_identity_fp64_dots(cx):
+    caxsi, torch = cx
+    g = synth.tiny_geometry()
+    phi = synth.tungsten_spectrum(g)
+    plan = caxsi.Plan(g, phi, synth.random_mask(g, synth.TINY_MASK_SEED))
+    f = _t(torch, synth.uniform_random((g.X, g.J, g.Q), 8))
+    w = _t(torch, synth.normal_random((g.M, g.N), 9))
+    lhs = torch.sum(plan.forward(f).double() * w.double()).item()
+    rhs = torch.sum(f.double() * plan.adjoint(w).double()).item()
+    assert abs(lhs - rhs) <= 1e-6 * (abs(lhs) + abs(rhs))
+    plan.close()
+
+
+def test_deterministic_and_host_forms_agree(cx):
+    caxsi, torch = cx
+    g = GEOMS["ragged"]()
+    phi = synth.tungsten_spectrum(g)
+    plan = caxsi.Plan(g, phi, synth.random_mask(g, 2))
+    f = synth.uniform_random((g.X, g.J, g.Q), 10).astype(np.float32)
+    w = synth.uniform_random((g.M, g.N), 11).astype(np.float32)
+    a1 = plan.forward(_t(torch, f)).cpu().numpy()
+    a2 = plan.forward(_t(torch, f)).cpu().numpy()
+    np.testing.assert_array_equal(a1, a2)
+    np.testing.assert_array_equal(plan.forward_host(f), a1)
+    b1 = plan.adjoint(_t(torch, w)).cpu().numpy()
+    np.testing.assert_array_equal(plan.adjoint(_t(torch, w)).cpu().numpy(), b1)
+    np.testing.assert_array_equal(plan.adjoint_host(w), b1)
+    plan.close()
+
+
+def test_wrong_lengths_are_rejected(cx):
+    caxsi, torch = cx
+    g = GEOMS["ragged"]()
+    plan = caxsi.Plan(g, synth.tungsten_spectrum(g), synth.random_mask(g, 2))
+    f = torch.zeros(g.f_len, device="cuda:0")
+    out = torch.zeros(g.g_len, device="cuda:0")
+    import ctypes
+    st = plan.lib.caxsi_forward(plan.handle, ctypes.c_void_p(f.data_ptr()), g.f_len - 1,
+                                ctypes.c_void_p(out.data_ptr()), g.g_len, 0, None)
+    assert st == 1
+    st = plan.lib.caxsi_forward(plan.handle, ctypes.c_void_p(f.data_ptr()), g.f_len,
+                                ctypes.c_void_p(out.data_ptr()), g.g_len, 7, None)
+    assert st == 1
+    plan.close()
+
+
+# --------------------------------------------------------------------------
+# Reconstruction step
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("beta", [0.0, 0.5])
+def test_recon_step_parity(cx, beta):
+    caxsi, torch = cx
+    g = synth.tiny_geometry()
+    phi = synth.tungsten_spectrum(g)
+    mask = synth.random_mask(g, synth.TINY_MASK_SEED)
+    f_true = synth.phantom(g, 1, n_ellipses=3)
+    mean = oracle.forward(g, phi, mask, f_true)
+    y = synth.poisson_counts(mean * (1e3 / mean.max()), 2)
+    r = np.full_like(y, 0.25)
+    plan = caxsi.Plan(g, phi, mask)
+    b1 = oracle.adjoint(g, phi, mask, np.ones_like(y))
+    f0 = np.full((g.X, g.J, g.Q), y.sum() / b1.sum())
+    delta = 0.02
+    ft = _t(torch, f0)
+    yt, rt = _t(torch, y), _t(torch, r)
+    f = _f32(f0)
+    for it in range(3):
+        nll_gpu = plan.recon_step(yt, ft, r=rt, beta=beta, delta=delta, want_nll=True)
+        A = lambda x: oracle.forward(g, phi, mask, x)
+        At = lambda x: oracle.adjoint(g, phi, mask, x)
+        f_next, nll_ref = oracle.em_iteration(A, At, y, r, f, b1, beta, delta)
+        assert nll_gpu == pytest.approx(nll_ref, rel=1e-6)
+        got = ft.cpu().numpy()
+        assert rel_l2(got, f_next) <= 5 * REL_L2_TOL * (it + 1)
+        f = _f32(got)   # continue both from the GPU iterate
+    plan.close()
+
+
+def test_recon_reports_nonpositive_mean(cx):
+    caxsi, torch = cx
+    g = GEOMS["ragged"]()
+    phi = synth.tungsten_spectrum(g)
+    plan = caxsi.Plan(g, phi, np.zeros((g.mask_rows, g.mask_cols), np.uint8))
+    y = torch.ones(g.g_len, device="cuda:0")
+    f = torch.ones(g.f_len, device="cuda:0")
+    before = f.clone()
+    with pytest.raises(caxsi.CaxsiError) as e:
+        plan.recon_step(y, f, want_nll=True)
+    assert e.value.status == 4
+    assert torch.equal(f, before)
+    # y = 0 where z = 0 is allowed: ratio 0, likelihood 0
+    nll = plan.recon_step(torch.zeros(g.g_len, device="cuda:0"), f, want_nll=True)
+    assert nll == 0.0
+    plan.close()
+
+
+# --------------------------------------------------------------------------
+# Paper-scale workload (256 x 128 voxels x 128 q, 256 x 64 detector, 64 energies):
+# the launch configuration the benchmark times, checked on sampled outputs
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("path", ["direct"])
+def test_paper_scale_sampled(cx, path):
+    caxsi, torch = cx
+    g = synth.paper_geometry()
+    phi = synth.tungsten_spectrum(g)
+    mask = synth.random_mask(g, synth.PAPER_MASK_SEED)
+    f = synth.phantom(g, 0)
+    w = synth.uniform_random((g.M, g.N), 1) + 0.5
+    plan = caxsi.Plan(g, phi, mask)
+    p = caxsi.PATHS[path]
+    gg = plan.forward(_t(torch, f), path=p).cpu().numpy().ravel()
+    fa = plan.adjoint(_t(torch, w), path=p).cpu().numpy().reshape(g.X * g.J, g.Q)
+    rng = np.random.default_rng(5)
+    pix = np.concatenate([rng.choice(g.M * g.N, 40, replace=False), [0, g.M * g.N - 1]])
+    ref = oracle.forward_pixels(g, phi, mask, _f32(f), pix)
+    assert rel_l2(gg[pix], ref) <= REL_L2_TOL
+    vox = np.concatenate([rng.choice(g.X * g.J, 24, replace=False), [0, g.X * g.J - 1]])
+    refv = oracle.adjoint_voxels(g, phi, mask, _f32(w), vox)
+    assert rel_l2(fa[vox], refv) <= REL_L2_TOL
+    plan.close()
