@@ -49,25 +49,31 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--path", default="direct",
                     choices=["direct", "table_fp32", "table_bf16", "table_fp16"])
-    ap.add_argument("--workload", choices=["paper", "tiny"], default="paper")
+    ap.add_argument("--workload", choices=["paper", "tiny", "small"], default="paper")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
 def geometry(name):
-    return synth.paper_geometry() if name == "paper" else synth.tiny_geometry()
+    if name == "paper":
+        return synth.paper_geometry()
+    if name == "small":
+        # the paper-scale detector, q grid and spectrum with 16 voxels along the beam
+        # (for profiler captures: same per-pair work, 1/8 of the pairs)
+        return synth.paper_geometry().with_(X=16, dx=4.375)
+    return synth.tiny_geometry()
 
 
 def workload_desc(g, name):
-    return (f"{'paper-scale' if name == 'paper' else 'tiny'} fan-beam coded-aperture scatter: "
+    return (f"{name} fan-beam coded-aperture scatter: "
             f"object {g.J}(y) x {g.X}(x) voxels x {g.Q} q bins ({g.q_min}-{g.q_max} nm^-1), "
             f"detector {g.N}x{g.M} pixels, {g.K} energy bins ({g.E_min:g}-{g.E_max:g} keV); "
             f"penalised EM step (A, ratio, A^T, update) over {N_PHANTOMS} seeded phantoms")
 
 
 def mask_seed(name):
-    return synth.PAPER_MASK_SEED if name == "paper" else synth.TINY_MASK_SEED
+    return synth.TINY_MASK_SEED if name == "tiny" else synth.PAPER_MASK_SEED
 
 
 # ---------------------------------------------------------------------------
@@ -194,7 +200,7 @@ def oracle_eval_seconds(g, phi, mask, f, w, n_pix, n_vox, seed):
 
 def cpu_inputs(g):
     phi = synth.tungsten_spectrum(g)
-    mask = synth.random_mask(g, mask_seed("paper" if g.X == 128 else "tiny"))
+    mask = synth.random_mask(g, mask_seed("tiny" if g.M == 16 else "paper"))
     f = synth.phantom(g, 0)
     w = synth.uniform_random((g.M, g.N), 1)
     return phi, mask, f, w

@@ -134,6 +134,7 @@ caxsi_status caxsi_plan_create(const caxsi_geometry *geom, const double *phi_hos
     if (!p) return CAXSI_ERR_OOM;
     p->g = *geom;
     p->device = dev;
+    p->phi.assign(phi_host, phi_host + geom->K);
     if (cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         delete p;
         return CAXSI_ERR_CUDA;
@@ -270,7 +271,7 @@ caxsi_status caxsi_plan_info(const caxsi_plan *p, caxsi_plan_info_t *info) {
     if (!p || !info) return CAXSI_ERR_INVALID;
     info->n_offsets = p->dg.ND;
     info->table_bytes = p->table_bytes;
-    info->n_breakpoints = 0;
+    info->n_breakpoints = table_breakpoints(p);
     info->kernel_launches = p->launches;
     info->n_open_pairs = p->open_pairs;
     return CAXSI_OK;

@@ -186,6 +186,12 @@ size_t adj_smem(const DevGeo &g) {
 
 }  // namespace
 
+cudaError_t launch_sum_parts(const float *part, int nparts, int64_t stride, float *out,
+                             int64_t n, cudaStream_t s) {
+    k_sum_parts<<<(unsigned)ceil_div64(n, 256), 256, 0, s>>>(part, nparts, stride, out, n);
+    return cudaGetLastError();
+}
+
 void direct_configure(caxsi_plan *p) {
     const DevGeo &g = p->dg;
     const int tiles = (int)(ceil_div64(g.M, FWD_WARPS) * ceil_div64(g.N, 32));

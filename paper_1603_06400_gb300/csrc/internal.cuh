@@ -78,6 +78,7 @@ struct caxsi_plan {
     int64_t table_bytes;
     int64_t launches;   // kernels launched by the current / last call
     int64_t open_pairs; // (voxel, pixel) pairs with mask factor 1
+    std::vector<double> phi;  // host copy of the spectrum Phi_k
     KernelProfiler prof;
 };
 
@@ -93,6 +94,7 @@ void direct_configure(caxsi_plan *p);
 caxsi_status table_forward(caxsi_plan *p, const float *f, float *g, int path, cudaStream_t s);
 caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f, int path, cudaStream_t s);
 void table_destroy(caxsi_plan *p);
+int64_t table_breakpoints(const caxsi_plan *p);
 
 // ---- recon.cu ----------------------------------------------------------------
 caxsi_status recon_ratio(caxsi_plan *p, const float *y, const float *r, cudaStream_t s);

@@ -1,10 +1,563 @@
-// Table paths (exact piecewise-linear evaluation in u = sin(theta/2)).
-#include "internal.cuh"
+// Table paths: exact evaluation through the piecewise-linear structure of the
+// effective spectral factor W(r, theta) (Eq. 4) in u = sin(theta/2).
+//
+// In energy form W(r, u) = ang(theta) * sum_k c_k f~(r, a_k u - b), with f~ the
+// hat-function interpolation of the q samples (knots at every integer bin
+// position).  For each energy k, f~(a_k u - b) is linear in u between the
+// points u_{k,m} = (m + b)/a_k, m = -1..Q, where a q-grid node is crossed.  So
+// sum_k c_k f~(...) is linear in u between consecutive elements of the sorted
+// union of these points ("knots" u_1 < ... < u_B), and linear interpolation
+// between its values at the knots is exact.  This turns the paper's
+// scatter-angle interpolation (Sec. III-B, which samples theta uniformly and
+// so approximates S) into an exact scheme:
+//
+//   Wtab[r][t] = sum_l f[r][l] S~[t][l],  S~[t][l] = sum_k c_k hat(a_k u_t - b - l)
+//
+// is a dense contraction over q (a GEMM); each (voxel, pixel) pair then finds
+// the interval [u_t, u_t+1] holding its u and interpolates (forward).  The
+// adjoint scatters each pair's weight onto the two knots of its interval,
+// V[r][t] += (1 - alpha) w, V[r][t+1] += alpha w, and contracts
+// f[r][l] = sum_t V[r][t] S~[t][l] -- the exact transpose.
+//
+// Knot positions are generated in FP64, rounded to FP32 (the precision of the
+// per-pair u), sorted and deduplicated; S~ is evaluated in FP64 at the rounded
+// knots.  Only knots inside the range of u over the open pairs, plus one
+// bracketing knot on each side, are kept.  The interval search uses a uniform
+// bucket grid over the knot range followed by a short scan.
+#include <math.h>
+#include <string.h>
 
-caxsi_status table_forward(caxsi_plan *, const float *, float *, int, cudaStream_t) {
-    return CAXSI_ERR_UNSUPPORTED;
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+#include "pairgeo.cuh"
+
+cudaError_t sgemm_kmajor(int M, int N, int K, const float *A, int64_t lda, const float *Bm,
+                         int64_t ldb, float *C, int64_t ldc, const int2 *kband, cudaStream_t s);
+cudaError_t sgemm_nmajor_splitk(int M, int N, int K, const float *A, int64_t lda, const float *Bm,
+                                int64_t ldb, float *C, int64_t ldc, int64_t plane, int splits,
+                                cudaStream_t s);
+cudaError_t launch_sum_parts(const float *part, int nparts, int64_t stride, float *out,
+                             int64_t n, cudaStream_t s);
+
+struct TablePath {
+    int B = 0;          // knots
+    int Bp = 0;         // padded row length of Wtab / Vtab (>= B + 1, multiple of 4)
+    int NB = 0;         // buckets
+    float u0 = 0.f, inv_h = 0.f;
+    float2 *knots = nullptr;    // [B] {u_t, 1/(u_{t+1} - u_t)}; last {u_B, 0}
+    uint16_t *bstart = nullptr; // [NB] last knot index at or below the bucket start
+    float *S = nullptr;         // [B][Q] S~ (FP32)
+    int2 *kband = nullptr;      // [ceil(B/128)] q range where S~ can be nonzero
+    float *tab = nullptr;       // [R][Bp] Wtab (forward) / Vtab (adjoint)
+    float *fwd_part = nullptr;  // [fwd_chunks][M*N]
+    int fwd_chunks = 0, fwd_vc = 0, ppt = 1, threads = 1024, pix_chunks = 1;
+    float *adj_part = nullptr;  // [adj_splits][R*Q]
+    int adj_splits = 1;
+    int adj_chunks = 0, adj_vc = 0;
+    size_t smem_fwd = 0, smem_adj = 0;
+};
+
+namespace {
+
+constexpr int TAB_THREADS = 1024;
+
+struct PairArgs {
+    DevGeo g;
+    const float4 *vox;
+    const float *zrow;
+    const float *god;
+    const uint32_t *tbits;
+};
+
+PairArgs pair_args(const caxsi_plan *p) {
+    PairArgs a;
+    a.g = p->dg;
+    a.vox = p->vox;
+    a.zrow = p->zrow;
+    a.god = p->god;
+    a.tbits = p->tbits;
+    return a;
 }
-caxsi_status table_adjoint(caxsi_plan *, const float *, float *, int, cudaStream_t) {
-    return CAXSI_ERR_UNSUPPORTED;
+
+// Range of u over all open pairs (plan set-up).
+__global__ void k_pair_urange(PairArgs A, unsigned int *umin, unsigned int *umax) {
+    const DevGeo &g = A.g;
+    const int64_t npairs = (int64_t)g.R * g.M * g.N;
+    float lo = 3.4e38f, hi = 0.f;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < npairs;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int n = (int)(t % g.N);
+        const int m = (int)((t / g.N) % g.M);
+        const int v = (int)(t / ((int64_t)g.N * g.M));
+        const uint32_t word = A.tbits[((int64_t)v * g.M + m) * g.Nw + (n >> 5)];
+        if (!((word >> (n & 31)) & 1u)) continue;
+        const float4 vx = A.vox[v];
+        float u, ang;
+        pair_u_angular(vx.x, vx.y, vx.w, (float)n - g.cN, A.zrow[m], g.p_y, g.Xd, u, ang);
+        lo = fminf(lo, u);
+        hi = fmaxf(hi, u);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_down_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_down_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(umin, __float_as_uint(lo));
+        atomicMax(umax, __float_as_uint(hi));
+    }
 }
-void table_destroy(caxsi_plan *) {}
+
+// S~[t][l] = sum_k c_k max(0, 1 - |a_k u_t - b - l|) in FP64.
+__global__ void k_build_S(int B, int Q, int K, const float2 *knots, const double *ak,
+                          const double *ck, double b, float *S) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)B * Q) return;
+    const int t = (int)(idx / Q), l = (int)(idx % Q);
+    const double u = (double)knots[t].x;
+    double s = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double x = ak[k] * u - b - (double)l;
+        const double h = 1.0 - fabs(x);
+        if (h > 0.0) s += ck[k] * h;
+    }
+    S[idx] = (float)s;
+}
+
+// Interval t with u_t <= u < u_{t+1} (u inside [u_1, u_B]).
+__device__ __forceinline__ int find_interval(float u, const float2 *kn, const uint16_t *bstart,
+                                             int B, int NB, float u0, float inv_h) {
+    int bk = (int)((u - u0) * inv_h);
+    bk = min(max(bk, 0), NB - 1);
+    int t = bstart[bk];
+    while (t + 1 < B && kn[t + 1].x <= u) ++t;
+    while (t > 0 && kn[t].x > u) --t;
+    return t;
+}
+
+struct TabArgs {
+    int B, NB, Bp;
+    float u0, inv_h;
+    const float2 *knots;
+    const uint16_t *bstart;
+};
+
+TabArgs tab_args(const TablePath *T) {
+    TabArgs a;
+    a.B = T->B;
+    a.NB = T->NB;
+    a.Bp = T->Bp;
+    a.u0 = T->u0;
+    a.inv_h = T->inv_h;
+    a.knots = T->knots;
+    a.bstart = T->bstart;
+    return a;
+}
+
+// Forward per-pair stage: block = 1024 threads over a chunk of PPT*1024
+// detector pixels and a chunk of voxels; each voxel's Wtab row is staged in
+// shared memory together with the knot and bucket tables.
+template <int PPT>
+__global__ void __launch_bounds__(TAB_THREADS, 1)
+k_fwd_table(PairArgs A, TabArgs T, const float *__restrict__ Wtab, float *__restrict__ part,
+            int vc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const DevGeo &g = A.g;
+    float2 *s_kn = reinterpret_cast<float2 *>(smem_raw);
+    float *s_w = reinterpret_cast<float *>(s_kn + T.B);
+    uint16_t *s_bs = reinterpret_cast<uint16_t *>(s_w + T.Bp);
+    const int tid = threadIdx.x;
+    for (int t = tid; t < T.B; t += TAB_THREADS) s_kn[t] = T.knots[t];
+    for (int t = tid; t < T.NB; t += TAB_THREADS) s_bs[t] = T.bstart[t];
+
+    const int64_t npix = (int64_t)g.M * g.N;
+    const int64_t p0 = (int64_t)blockIdx.y * PPT * TAB_THREADS + tid;
+    // pixel coordinates of this thread's first pixel, stepped by TAB_THREADS
+    const int step_m = TAB_THREADS / g.N, step_n = TAB_THREADS % g.N;
+    const int v0 = blockIdx.x * vc;
+    const int v1 = min(v0 + vc, g.R);
+    float acc[PPT];
+#pragma unroll
+    for (int s = 0; s < PPT; ++s) acc[s] = 0.f;
+    const float u_first = T.knots[0].x, u_last = T.knots[T.B - 1].x;
+
+    for (int v = v0; v < v1; ++v) {
+        __syncthreads();
+        const float *wrow = Wtab + (int64_t)v * T.Bp;
+        for (int t = tid; t <= T.B; t += TAB_THREADS) s_w[t] = wrow[t];
+        __syncthreads();
+        const int i = v / g.J, j = v - i * g.J;
+        const float4 vx = A.vox[v];
+        const uint32_t *tb = A.tbits + (int64_t)v * g.M * g.Nw;
+        const float *god_i = A.god + (int64_t)i * g.M * g.ND - g.d_min - g.rho_y * j;
+        int m = (int)(p0 / g.N), n = (int)(p0 % g.N);
+#pragma unroll
+        for (int s = 0; s < PPT; ++s) {
+            if (p0 + (int64_t)s * TAB_THREADS < npix) {
+                const uint32_t word = tb[m * g.Nw + (n >> 5)];
+                if ((word >> (n & 31)) & 1u) {
+                    float u, ang;
+                    pair_u_angular(vx.x, vx.y, vx.w, (float)n - g.cN, A.zrow[m], g.p_y, g.Xd, u, ang);
+                    if (u >= u_first && u <= u_last) {
+                        const int t = find_interval(u, s_kn, s_bs, T.B, T.NB, T.u0, T.inv_h);
+                        const float2 kn = s_kn[t];
+                        const float al = (u - kn.x) * kn.y;
+                        const float w0 = s_w[t];
+                        const float W = fmaf(al, s_w[t + 1] - w0, w0);
+                        acc[s] = fmaf(vx.z * god_i[(int64_t)m * g.ND + n] * ang, W, acc[s]);
+                    }
+                }
+            }
+            m += step_m;
+            n += step_n;
+            if (n >= g.N) { n -= g.N; ++m; }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < PPT; ++s) {
+        const int64_t p = p0 + (int64_t)s * TAB_THREADS;
+        if (p < npix) part[(int64_t)blockIdx.x * npix + p] = acc[s];
+    }
+}
+
+// Adjoint per-pair stage: per voxel, scatter w-weighted pair contributions onto
+// the two knots of each pair's interval in a shared-memory row, then write the
+// row to Vtab.
+template <int PPT>
+__global__ void __launch_bounds__(TAB_THREADS, 1)
+k_adj_table(PairArgs A, TabArgs T, const float *__restrict__ w, float *__restrict__ Vtab, int vc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const DevGeo &g = A.g;
+    float2 *s_kn = reinterpret_cast<float2 *>(smem_raw);
+    float *s_v = reinterpret_cast<float *>(s_kn + T.B);
+    uint16_t *s_bs = reinterpret_cast<uint16_t *>(s_v + T.Bp);
+    const int tid = threadIdx.x;
+    for (int t = tid; t < T.B; t += TAB_THREADS) s_kn[t] = T.knots[t];
+    for (int t = tid; t < T.NB; t += TAB_THREADS) s_bs[t] = T.bstart[t];
+
+    const int64_t npix = (int64_t)g.M * g.N;
+    const int step_m = TAB_THREADS / g.N, step_n = TAB_THREADS % g.N;
+    const int v0 = blockIdx.x * vc;
+    const int v1 = min(v0 + vc, g.R);
+    const float u_first = T.knots[0].x, u_last = T.knots[T.B - 1].x;
+
+    for (int v = v0; v < v1; ++v) {
+        __syncthreads();
+        for (int t = tid; t < T.Bp; t += TAB_THREADS) s_v[t] = 0.f;
+        __syncthreads();
+        const int i = v / g.J, j = v - i * g.J;
+        const float4 vx = A.vox[v];
+        const uint32_t *tb = A.tbits + (int64_t)v * g.M * g.Nw;
+        const float *god_i = A.god + (int64_t)i * g.M * g.ND - g.d_min - g.rho_y * j;
+        for (int64_t pc = 0; pc < npix; pc += (int64_t)PPT * TAB_THREADS) {
+            const int64_t p0 = pc + tid;
+            int m = (int)(p0 / g.N), n = (int)(p0 % g.N);
+#pragma unroll
+            for (int s = 0; s < PPT; ++s) {
+                const int64_t p = p0 + (int64_t)s * TAB_THREADS;
+                if (p < npix) {
+                    const uint32_t word = tb[m * g.Nw + (n >> 5)];
+                    const float wv = w[p];
+                    if (((word >> (n & 31)) & 1u) && wv != 0.f) {
+                        float u, ang;
+                        pair_u_angular(vx.x, vx.y, vx.w, (float)n - g.cN, A.zrow[m], g.p_y, g.Xd, u, ang);
+                        if (u >= u_first && u <= u_last) {
+                            const int t = find_interval(u, s_kn, s_bs, T.B, T.NB, T.u0, T.inv_h);
+                            const float2 kn = s_kn[t];
+                            const float al = (u - kn.x) * kn.y;
+                            const float c = vx.z * god_i[(int64_t)m * g.ND + n] * ang * wv;
+                            const float hi = c * al;
+                            atomicAdd(&s_v[t], c - hi);
+                            atomicAdd(&s_v[t + 1], hi);
+                        }
+                    }
+                }
+                m += step_m;
+                n += step_n;
+                if (n >= g.N) { n -= g.N; ++m; }
+            }
+        }
+        __syncthreads();
+        float *vrow = Vtab + (int64_t)v * T.Bp;
+        for (int t = tid; t < T.B; t += TAB_THREADS) vrow[t] = s_v[t];
+    }
+}
+
+template <int PPT>
+cudaError_t launch_fwd(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s) {
+    dim3 grid(T->fwd_chunks, T->pix_chunks);
+    auto kfn = k_fwd_table<PPT>;
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T->smem_fwd);
+    if (e != cudaSuccess) return e;
+    TabArgs ta = tab_args(T);
+    kfn<<<grid, TAB_THREADS, T->smem_fwd, s>>>(pair_args(p), ta, T->tab, part, T->fwd_vc);
+    return cudaGetLastError();
+}
+
+template <int PPT>
+cudaError_t launch_adj(const caxsi_plan *p, const TablePath *T, const float *w, cudaStream_t s) {
+    auto kfn = k_adj_table<PPT>;
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T->smem_adj);
+    if (e != cudaSuccess) return e;
+    TabArgs ta = tab_args(T);
+    kfn<<<T->adj_chunks, TAB_THREADS, T->smem_adj, s>>>(pair_args(p), ta, w, T->tab, T->adj_vc);
+    return cudaGetLastError();
+}
+
+cudaError_t dispatch_fwd(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s) {
+    switch (T->ppt) {
+        case 1: return launch_fwd<1>(p, T, part, s);
+        case 2: return launch_fwd<2>(p, T, part, s);
+        case 4: return launch_fwd<4>(p, T, part, s);
+        case 8: return launch_fwd<8>(p, T, part, s);
+        default: return launch_fwd<16>(p, T, part, s);
+    }
+}
+
+cudaError_t dispatch_adj(const caxsi_plan *p, const TablePath *T, const float *w, cudaStream_t s) {
+    switch (T->ppt) {
+        case 1: return launch_adj<1>(p, T, w, s);
+        case 2: return launch_adj<2>(p, T, w, s);
+        case 4: return launch_adj<4>(p, T, w, s);
+        case 8: return launch_adj<8>(p, T, w, s);
+        default: return launch_adj<16>(p, T, w, s);
+    }
+}
+
+void free_table(TablePath *T) {
+    if (!T) return;
+    cudaFree(T->knots);
+    cudaFree(T->bstart);
+    cudaFree(T->S);
+    cudaFree(T->kband);
+    cudaFree(T->tab);
+    cudaFree(T->fwd_part);
+    cudaFree(T->adj_part);
+    delete T;
+}
+
+caxsi_status build_table(caxsi_plan *p) {
+    const caxsi_geometry &G = p->g;
+    const DevGeo &d = p->dg;
+    TablePath *T = new TablePath();
+    caxsi_status st = CAXSI_OK;
+    unsigned int *ur = nullptr;
+    double *ak_d = nullptr, *ck_d = nullptr;
+    do {
+        // 1. range of u over the open pairs
+        if (cudaMalloc(&ur, 2 * sizeof(unsigned int)) != cudaSuccess) { st = CAXSI_ERR_OOM; break; }
+        unsigned int init[2] = {0x7f7fffffu, 0u};
+        cudaMemcpy(ur, init, sizeof(init), cudaMemcpyHostToDevice);
+        k_pair_urange<<<4 * p->num_sms, 256>>>(pair_args(p), ur, ur + 1);
+        unsigned int got[2];
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(got, ur, sizeof(got), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            st = CAXSI_ERR_CUDA;
+            break;
+        }
+        float ulo, uhi;
+        memcpy(&ulo, &got[0], 4);
+        memcpy(&uhi, &got[1], 4);
+
+        // 2. knots u_{k,m} = (m + b)/a_k in FP64, rounded to FP32, sorted, unique
+        const double dE = (G.E_max - G.E_min) / G.K;
+        const double dq = (G.q_max - G.q_min) / (G.Q - 1);
+        const double b = G.q_min / dq;
+        std::vector<double> ak(G.K), ck(G.K);
+        std::vector<float> kn;
+        kn.reserve((size_t)G.K * (G.Q + 2));
+        for (int k = 0; k < G.K; ++k) {
+            const double E = G.E_min + (k + 0.5) * dE;
+            ak[k] = E / (G.hc * dq);
+            for (int m = -1; m <= G.Q; ++m) {
+                const double u = (m + b) / ak[k];
+                if (u > 0.0) kn.push_back((float)u);
+            }
+        }
+        // with q_min < dq every tau_k(0) = -b lies inside (-1, 0], where f~ is
+        // already nonzero: W is then linear on [0, first crossing] and u = 0
+        // must be a knot too
+        if (b < 1.0) kn.push_back(0.f);
+        std::sort(kn.begin(), kn.end());
+        kn.erase(std::unique(kn.begin(), kn.end()), kn.end());
+        if (kn.size() < 2) { st = CAXSI_ERR_UNSUPPORTED; break; }
+        // keep [last knot <= ulo, first knot >= uhi]
+        int lo = 0, hi = (int)kn.size() - 1;
+        if (got[1] >= got[0]) {
+            auto itl = std::upper_bound(kn.begin(), kn.end(), ulo);
+            lo = itl == kn.begin() ? 0 : (int)(itl - kn.begin()) - 1;
+            auto ith = std::lower_bound(kn.begin(), kn.end(), uhi);
+            hi = ith == kn.end() ? (int)kn.size() - 1 : (int)(ith - kn.begin());
+        }
+        if (hi - lo + 1 < 2) { if (hi + 1 < (int)kn.size()) ++hi; else if (lo > 0) --lo; }
+        std::vector<float> knots(kn.begin() + lo, kn.begin() + hi + 1);
+        const int B = (int)knots.size();
+        if (B < 2 || B > 65535) { st = CAXSI_ERR_UNSUPPORTED; break; }
+        T->B = B;
+        T->Bp = ((B + 1) + 3) / 4 * 4;
+
+        // spectral weights c_k = Phi_k E_k dE / hc^2 in FP64 (energy form of Eq. 4)
+        for (int k = 0; k < G.K; ++k) {
+            const double E = G.E_min + (k + 0.5) * dE;
+            ck[k] = p->phi[k] * E * dE / (G.hc * G.hc);
+        }
+
+        // 3. knot records and bucket grid
+        std::vector<float2> krec(B);
+        for (int t = 0; t < B; ++t) {
+            const float ut = knots[t];
+            const float inv = (t + 1 < B) ? (float)(1.0 / ((double)knots[t + 1] - (double)ut)) : 0.f;
+            krec[t] = make_float2(ut, inv);
+        }
+        const int NB = std::min(65535, 2 * B);
+        const double span = (double)knots[B - 1] - (double)knots[0];
+        const double h = span / NB;
+        T->NB = NB;
+        T->u0 = knots[0];
+        T->inv_h = (float)(1.0 / h);
+        std::vector<uint16_t> bs(NB);
+        {
+            int t = 0;
+            for (int bk = 0; bk < NB; ++bk) {
+                const double start = (double)knots[0] + bk * h;
+                while (t + 1 < B && (double)knots[t + 1] <= start) ++t;
+                bs[bk] = (uint16_t)t;
+            }
+        }
+        // q band of S~ per 128-knot column tile: |a_k u - b - l| < 1 for some k
+        const int ntile = (B + 127) / 128;
+        std::vector<int2> band(ntile);
+        for (int c = 0; c < ntile; ++c) {
+            const double ulo_t = knots[c * 128];
+            const double uhi_t = knots[std::min(B - 1, c * 128 + 127)];
+            int l0 = (int)floor(ak[0] * ulo_t - b) - 1;
+            int l1 = (int)ceil(ak[G.K - 1] * uhi_t - b) + 2;
+            band[c] = make_int2(std::max(0, l0), std::min(G.Q, l1));
+        }
+
+        const int64_t R = d.R;
+        if (cudaMalloc(&T->knots, B * sizeof(float2)) != cudaSuccess ||
+            cudaMalloc(&T->bstart, NB * sizeof(uint16_t)) != cudaSuccess ||
+            cudaMalloc(&T->S, (size_t)B * G.Q * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&T->kband, ntile * sizeof(int2)) != cudaSuccess ||
+            cudaMalloc(&T->tab, (size_t)R * T->Bp * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&ak_d, G.K * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&ck_d, G.K * sizeof(double)) != cudaSuccess) {
+            st = CAXSI_ERR_OOM;
+            break;
+        }
+        cudaMemcpy(T->knots, krec.data(), B * sizeof(float2), cudaMemcpyHostToDevice);
+        cudaMemcpy(T->bstart, bs.data(), NB * sizeof(uint16_t), cudaMemcpyHostToDevice);
+        cudaMemcpy(T->kband, band.data(), ntile * sizeof(int2), cudaMemcpyHostToDevice);
+        cudaMemcpy(ak_d, ak.data(), G.K * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(ck_d, ck.data(), G.K * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemset(T->tab, 0, (size_t)R * T->Bp * sizeof(float));
+        k_build_S<<<(unsigned)ceil_div64((int64_t)B * G.Q, 256), 256>>>(B, G.Q, G.K, T->knots, ak_d, ck_d, b, T->S);
+        if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+            st = CAXSI_ERR_CUDA;
+            break;
+        }
+
+        // 4. launch shapes
+        const int64_t npix = (int64_t)G.M * G.N;
+        int ppt = 1;
+        while (ppt < 16 && (int64_t)ppt * TAB_THREADS < npix) ppt *= 2;
+        T->ppt = ppt;
+        T->pix_chunks = (int)ceil_div64(npix, (int64_t)ppt * TAB_THREADS);
+        int chunks = (int)ceil_div64(2 * p->num_sms, T->pix_chunks);
+        if (chunks > d.R) chunks = d.R;
+        T->fwd_vc = (int)ceil_div64(d.R, chunks);
+        T->fwd_chunks = (int)ceil_div64(d.R, T->fwd_vc);
+        int ac = 2 * p->num_sms;
+        if (ac > d.R) ac = d.R;
+        T->adj_vc = (int)ceil_div64(d.R, ac);
+        T->adj_chunks = (int)ceil_div64(d.R, T->adj_vc);
+        T->adj_splits = 8;
+        T->smem_fwd = (size_t)B * sizeof(float2) + (size_t)T->Bp * sizeof(float) + (size_t)NB * sizeof(uint16_t);
+        T->smem_adj = T->smem_fwd;
+        int smem_max = 0;
+        cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+        if ((size_t)smem_max < T->smem_fwd) { st = CAXSI_ERR_UNSUPPORTED; break; }
+        if (cudaMalloc(&T->fwd_part, (size_t)T->fwd_chunks * npix * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&T->adj_part, (size_t)T->adj_splits * R * G.Q * sizeof(float)) != cudaSuccess) {
+            st = CAXSI_ERR_OOM;
+            break;
+        }
+        p->table_bytes += (int64_t)B * 8 + NB * 2 + (int64_t)B * G.Q * 4 + R * T->Bp * 4 +
+                          (int64_t)T->fwd_chunks * npix * 4 + (int64_t)T->adj_splits * R * G.Q * 4;
+    } while (0);
+    cudaFree(ur);
+    cudaFree(ak_d);
+    cudaFree(ck_d);
+    if (st != CAXSI_OK) {
+        free_table(T);
+        return st;
+    }
+    p->table = T;
+    return CAXSI_OK;
+}
+
+}  // namespace
+
+int64_t table_breakpoints(const caxsi_plan *p) { return p->table ? p->table->B : 0; }
+
+caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path, cudaStream_t s) {
+    if (path != CAXSI_PATH_TABLE_FP32) return CAXSI_ERR_UNSUPPORTED;
+    if (!p->table) {
+        caxsi_status st = build_table(p);
+        if (st != CAXSI_OK) return st;
+    }
+    TablePath *T = p->table;
+    const DevGeo &d = p->dg;
+    {
+        CAXSI_PROF(p, "tab_gemm_fwd", s);
+        CAXSI_CUDA_TRY(sgemm_kmajor(d.R, T->B, d.Q, f, d.Q, T->S, d.Q, T->tab, T->Bp, T->kband, s));
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    {
+        CAXSI_PROF(p, "tab_pairs_fwd", s);
+        CAXSI_CUDA_TRY(dispatch_fwd(p, T, T->fwd_part, s));
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    const int64_t npix = (int64_t)d.M * d.N;
+    {
+        CAXSI_PROF(p, "sum_parts", s);
+        CAXSI_CUDA_TRY(launch_sum_parts(T->fwd_part, T->fwd_chunks, npix, g_out, npix, s));
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    return CAXSI_OK;
+}
+
+caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path, cudaStream_t s) {
+    if (path != CAXSI_PATH_TABLE_FP32) return CAXSI_ERR_UNSUPPORTED;
+    if (!p->table) {
+        caxsi_status st = build_table(p);
+        if (st != CAXSI_OK) return st;
+    }
+    TablePath *T = p->table;
+    const DevGeo &d = p->dg;
+    {
+        CAXSI_PROF(p, "tab_pairs_adj", s);
+        CAXSI_CUDA_TRY(dispatch_adj(p, T, w, s));
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    const int64_t nf = (int64_t)d.R * d.Q;
+    {
+        CAXSI_PROF(p, "tab_gemm_adj", s);
+        CAXSI_CUDA_TRY(sgemm_nmajor_splitk(d.R, d.Q, T->B, T->tab, T->Bp, T->S, d.Q, T->adj_part, d.Q,
+                                           nf, T->adj_splits, s));
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    {
+        CAXSI_PROF(p, "sum_parts", s);
+        CAXSI_CUDA_TRY(launch_sum_parts(T->adj_part, T->adj_splits, nf, f_out, nf, s));
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    return CAXSI_OK;
+}
+
+void table_destroy(caxsi_plan *p) {
+    free_table(p->table);
+    p->table = nullptr;
+}

@@ -52,8 +52,11 @@ GEOMS = {
 }
 
 
+FP32_PATHS = ["direct", "table_fp32"]
+
+
 @pytest.mark.parametrize("name", sorted(GEOMS))
-@pytest.mark.parametrize("path", ["direct"])
+@pytest.mark.parametrize("path", FP32_PATHS)
 def test_forward_adjoint_parity(cx, name, path):
     caxsi, torch = cx
     g = GEOMS[name]()
@@ -77,29 +80,33 @@ def test_forward_adjoint_parity(cx, name, path):
     plan.close()
 
 
-def test_zero_inputs_and_closed_mask(cx):
+@pytest.mark.parametrize("path", FP32_PATHS)
+def test_zero_inputs_and_closed_mask(cx, path):
     caxsi, torch = cx
     g = GEOMS["ragged"]()
     phi = synth.tungsten_spectrum(g)
+    p = caxsi.PATHS[path]
     plan = caxsi.Plan(g, phi, synth.random_mask(g, 1))
-    assert not torch.any(plan.forward(torch.zeros(g.f_len, device="cuda:0")))
-    assert not torch.any(plan.adjoint(torch.zeros(g.g_len, device="cuda:0")))
+    assert not torch.any(plan.forward(torch.zeros(g.f_len, device="cuda:0"), path=p))
+    assert not torch.any(plan.adjoint(torch.zeros(g.g_len, device="cuda:0"), path=p))
     plan.close()
     closed = caxsi.Plan(g, phi, np.zeros((g.mask_rows, g.mask_cols), np.uint8))
-    assert not torch.any(closed.forward(torch.ones(g.f_len, device="cuda:0")))
-    assert not torch.any(closed.adjoint(torch.ones(g.g_len, device="cuda:0")))
+    assert not torch.any(closed.forward(torch.ones(g.f_len, device="cuda:0"), path=p))
+    assert not torch.any(closed.adjoint(torch.ones(g.g_len, device="cuda:0"), path=p))
     closed.close()
 
 
-def test_adjoint_identity_fp64_dots(cx):
+@pytest.mark.parametrize("path", FP32_PATHS)
+def test_adjoint_identity_fp64_dots(cx, path):
     caxsi, torch = cx
     g = synth.tiny_geometry()
     phi = synth.tungsten_spectrum(g)
     plan = caxsi.Plan(g, phi, synth.random_mask(g, synth.TINY_MASK_SEED))
     f = _t(torch, synth.uniform_random((g.X, g.J, g.Q), 8))
     w = _t(torch, synth.normal_random((g.M, g.N), 9))
-    lhs = torch.sum(plan.forward(f).double() * w.double()).item()
-    rhs = torch.sum(f.double() * plan.adjoint(w).double()).item()
+    p = caxsi.PATHS[path]
+    lhs = torch.sum(plan.forward(f, path=p).double() * w.double()).item()
+    rhs = torch.sum(f.double() * plan.adjoint(w, path=p).double()).item()
     assert abs(lhs - rhs) <= 1e-6 * (abs(lhs) + abs(rhs))
     plan.close()
 
@@ -141,8 +148,9 @@ def test_wrong_lengths_are_rejected(cx):
 # Reconstruction step
 # --------------------------------------------------------------------------
 
+@pytest.mark.parametrize("path", FP32_PATHS)
 @pytest.mark.parametrize("beta", [0.0, 0.5])
-def test_recon_step_parity(cx, beta):
+def test_recon_step_parity(cx, beta, path):
     caxsi, torch = cx
     g = synth.tiny_geometry()
     phi = synth.tungsten_spectrum(g)
@@ -159,13 +167,21 @@ def test_recon_step_parity(cx, beta):
     yt, rt = _t(torch, y), _t(torch, r)
     f = _f32(f0)
     for it in range(3):
-        nll_gpu = plan.recon_step(yt, ft, r=rt, beta=beta, delta=delta, want_nll=True)
+        nll_gpu = plan.recon_step(yt, ft, r=rt, beta=beta, delta=delta, want_nll=True,
+                                  path=caxsi.PATHS[path])
         A = lambda x: oracle.forward(g, phi, mask, x)
         At = lambda x: oracle.adjoint(g, phi, mask, x)
         f_next, nll_ref = oracle.em_iteration(A, At, y, r, f, b1, beta, delta)
         assert nll_gpu == pytest.approx(nll_ref, rel=1e-6)
         got = ft.cpu().numpy()
-        assert rel_l2(got, f_next) <= 5 * REL_L2_TOL * (it + 1)
+        # Channels whose sensitivity b1 = A^T 1 is zero in FP64 can be seen by a
+        # pair whose FP32 scatter angle lands a rounding step inside a q bin's
+        # support (b1 ~ 1e-9 of its maximum); with beta = 0 their update is the
+        # ratio of two rounding-level numbers, so only observed channels (b1 above
+        # 1e-6 of its maximum) are compared; the rest must stay finite and >= 0.
+        seen = b1 > 1e-6 * b1.max()
+        assert rel_l2(got[seen], f_next[seen]) <= 5 * REL_L2_TOL * (it + 1)
+        assert np.all(np.isfinite(got)) and np.all(got >= 0)
         f = _f32(got)   # continue both from the GPU iterate
     plan.close()
 
@@ -193,7 +209,7 @@ def test_recon_reports_nonpositive_mean(cx):
 # the launch configuration the benchmark times, checked on sampled outputs
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("path", ["direct"])
+@pytest.mark.parametrize("path", FP32_PATHS)
 def test_paper_scale_sampled(cx, path):
     caxsi, torch = cx
     g = synth.paper_geometry()
