@@ -61,7 +61,8 @@ typedef enum {
     CAXSI_ERR_OOM = 3,          /* device allocation failed */
     CAXSI_ERR_NONPOS_MEAN = 4,  /* a positive count met a non-positive mean A f + r */
     CAXSI_ERR_INTERNAL = 5,     /* a device-side consistency check failed */
-    CAXSI_ERR_UNSUPPORTED = 6   /* option not available for this plan */
+    CAXSI_ERR_UNSUPPORTED = 6,  /* option not available for this plan */
+    CAXSI_ERR_SCRATCH_LIMIT = 7 /* problem larger than a fixed scratch array allows */
 } caxsi_status;
 
 /* How A and A^T are evaluated.
@@ -190,6 +191,31 @@ typedef struct {
 caxsi_status caxsi_profile_enable(caxsi_plan *plan, int enable);
 caxsi_status caxsi_profile_read(caxsi_plan *plan, caxsi_kernel_stat *out, int capacity,
                                 int *count);
+
+/* Forward model g = A f (DIRECT path arithmetic) whose scratch lives in a
+ * fixed static device array of CAXSI_STATIC_SCRATCH_FLOATS floats (4 MiB per
+ * GPU that loads the library, held until the process exits) instead of the
+ * plan.  The paper has no counterpart: this entry point exists for callers
+ * that must not allocate device memory at the point of the call -- code that
+ * runs while another thread captures a CUDA graph in global capture mode
+ * (cudaMalloc fails there), real-time loops that forbid allocation after
+ * start-up, or hosts whose memory pool owns all device memory.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   plan      an existing plan (created beforehand, at set-up time).
+ *   f_dev     device, f_len = X*J*Q floats.   g_dev  device, g_len = M*N floats.
+ * The scratch holds one partial image of M*N floats per chunk of voxels, at
+ * least one chunk: M*N > CAXSI_STATIC_SCRATCH_FLOATS is rejected with
+ * CAXSI_ERR_SCRATCH_LIMIT before anything is launched.  The first call on a
+ * device looks up the array's device address with that device current, so
+ * make that first call before any stream capture.  Every call shares the one
+ * array (each call overwrites all of it that it reads, so nothing carries over
+ * between calls); calls that overlap on the GPU -- on several streams, several
+ * plans or several host threads -- race on it and must be serialised by the
+ * caller.  Asynchronous on stream.
+ * Errors: INVALID, SCRATCH_LIMIT, CUDA. */
+#define CAXSI_STATIC_SCRATCH_FLOATS (1 << 20)
+caxsi_status caxsi_forward_static_scratch(caxsi_plan *plan, const float *f_dev, int64_t f_len,
+                                          float *g_dev, int64_t g_len, void *stream);
 
 /* Human-readable name of a status code (static storage). */
 const char *caxsi_status_string(caxsi_status status);

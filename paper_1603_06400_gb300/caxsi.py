@@ -24,7 +24,7 @@ PATHS = {"direct": PATH_DIRECT, "table_fp32": PATH_TABLE_FP32,
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
           4: "positive count with non-positive mean", 5: "internal check failed",
-          6: "unsupported option"}
+          6: "unsupported option", 7: "problem exceeds the static scratch array"}
 
 
 class CaxsiError(RuntimeError):
@@ -86,6 +86,8 @@ def load():
             lib.caxsi_forward_host.argtypes = [P, F, I64, F, I64, ctypes.c_int]
             lib.caxsi_adjoint_host.argtypes = [P, F, I64, F, I64, ctypes.c_int]
             lib.caxsi_plan_info.argtypes = [P, ctypes.POINTER(CPlanInfo)]
+            lib.caxsi_forward_static_scratch.argtypes = [P, P, I64, P, I64, P]
+            lib.caxsi_forward_static_scratch.restype = ctypes.c_int
             lib.caxsi_profile_enable.argtypes = [P, ctypes.c_int]
             lib.caxsi_profile_read.argtypes = [P, ctypes.POINTER(CKernelStat), ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_int)]

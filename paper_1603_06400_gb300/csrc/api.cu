@@ -277,6 +277,17 @@ caxsi_status caxsi_plan_info(const caxsi_plan *p, caxsi_plan_info_t *info) {
     return CAXSI_OK;
 }
 
+caxsi_status caxsi_forward_static_scratch(caxsi_plan *p, const float *f_dev, int64_t f_len,
+                                          float *g_dev, int64_t g_len, void *stream) {
+    if (!p || !f_dev || !g_dev) return CAXSI_ERR_INVALID;
+    if (f_len != (int64_t)p->dg.R * p->dg.Q || g_len != (int64_t)p->dg.M * p->dg.N)
+        return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return CAXSI_ERR_CUDA;
+    p->launches = 0;
+    return direct_forward_static_scratch(p, f_dev, g_dev, (cudaStream_t)stream);
+}
+
 static void prof_clear(caxsi_plan *p) {
     for (auto &r : p->prof.recs) {
         cudaEventSynchronize(r.b);
@@ -328,6 +339,7 @@ const char *caxsi_status_string(caxsi_status s) {
         case CAXSI_ERR_NONPOS_MEAN: return "positive count with non-positive mean";
         case CAXSI_ERR_INTERNAL: return "internal consistency check failed";
         case CAXSI_ERR_UNSUPPORTED: return "unsupported option";
+        case CAXSI_ERR_SCRATCH_LIMIT: return "problem exceeds the static scratch array";
     }
     return "unknown status";
 }

@@ -14,6 +14,8 @@
 // lane-private row of Q+3 q bins in shared memory laid out [bin][lane] (bank
 // = lane, so the scatter is conflict-free), and the 32 private rows are
 // summed at the end with a rotated read (also conflict-free).  No atomics.
+#include <mutex>
+
 #include "internal.cuh"
 #include "pairgeo.cuh"
 
@@ -254,5 +256,65 @@ caxsi_status direct_adjoint(caxsi_plan *p, const float *w, float *f_out, cudaStr
         }
         CAXSI_LAUNCH_CHECK(p);
     }
+    return CAXSI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Forward model with scratch in a static device array (allocates nothing).
+//
+// The chunked forward above keeps its per-chunk partial images in plan-owned
+// scratch.  This variant keeps them in a fixed file-scope device array instead,
+// so a call performs no device allocation of any kind: it is for callers that
+// must not allocate device memory at the point of the call -- for example code
+// running while another thread captures a CUDA graph in global capture mode
+// (where cudaMalloc fails), real-time loops that forbid allocation after
+// start-up, or hosts whose memory pool owns all device memory.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Partial images of the forward chunks; every GPU that loads the library holds
+// this array until the process exits.
+static __device__ __align__(256) float g_static_fwd_scratch[CAXSI_STATIC_SCRATCH_FLOATS];
+
+// Device address of the array, looked up once per device (with that device
+// current) on the first call that uses the device.
+std::mutex g_static_scratch_mu;
+float *g_static_scratch_ptr[CAXSI_MAX_DEVICES] = {};
+
+cudaError_t static_scratch_address(int dev, float **out) {
+    if (dev < 0 || dev >= CAXSI_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_static_scratch_mu);
+    if (!g_static_scratch_ptr[dev]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_fwd_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_scratch_ptr[dev] = static_cast<float *>(ptr);
+    }
+    *out = g_static_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+caxsi_status direct_forward_static_scratch(caxsi_plan *p, const float *f, float *g_out,
+                                           cudaStream_t s) {
+    const DevGeo &g = p->dg;
+    const int64_t npix = (int64_t)g.M * g.N;
+    const int64_t max_chunks = (int64_t)CAXSI_STATIC_SCRATCH_FLOATS / npix;
+    if (max_chunks < 1) return CAXSI_ERR_SCRATCH_LIMIT;
+    int chunks = p->fwd_chunks < max_chunks ? p->fwd_chunks : (int)max_chunks;
+    const int vc = (int)ceil_div64(g.R, chunks);
+    chunks = (int)ceil_div64(g.R, vc);
+    float *part = nullptr;
+    CAXSI_CUDA_TRY(static_scratch_address(p->device, &part));
+    const int tiles_n = (int)ceil_div64(g.N, 32);
+    const int tiles = (int)ceil_div64(g.M, FWD_WARPS) * tiles_n;
+    const size_t sm = fwd_smem(g);
+    CAXSI_CUDA_TRY(cudaFuncSetAttribute(k_fwd_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    // every chunk overwrites its whole partial image, so nothing needs clearing
+    k_fwd_direct<<<dim3(tiles, chunks), FWD_THREADS, sm, s>>>(tables_of(p), f, part, vc, tiles_n);
+    CAXSI_LAUNCH_CHECK(p);
+    k_sum_parts<<<(unsigned)ceil_div64(npix, 256), 256, 0, s>>>(part, chunks, npix, g_out, npix);
+    CAXSI_LAUNCH_CHECK(p);
     return CAXSI_OK;
 }

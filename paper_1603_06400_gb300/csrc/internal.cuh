@@ -9,6 +9,7 @@
 #include "caxsi.h"
 
 #define CAXSI_MAX_K 1024
+#define CAXSI_MAX_DEVICES 64
 
 // Geometry scalars needed by the kernels, derived once per plan.
 struct DevGeo {
@@ -89,6 +90,7 @@ caxsi_status plan_build_tables(caxsi_plan *p, const double *phi_host, const uint
 caxsi_status direct_forward(caxsi_plan *p, const float *f, float *g, cudaStream_t s);
 caxsi_status direct_adjoint(caxsi_plan *p, const float *w, float *f, cudaStream_t s);
 void direct_configure(caxsi_plan *p);
+caxsi_status direct_forward_static_scratch(caxsi_plan *p, const float *f, float *g, cudaStream_t s);
 
 // ---- table.cu ----------------------------------------------------------------
 caxsi_status table_forward(caxsi_plan *p, const float *f, float *g, int path, cudaStream_t s);
