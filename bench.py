@@ -311,6 +311,7 @@ def run_ours(args):
     for t in range(args.warmup):
         step(t)
     torch.cuda.synchronize()
+    info = plan.info()   # after warm-up: the table paths build their tables on first use
 
     sampler = ClockSampler(gpu_query_id(torch, local))
     time.sleep(0.6)  # let the sampler start

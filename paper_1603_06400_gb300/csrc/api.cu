@@ -95,8 +95,8 @@ caxsi_status alloc_scratch(caxsi_plan *p) {
     if (p->nll_blocks < 1) p->nll_blocks = 1;
     CAXSI_CUDA_TRY(cudaMalloc(&p->nll_part, p->nll_blocks * sizeof(double)));
     CAXSI_CUDA_TRY(cudaMalloc(&p->nll_dev, sizeof(double)));
-    CAXSI_CUDA_TRY(cudaMalloc(&p->err_flag, sizeof(int)));
-    CAXSI_CUDA_TRY(cudaMemset(p->err_flag, 0, sizeof(int)));
+    CAXSI_CUDA_TRY(cudaMalloc(&p->err_flag, 2 * sizeof(int)));
+    CAXSI_CUDA_TRY(cudaMemset(p->err_flag, 0, 2 * sizeof(int)));
     k_fill<<<(unsigned)ceil_div64(npix, 256), 256>>>(p->ones, 1.f, npix);
     CAXSI_CUDA_TRY(cudaGetLastError());
     CAXSI_CUDA_TRY(cudaDeviceSynchronize());

@@ -71,7 +71,7 @@ struct caxsi_plan {
     double *nll_part;   // [nll_blocks]
     double *nll_dev;    // [1]
     int nll_blocks;
-    int *err_flag;      // [1] device error word
+    int *err_flag;      // [2] device error words: [0] non-positive mean, [1] copy wait timed out
     float *stage_in, *stage_out;  // host-API staging, lazily
 
     TablePath *table;

@@ -126,14 +126,14 @@ caxsi_status recon_update(caxsi_plan *p, const float *f_old, float beta, float d
 }
 
 caxsi_status recon_nll_fetch(caxsi_plan *p, double *out, cudaStream_t s) {
-    int err = 0;
+    int err[2] = {0, 0};
     CAXSI_CUDA_TRY(cudaMemcpyAsync(out, p->nll_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CAXSI_CUDA_TRY(cudaMemcpyAsync(&err, p->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CAXSI_CUDA_TRY(cudaMemcpyAsync(err, p->err_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CAXSI_CUDA_TRY(cudaStreamSynchronize(s));
-    if (err) {
-        CAXSI_CUDA_TRY(cudaMemsetAsync(p->err_flag, 0, sizeof(int), s));
+    if (err[0] || err[1]) {
+        CAXSI_CUDA_TRY(cudaMemsetAsync(p->err_flag, 0, 2 * sizeof(int), s));
         CAXSI_CUDA_TRY(cudaStreamSynchronize(s));
-        return CAXSI_ERR_NONPOS_MEAN;
+        return err[1] ? CAXSI_ERR_INTERNAL : CAXSI_ERR_NONPOS_MEAN;
     }
     return CAXSI_OK;
 }

@@ -32,6 +32,7 @@
 
 #include "internal.cuh"
 #include "pairgeo.cuh"
+#include "table.cuh"
 
 cudaError_t sgemm_kmajor(int M, int N, int K, const float *A, int64_t lda, const float *Bm,
                          int64_t ldb, float *C, int64_t ldc, const int2 *kband, cudaStream_t s);
@@ -41,45 +42,9 @@ cudaError_t sgemm_nmajor_splitk(int M, int N, int K, const float *A, int64_t lda
 cudaError_t launch_sum_parts(const float *part, int nparts, int64_t stride, float *out,
                              int64_t n, cudaStream_t s);
 
-struct TablePath {
-    int B = 0;          // knots
-    int Bp = 0;         // padded row length of Wtab / Vtab (>= B + 1, multiple of 4)
-    int NB = 0;         // buckets
-    float u0 = 0.f, inv_h = 0.f;
-    float2 *knots = nullptr;    // [B] {u_t, 1/(u_{t+1} - u_t)}; last {u_B, 0}
-    uint16_t *bstart = nullptr; // [NB] last knot index at or below the bucket start
-    float *S = nullptr;         // [B][Q] S~ (FP32)
-    int2 *kband = nullptr;      // [ceil(B/128)] q range where S~ can be nonzero
-    float *tab = nullptr;       // [R][Bp] Wtab (forward) / Vtab (adjoint)
-    float *fwd_part = nullptr;  // [fwd_chunks][M*N]
-    int fwd_chunks = 0, fwd_vc = 0, ppt = 1, threads = 1024, pix_chunks = 1;
-    float *adj_part = nullptr;  // [adj_splits][R*Q]
-    int adj_splits = 1;
-    int adj_chunks = 0, adj_vc = 0;
-    size_t smem_fwd = 0, smem_adj = 0;
-};
-
 namespace {
 
 constexpr int TAB_THREADS = 1024;
-
-struct PairArgs {
-    DevGeo g;
-    const float4 *vox;
-    const float *zrow;
-    const float *god;
-    const uint32_t *tbits;
-};
-
-PairArgs pair_args(const caxsi_plan *p) {
-    PairArgs a;
-    a.g = p->dg;
-    a.vox = p->vox;
-    a.zrow = p->zrow;
-    a.god = p->god;
-    a.tbits = p->tbits;
-    return a;
-}
 
 // Range of u over all open pairs (plan set-up).
 __global__ void k_pair_urange(PairArgs A, unsigned int *umin, unsigned int *umax) {
@@ -123,36 +88,6 @@ __global__ void k_build_S(int B, int Q, int K, const float2 *knots, const double
         if (h > 0.0) s += ck[k] * h;
     }
     S[idx] = (float)s;
-}
-
-// Interval t with u_t <= u < u_{t+1} (u inside [u_1, u_B]).
-__device__ __forceinline__ int find_interval(float u, const float2 *kn, const uint16_t *bstart,
-                                             int B, int NB, float u0, float inv_h) {
-    int bk = (int)((u - u0) * inv_h);
-    bk = min(max(bk, 0), NB - 1);
-    int t = bstart[bk];
-    while (t + 1 < B && kn[t + 1].x <= u) ++t;
-    while (t > 0 && kn[t].x > u) --t;
-    return t;
-}
-
-struct TabArgs {
-    int B, NB, Bp;
-    float u0, inv_h;
-    const float2 *knots;
-    const uint16_t *bstart;
-};
-
-TabArgs tab_args(const TablePath *T) {
-    TabArgs a;
-    a.B = T->B;
-    a.NB = T->NB;
-    a.Bp = T->Bp;
-    a.u0 = T->u0;
-    a.inv_h = T->inv_h;
-    a.knots = T->knots;
-    a.bstart = T->bstart;
-    return a;
 }
 
 // Forward per-pair stage: block = 1024 threads over a chunk of PPT*1024
@@ -327,6 +262,7 @@ cudaError_t dispatch_adj(const caxsi_plan *p, const TablePath *T, const float *w
 
 void free_table(TablePath *T) {
     if (!T) return;
+    records_free(T);
     cudaFree(T->knots);
     cudaFree(T->bstart);
     cudaFree(T->S);
@@ -486,6 +422,16 @@ caxsi_status build_table(caxsi_plan *p) {
         }
         p->table_bytes += (int64_t)B * 8 + NB * 2 + (int64_t)B * G.Q * 4 + R * T->Bp * 4 +
                           (int64_t)T->fwd_chunks * npix * 4 + (int64_t)T->adj_splits * R * G.Q * 4;
+        // 5. per-pair records (precomputed intervals and weights), when they fit
+        if ((st = records_build(p, T)) != CAXSI_OK) break;
+        if (T->use_records && T->rec_chunks > T->fwd_chunks) {
+            cudaFree(T->fwd_part);
+            T->fwd_part = nullptr;
+            if (cudaMalloc(&T->fwd_part, (size_t)T->rec_chunks * npix * sizeof(float)) != cudaSuccess) {
+                st = CAXSI_ERR_OOM;
+                break;
+            }
+        }
     } while (0);
     cudaFree(ur);
     cudaFree(ak_d);
@@ -515,7 +461,10 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
         CAXSI_CUDA_TRY(sgemm_kmajor(d.R, T->B, d.Q, f, d.Q, T->S, d.Q, T->tab, T->Bp, T->kband, s));
     }
     CAXSI_LAUNCH_CHECK(p);
-    {
+    if (T->use_records) {
+        CAXSI_PROF(p, "rec_pairs_fwd", s);
+        CAXSI_CUDA_TRY(records_forward(p, T, T->fwd_part, s));
+    } else {
         CAXSI_PROF(p, "tab_pairs_fwd", s);
         CAXSI_CUDA_TRY(dispatch_fwd(p, T, T->fwd_part, s));
     }
@@ -523,7 +472,8 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
     const int64_t npix = (int64_t)d.M * d.N;
     {
         CAXSI_PROF(p, "sum_parts", s);
-        CAXSI_CUDA_TRY(launch_sum_parts(T->fwd_part, T->fwd_chunks, npix, g_out, npix, s));
+        CAXSI_CUDA_TRY(launch_sum_parts(T->fwd_part, T->use_records ? T->rec_chunks : T->fwd_chunks,
+                                        npix, g_out, npix, s));
     }
     CAXSI_LAUNCH_CHECK(p);
     return CAXSI_OK;
@@ -537,7 +487,10 @@ caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path
     }
     TablePath *T = p->table;
     const DevGeo &d = p->dg;
-    {
+    if (T->use_records) {
+        CAXSI_PROF(p, "rec_pairs_adj", s);
+        CAXSI_CUDA_TRY(records_adjoint(p, T, w, s));
+    } else {
         CAXSI_PROF(p, "tab_pairs_adj", s);
         CAXSI_CUDA_TRY(dispatch_adj(p, T, w, s));
     }

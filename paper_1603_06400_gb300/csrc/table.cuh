@@ -1,0 +1,87 @@
+// Shared state and device helpers of the table paths (see table.cu).
+#pragma once
+
+#include "internal.cuh"
+
+struct TablePath {
+    int B = 0;          // knots
+    int Bp = 0;         // padded row length of Wtab / Vtab (>= B + 1, multiple of 4)
+    int NB = 0;         // buckets
+    float u0 = 0.f, inv_h = 0.f;
+    float2 *knots = nullptr;    // [B] {u_t, 1/(u_{t+1} - u_t)}; last {u_B, 0}
+    uint16_t *bstart = nullptr; // [NB] last knot index at or below the bucket start
+    float *S = nullptr;         // [B][Q] S~ (FP32)
+    int2 *kband = nullptr;      // [ceil(B/128)] q range where S~ can be nonzero
+    float *tab = nullptr;       // [R][Bp] Wtab (forward) / Vtab (adjoint)
+    float *fwd_part = nullptr;  // [fwd_chunks][M*N]
+    int fwd_chunks = 0, fwd_vc = 0, ppt = 1, threads = 1024, pix_chunks = 1;
+    float *adj_part = nullptr;  // [adj_splits][R*Q]
+    int adj_splits = 1;
+    int adj_chunks = 0, adj_vc = 0;
+    size_t smem_fwd = 0, smem_adj = 0;
+
+    // Pair records (precomputed per-pair interval and weights), voxel-major,
+    // sorted by (knot interval t, pixel) within each voxel.
+    bool use_records = false;
+    int64_t n_rec = 0;
+    int64_t *rec_off = nullptr;   // [R + 1] record range of each voxel
+    uint32_t *rec_key = nullptr;  // [n_rec] pixel | (t << 16)
+    float *rec_w0 = nullptr;      // [n_rec] c (1 - alpha)
+    float *rec_w1 = nullptr;      // [n_rec] c alpha
+    int rec_chunks = 0, rec_vc = 0;
+};
+
+
+struct PairArgs {
+    DevGeo g;
+    const float4 *vox;
+    const float *zrow;
+    const float *god;
+    const uint32_t *tbits;
+};
+
+inline PairArgs pair_args(const caxsi_plan *p) {
+    PairArgs a;
+    a.g = p->dg;
+    a.vox = p->vox;
+    a.zrow = p->zrow;
+    a.god = p->god;
+    a.tbits = p->tbits;
+    return a;
+}
+
+// Interval t with u_t <= u < u_{t+1} (u inside [u_1, u_B]).
+static __device__ __forceinline__ int find_interval(float u, const float2 *kn, const uint16_t *bstart,
+                                             int B, int NB, float u0, float inv_h) {
+    int bk = (int)((u - u0) * inv_h);
+    bk = min(max(bk, 0), NB - 1);
+    int t = bstart[bk];
+    while (t + 1 < B && kn[t + 1].x <= u) ++t;
+    while (t > 0 && kn[t].x > u) --t;
+    return t;
+}
+
+struct TabArgs {
+    int B, NB, Bp;
+    float u0, inv_h;
+    const float2 *knots;
+    const uint16_t *bstart;
+};
+
+inline TabArgs tab_args(const TablePath *T) {
+    TabArgs a;
+    a.B = T->B;
+    a.NB = T->NB;
+    a.Bp = T->Bp;
+    a.u0 = T->u0;
+    a.inv_h = T->inv_h;
+    a.knots = T->knots;
+    a.bstart = T->bstart;
+    return a;
+}
+
+// records.cu
+caxsi_status records_build(caxsi_plan *p, TablePath *T);
+cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s);
+cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, const float *w, cudaStream_t s);
+void records_free(TablePath *T);

@@ -111,20 +111,23 @@ def test_adjoint_identity_fp64_dots(cx, path):
     plan.close()
 
 
-def test_deterministic_and_host_forms_agree(cx):
+@pytest.mark.parametrize("path", FP32_PATHS)
+@pytest.mark.parametrize("name", ["ragged", "tiny"])
+def test_deterministic_and_host_forms_agree(cx, path, name):
     caxsi, torch = cx
-    g = GEOMS["ragged"]()
+    g = GEOMS[name]()
     phi = synth.tungsten_spectrum(g)
     plan = caxsi.Plan(g, phi, synth.random_mask(g, 2))
+    p = caxsi.PATHS[path]
     f = synth.uniform_random((g.X, g.J, g.Q), 10).astype(np.float32)
     w = synth.uniform_random((g.M, g.N), 11).astype(np.float32)
-    a1 = plan.forward(_t(torch, f)).cpu().numpy()
-    a2 = plan.forward(_t(torch, f)).cpu().numpy()
+    a1 = plan.forward(_t(torch, f), path=p).cpu().numpy()
+    a2 = plan.forward(_t(torch, f), path=p).cpu().numpy()
     np.testing.assert_array_equal(a1, a2)
-    np.testing.assert_array_equal(plan.forward_host(f), a1)
-    b1 = plan.adjoint(_t(torch, w)).cpu().numpy()
-    np.testing.assert_array_equal(plan.adjoint(_t(torch, w)).cpu().numpy(), b1)
-    np.testing.assert_array_equal(plan.adjoint_host(w), b1)
+    np.testing.assert_array_equal(plan.forward_host(f, path=p), a1)
+    b1 = plan.adjoint(_t(torch, w), path=p).cpu().numpy()
+    np.testing.assert_array_equal(plan.adjoint(_t(torch, w), path=p).cpu().numpy(), b1)
+    np.testing.assert_array_equal(plan.adjoint_host(w, path=p), b1)
     plan.close()
 
 
