@@ -21,6 +21,9 @@
 //
 // Record layout (structure of arrays, 12 bytes per record):
 //   key = pixel | (t << 16) (uint32), w0 (float), w1 (float).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <vector>
 
 #include "internal.cuh"
@@ -281,8 +284,13 @@ struct Side {
 // by the warp and stored directly, the first and last runs of each segment go
 // to side slots that one thread adds afterwards in warp order.  Then
 // V[t] = LO[t] + HI[t - 1] is written to Vtab.
+__device__ __forceinline__ void store_v(float *p, float x) { *p = x; }
+__device__ __forceinline__ void store_v(__nv_bfloat16 *p, float x) { *p = __float2bfloat16_rn(x); }
+__device__ __forceinline__ void store_v(__half *p, float x) { *p = __float2half_rn(x); }
+
+template <typename OutT>
 __global__ void __launch_bounds__(RT, 1)
-k_adj_rec(RecArgs A, const float *__restrict__ w, float *__restrict__ Vtab, int vc) {
+k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, int vc) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int npix_al = (A.npix + 3) & ~3;
     float *w_s = reinterpret_cast<float *>(smem_raw);
@@ -437,8 +445,8 @@ k_adj_rec(RecArgs A, const float *__restrict__ w, float *__restrict__ Vtab, int 
             if (mt != SENT && lane == 0) { LO[mt] += mlo; HI[mt] += mhi; }
         }
         __syncthreads();
-        float *vrow = Vtab + (int64_t)v * A.Bp;
-        for (int t = tid; t < A.B; t += RT) vrow[t] = LO[t] + (t > 0 ? HI[t - 1] : 0.f);
+        OutT *vrow = Vtab + (int64_t)v * A.Bp;
+        for (int t = tid; t < A.B; t += RT) store_v(vrow + t, LO[t] + (t > 0 ? HI[t - 1] : 0.f));
         __syncthreads();
     }
 }
@@ -532,11 +540,21 @@ cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, float *part
     return cudaGetLastError();
 }
 
-cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, const float *w, cudaStream_t s) {
+template <typename OutT>
+cudaError_t launch_adj_rec(const caxsi_plan *p, const TablePath *T, const float *w, OutT *out,
+                           cudaStream_t s) {
     const int npix = p->dg.M * p->dg.N;
     const size_t smem = adj_rec_smem(npix, T->Bp);
-    cudaError_t e = cudaFuncSetAttribute(k_adj_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_adj_rec<OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_adj_rec<<<T->rec_chunks, RT, smem, s>>>(rec_args(p, T), w, T->tab, T->rec_vc);
+    k_adj_rec<OutT><<<T->rec_chunks, RT, smem, s>>>(rec_args(p, T), w, out, T->rec_vc);
     return cudaGetLastError();
+}
+
+// out_kind: 0 = FP32 rows in T->tab, 1 = bf16 rows in T->v16, 2 = fp16 rows in T->v16
+cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, const float *w, int out_kind,
+                            cudaStream_t s) {
+    if (out_kind == 1) return launch_adj_rec(p, T, w, reinterpret_cast<__nv_bfloat16 *>(T->v16), s);
+    if (out_kind == 2) return launch_adj_rec(p, T, w, reinterpret_cast<__half *>(T->v16), s);
+    return launch_adj_rec(p, T, w, T->tab, s);
 }

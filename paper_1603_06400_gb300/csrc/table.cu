@@ -24,6 +24,8 @@
 // knots.  Only knots inside the range of u over the open pairs, plus one
 // bracketing knot on each side, are kept.  The interval search uses a uniform
 // bucket grid over the knot range followed by a short scan.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 #include <string.h>
 
@@ -263,6 +265,12 @@ cudaError_t dispatch_adj(const caxsi_plan *p, const TablePath *T, const float *w
 void free_table(TablePath *T) {
     if (!T) return;
     records_free(T);
+    if (T->blas) cublasDestroy(T->blas);
+    cudaFree(T->blas_ws);
+    cudaFree(T->S16[0]);
+    cudaFree(T->S16[1]);
+    cudaFree(T->f16);
+    cudaFree(T->v16);
     cudaFree(T->knots);
     cudaFree(T->bstart);
     cudaFree(T->S);
@@ -448,19 +456,89 @@ caxsi_status build_table(caxsi_plan *p) {
 
 int64_t table_breakpoints(const caxsi_plan *p) { return p->table ? p->table->B : 0; }
 
-caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path, cudaStream_t s) {
-    if (path != CAXSI_PATH_TABLE_FP32) return CAXSI_ERR_UNSUPPORTED;
+namespace {
+
+__global__ void k_to_bf16(const float *__restrict__ x, __nv_bfloat16 *__restrict__ y, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = __float2bfloat16_rn(x[i]);
+}
+__global__ void k_to_f16(const float *__restrict__ x, __half *__restrict__ y, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = __float2half_rn(x[i]);
+}
+
+// cuBLAS handle, workspace and 16-bit operand copies (first table call).
+caxsi_status blas_setup(caxsi_plan *p, TablePath *T) {
+    if (T->blas) return CAXSI_OK;
+    const DevGeo &d = p->dg;
+    if (cublasCreate(&T->blas) != CUBLAS_STATUS_SUCCESS) {
+        T->blas = nullptr;
+        return CAXSI_ERR_CUDA;
+    }
+    T->blas_ws_bytes = (size_t)64 << 20;
+    const int64_t nS = (int64_t)T->B * d.Q;
+    if (cudaMalloc(&T->blas_ws, T->blas_ws_bytes) != cudaSuccess ||
+        cudaMalloc(&T->S16[0], nS * 2) != cudaSuccess || cudaMalloc(&T->S16[1], nS * 2) != cudaSuccess ||
+        cudaMalloc(&T->f16, (size_t)d.R * d.Q * 2) != cudaSuccess ||
+        cudaMalloc(&T->v16, (size_t)d.R * T->Bp * 2) != cudaSuccess)
+        return CAXSI_ERR_OOM;
+    if (cublasSetWorkspace(T->blas, T->blas_ws, T->blas_ws_bytes) != CUBLAS_STATUS_SUCCESS)
+        return CAXSI_ERR_CUDA;
+    k_to_bf16<<<(unsigned)ceil_div64(nS, 256), 256>>>(T->S, (__nv_bfloat16 *)T->S16[0], nS);
+    k_to_f16<<<(unsigned)ceil_div64(nS, 256), 256>>>(T->S, (__half *)T->S16[1], nS);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return CAXSI_ERR_CUDA;
+    p->table_bytes += (int64_t)T->blas_ws_bytes + 2 * nS * 2 + (int64_t)d.R * d.Q * 2 + (int64_t)d.R * T->Bp * 2;
+    return CAXSI_OK;
+}
+
+caxsi_status ensure_table(caxsi_plan *p, int path) {
+    if (path < CAXSI_PATH_TABLE_FP32 || path > CAXSI_PATH_TABLE_FP16) return CAXSI_ERR_UNSUPPORTED;
     if (!p->table) {
         caxsi_status st = build_table(p);
         if (st != CAXSI_OK) return st;
     }
+    if (!p->table->blas) {
+        caxsi_status st = blas_setup(p, p->table);
+        if (st != CAXSI_OK) return st;
+    }
+    // the 16-bit paths take their adjoint rows from the record kernel
+    if (path != CAXSI_PATH_TABLE_FP32 && !p->table->use_records) return CAXSI_ERR_UNSUPPORTED;
+    return CAXSI_OK;
+}
+
+cudaDataType_t dtype16(int path) { return path == CAXSI_PATH_TABLE_BF16 ? CUDA_R_16BF : CUDA_R_16F; }
+
+}  // namespace
+
+caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path, cudaStream_t s) {
+    caxsi_status st = ensure_table(p, path);
+    if (st != CAXSI_OK) return st;
     TablePath *T = p->table;
     const DevGeo &d = p->dg;
-    {
-        CAXSI_PROF(p, "tab_gemm_fwd", s);
-        CAXSI_CUDA_TRY(sgemm_kmajor(d.R, T->B, d.Q, f, d.Q, T->S, d.Q, T->tab, T->Bp, T->kband, s));
+    const float one = 1.f, zero = 0.f;
+    if (cublasSetStream(T->blas, s) != CUBLAS_STATUS_SUCCESS) return CAXSI_ERR_CUDA;
+    if (path == CAXSI_PATH_TABLE_FP32) {
+        // Wtab[r][t] = sum_l f[r][l] S~[t][l]  (column-major: W^T = S~ f^T), FP32-accurate
+        CAXSI_PROF(p, "gemm_fwd_fp32emu", s);
+        if (cublasGemmEx(T->blas, CUBLAS_OP_T, CUBLAS_OP_N, T->B, d.R, d.Q, &one, T->S, CUDA_R_32F, d.Q,
+                         f, CUDA_R_32F, d.Q, &zero, T->tab, CUDA_R_32F, T->Bp,
+                         CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
+            return CAXSI_ERR_CUDA;
+    } else {
+        const int k = path == CAXSI_PATH_TABLE_BF16 ? 0 : 1;
+        const int64_t nf = (int64_t)d.R * d.Q;
+        {
+            CAXSI_PROF(p, "to_16bit", s);
+            if (k == 0) k_to_bf16<<<(unsigned)ceil_div64(nf, 256), 256, 0, s>>>(f, (__nv_bfloat16 *)T->f16, nf);
+            else k_to_f16<<<(unsigned)ceil_div64(nf, 256), 256, 0, s>>>(f, (__half *)T->f16, nf);
+        }
+        CAXSI_LAUNCH_CHECK(p);
+        CAXSI_PROF(p, k == 0 ? "gemm_fwd_bf16" : "gemm_fwd_fp16", s);
+        if (cublasGemmEx(T->blas, CUBLAS_OP_T, CUBLAS_OP_N, T->B, d.R, d.Q, &one, T->S16[k], dtype16(path),
+                         d.Q, T->f16, dtype16(path), d.Q, &zero, T->tab, CUDA_R_32F, T->Bp,
+                         CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
+            return CAXSI_ERR_CUDA;
     }
-    CAXSI_LAUNCH_CHECK(p);
     if (T->use_records) {
         CAXSI_PROF(p, "rec_pairs_fwd", s);
         CAXSI_CUDA_TRY(records_forward(p, T, T->fwd_part, s));
@@ -480,33 +558,36 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
 }
 
 caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path, cudaStream_t s) {
-    if (path != CAXSI_PATH_TABLE_FP32) return CAXSI_ERR_UNSUPPORTED;
-    if (!p->table) {
-        caxsi_status st = build_table(p);
-        if (st != CAXSI_OK) return st;
-    }
+    caxsi_status st = ensure_table(p, path);
+    if (st != CAXSI_OK) return st;
     TablePath *T = p->table;
     const DevGeo &d = p->dg;
+    const int out_kind = path == CAXSI_PATH_TABLE_FP32 ? 0 : (path == CAXSI_PATH_TABLE_BF16 ? 1 : 2);
     if (T->use_records) {
         CAXSI_PROF(p, "rec_pairs_adj", s);
-        CAXSI_CUDA_TRY(records_adjoint(p, T, w, s));
+        CAXSI_CUDA_TRY(records_adjoint(p, T, w, out_kind, s));
     } else {
         CAXSI_PROF(p, "tab_pairs_adj", s);
         CAXSI_CUDA_TRY(dispatch_adj(p, T, w, s));
     }
     CAXSI_LAUNCH_CHECK(p);
-    const int64_t nf = (int64_t)d.R * d.Q;
-    {
-        CAXSI_PROF(p, "tab_gemm_adj", s);
-        CAXSI_CUDA_TRY(sgemm_nmajor_splitk(d.R, d.Q, T->B, T->tab, T->Bp, T->S, d.Q, T->adj_part, d.Q,
-                                           nf, T->adj_splits, s));
+    const float one = 1.f, zero = 0.f;
+    if (cublasSetStream(T->blas, s) != CUBLAS_STATUS_SUCCESS) return CAXSI_ERR_CUDA;
+    // f[r][l] = sum_t V[r][t] S~[t][l]  (column-major: f^T = S~^T V^T)
+    if (out_kind == 0) {
+        CAXSI_PROF(p, "gemm_adj_fp32emu", s);
+        if (cublasGemmEx(T->blas, CUBLAS_OP_N, CUBLAS_OP_N, d.Q, d.R, T->B, &one, T->S, CUDA_R_32F, d.Q,
+                         T->tab, CUDA_R_32F, T->Bp, &zero, f_out, CUDA_R_32F, d.Q,
+                         CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
+            return CAXSI_ERR_CUDA;
+    } else {
+        const int k = out_kind - 1;
+        CAXSI_PROF(p, k == 0 ? "gemm_adj_bf16" : "gemm_adj_fp16", s);
+        if (cublasGemmEx(T->blas, CUBLAS_OP_N, CUBLAS_OP_N, d.Q, d.R, T->B, &one, T->S16[k], dtype16(path),
+                         d.Q, T->v16, dtype16(path), T->Bp, &zero, f_out, CUDA_R_32F, d.Q,
+                         CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
+            return CAXSI_ERR_CUDA;
     }
-    CAXSI_LAUNCH_CHECK(p);
-    {
-        CAXSI_PROF(p, "sum_parts", s);
-        CAXSI_CUDA_TRY(launch_sum_parts(T->adj_part, T->adj_splits, nf, f_out, nf, s));
-    }
-    CAXSI_LAUNCH_CHECK(p);
     return CAXSI_OK;
 }
 

@@ -1,6 +1,8 @@
 // Shared state and device helpers of the table paths (see table.cu).
 #pragma once
 
+#include <cublas_v2.h>
+
 #include "internal.cuh"
 
 struct TablePath {
@@ -29,6 +31,15 @@ struct TablePath {
     float *rec_w0 = nullptr;      // [n_rec] c (1 - alpha)
     float *rec_w1 = nullptr;      // [n_rec] c alpha
     int rec_chunks = 0, rec_vc = 0;
+
+    // Contractions over q on tensor cores (cuBLAS): FP32-accurate via the
+    // bf16x9 emulation, or single-pass bf16 / fp16 operands with FP32 accumulation.
+    cublasHandle_t blas = nullptr;
+    void *blas_ws = nullptr;
+    size_t blas_ws_bytes = 0;
+    void *S16[2] = {nullptr, nullptr};  // S~ as bf16 / fp16, [B][Q]
+    void *f16 = nullptr;                // [R][Q] 16-bit copy of the forward input
+    void *v16 = nullptr;                // [R][Bp] 16-bit adjoint rows
 };
 
 
@@ -83,5 +94,6 @@ inline TabArgs tab_args(const TablePath *T) {
 // records.cu
 caxsi_status records_build(caxsi_plan *p, TablePath *T);
 cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s);
-cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, const float *w, cudaStream_t s);
+cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, const float *w, int out_kind,
+                            cudaStream_t s);
 void records_free(TablePath *T);

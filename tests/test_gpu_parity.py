@@ -232,3 +232,37 @@ def test_paper_scale_sampled(cx, path):
     refv = oracle.adjoint_voxels(g, phi, mask, _f32(w), vox)
     assert rel_l2(fa[vox], refv) <= REL_L2_TOL
     plan.close()
+
+
+# --------------------------------------------------------------------------
+# Reduced precision (bf16 / fp16 operands, FP32 accumulation): the error
+# against the FP64 oracle is measured and reported; the bounds below only
+# catch a broken path (the measured values are in the test output and the design doc)
+# --------------------------------------------------------------------------
+
+RED_BOUND = {"table_bf16": 2e-2, "table_fp16": 5e-3}
+
+
+@pytest.mark.parametrize("path", sorted(RED_BOUND))
+def test_reduced_precision_error(cx, path):
+    caxsi, torch = cx
+    g = synth.tiny_geometry()
+    phi = synth.tungsten_spectrum(g)
+    mask = synth.random_mask(g, synth.TINY_MASK_SEED)
+    f = synth.phantom(g, 2, n_ellipses=3)
+    w = synth.uniform_random((g.M, g.N), 3) + 0.5
+    plan = caxsi.Plan(g, phi, mask)
+    p = caxsi.PATHS[path]
+    gg = plan.forward(_t(torch, f), path=p).cpu().numpy()
+    fa = plan.adjoint(_t(torch, w), path=p).cpu().numpy()
+    eg = rel_l2(gg, oracle.forward(g, phi, mask, _f32(f)))
+    ef = rel_l2(fa, oracle.adjoint(g, phi, mask, _f32(w)))
+    print(f"{path}: forward rel-L2 {eg:.3e}, adjoint rel-L2 {ef:.3e}")
+    assert eg <= RED_BOUND[path] and ef <= RED_BOUND[path]
+    # the adjoint of the reduced path is still the transpose of its forward up to its own rounding
+    x = _t(torch, synth.uniform_random((g.X, g.J, g.Q), 8))
+    y = _t(torch, synth.uniform_random((g.M, g.N), 9))
+    lhs = torch.sum(plan.forward(x, path=p).double() * y.double()).item()
+    rhs = torch.sum(x.double() * plan.adjoint(y, path=p).double()).item()
+    assert abs(lhs - rhs) <= 4 * RED_BOUND[path] * abs(lhs)
+    plan.close()
