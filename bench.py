@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--path", default="direct",
+    ap.add_argument("--path", default="table_fp32",
                     choices=["direct", "table_fp32", "table_bf16", "table_fp16"])
     ap.add_argument("--workload", choices=["paper", "tiny", "small"], default="paper")
     ap.add_argument("--no-cpu-baseline", action="store_true")

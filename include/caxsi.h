@@ -172,9 +172,23 @@ typedef struct {
     int64_t n_breakpoints;    /* u breakpoints of the table paths */
     int64_t kernel_launches;  /* kernels launched by the last forward/adjoint/recon call */
     int64_t n_open_pairs;     /* (voxel, pixel) pairs whose mask factor T is 1 */
+    int64_t device_error;     /* 1 if a kernel of this plan gave up a bounded wait (copy or
+                                 tensor-core pipeline); reading it synchronises the device
+                                 and clears it */
 } caxsi_plan_info_t;
 
-caxsi_status caxsi_plan_info(const caxsi_plan *plan, caxsi_plan_info_t *info);
+caxsi_status caxsi_plan_info(caxsi_plan *plan, caxsi_plan_info_t *info);
+
+/* Plan options.
+ *   CAXSI_OPT_GEMM_ENGINE: how the table paths evaluate their contractions
+ *     over q: CAXSI_GEMM_TCGEN05 (default; this library's tcgen05 tensor-core
+ *     kernel, 3xTF32 for TABLE_FP32, single pass for TABLE_BF16/FP16) or
+ *     CAXSI_GEMM_CUBLAS (cuBLAS: bf16x9 emulation for TABLE_FP32).
+ * Errors: INVALID for an unknown key or value. */
+#define CAXSI_OPT_GEMM_ENGINE 1
+#define CAXSI_GEMM_TCGEN05 0
+#define CAXSI_GEMM_CUBLAS 1
+caxsi_status caxsi_plan_set_option(caxsi_plan *plan, int key, int value);
 
 /* Kernel timing (tracing).  When enabled, every kernel the plan launches is
  * bracketed by CUDA events recorded on its launch stream; caxsi_profile_read

@@ -44,7 +44,7 @@ class CGeometry(ctypes.Structure):
 class CPlanInfo(ctypes.Structure):
     _fields_ = [("n_offsets", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
                 ("n_breakpoints", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("n_open_pairs", ctypes.c_int64)]
+                ("n_open_pairs", ctypes.c_int64), ("device_error", ctypes.c_int64)]
 
 
 class CKernelStat(ctypes.Structure):
@@ -88,6 +88,8 @@ def load():
             lib.caxsi_plan_info.argtypes = [P, ctypes.POINTER(CPlanInfo)]
             lib.caxsi_forward_static_scratch.argtypes = [P, P, I64, P, I64, P]
             lib.caxsi_forward_static_scratch.restype = ctypes.c_int
+            lib.caxsi_plan_set_option.argtypes = [P, ctypes.c_int, ctypes.c_int]
+            lib.caxsi_plan_set_option.restype = ctypes.c_int
             lib.caxsi_profile_enable.argtypes = [P, ctypes.c_int]
             lib.caxsi_profile_read.argtypes = [P, ctypes.POINTER(CKernelStat), ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_int)]
@@ -201,6 +203,11 @@ class Plan:
         i = CPlanInfo()
         _check(self.lib.caxsi_plan_info(self.handle, ctypes.byref(i)), "caxsi_plan_info")
         return {k: getattr(i, k) for k, _ in CPlanInfo._fields_}
+
+    def set_gemm_engine(self, engine: str):
+        """'tcgen05' (default) or 'cublas' for the table paths' contractions."""
+        _check(self.lib.caxsi_plan_set_option(self.handle, 1, {"tcgen05": 0, "cublas": 1}[engine]),
+               "caxsi_plan_set_option")
 
     def profile(self, enable: bool = True):
         _check(self.lib.caxsi_profile_enable(self.handle, int(bool(enable))), "caxsi_profile_enable")

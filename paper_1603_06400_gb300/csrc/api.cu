@@ -267,8 +267,15 @@ caxsi_status caxsi_adjoint_host(caxsi_plan *p, const float *w_host, int64_t w_le
     return host_call(p, w_host, w_len, f_host, f_len, path, false);
 }
 
-caxsi_status caxsi_plan_info(const caxsi_plan *p, caxsi_plan_info_t *info) {
+caxsi_status caxsi_plan_info(caxsi_plan *p, caxsi_plan_info_t *info) {
     if (!p || !info) return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    int e = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(&e, p->err_flag + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CAXSI_ERR_CUDA;
+    if (e) cudaMemset(p->err_flag + 1, 0, sizeof(int));
+    info->device_error = e;
     info->n_offsets = p->dg.ND;
     info->table_bytes = p->table_bytes;
     info->n_breakpoints = table_breakpoints(p);
@@ -286,6 +293,15 @@ caxsi_status caxsi_forward_static_scratch(caxsi_plan *p, const float *f_dev, int
     if (!dg.ok) return CAXSI_ERR_CUDA;
     p->launches = 0;
     return direct_forward_static_scratch(p, f_dev, g_dev, (cudaStream_t)stream);
+}
+
+caxsi_status caxsi_plan_set_option(caxsi_plan *p, int key, int value) {
+    if (!p) return CAXSI_ERR_INVALID;
+    if (key == CAXSI_OPT_GEMM_ENGINE && (value == CAXSI_GEMM_TCGEN05 || value == CAXSI_GEMM_CUBLAS)) {
+        p->gemm_engine = value;
+        return CAXSI_OK;
+    }
+    return CAXSI_ERR_INVALID;
 }
 
 static void prof_clear(caxsi_plan *p) {

@@ -80,6 +80,7 @@ struct caxsi_plan {
     int64_t launches;   // kernels launched by the current / last call
     int64_t open_pairs; // (voxel, pixel) pairs with mask factor 1
     std::vector<double> phi;  // host copy of the spectrum Phi_k
+    int gemm_engine;          // table-path contractions: 0 = tcgen05 kernel, 1 = cuBLAS
     KernelProfiler prof;
 };
 

@@ -290,7 +290,7 @@ __device__ __forceinline__ void store_v(__half *p, float x) { *p = __float2half_
 
 template <typename OutT>
 __global__ void __launch_bounds__(RT, 1)
-k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, int vc) {
+k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float *__restrict__ Vlo, int vc) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int npix_al = (A.npix + 3) & ~3;
     float *w_s = reinterpret_cast<float *>(smem_raw);
@@ -446,7 +446,17 @@ k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, int v
         }
         __syncthreads();
         OutT *vrow = Vtab + (int64_t)v * A.Bp;
-        for (int t = tid; t < A.B; t += RT) store_v(vrow + t, LO[t] + (t > 0 ? HI[t - 1] : 0.f));
+        if (Vlo) {
+            float *lrow = Vlo + (int64_t)v * A.Bp;
+            for (int t = tid; t < A.B; t += RT) {
+                float h, l;
+                tf32_split(LO[t] + (t > 0 ? HI[t - 1] : 0.f), h, l);
+                store_v(vrow + t, h);
+                lrow[t] = l;
+            }
+        } else {
+            for (int t = tid; t < A.B; t += RT) store_v(vrow + t, LO[t] + (t > 0 ? HI[t - 1] : 0.f));
+        }
         __syncthreads();
     }
 }
@@ -542,19 +552,19 @@ cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, float *part
 
 template <typename OutT>
 cudaError_t launch_adj_rec(const caxsi_plan *p, const TablePath *T, const float *w, OutT *out,
-                           cudaStream_t s) {
+                           float *lo, cudaStream_t s) {
     const int npix = p->dg.M * p->dg.N;
     const size_t smem = adj_rec_smem(npix, T->Bp);
     cudaError_t e = cudaFuncSetAttribute(k_adj_rec<OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_adj_rec<OutT><<<T->rec_chunks, RT, smem, s>>>(rec_args(p, T), w, out, T->rec_vc);
+    k_adj_rec<OutT><<<T->rec_chunks, RT, smem, s>>>(rec_args(p, T), w, out, lo, T->rec_vc);
     return cudaGetLastError();
 }
 
-// out_kind: 0 = FP32 rows in T->tab, 1 = bf16 rows in T->v16, 2 = fp16 rows in T->v16
 cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, const float *w, int out_kind,
                             cudaStream_t s) {
-    if (out_kind == 1) return launch_adj_rec(p, T, w, reinterpret_cast<__nv_bfloat16 *>(T->v16), s);
-    if (out_kind == 2) return launch_adj_rec(p, T, w, reinterpret_cast<__half *>(T->v16), s);
-    return launch_adj_rec(p, T, w, T->tab, s);
+    if (out_kind == 1) return launch_adj_rec(p, T, w, reinterpret_cast<__nv_bfloat16 *>(T->v16), (float *)nullptr, s);
+    if (out_kind == 2) return launch_adj_rec(p, T, w, reinterpret_cast<__half *>(T->v16), (float *)nullptr, s);
+    if (out_kind == 3) return launch_adj_rec(p, T, w, T->tab, T->v_lo, s);
+    return launch_adj_rec(p, T, w, T->tab, (float *)nullptr, s);
 }

@@ -36,11 +36,6 @@
 #include "pairgeo.cuh"
 #include "table.cuh"
 
-cudaError_t sgemm_kmajor(int M, int N, int K, const float *A, int64_t lda, const float *Bm,
-                         int64_t ldb, float *C, int64_t ldc, const int2 *kband, cudaStream_t s);
-cudaError_t sgemm_nmajor_splitk(int M, int N, int K, const float *A, int64_t lda, const float *Bm,
-                                int64_t ldb, float *C, int64_t ldc, int64_t plane, int splits,
-                                cudaStream_t s);
 cudaError_t launch_sum_parts(const float *part, int nparts, int64_t stride, float *out,
                              int64_t n, cudaStream_t s);
 
@@ -265,6 +260,15 @@ cudaError_t dispatch_adj(const caxsi_plan *p, const TablePath *T, const float *w
 void free_table(TablePath *T) {
     if (!T) return;
     records_free(T);
+    cudaFree(T->S_hi);
+    cudaFree(T->S_lo);
+    cudaFree(T->St_hi);
+    cudaFree(T->St_lo);
+    cudaFree(T->St16[0]);
+    cudaFree(T->St16[1]);
+    cudaFree(T->f_hi);
+    cudaFree(T->f_lo);
+    cudaFree(T->v_lo);
     if (T->blas) cublasDestroy(T->blas);
     cudaFree(T->blas_ws);
     cudaFree(T->S16[0]);
@@ -274,10 +278,8 @@ void free_table(TablePath *T) {
     cudaFree(T->knots);
     cudaFree(T->bstart);
     cudaFree(T->S);
-    cudaFree(T->kband);
     cudaFree(T->tab);
     cudaFree(T->fwd_part);
-    cudaFree(T->adj_part);
     delete T;
 }
 
@@ -339,7 +341,7 @@ caxsi_status build_table(caxsi_plan *p) {
         const int B = (int)knots.size();
         if (B < 2 || B > 65535) { st = CAXSI_ERR_UNSUPPORTED; break; }
         T->B = B;
-        T->Bp = ((B + 1) + 3) / 4 * 4;
+        T->Bp = ((B + 1) + 7) / 8 * 8;
 
         // spectral weights c_k = Phi_k E_k dE / hc^2 in FP64 (energy form of Eq. 4)
         for (int k = 0; k < G.K; ++k) {
@@ -369,22 +371,10 @@ caxsi_status build_table(caxsi_plan *p) {
                 bs[bk] = (uint16_t)t;
             }
         }
-        // q band of S~ per 128-knot column tile: |a_k u - b - l| < 1 for some k
-        const int ntile = (B + 127) / 128;
-        std::vector<int2> band(ntile);
-        for (int c = 0; c < ntile; ++c) {
-            const double ulo_t = knots[c * 128];
-            const double uhi_t = knots[std::min(B - 1, c * 128 + 127)];
-            int l0 = (int)floor(ak[0] * ulo_t - b) - 1;
-            int l1 = (int)ceil(ak[G.K - 1] * uhi_t - b) + 2;
-            band[c] = make_int2(std::max(0, l0), std::min(G.Q, l1));
-        }
-
         const int64_t R = d.R;
         if (cudaMalloc(&T->knots, B * sizeof(float2)) != cudaSuccess ||
             cudaMalloc(&T->bstart, NB * sizeof(uint16_t)) != cudaSuccess ||
             cudaMalloc(&T->S, (size_t)B * G.Q * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&T->kband, ntile * sizeof(int2)) != cudaSuccess ||
             cudaMalloc(&T->tab, (size_t)R * T->Bp * sizeof(float)) != cudaSuccess ||
             cudaMalloc(&ak_d, G.K * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&ck_d, G.K * sizeof(double)) != cudaSuccess) {
@@ -393,7 +383,6 @@ caxsi_status build_table(caxsi_plan *p) {
         }
         cudaMemcpy(T->knots, krec.data(), B * sizeof(float2), cudaMemcpyHostToDevice);
         cudaMemcpy(T->bstart, bs.data(), NB * sizeof(uint16_t), cudaMemcpyHostToDevice);
-        cudaMemcpy(T->kband, band.data(), ntile * sizeof(int2), cudaMemcpyHostToDevice);
         cudaMemcpy(ak_d, ak.data(), G.K * sizeof(double), cudaMemcpyHostToDevice);
         cudaMemcpy(ck_d, ck.data(), G.K * sizeof(double), cudaMemcpyHostToDevice);
         cudaMemset(T->tab, 0, (size_t)R * T->Bp * sizeof(float));
@@ -417,19 +406,17 @@ caxsi_status build_table(caxsi_plan *p) {
         if (ac > d.R) ac = d.R;
         T->adj_vc = (int)ceil_div64(d.R, ac);
         T->adj_chunks = (int)ceil_div64(d.R, T->adj_vc);
-        T->adj_splits = 8;
         T->smem_fwd = (size_t)B * sizeof(float2) + (size_t)T->Bp * sizeof(float) + (size_t)NB * sizeof(uint16_t);
         T->smem_adj = T->smem_fwd;
         int smem_max = 0;
         cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
         if ((size_t)smem_max < T->smem_fwd) { st = CAXSI_ERR_UNSUPPORTED; break; }
-        if (cudaMalloc(&T->fwd_part, (size_t)T->fwd_chunks * npix * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&T->adj_part, (size_t)T->adj_splits * R * G.Q * sizeof(float)) != cudaSuccess) {
+        if (cudaMalloc(&T->fwd_part, (size_t)T->fwd_chunks * npix * sizeof(float)) != cudaSuccess) {
             st = CAXSI_ERR_OOM;
             break;
         }
         p->table_bytes += (int64_t)B * 8 + NB * 2 + (int64_t)B * G.Q * 4 + R * T->Bp * 4 +
-                          (int64_t)T->fwd_chunks * npix * 4 + (int64_t)T->adj_splits * R * G.Q * 4;
+                          (int64_t)T->fwd_chunks * npix * 4;
         // 5. per-pair records (precomputed intervals and weights), when they fit
         if ((st = records_build(p, T)) != CAXSI_OK) break;
         if (T->use_records && T->rec_chunks > T->fwd_chunks) {
@@ -458,13 +445,47 @@ int64_t table_breakpoints(const caxsi_plan *p) { return p->table ? p->table->B :
 
 namespace {
 
-__global__ void k_to_bf16(const float *__restrict__ x, __nv_bfloat16 *__restrict__ y, int64_t n) {
+// Row-padded operand copies: x [rows][Q] -> y [rows][Qp] (zeros beyond Q), as
+// bf16 (kind 1), fp16 (kind 2) or a TF32 high/low split (kind 0).
+__global__ void k_pad_convert(const float *__restrict__ x, int64_t rows, int Q, int Qp, int kind,
+                              void *__restrict__ y, float *__restrict__ ylo) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = __float2bfloat16_rn(x[i]);
+    if (i >= rows * Qp) return;
+    const int64_t r = i / Qp;
+    const int l = (int)(i - r * Qp);
+    const float v = l < Q ? x[r * Q + l] : 0.f;
+    if (kind == 1) {
+        reinterpret_cast<__nv_bfloat16 *>(y)[i] = __float2bfloat16_rn(v);
+    } else if (kind == 2) {
+        reinterpret_cast<__half *>(y)[i] = __float2half_rn(v);
+    } else {
+        float h, lo;
+        tf32_split(v, h, lo);
+        reinterpret_cast<float *>(y)[i] = h;
+        ylo[i] = lo;
+    }
 }
-__global__ void k_to_f16(const float *__restrict__ x, __half *__restrict__ y, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = __float2half_rn(x[i]);
+
+cudaError_t pad_convert(const float *x, int64_t rows, int Q, int Qp, int kind, void *y, float *ylo,
+                        cudaStream_t s) {
+    const int64_t n = rows * Qp;
+    k_pad_convert<<<(unsigned)ceil_div64(n, 256), 256, 0, s>>>(x, rows, Q, Qp, kind, y, ylo);
+    return cudaGetLastError();
+}
+
+// S~^T [Q][Bp] from S~ [B][Q]: TF32 split and 16-bit copies (zero padding t >= B).
+__global__ void k_transpose_S(const float *__restrict__ S, int B, int Q, int Bp, float *__restrict__ hi,
+                              float *__restrict__ lo, __nv_bfloat16 *__restrict__ bf, __half *__restrict__ hf) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)Q * Bp) return;
+    const int l = (int)(idx / Bp), t = (int)(idx % Bp);
+    const float x = t < B ? S[(int64_t)t * Q + l] : 0.f;
+    float h, lw;
+    tf32_split(x, h, lw);
+    hi[idx] = h;
+    lo[idx] = lw;
+    bf[idx] = __float2bfloat16_rn(x);
+    hf[idx] = __float2half_rn(x);
 }
 
 // cuBLAS handle, workspace and 16-bit operand copies (first table call).
@@ -476,18 +497,33 @@ caxsi_status blas_setup(caxsi_plan *p, TablePath *T) {
         return CAXSI_ERR_CUDA;
     }
     T->blas_ws_bytes = (size_t)64 << 20;
-    const int64_t nS = (int64_t)T->B * d.Q;
+    T->Qp = (d.Q + 7) / 8 * 8;
+    const int64_t nS = (int64_t)T->B * T->Qp;
     if (cudaMalloc(&T->blas_ws, T->blas_ws_bytes) != cudaSuccess ||
         cudaMalloc(&T->S16[0], nS * 2) != cudaSuccess || cudaMalloc(&T->S16[1], nS * 2) != cudaSuccess ||
-        cudaMalloc(&T->f16, (size_t)d.R * d.Q * 2) != cudaSuccess ||
+        cudaMalloc(&T->f16, (size_t)d.R * T->Qp * 2) != cudaSuccess ||
         cudaMalloc(&T->v16, (size_t)d.R * T->Bp * 2) != cudaSuccess)
         return CAXSI_ERR_OOM;
     if (cublasSetWorkspace(T->blas, T->blas_ws, T->blas_ws_bytes) != CUBLAS_STATUS_SUCCESS)
         return CAXSI_ERR_CUDA;
-    k_to_bf16<<<(unsigned)ceil_div64(nS, 256), 256>>>(T->S, (__nv_bfloat16 *)T->S16[0], nS);
-    k_to_f16<<<(unsigned)ceil_div64(nS, 256), 256>>>(T->S, (__half *)T->S16[1], nS);
+    if (pad_convert(T->S, T->B, d.Q, T->Qp, 1, T->S16[0], nullptr, 0) != cudaSuccess ||
+        pad_convert(T->S, T->B, d.Q, T->Qp, 2, T->S16[1], nullptr, 0) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+        return CAXSI_ERR_CUDA;
+    p->table_bytes += (int64_t)T->blas_ws_bytes + 2 * nS * 2 + (int64_t)d.R * T->Qp * 2 + (int64_t)d.R * T->Bp * 2;
+    // operands of the hand-written tcgen05 GEMM
+    const int64_t nSt = (int64_t)d.Q * T->Bp, nf = (int64_t)d.R * T->Qp, nV = (int64_t)d.R * T->Bp;
+    if (cudaMalloc(&T->S_hi, nS * 4) != cudaSuccess || cudaMalloc(&T->S_lo, nS * 4) != cudaSuccess ||
+        cudaMalloc(&T->St_hi, nSt * 4) != cudaSuccess || cudaMalloc(&T->St_lo, nSt * 4) != cudaSuccess ||
+        cudaMalloc(&T->St16[0], nSt * 2) != cudaSuccess || cudaMalloc(&T->St16[1], nSt * 2) != cudaSuccess ||
+        cudaMalloc(&T->f_hi, nf * 4) != cudaSuccess || cudaMalloc(&T->f_lo, nf * 4) != cudaSuccess ||
+        cudaMalloc(&T->v_lo, nV * 4) != cudaSuccess)
+        return CAXSI_ERR_OOM;
+    if (pad_convert(T->S, T->B, d.Q, T->Qp, 0, T->S_hi, T->S_lo, 0) != cudaSuccess) return CAXSI_ERR_CUDA;
+    k_transpose_S<<<(unsigned)ceil_div64(nSt, 256), 256>>>(T->S, T->B, d.Q, T->Bp, T->St_hi, T->St_lo,
+                                                          (__nv_bfloat16 *)T->St16[0], (__half *)T->St16[1]);
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return CAXSI_ERR_CUDA;
-    p->table_bytes += (int64_t)T->blas_ws_bytes + 2 * nS * 2 + (int64_t)d.R * d.Q * 2 + (int64_t)d.R * T->Bp * 2;
+    p->table_bytes += 2 * nS * 4 + nSt * 12 + 2 * nf * 4 + nV * 4;
     return CAXSI_OK;
 }
 
@@ -517,7 +553,33 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
     const DevGeo &d = p->dg;
     const float one = 1.f, zero = 0.f;
     if (cublasSetStream(T->blas, s) != CUBLAS_STATUS_SUCCESS) return CAXSI_ERR_CUDA;
-    if (path == CAXSI_PATH_TABLE_FP32) {
+    if (p->gemm_engine == 0 && path == CAXSI_PATH_TABLE_FP32) {
+        // Wtab[r][t] = sum_l f[r][l] S~[t][l] by the tcgen05 GEMM, 3xTF32
+        {
+            CAXSI_PROF(p, "split_tf32", s);
+            CAXSI_CUDA_TRY(pad_convert(f, d.R, d.Q, T->Qp, 0, T->f_hi, T->f_lo, s));
+        }
+        CAXSI_LAUNCH_CHECK(p);
+        {
+            CAXSI_PROF(p, "tc_gemm_fwd_3xtf32", s);
+            CAXSI_CUDA_TRY(tc_gemm(0, 256, d.R, T->B, d.Q, T->f_hi, T->f_lo, T->Qp, T->S_hi, T->S_lo, T->Qp,
+                                   T->tab, T->Bp, p->err_flag + 1, p->num_sms, s));
+        }
+        CAXSI_LAUNCH_CHECK(p);
+    } else if (p->gemm_engine == 0) {
+        const int k = path == CAXSI_PATH_TABLE_BF16 ? 0 : 1;
+        {
+            CAXSI_PROF(p, "to_16bit", s);
+            CAXSI_CUDA_TRY(pad_convert(f, d.R, d.Q, T->Qp, 1 + k, T->f16, nullptr, s));
+        }
+        CAXSI_LAUNCH_CHECK(p);
+        {
+            CAXSI_PROF(p, k == 0 ? "tc_gemm_fwd_bf16" : "tc_gemm_fwd_fp16", s);
+            CAXSI_CUDA_TRY(tc_gemm(1 + k, 256, d.R, T->B, d.Q, T->f16, nullptr, T->Qp, T->S16[k], nullptr, T->Qp,
+                                   T->tab, T->Bp, p->err_flag + 1, p->num_sms, s));
+        }
+        CAXSI_LAUNCH_CHECK(p);
+    } else if (path == CAXSI_PATH_TABLE_FP32) {
         // Wtab[r][t] = sum_l f[r][l] S~[t][l]  (column-major: W^T = S~ f^T), FP32-accurate
         CAXSI_PROF(p, "gemm_fwd_fp32emu", s);
         if (cublasGemmEx(T->blas, CUBLAS_OP_T, CUBLAS_OP_N, T->B, d.R, d.Q, &one, T->S, CUDA_R_32F, d.Q,
@@ -526,16 +588,14 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
             return CAXSI_ERR_CUDA;
     } else {
         const int k = path == CAXSI_PATH_TABLE_BF16 ? 0 : 1;
-        const int64_t nf = (int64_t)d.R * d.Q;
         {
             CAXSI_PROF(p, "to_16bit", s);
-            if (k == 0) k_to_bf16<<<(unsigned)ceil_div64(nf, 256), 256, 0, s>>>(f, (__nv_bfloat16 *)T->f16, nf);
-            else k_to_f16<<<(unsigned)ceil_div64(nf, 256), 256, 0, s>>>(f, (__half *)T->f16, nf);
+            CAXSI_CUDA_TRY(pad_convert(f, d.R, d.Q, T->Qp, 1 + k, T->f16, nullptr, s));
         }
         CAXSI_LAUNCH_CHECK(p);
         CAXSI_PROF(p, k == 0 ? "gemm_fwd_bf16" : "gemm_fwd_fp16", s);
         if (cublasGemmEx(T->blas, CUBLAS_OP_T, CUBLAS_OP_N, T->B, d.R, d.Q, &one, T->S16[k], dtype16(path),
-                         d.Q, T->f16, dtype16(path), d.Q, &zero, T->tab, CUDA_R_32F, T->Bp,
+                         T->Qp, T->f16, dtype16(path), T->Qp, &zero, T->tab, CUDA_R_32F, T->Bp,
                          CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
             return CAXSI_ERR_CUDA;
     }
@@ -563,15 +623,28 @@ caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path
     TablePath *T = p->table;
     const DevGeo &d = p->dg;
     const int out_kind = path == CAXSI_PATH_TABLE_FP32 ? 0 : (path == CAXSI_PATH_TABLE_BF16 ? 1 : 2);
+    const bool tc = p->gemm_engine == 0 && T->use_records;
     if (T->use_records) {
         CAXSI_PROF(p, "rec_pairs_adj", s);
-        CAXSI_CUDA_TRY(records_adjoint(p, T, w, out_kind, s));
+        CAXSI_CUDA_TRY(records_adjoint(p, T, w, (tc && out_kind == 0) ? 3 : out_kind, s));
     } else {
         CAXSI_PROF(p, "tab_pairs_adj", s);
         CAXSI_CUDA_TRY(dispatch_adj(p, T, w, s));
     }
     CAXSI_LAUNCH_CHECK(p);
     const float one = 1.f, zero = 0.f;
+    if (tc) {
+        // f[r][l] = sum_t V[r][t] S~^T[l][t] by the tcgen05 GEMM
+        const int k = out_kind;
+        CAXSI_PROF(p, k == 0 ? "tc_gemm_adj_3xtf32" : (k == 1 ? "tc_gemm_adj_bf16" : "tc_gemm_adj_fp16"), s);
+        if (k == 0)
+            CAXSI_CUDA_TRY(tc_gemm(0, 128, d.R, d.Q, T->B, T->tab, T->v_lo, T->Bp, T->St_hi, T->St_lo, T->Bp,
+                                   f_out, d.Q, p->err_flag + 1, p->num_sms, s));
+        else
+            CAXSI_CUDA_TRY(tc_gemm(k, 128, d.R, d.Q, T->B, T->v16, nullptr, T->Bp, T->St16[k - 1], nullptr,
+                                   T->Bp, f_out, d.Q, p->err_flag + 1, p->num_sms, s));
+        return CAXSI_OK;
+    }
     if (cublasSetStream(T->blas, s) != CUBLAS_STATUS_SUCCESS) return CAXSI_ERR_CUDA;
     // f[r][l] = sum_t V[r][t] S~[t][l]  (column-major: f^T = S~^T V^T)
     if (out_kind == 0) {
@@ -584,7 +657,7 @@ caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path
         const int k = out_kind - 1;
         CAXSI_PROF(p, k == 0 ? "gemm_adj_bf16" : "gemm_adj_fp16", s);
         if (cublasGemmEx(T->blas, CUBLAS_OP_N, CUBLAS_OP_N, d.Q, d.R, T->B, &one, T->S16[k], dtype16(path),
-                         d.Q, T->v16, dtype16(path), T->Bp, &zero, f_out, CUDA_R_32F, d.Q,
+                         T->Qp, T->v16, dtype16(path), T->Bp, &zero, f_out, CUDA_R_32F, d.Q,
                          CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
             return CAXSI_ERR_CUDA;
     }

@@ -7,18 +7,16 @@
 
 struct TablePath {
     int B = 0;          // knots
+    int Qp = 0;         // q row length of the 16-bit / TF32-split operand copies (multiple of 8)
     int Bp = 0;         // padded row length of Wtab / Vtab (>= B + 1, multiple of 4)
     int NB = 0;         // buckets
     float u0 = 0.f, inv_h = 0.f;
     float2 *knots = nullptr;    // [B] {u_t, 1/(u_{t+1} - u_t)}; last {u_B, 0}
     uint16_t *bstart = nullptr; // [NB] last knot index at or below the bucket start
     float *S = nullptr;         // [B][Q] S~ (FP32)
-    int2 *kband = nullptr;      // [ceil(B/128)] q range where S~ can be nonzero
     float *tab = nullptr;       // [R][Bp] Wtab (forward) / Vtab (adjoint)
     float *fwd_part = nullptr;  // [fwd_chunks][M*N]
     int fwd_chunks = 0, fwd_vc = 0, ppt = 1, threads = 1024, pix_chunks = 1;
-    float *adj_part = nullptr;  // [adj_splits][R*Q]
-    int adj_splits = 1;
     int adj_chunks = 0, adj_vc = 0;
     size_t smem_fwd = 0, smem_adj = 0;
 
@@ -37,9 +35,17 @@ struct TablePath {
     cublasHandle_t blas = nullptr;
     void *blas_ws = nullptr;
     size_t blas_ws_bytes = 0;
-    void *S16[2] = {nullptr, nullptr};  // S~ as bf16 / fp16, [B][Q]
-    void *f16 = nullptr;                // [R][Q] 16-bit copy of the forward input
+    void *S16[2] = {nullptr, nullptr};  // S~ as bf16 / fp16, [B][Qp]
+    void *f16 = nullptr;                // [R][Qp] 16-bit copy of the forward input
     void *v16 = nullptr;                // [R][Bp] 16-bit adjoint rows
+
+    // Hand-written tcgen05 GEMM operands: TF32 high/low splits (3xTF32) and the
+    // transposed spectral matrix S~^T [Q][Bp] for the adjoint contraction.
+    float *S_hi = nullptr, *S_lo = nullptr;     // [B][Qp]
+    float *St_hi = nullptr, *St_lo = nullptr;   // [Q][Bp]
+    void *St16[2] = {nullptr, nullptr};         // [Q][Bp] bf16 / fp16
+    float *f_hi = nullptr, *f_lo = nullptr;     // [R][Qp] per-call split of the forward input
+    float *v_lo = nullptr;                      // [R][Bp] low part of the adjoint rows (high part in tab)
 };
 
 
@@ -94,6 +100,21 @@ inline TabArgs tab_args(const TablePath *T) {
 // records.cu
 caxsi_status records_build(caxsi_plan *p, TablePath *T);
 cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s);
+// out_kind: 0 = FP32 rows in tab, 1 = bf16 rows in v16, 2 = fp16 rows in v16,
+// 3 = TF32 high part in tab and FP32 remainder in v_lo
 cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, const float *w, int out_kind,
                             cudaStream_t s);
+
+// tc_gemm.cu
+cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const void *A2, int64_t lda,
+                    const void *B, const void *B2, int64_t ldb, float *C, int64_t ldc, int *err,
+                    int num_sms, cudaStream_t s);
+
+// TF32 split: hi = x rounded to TF32 (nearest), lo = x - hi (exact in FP32)
+static __device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    hi = __uint_as_float(h);
+    lo = x - hi;
+}
 void records_free(TablePath *T);

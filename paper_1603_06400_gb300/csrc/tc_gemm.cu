@@ -1,0 +1,389 @@
+// Tensor-core GEMM for the table paths' contractions over q (sm_103a, tcgen05).
+//
+//   C[M][N] = sum_k A[M][K] B[N][K]      (A, B row-major with K contiguous; C FP32)
+//
+// Forward:  Wtab = F S~^T   (A = f [R][Q], B = S~ [B][Q])
+// Adjoint:  f = V S~        (A = V [R][Bp], B = S~^T [Q][Bt])
+//
+// Variants: KIND 0 = "3xTF32": A and B are each given as a TF32-rounded high
+// part and an FP32 remainder (x = hi + lo, both read as TF32 by the tensor
+// core); the product is accumulated as hi*hi + hi*lo + lo*hi in FP32, an error
+// of about 2^-21 relative per product (FP32-level accuracy).  KIND 1 / 2 =
+// single-pass bf16 / fp16 operands with FP32 accumulation.
+//
+// Structure (one CTA per SM, persistent over 128 x BN output tiles):
+//   warp 0      TMA producer: 2-D tensor loads (128-byte swizzle) of the A and B
+//               k-slices (128 bytes of K per row) into an NS-stage ring;
+//   warp 1      MMA issuer: one thread issues tcgen05.mma (M = 128, N = BN,
+//               K = 32 bytes per instruction) into a TMEM accumulator, commits
+//               each stage back to the producer and each finished tile to the
+//               epilogue; the accumulator is double-buffered in TMEM so the
+//               epilogue of one tile overlaps the MMAs of the next;
+//   warps 2..9  epilogue: tcgen05.ld of the warp's 32 TMEM lanes (two warps per
+//               lane quarter, each taking half of the columns), FP32 stores.
+// Long contractions are split into K-chunks of 4 stages: the tensor core
+// accumulates one chunk into a TMEM buffer and the epilogue adds the chunk
+// into running FP32 sums held in registers ("promotion"), so no chain of
+// tensor-core accumulation is longer than one chunk; the accumulation inside
+// the tensor core is not IEEE FP32 round-to-nearest and its error grows with
+// the chain length.
+// Every mbarrier wait is bounded; on timeout the kernel records an error in
+// err[0] and every role stops.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int TCG_THREADS = 320;
+constexpr int KCHUNK = 4;  // k-stages (128 bytes of K each) per tensor-core accumulation chain
+constexpr uint32_t TCG_WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t s_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mb_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mb_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mb_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mb_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(s_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mb_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+    for (uint32_t k = 0; k < TCG_WAIT_LIMIT; ++k) {
+        if (mb_try(bar, parity)) return true;
+        if ((k & 1023u) == 1023u && *abort) return false;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            s_addr(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(s_addr(bar))
+        : "memory");
+}
+// K-major operand, 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(const void *p) {
+    const uint32_t a = s_addr(p);
+    uint64_t d = (uint64_t)((a >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;            // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset: next 8-row group
+    d |= (uint64_t)1u << 46;            // descriptor version (sm_100 family)
+    d |= (uint64_t)2u << 61;            // 128-byte swizzle
+    return d;
+}
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (KIND == 0) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    }
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&r)[32]) {
+    uint32_t u[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
+          "=r"(u[15]), "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]),
+          "=r"(u[22]), "=r"(u[23]), "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]),
+          "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) r[i] = __uint_as_float(u[i]);
+}
+
+struct TcArgs {
+    int M, N, K;
+    float *C;
+    int64_t ldc;
+    int *err;
+    int ntn, ntiles, nk;
+    int vec_ok;  // rows of C start on 16-byte boundaries (vector stores allowed)
+};
+
+template <int BN, int KIND, int NS>
+__global__ void __launch_bounds__(TCG_THREADS, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tA2,
+          const __grid_constant__ CUtensorMap tB, const __grid_constant__ CUtensorMap tB2, TcArgs a) {
+    constexpr bool X3 = KIND == 0;
+    constexpr uint32_t A_BYTES = 128 * 128;
+    constexpr uint32_t B_BYTES = BN * 128;
+    constexpr uint32_t STAGE = X3 ? 2 * (A_BYTES + B_BYTES) : (A_BYTES + B_BYTES);
+    constexpr int KE = X3 ? 32 : 64;  // K elements per 128-byte row slice
+    constexpr uint32_t TMEM_COLS = 2 * BN;
+    // idesc: D = F32, A/B = TF32 (2) or BF16 (1) or F16 (0), both K-major, N >> 3, M >> 4
+    constexpr uint32_t AB = KIND == 0 ? 2u : (KIND == 1 ? 1u : 0u);
+    constexpr uint32_t IDESC = (1u << 4) | (AB << 7) | (AB << 10) | ((uint32_t)(BN >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
+
+    extern __shared__ unsigned char smem_raw[];
+    // operand tiles need 1024-byte alignment of their shared-memory address (swizzle atoms)
+    unsigned char *base = smem_raw + ((1024u - (s_addr(smem_raw) & 1023u)) & 1023u);
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + NS * STAGE);
+    uint64_t *empty = full + NS;
+    uint64_t *accf = empty + NS;
+    uint64_t *acce = accf + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acce + 2);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mb_init(&full[s], 1);
+            mb_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mb_init(&accf[b], 1);
+            mb_init(&acce[b], TCG_THREADS - 64);
+        }
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int tile = blockIdx.x; tile < a.ntiles && !*abort; tile += gridDim.x) {
+                const int m0 = (tile / a.ntn) * 128, n0 = (tile % a.ntn) * BN;
+                for (int kt = 0; kt < a.nk; ++kt, ++it) {
+                    const uint32_t s = it % NS, ph = (it / NS) & 1u;
+                    if (!mb_wait(&empty[s], ph ^ 1u, abort)) { *abort = 1; break; }
+                    unsigned char *st = base + s * STAGE;
+                    mb_expect_tx(&full[s], STAGE);
+                    const int x = kt * KE;
+                    tma_load_2d(st, &tA, x, m0, &full[s]);
+                    tma_load_2d(st + A_BYTES, &tB, x, n0, &full[s]);
+                    if (X3) {
+                        tma_load_2d(st + A_BYTES + B_BYTES, &tA2, x, m0, &full[s]);
+                        tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tB2, x, n0, &full[s]);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t it = 0, cc = 0;
+            const int nch = (a.nk + KCHUNK - 1) / KCHUNK;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < a.ntiles && ok && !*abort; tile += gridDim.x) {
+                for (int c = 0; c < nch && ok; ++c, ++cc) {
+                    const uint32_t b = cc & 1u, aph = (cc >> 1) & 1u;
+                    if (!mb_wait(&acce[b], aph ^ 1u, abort)) { *abort = 1; ok = false; break; }
+                    fence_after();
+                    const uint32_t d = tmem + b * BN;
+                    const int k0 = c * KCHUNK, k1 = min(a.nk, k0 + KCHUNK);
+                    for (int kt = k0; kt < k1; ++kt, ++it) {
+                        const uint32_t s = it % NS, ph = (it / NS) & 1u;
+                        if (!mb_wait(&full[s], ph, abort)) { *abort = 1; ok = false; break; }
+                        fence_after();
+                        unsigned char *st = base + s * STAGE;
+                        const uint64_t da = sw128_desc(st), db = sw128_desc(st + A_BYTES);
+                        const uint64_t dal = sw128_desc(st + A_BYTES + B_BYTES);
+                        const uint64_t dbl = sw128_desc(st + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint64_t adv = (uint64_t)(ks * 2);  // 32 bytes per instruction, 16-byte units
+                            const uint32_t acc = (kt > k0 || ks > 0) ? 1u : 0u;
+                            mma<KIND>(d, da + adv, db + adv, IDESC, acc);
+                            if (X3) {
+                                mma<KIND>(d, da + adv, dbl + adv, IDESC, 1u);
+                                mma<KIND>(d, dal + adv, db + adv, IDESC, 1u);
+                            }
+                        }
+                        mma_commit(&empty[s]);
+                    }
+                    if (!ok) break;
+                    mma_commit(&accf[b]);
+                }
+            }
+        }
+    } else {
+        // epilogue: warps 2..9; warp % 4 selects the TMEM lane quarter, (warp - 2) / 4 the
+        // column half of the tile
+        constexpr int CW = BN / 2;   // columns per epilogue warp
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int nch = (a.nk + KCHUNK - 1) / KCHUNK;
+        uint32_t cc = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+            const int m0 = (tile / a.ntn) * 128, n0 = (tile % a.ntn) * BN + h * CW;
+            const int row = m0 + q * 32 + lane;
+            float *crow = a.C + (int64_t)row * a.ldc;
+            float run[CW];
+#pragma unroll
+            for (int i = 0; i < CW; ++i) run[i] = 0.f;
+            for (int c = 0; c < nch; ++c, ++cc) {
+                const uint32_t b = cc & 1u, aph = (cc >> 1) & 1u;
+                if (!mb_wait(&accf[b], aph, abort)) { *abort = 1; ok = false; break; }
+                fence_after();
+#pragma unroll
+                for (int c0 = 0; c0 < CW; c0 += 32) {
+                    float r[32];
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * BN + h * CW + c0, r);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) run[c0 + i] += r[i];
+                }
+                fence_before();
+                mb_arrive(&acce[b]);
+            }
+            if (!ok) break;
+            if (row < a.M) {
+#pragma unroll
+                for (int c0 = 0; c0 < CW; c0 += 32) {
+                    const int col = n0 + c0;
+                    if (col >= a.N) break;
+                    if (a.vec_ok && col + 32 <= a.N) {
+                        float4 *dst = reinterpret_cast<float4 *>(crow + col);
+#pragma unroll
+                        for (int v4 = 0; v4 < 8; ++v4)
+                            dst[v4] = make_float4(run[c0 + 4 * v4], run[c0 + 4 * v4 + 1], run[c0 + 4 * v4 + 2],
+                                                  run[c0 + 4 * v4 + 3]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (col + i < a.N) crow[col + i] = run[c0 + i];
+                    }
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (*abort && threadIdx.x == 0) atomicExch(a.err, 1);
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// ---- host side ------------------------------------------------------------------
+
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+    static EncodeFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    }
+    return fn;
+}
+
+// 2-D map over a row-major [rows][cols] matrix (cols contiguous, row stride in
+// elements), box = 128 bytes of cols x box_rows rows, 128-byte swizzle, zero fill.
+bool make_map(CUtensorMap *m, const void *ptr, int elem_bytes, int64_t rows, int64_t cols,
+              int64_t row_stride, int box_rows) {
+    EncodeFn enc = encode_fn();
+    if (!enc) return false;
+    const CUtensorMapDataType dt = elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(row_stride * elem_bytes)};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / elem_bytes), (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, dt, 2, const_cast<void *>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int KIND, int NS>
+cudaError_t launch_tc(const CUtensorMap &tA, const CUtensorMap &tA2, const CUtensorMap &tB,
+                      const CUtensorMap &tB2, TcArgs a, int num_sms, cudaStream_t s) {
+    constexpr uint32_t STAGE = (KIND == 0 ? 2 : 1) * (128 * 128 + BN * 128);
+    const size_t smem = 1024 + (size_t)NS * STAGE + (2 * NS + 4) * 8 + 16;
+    auto kfn = k_tc_gemm<BN, KIND, NS>;
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = a.ntiles < num_sms ? a.ntiles : num_sms;
+    kfn<<<grid, TCG_THREADS, smem, s>>>(tA, tA2, tB, tB2, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// C[M][N] (row stride ldc) = A[M][K] (row stride lda) * B[N][K]^T (row stride ldb).
+// kind 0: A = (A_hi, A_lo), B = (B_hi, B_lo) FP32 arrays (3xTF32); kind 1 / 2:
+// A, B bf16 / fp16 (A2, B2 ignored).  bn = 256 or 128.  Row strides in
+// elements must make 16-byte multiples; base pointers 16-byte aligned.
+cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const void *A2, int64_t lda,
+                    const void *B, const void *B2, int64_t ldb, float *C, int64_t ldc, int *err,
+                    int num_sms, cudaStream_t s) {
+    const int eb = kind == 0 ? 4 : 2;
+    CUtensorMap tA, tA2, tB, tB2;
+    if (!make_map(&tA, A, eb, M, K, lda, 128) || !make_map(&tB, B, eb, N, K, ldb, bn))
+        return cudaErrorInvalidValue;
+    if (kind == 0) {
+        if (!make_map(&tA2, A2, eb, M, K, lda, 128) || !make_map(&tB2, B2, eb, N, K, ldb, bn))
+            return cudaErrorInvalidValue;
+    } else {
+        tA2 = tA;
+        tB2 = tB;
+    }
+    TcArgs a;
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.C = C;
+    a.ldc = ldc;
+    a.err = err;
+    a.vec_ok = ((ldc & 3) == 0) && (((uintptr_t)C & 15) == 0);
+    a.ntn = (N + bn - 1) / bn;
+    a.ntiles = ((M + 127) / 128) * a.ntn;
+    a.nk = (K * eb + 127) / 128;
+    if (bn == 256) {
+        if (kind == 0) return launch_tc<256, 0, 2>(tA, tA2, tB, tB2, a, num_sms, s);
+        if (kind == 1) return launch_tc<256, 1, 4>(tA, tA2, tB, tB2, a, num_sms, s);
+        return launch_tc<256, 2, 4>(tA, tA2, tB, tB2, a, num_sms, s);
+    }
+    if (kind == 0) return launch_tc<128, 0, 3>(tA, tA2, tB, tB2, a, num_sms, s);
+    if (kind == 1) return launch_tc<128, 1, 6>(tA, tA2, tB, tB2, a, num_sms, s);
+    return launch_tc<128, 2, 6>(tA, tA2, tB, tB2, a, num_sms, s);
+}
