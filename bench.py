@@ -152,20 +152,40 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def kernel_work(name, g, info, path):
-    """Algorithmic work of one launch of the named kernel (units, amount, bound)."""
+def kernel_work(name, g, info, path, nsm):
+    """Algorithmic work of one launch of the named kernel: (unit, amount, bound).
+
+    The amounts are the minimum bytes or flops the kernel's job needs (formulas in the design doc)."""
     open_pairs = info["n_open_pairs"]
+    B = info["n_breakpoints"]
+    Bp = (B + 1 + 7) // 8 * 8
+    n_rec = info["n_records"]
+    R, npix = g.X * g.J, g.M * g.N
+    chunks = min(2 * nsm, R)
     if name in ("fwd_direct", "adj_direct"):
         # per open (voxel, pixel) pair: K energy terms of 8 flop (tau FMA, floor,
         # fraction, lerp FMA, accumulate FMA) plus 30 flop of scatter geometry
         return "TFLOP/s", open_pairs * (8.0 * g.K + 30.0), "alu"
+    if name == "rec_pairs_fwd":
+        # 12-byte records, one W row per voxel, one partial image per block
+        return "GB/s", 12.0 * n_rec + 4.0 * R * Bp + 4.0 * chunks * npix, "hbm"
+    if name == "rec_pairs_adj":
+        vb = {"table_fp32": 8.0, "table_bf16": 2.0, "table_fp16": 2.0}[path]
+        return "GB/s", 12.0 * n_rec + vb * R * B + 4.0 * chunks * npix, "hbm"
+    if name.startswith("tc_gemm_fwd"):
+        # the forward contraction is bound by writing the FP32 knot table
+        ab = 8.0 if name.endswith("3xtf32") else 2.0
+        return "GB/s", 4.0 * R * B + ab * R * g.Q, "hbm"
+    if name.startswith("tc_gemm_adj"):
+        passes = 3 if name.endswith("3xtf32") else 1
+        return "TFLOP/s", passes * 2.0 * R * B * g.Q, "tensor"
     return None, None, None
 
 
 def traffic_for(name, path):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(p):
         return None
     try:
@@ -385,7 +405,7 @@ def run_ours(args):
     dom = max(kernels, key=lambda k: kernels[k]["total_ms"]) if kernels else None
     roofline = None
     if dom:
-        unit, work, bound = kernel_work(dom, g, info, path)
+        unit, work, bound = kernel_work(dom, g, info, args.path, nsm)
         if work is not None:
             avg_s = kernels[dom]["avg_ms"] / 1e3
             if bound == "alu":
@@ -393,10 +413,21 @@ def run_ours(args):
                 peak = nsm * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
                 peak_note = (f"FP32 SIMT: {nsm} SMs x 128 lanes x 2 flop x "
                              f"{peaks.get('sm_max_mhz', 2070.0):g} MHz ({peak_kind} clock)")
-            achieved = work / avg_s / 1e12
+                achieved = work / avg_s / 1e12
+            elif bound == "hbm":
+                peak = float(peaks["hbm_gbs"])
+                peak_note = f"HBM copy bandwidth, {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                achieved = work / avg_s / 1e9
+            else:
+                bf16 = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]))
+                tf32 = args.path == "table_fp32"
+                peak = bf16 / 2.0 if tf32 else bf16
+                peak_note = (f"dense {'TF32 = bf16 / 2 (nominal ratio)' if tf32 else 'bf16/fp16'} from "
+                             f"the {peak_kind} sustained bf16 GEMM rate")
+                achieved = work / avg_s / 1e12
             roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
                         "unit": unit, "frac": achieved / peak,
-                        "traffic": traffic_for(dom, path), "peak_source": peak_note,
+                        "traffic": traffic_for(dom, args.path), "peak_source": peak_note,
                         "work_per_launch": work}
     launches = sum(n for n, _ in kstats.values())
     line = {

@@ -172,6 +172,7 @@ typedef struct {
     int64_t n_breakpoints;    /* u breakpoints of the table paths */
     int64_t kernel_launches;  /* kernels launched by the last forward/adjoint/recon call */
     int64_t n_open_pairs;     /* (voxel, pixel) pairs whose mask factor T is 1 */
+    int64_t n_records;        /* precomputed pair records of the table paths (0 until built) */
     int64_t device_error;     /* 1 if a kernel of this plan gave up a bounded wait (copy or
                                  tensor-core pipeline); reading it synchronises the device
                                  and clears it */

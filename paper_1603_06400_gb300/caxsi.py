@@ -44,7 +44,8 @@ class CGeometry(ctypes.Structure):
 class CPlanInfo(ctypes.Structure):
     _fields_ = [("n_offsets", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
                 ("n_breakpoints", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("n_open_pairs", ctypes.c_int64), ("device_error", ctypes.c_int64)]
+                ("n_open_pairs", ctypes.c_int64), ("n_records", ctypes.c_int64),
+                ("device_error", ctypes.c_int64)]
 
 
 class CKernelStat(ctypes.Structure):

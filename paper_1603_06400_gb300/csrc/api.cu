@@ -281,6 +281,7 @@ caxsi_status caxsi_plan_info(caxsi_plan *p, caxsi_plan_info_t *info) {
     info->n_breakpoints = table_breakpoints(p);
     info->kernel_launches = p->launches;
     info->n_open_pairs = p->open_pairs;
+    info->n_records = table_records(p);
     return CAXSI_OK;
 }
 

@@ -98,6 +98,7 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g, int path, cu
 caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f, int path, cudaStream_t s);
 void table_destroy(caxsi_plan *p);
 int64_t table_breakpoints(const caxsi_plan *p);
+int64_t table_records(const caxsi_plan *p);
 
 // ---- recon.cu ----------------------------------------------------------------
 caxsi_status recon_ratio(caxsi_plan *p, const float *y, const float *r, cudaStream_t s);

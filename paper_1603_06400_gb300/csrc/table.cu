@@ -442,6 +442,7 @@ caxsi_status build_table(caxsi_plan *p) {
 }  // namespace
 
 int64_t table_breakpoints(const caxsi_plan *p) { return p->table ? p->table->B : 0; }
+int64_t table_records(const caxsi_plan *p) { return p->table ? p->table->n_rec : 0; }
 
 namespace {
 
