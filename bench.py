@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--workload", choices=["paper", "tiny", "small"], default="paper")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-recon", action="store_true")
     return ap.parse_args()
 
 
@@ -278,6 +279,81 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank bookkeeping (independent phantoms per rank, no data-path collective)
+# ---------------------------------------------------------------------------
+
+def rank_phantoms(rank, world, n=N_PHANTOMS):
+    """Phantoms owned by a rank: disjoint across ranks and covering all n when
+    world <= n; with more ranks than phantoms the extra ranks repeat phantoms."""
+    mine = [p for p in range(n) if p % world == rank]
+    return mine or [rank % n]
+
+
+def max_over_ranks(value, dist, device=None):
+    """Maximum of a per-rank scalar (the timing rule: the slowest rank counts)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# reconstruction: time to the plain FP32 method's final NMSE
+# ---------------------------------------------------------------------------
+
+def recon_experiment(caxsi, plan, g, dev, phantom, iters=100, max_iters=300):
+    """Penalised EM (Huber on the spatial neighbours) on one phantom: the plain
+    FP32 table path for `iters` iterations gives the target NMSE; each
+    reduced-precision path is run until it reaches that NMSE.  Device time of
+    the iterations only (CUDA events); NMSE = |f - f_true|^2 / |f_true|^2."""
+    import torch
+    f_true = torch.tensor(synth.phantom(g, phantom), dtype=torch.float32, device=dev)
+    P = caxsi.PATHS
+    mean = plan.forward(f_true, path=P["table_fp32"])
+    peak = synth.log_uniform_peak(phantom)
+    y = torch.tensor(synth.poisson_counts((mean * (peak / mean.max())).cpu().numpy().astype(np.float64),
+                                          100 + phantom), dtype=torch.float32, device=dev)
+    scale = peak / float(mean.max())     # counts per unit of A f_true
+    f_ref = f_true * scale               # the object in count units
+    b1 = plan.adjoint(torch.ones((g.M, g.N), device=dev), path=P["table_fp32"])
+    f_init = float(y.sum() / b1.sum())
+    beta = 1e-3 * float(y.sum()) / (g.X * g.J * g.Q)
+    delta = 0.01 * f_init
+    nref = float(torch.sum(f_ref.double() ** 2))
+
+    def run(path, target=None, n=iters):
+        f = torch.full((g.X, g.J, g.Q), f_init, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        total, hist = 0.0, []
+        for it in range(n):
+            e0.record()
+            plan.recon_step(y, f, beta=beta, delta=delta, path=P[path])
+            e1.record()
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1) / 1e3
+            nmse = float(torch.sum((f.double() - f_ref.double()) ** 2)) / nref
+            hist.append(nmse)
+            if target is not None and nmse <= target:
+                return {"iterations": it + 1, "seconds": total, "nmse": nmse, "reached": True}
+        out = {"iterations": n, "seconds": total, "nmse": hist[-1]}
+        if target is not None:
+            out["reached"] = False
+        return out
+
+    plain = run("table_fp32")
+    res = {"phantom": phantom, "peak_counts": peak, "beta": beta, "delta": delta,
+           "plain_fp32": plain, "target_nmse": plain["nmse"]}
+    for path in ("table_bf16", "table_fp16"):
+        r = run(path, target=plain["nmse"], n=max_iters)
+        r["speedup_vs_plain"] = plain["seconds"] / r["seconds"] if r["reached"] else None
+        res[path] = r
+    res["learned"] = None
+    return res
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -307,8 +383,7 @@ def run_ours(args):
     plan = caxsi.Plan(g, phi, mask)
     info = plan.info()
 
-    # this rank's phantoms (disjoint across ranks)
-    mine = [p for p in range(N_PHANTOMS) if p % world == rank] or [rank % N_PHANTOMS]
+    mine = rank_phantoms(rank, world)
     states = []
     ones = torch.ones((g.M, g.N), device=dev)
     b1 = plan.adjoint(ones, path=path)
@@ -357,11 +432,7 @@ def run_ours(args):
     sampler.stop()
     clocks = sampler.summary(t_wall0, t_wall1)
 
-    ms_max = ms
-    if dist:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_max = float(tt.item())
+    ms_max = max_over_ranks(ms, dist, dev)
     total_evals = args.steps * world
     value = total_evals / (ms_max / 1e3)
 
@@ -383,11 +454,7 @@ def run_ours(args):
         for _ in range(n_e2e):
             plan.forward_host(fh, out=gh, path=path)
             plan.adjoint_host(wh, out=fo, path=path)
-        el = time.perf_counter() - t0
-        if dist:
-            tt = torch.tensor([el], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            el = float(tt.item())
+        el = max_over_ranks(time.perf_counter() - t0, dist, dev)
         e2e = {"value": n_e2e * world / el, "unit": UNIT,
                "h2d_bytes_per_step": int((g.f_len + g.g_len) * 4),
                "d2h_bytes_per_step": int((g.g_len + g.f_len) * 4),
@@ -448,6 +515,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "kernels": kernels,
     }
+    if world == 1 and args.workload != "small" and not args.no_recon:
+        line["recon"] = recon_experiment(caxsi, plan, g, dev, phantom=0)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g)
     print(json.dumps(line), flush=True)
