@@ -565,6 +565,5 @@ cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, const float
                             cudaStream_t s) {
     if (out_kind == 1) return launch_adj_rec(p, T, w, reinterpret_cast<__nv_bfloat16 *>(T->v16), (float *)nullptr, s);
     if (out_kind == 2) return launch_adj_rec(p, T, w, reinterpret_cast<__half *>(T->v16), (float *)nullptr, s);
-    if (out_kind == 3) return launch_adj_rec(p, T, w, T->tab, T->v_lo, s);
     return launch_adj_rec(p, T, w, T->tab, (float *)nullptr, s);
 }

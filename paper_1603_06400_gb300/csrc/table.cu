@@ -268,7 +268,6 @@ void free_table(TablePath *T) {
     cudaFree(T->St16[1]);
     cudaFree(T->f_hi);
     cudaFree(T->f_lo);
-    cudaFree(T->v_lo);
     if (T->blas) cublasDestroy(T->blas);
     cudaFree(T->blas_ws);
     cudaFree(T->S16[0]);
@@ -513,18 +512,17 @@ caxsi_status blas_setup(caxsi_plan *p, TablePath *T) {
         return CAXSI_ERR_CUDA;
     p->table_bytes += (int64_t)T->blas_ws_bytes + 2 * nS * 2 + (int64_t)d.R * T->Qp * 2 + (int64_t)d.R * T->Bp * 2;
     // operands of the hand-written tcgen05 GEMM
-    const int64_t nSt = (int64_t)d.Q * T->Bp, nf = (int64_t)d.R * T->Qp, nV = (int64_t)d.R * T->Bp;
+    const int64_t nSt = (int64_t)d.Q * T->Bp, nf = (int64_t)d.R * T->Qp;
     if (cudaMalloc(&T->S_hi, nS * 4) != cudaSuccess || cudaMalloc(&T->S_lo, nS * 4) != cudaSuccess ||
         cudaMalloc(&T->St_hi, nSt * 4) != cudaSuccess || cudaMalloc(&T->St_lo, nSt * 4) != cudaSuccess ||
         cudaMalloc(&T->St16[0], nSt * 2) != cudaSuccess || cudaMalloc(&T->St16[1], nSt * 2) != cudaSuccess ||
-        cudaMalloc(&T->f_hi, nf * 4) != cudaSuccess || cudaMalloc(&T->f_lo, nf * 4) != cudaSuccess ||
-        cudaMalloc(&T->v_lo, nV * 4) != cudaSuccess)
+        cudaMalloc(&T->f_hi, nf * 4) != cudaSuccess || cudaMalloc(&T->f_lo, nf * 4) != cudaSuccess)
         return CAXSI_ERR_OOM;
     if (pad_convert(T->S, T->B, d.Q, T->Qp, 0, T->S_hi, T->S_lo, 0) != cudaSuccess) return CAXSI_ERR_CUDA;
     k_transpose_S<<<(unsigned)ceil_div64(nSt, 256), 256>>>(T->S, T->B, d.Q, T->Bp, T->St_hi, T->St_lo,
                                                           (__nv_bfloat16 *)T->St16[0], (__half *)T->St16[1]);
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return CAXSI_ERR_CUDA;
-    p->table_bytes += 2 * nS * 4 + nSt * 12 + 2 * nf * 4 + nV * 4;
+    p->table_bytes += 2 * nS * 4 + nSt * 12 + 2 * nf * 4;
     return CAXSI_OK;
 }
 
@@ -627,7 +625,7 @@ caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path
     const bool tc = p->gemm_engine == 0 && T->use_records;
     if (T->use_records) {
         CAXSI_PROF(p, "rec_pairs_adj", s);
-        CAXSI_CUDA_TRY(records_adjoint(p, T, w, (tc && out_kind == 0) ? 3 : out_kind, s));
+        CAXSI_CUDA_TRY(records_adjoint(p, T, w, out_kind, s));
     } else {
         CAXSI_PROF(p, "tab_pairs_adj", s);
         CAXSI_CUDA_TRY(dispatch_adj(p, T, w, s));
@@ -639,7 +637,7 @@ caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path
         const int k = out_kind;
         CAXSI_PROF(p, k == 0 ? "tc_gemm_adj_3xtf32" : (k == 1 ? "tc_gemm_adj_bf16" : "tc_gemm_adj_fp16"), s);
         if (k == 0)
-            CAXSI_CUDA_TRY(tc_gemm(0, 128, d.R, d.Q, T->B, T->tab, T->v_lo, T->Bp, T->St_hi, T->St_lo, T->Bp,
+            CAXSI_CUDA_TRY(tc_gemm(3, 128, d.R, d.Q, T->B, T->tab, nullptr, T->Bp, T->St_hi, T->St_lo, T->Bp,
                                    f_out, d.Q, p->err_flag + 1, p->num_sms, s));
         else
             CAXSI_CUDA_TRY(tc_gemm(k, 128, d.R, d.Q, T->B, T->v16, nullptr, T->Bp, T->St16[k - 1], nullptr,

@@ -45,7 +45,6 @@ struct TablePath {
     float *St_hi = nullptr, *St_lo = nullptr;   // [Q][Bp]
     void *St16[2] = {nullptr, nullptr};         // [Q][Bp] bf16 / fp16
     float *f_hi = nullptr, *f_lo = nullptr;     // [R][Qp] per-call split of the forward input
-    float *v_lo = nullptr;                      // [R][Bp] low part of the adjoint rows (high part in tab)
 };
 
 
@@ -100,8 +99,7 @@ inline TabArgs tab_args(const TablePath *T) {
 // records.cu
 caxsi_status records_build(caxsi_plan *p, TablePath *T);
 cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s);
-// out_kind: 0 = FP32 rows in tab, 1 = bf16 rows in v16, 2 = fp16 rows in v16,
-// 3 = TF32 high part in tab and FP32 remainder in v_lo
+// out_kind: 0 = FP32 rows in tab, 1 = bf16 rows in v16, 2 = fp16 rows in v16
 cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, const float *w, int out_kind,
                             cudaStream_t s);
 

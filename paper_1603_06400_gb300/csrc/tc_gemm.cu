@@ -8,8 +8,10 @@
 // Variants: KIND 0 = "3xTF32": A and B are each given as a TF32-rounded high
 // part and an FP32 remainder (x = hi + lo, both read as TF32 by the tensor
 // core); the product is accumulated as hi*hi + hi*lo + lo*hi in FP32, an error
-// of about 2^-21 relative per product (FP32-level accuracy).  KIND 1 / 2 =
-// single-pass bf16 / fp16 operands with FP32 accumulation.
+// of about 2^-21 relative per product (FP32-level accuracy).  KIND 3 = the same
+// with A given once in FP32 and split in shared memory by four converter warps
+// (half the A traffic).  KIND 1 / 2 = single-pass bf16 / fp16 operands with
+// FP32 accumulation.
 //
 // Structure (one CTA per SM, persistent over 128 x BN output tiles):
 //   warp 0      TMA producer: 2-D tensor loads (128-byte swizzle) of the A and B
@@ -38,7 +40,8 @@
 
 namespace {
 
-constexpr int TCG_THREADS = 320;
+constexpr int TCG_THREADS = 320;   // producer, MMA, 8 epilogue warps
+constexpr int TCG_EPI = 256;       // epilogue threads
 constexpr int KCHUNK = 4;  // k-stages (128 bytes of K each) per tensor-core accumulation chain
 constexpr uint32_t TCG_WAIT_LIMIT = 1u << 22;
 
@@ -106,6 +109,12 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_addr(bar))
                  : "memory");
 }
+__device__ __forceinline__ void tf32_split_dev(float x, float &hi, float &lo) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    hi = __uint_as_float(h);
+    lo = x - hi;
+}
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -134,18 +143,19 @@ struct TcArgs {
     int vec_ok;  // rows of C start on 16-byte boundaries (vector stores allowed)
 };
 
-template <int BN, int KIND, int NS>
-__global__ void __launch_bounds__(TCG_THREADS, 1)
+template <int BN, int KIND, int NS, int NT>
+__global__ void __launch_bounds__(NT, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tA2,
           const __grid_constant__ CUtensorMap tB, const __grid_constant__ CUtensorMap tB2, TcArgs a) {
-    constexpr bool X3 = KIND == 0;
+    constexpr bool X3 = KIND == 0 || KIND == 3;
+    constexpr bool SPLIT_A = KIND == 3;   // converter warps 10..13 split A in shared memory
     constexpr uint32_t A_BYTES = 128 * 128;
     constexpr uint32_t B_BYTES = BN * 128;
     constexpr uint32_t STAGE = X3 ? 2 * (A_BYTES + B_BYTES) : (A_BYTES + B_BYTES);
     constexpr int KE = X3 ? 32 : 64;  // K elements per 128-byte row slice
     constexpr uint32_t TMEM_COLS = 2 * BN;
     // idesc: D = F32, A/B = TF32 (2) or BF16 (1) or F16 (0), both K-major, N >> 3, M >> 4
-    constexpr uint32_t AB = KIND == 0 ? 2u : (KIND == 1 ? 1u : 0u);
+    constexpr uint32_t AB = X3 ? 2u : (KIND == 1 ? 1u : 0u);
     constexpr uint32_t IDESC = (1u << 4) | (AB << 7) | (AB << 10) | ((uint32_t)(BN >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
 
@@ -156,7 +166,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
     uint64_t *empty = full + NS;
     uint64_t *accf = empty + NS;
     uint64_t *acce = accf + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acce + 2);
+    uint64_t *conv = acce + 2;   // [NS] A split done (SPLIT_A)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(conv + NS);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -164,10 +175,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
         for (int s = 0; s < NS; ++s) {
             mb_init(&full[s], 1);
             mb_init(&empty[s], 1);
+            mb_init(&conv[s], 128);
         }
         for (int b = 0; b < 2; ++b) {
             mb_init(&accf[b], 1);
-            mb_init(&acce[b], TCG_THREADS - 64);
+            mb_init(&acce[b], TCG_EPI);
         }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -192,12 +204,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                     const uint32_t s = it % NS, ph = (it / NS) & 1u;
                     if (!mb_wait(&empty[s], ph ^ 1u, abort)) { *abort = 1; break; }
                     unsigned char *st = base + s * STAGE;
-                    mb_expect_tx(&full[s], STAGE);
+                    mb_expect_tx(&full[s], SPLIT_A ? STAGE - A_BYTES : STAGE);
                     const int x = kt * KE;
                     tma_load_2d(st, &tA, x, m0, &full[s]);
                     tma_load_2d(st + A_BYTES, &tB, x, n0, &full[s]);
                     if (X3) {
-                        tma_load_2d(st + A_BYTES + B_BYTES, &tA2, x, m0, &full[s]);
+                        if (!SPLIT_A) tma_load_2d(st + A_BYTES + B_BYTES, &tA2, x, m0, &full[s]);
                         tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tB2, x, n0, &full[s]);
                     }
                 }
@@ -217,7 +229,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                     const int k0 = c * KCHUNK, k1 = min(a.nk, k0 + KCHUNK);
                     for (int kt = k0; kt < k1; ++kt, ++it) {
                         const uint32_t s = it % NS, ph = (it / NS) & 1u;
-                        if (!mb_wait(&full[s], ph, abort)) { *abort = 1; ok = false; break; }
+                        if (!mb_wait(SPLIT_A ? &conv[s] : &full[s], ph, abort)) { *abort = 1; ok = false; break; }
                         fence_after();
                         unsigned char *st = base + s * STAGE;
                         const uint64_t da = sw128_desc(st), db = sw128_desc(st + A_BYTES);
@@ -238,6 +250,36 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                     if (!ok) break;
                     mma_commit(&accf[b]);
                 }
+            }
+        }
+    } else if (SPLIT_A && warp >= 10) {
+        // converters: split each landed A tile into its TF32 high part (in place)
+        // and the FP32 remainder (the A_lo slot); element-wise, so the 128-byte
+        // swizzle of the tile is kept as is
+        const int ct = threadIdx.x - 320;
+        uint32_t it = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < a.ntiles && ok && !*abort; tile += gridDim.x) {
+            for (int kt = 0; kt < a.nk; ++kt, ++it) {
+                const uint32_t s = it % NS, ph = (it / NS) & 1u;
+                if (!mb_wait(&full[s], ph, abort)) { *abort = 1; ok = false; break; }
+                unsigned char *st = base + s * STAGE;
+                float4 *hi = reinterpret_cast<float4 *>(st);
+                float4 *lo = reinterpret_cast<float4 *>(st + A_BYTES + B_BYTES);
+#pragma unroll
+                for (int e = ct; e < (int)(A_BYTES / 16); e += 128) {
+                    const float4 x = hi[e];
+                    float4 h, l;
+                    tf32_split_dev(x.x, h.x, l.x);
+                    tf32_split_dev(x.y, h.y, l.y);
+                    tf32_split_dev(x.z, h.z, l.z);
+                    tf32_split_dev(x.w, h.w, l.w);
+                    hi[e] = h;
+                    lo[e] = l;
+                }
+                // make the generic-proxy writes visible to the tensor core (async proxy)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mb_arrive(&conv[s]);
             }
         }
     } else {
@@ -337,32 +379,37 @@ bool make_map(CUtensorMap *m, const void *ptr, int elem_bytes, int64_t rows, int
 template <int BN, int KIND, int NS>
 cudaError_t launch_tc(const CUtensorMap &tA, const CUtensorMap &tA2, const CUtensorMap &tB,
                       const CUtensorMap &tB2, TcArgs a, int num_sms, cudaStream_t s) {
-    constexpr uint32_t STAGE = (KIND == 0 ? 2 : 1) * (128 * 128 + BN * 128);
-    const size_t smem = 1024 + (size_t)NS * STAGE + (2 * NS + 4) * 8 + 16;
-    auto kfn = k_tc_gemm<BN, KIND, NS>;
+    constexpr uint32_t STAGE = (KIND == 0 || KIND == 3 ? 2 : 1) * (128 * 128 + BN * 128);
+    constexpr int NT = KIND == 3 ? TCG_THREADS + 128 : TCG_THREADS;
+    const size_t smem = 1024 + (size_t)NS * STAGE + (3 * NS + 4) * 8 + 16;
+    auto kfn = k_tc_gemm<BN, KIND, NS, NT>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = a.ntiles < num_sms ? a.ntiles : num_sms;
-    kfn<<<grid, TCG_THREADS, smem, s>>>(tA, tA2, tB, tB2, a);
+    kfn<<<grid, NT, smem, s>>>(tA, tA2, tB, tB2, a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 // C[M][N] (row stride ldc) = A[M][K] (row stride lda) * B[N][K]^T (row stride ldb).
-// kind 0: A = (A_hi, A_lo), B = (B_hi, B_lo) FP32 arrays (3xTF32); kind 1 / 2:
-// A, B bf16 / fp16 (A2, B2 ignored).  bn = 256 or 128.  Row strides in
+// kind 0: A = (A_hi, A_lo), B = (B_hi, B_lo) FP32 arrays (3xTF32); kind 3: A in
+// FP32 (split on chip, A2 ignored), B = (B_hi, B_lo); kind 1 / 2: A, B bf16 / fp16
+// (A2, B2 ignored).  bn = 256 or 128.  Row strides in
 // elements must make 16-byte multiples; base pointers 16-byte aligned.
 cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const void *A2, int64_t lda,
                     const void *B, const void *B2, int64_t ldb, float *C, int64_t ldc, int *err,
                     int num_sms, cudaStream_t s) {
-    const int eb = kind == 0 ? 4 : 2;
+    const int eb = (kind == 0 || kind == 3) ? 4 : 2;
     CUtensorMap tA, tA2, tB, tB2;
     if (!make_map(&tA, A, eb, M, K, lda, 128) || !make_map(&tB, B, eb, N, K, ldb, bn))
         return cudaErrorInvalidValue;
     if (kind == 0) {
         if (!make_map(&tA2, A2, eb, M, K, lda, 128) || !make_map(&tB2, B2, eb, N, K, ldb, bn))
             return cudaErrorInvalidValue;
+    } else if (kind == 3) {
+        tA2 = tA;
+        if (!make_map(&tB2, B2, eb, N, K, ldb, bn)) return cudaErrorInvalidValue;
     } else {
         tA2 = tA;
         tB2 = tB;
@@ -379,11 +426,13 @@ cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const 
     a.ntiles = ((M + 127) / 128) * a.ntn;
     a.nk = (K * eb + 127) / 128;
     if (bn == 256) {
+        if (kind == 3) return cudaErrorInvalidValue;   // the on-chip A split is built for bn = 128
         if (kind == 0) return launch_tc<256, 0, 2>(tA, tA2, tB, tB2, a, num_sms, s);
         if (kind == 1) return launch_tc<256, 1, 4>(tA, tA2, tB, tB2, a, num_sms, s);
         return launch_tc<256, 2, 4>(tA, tA2, tB, tB2, a, num_sms, s);
     }
     if (kind == 0) return launch_tc<128, 0, 3>(tA, tA2, tB, tB2, a, num_sms, s);
+    if (kind == 3) return launch_tc<128, 3, 3>(tA, tA2, tB, tB2, a, num_sms, s);
     if (kind == 1) return launch_tc<128, 1, 6>(tA, tA2, tB, tB2, a, num_sms, s);
     return launch_tc<128, 2, 6>(tA, tA2, tB, tB2, a, num_sms, s);
 }
