@@ -171,7 +171,7 @@ def kernel_work(name, g, info, path, nsm):
         # 12-byte records, one W row per voxel, one partial image per block
         return "GB/s", 12.0 * n_rec + 4.0 * R * Bp + 4.0 * chunks * npix, "hbm"
     if name == "rec_pairs_adj":
-        vb = {"table_fp32": 8.0, "table_bf16": 2.0, "table_fp16": 2.0}[path]
+        vb = {"table_fp32": 4.0, "table_bf16": 2.0, "table_fp16": 2.0}[path]
         return "GB/s", 12.0 * n_rec + vb * R * B + 4.0 * chunks * npix, "hbm"
     if name.startswith("tc_gemm_fwd"):
         # the forward contraction is bound by writing the FP32 knot table
@@ -507,6 +507,8 @@ def run_ours(args):
                          f"{g.f_len * 4 / 1e6:.1f} MB cycled per step plus "
                          f"{info['table_bytes'] / 1e6:.0f} MB of plan tables",
                    "phantoms_per_rank": len(states)},
+        "plan": {"n_open_pairs": info["n_open_pairs"], "n_records": info["n_records"],
+                 "n_breakpoints": info["n_breakpoints"], "table_bytes": info["table_bytes"]},
         "roofline": roofline,
         "cpu_baseline": None,
         "e2e": e2e,

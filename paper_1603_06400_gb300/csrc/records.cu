@@ -35,7 +35,6 @@ namespace {
 constexpr int RT = 1024;                 // threads of the streaming kernels
 constexpr uint32_t SENT = 0xffffffffu;   // "no run" marker
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
-constexpr int PREF = 8;                  // record batches loaded ahead per warp
 
 struct RecArgs {
     int R, npix, Bp, B;
@@ -171,6 +170,16 @@ __global__ void k_rec_fill(PairArgs A, TabArgs T, int wpb, const int64_t *off, u
         }
         __syncwarp();
     }
+    // Pad the voxel's list to whole 16-byte quads with zero-weight copies of its
+    // last record (same pixel and interval, so the order by t is kept).
+    const int creal = __shfl_sync(0xffffffffu, incl, 31);
+    const int npadv = (int)(off[v + 1] - base) - creal;
+    if (lane < npadv) {
+        const int64_t q = base + creal + lane;
+        key[q] = key[base + creal - 1];
+        w0[q] = 0.f;
+        w1[q] = 0.f;
+    }
 }
 
 // ---- TMA bulk copy + mbarrier helpers -----------------------------------------
@@ -272,192 +281,257 @@ k_fwd_rec(RecArgs A, const float *__restrict__ Wtab, float *__restrict__ part, i
     for (int p = tid; p < A.npix; p += RT) dst[p] = g_s[p];
 }
 
-struct Side {
-    uint32_t t;
-    float lo, hi;
-};
+__device__ __forceinline__ void store_v4(float *p, float4 x) { *reinterpret_cast<float4 *>(p) = x; }
+__device__ __forceinline__ void store_v4(__nv_bfloat16 *p, float4 x) {
+    __nv_bfloat162 lo = __floats2bfloat162_rn(x.x, x.y), hi = __floats2bfloat162_rn(x.z, x.w);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t *>(&lo);
+    u.y = *reinterpret_cast<uint32_t *>(&hi);
+    *reinterpret_cast<uint2 *>(p) = u;
+}
+__device__ __forceinline__ void store_v4(__half *p, float4 x) {
+    __half2 lo = __floats2half2_rn(x.x, x.y), hi = __floats2half2_rn(x.z, x.w);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t *>(&lo);
+    u.y = *reinterpret_cast<uint32_t *>(&hi);
+    *reinterpret_cast<uint2 *>(p) = u;
+}
 
-// Adjoint streaming kernel.  Block = 1024 threads, a chunk of voxels; the
-// input image w is staged once in shared memory.  Per voxel, warp k reduces a
-// contiguous segment of the voxel's (t-sorted) records: runs of equal t are
-// summed by a segmented warp scan; complete runs inside the segment are owned
-// by the warp and stored directly, the first and last runs of each segment go
-// to side slots that one thread adds afterwards in warp order.  Then
-// V[t] = LO[t] + HI[t - 1] is written to Vtab.
-__device__ __forceinline__ void store_v(float *p, float x) { *p = x; }
-__device__ __forceinline__ void store_v(__nv_bfloat16 *p, float x) { *p = __float2bfloat16_rn(x); }
-__device__ __forceinline__ void store_v(__half *p, float x) { *p = __float2half_rn(x); }
+// Adjoint streaming kernel: V[t] = sum over records of interval t of w0 * w[pixel]
+// plus sum over records of interval t - 1 of w1 * w[pixel] (the two knots of each
+// record's interval).  One block of ADJ_T threads per SM, a chunk of voxels; the
+// input image w is staged once in shared memory and V is built in shared memory.
+//
+// Every voxel's list is whole 16-byte quads.  Per voxel, thread i takes the i-th of
+// ADJ_T equal parts (in quads) of the t-sorted list and sums each run of equal t in
+// registers.  A run that starts in the part is the thread's ("head" run); a run that
+// began in a lower part leaves its partial sums in the thread's slot.  Complete head
+// runs are written at once: V[t] = LO(t) + HI(t-1) when the same thread owns run
+// t-1, V[t'+1] = HI(t') at a gap.  After a barrier each thread adds the slots of the
+// following threads that continue its last run, in thread order, and writes that
+// run's V entry; after a second barrier it adds the run's HI to the next knot.  Every
+// V entry thus has one writer per phase and a fixed order of additions: no atomics,
+// deterministic results.
+//
+// Each warp's segment of the next voxel (its first ADJ_SQ quads of keys, w0 and w1,
+// and the quad before the segment) is brought into shared memory by TMA bulk copies
+// on the warp's mbarrier while the current voxel is processed.  Waits are bounded: a
+// copy that does not land sets *err, and the block drains its copies and stops.
+constexpr int ADJ_T = 1024;
+constexpr int ADJ_W = ADJ_T / 32;
+constexpr int ADJ_SQ = 64;
 
 template <typename OutT>
-__global__ void __launch_bounds__(RT, 1)
-k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float *__restrict__ Vlo, int vc) {
+__global__ void __launch_bounds__(ADJ_T, 1)
+k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float *__restrict__ Vlo, int vc,
+          int *err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int npix_al = (A.npix + 3) & ~3;
     float *w_s = reinterpret_cast<float *>(smem_raw);
-    float *LO = w_s + npix_al;
-    float *HI = LO + A.Bp;
-    Side *side = reinterpret_cast<Side *>(HI + A.Bp);   // [32][2]
-    Side *comp = side + 64;                              // [64] compacted side slots
+    float *V = w_s + npix_al;
+    uint4 *stg_k = reinterpret_cast<uint4 *>(V + A.Bp);           // [ADJ_W][ADJ_SQ]
+    float4 *stg_a = reinterpret_cast<float4 *>(stg_k + ADJ_W * ADJ_SQ);
+    float4 *stg_c = stg_a + ADJ_W * ADJ_SQ;
+    uint4 *stg_p = reinterpret_cast<uint4 *>(stg_c + ADJ_W * ADJ_SQ);   // [ADJ_W]
+    uint32_t *slot_t = reinterpret_cast<uint32_t *>(stg_p + ADJ_W);
+    float *slot_lo = reinterpret_cast<float *>(slot_t + ADJ_T);
+    float *slot_hi = slot_lo + ADJ_T;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(slot_hi + ADJ_T);    // [ADJ_W]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int v0 = blockIdx.x * vc;
     const int v1 = min(v0 + vc, A.R);
-    for (int p = tid; p < A.npix; p += RT) w_s[p] = w[p];
+    if (v0 >= v1) return;
+
+    // The warp's quads [ws, we) of the voxel with list [ob, oe): thread parts of perq
+    // quads, ADJ_T parts.
+    auto segment = [&](int64_t ob, int64_t oe, int &ws, int &we, int &perq) {
+        const int nq = (int)((oe - ob) >> 2);
+        perq = (nq + ADJ_T - 1) / ADJ_T;
+        ws = min(nq, warp * 32 * perq);
+        we = min(nq, ws + 32 * perq);
+    };
+    // Lane 0: stage the warp's segment of the voxel [ob, oe).  The stage was last
+    // read through the generic proxy, hence the proxy fence.
+    auto issue = [&](int64_t ob, int64_t oe) {
+        int ws, we, perq;
+        segment(ob, oe, ws, we, perq);
+        const int ns = min(we, ws + ADJ_SQ) - ws;
+        const bool kp = ws > 0 && ws < we;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar[warp], 48u * (uint32_t)ns + (kp ? 16u : 0u));
+        if (ns > 0) {
+            const int64_t r = ob + 4 * (int64_t)ws;
+            bulk_g2s(stg_k + warp * ADJ_SQ, A.key + r, 16u * ns, &bar[warp]);
+            bulk_g2s(stg_a + warp * ADJ_SQ, A.w0 + r, 16u * ns, &bar[warp]);
+            bulk_g2s(stg_c + warp * ADJ_SQ, A.w1 + r, 16u * ns, &bar[warp]);
+        }
+        if (kp) bulk_g2s(stg_p + warp, A.key + ob + 4 * (int64_t)(ws - 1), 16u, &bar[warp]);
+    };
+
+    if (tid == 0) {
+        for (int k = 0; k < ADJ_W; ++k) mbar_init(&bar[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int p = tid; p < A.npix; p += ADJ_T) w_s[p] = w[p];
+    for (int t = tid; t < A.Bp; t += ADJ_T) V[t] = 0.f;
+    __syncthreads();
+    int64_t ob = A.off[v0], oe = A.off[v0 + 1];
+    if (lane == 0) issue(ob, oe);
+    int64_t on0 = oe, on1 = A.off[min(v0 + 2, A.R)];   // the next voxel's list
+    uint32_t par = 0u;       // parity of the warp's outstanding phase
+    bool pending = true;     // lane 0: a staged copy is in flight
+    bool ok = true;
     for (int v = v0; v < v1; ++v) {
-        for (int t = tid; t < A.Bp; t += RT) {
-            LO[t] = 0.f;
-            HI[t] = 0.f;
-        }
-        __syncthreads();
-        const int64_t b = A.off[v], e = A.off[v + 1];
-        const int64_t n = e - b;
-        const int64_t seg = ((n + 31) / 32 + 31) / 32 * 32;
-        const int64_t sb = min(e, b + warp * seg), se = min(e, sb + seg);
-        uint32_t ct = SENT;       // carried run (warp-uniform)
-        float clo = 0.f, chi = 0.f;
-        bool first_pending = true;  // the segment's first run goes to side[warp][0]
-        const int nbat = (int)((se - sb + 31) / 32);
-        for (int g0 = 0; g0 < nbat; g0 += PREF) {
-            // issue the loads of PREF batches before reducing any of them
-            uint32_t kk[PREF];
-            float a0[PREF], a1[PREF];
-#pragma unroll
-            for (int bb = 0; bb < PREF; ++bb) {
-                const int64_t q = sb + (int64_t)(g0 + bb) * 32 + lane;
-                kk[bb] = SENT;
-                a0[bb] = a1[bb] = 0.f;
-                if (g0 + bb < nbat && q < se) {
-                    kk[bb] = A.key[q];
-                    a0[bb] = A.w0[q];
-                    a1[bb] = A.w1[q];
+        const int late = mbar_wait(&bar[warp], par) ? 0 : 1;
+        int ws, we, perq;
+        segment(ob, oe, ws, we, perq);
+        const int q0 = min(we, ws + lane * perq), q1 = min(we, q0 + perq);
+        const int i0 = q0 - ws, sb = warp * ADJ_SQ;
+        const uint4 *K4 = reinterpret_cast<const uint4 *>(A.key + ob);
+        const float4 *A4 = reinterpret_cast<const float4 *>(A.w0 + ob);
+        const float4 *C4 = reinterpret_cast<const float4 *>(A.w1 + ob);
+        uint4 k0 = make_uint4(0u, 0u, 0u, 0u), k1 = k0;
+        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, c0 = a0, c1 = a0;
+        uint32_t kprev = 0u;
+        if (!late) {
+            if (q0 < q1) {
+                if (i0 < ADJ_SQ) { k0 = stg_k[sb + i0]; a0 = stg_a[sb + i0]; c0 = stg_c[sb + i0]; }
+                else { k0 = K4[q0]; a0 = A4[q0]; c0 = C4[q0]; }
+                if (q0 > 0) {
+                    if (lane == 0) kprev = stg_p[warp].w;
+                    else if (i0 - 1 < ADJ_SQ) kprev = stg_k[sb + i0 - 1].w;
+                    else kprev = A.key[ob + 4 * (int64_t)q0 - 1];
                 }
             }
-#pragma unroll
-            for (int bb = 0; bb < PREF; ++bb) {
-                if (g0 + bb >= nbat) break;
-                const bool valid = kk[bb] != SENT;
-                uint32_t t = SENT;
-                float lo = 0.f, hi = 0.f;
-                if (valid) {
-                    t = kk[bb] >> 16;
-                    const float x = w_s[kk[bb] & 0xffffu];
-                    lo = a0[bb] * x;
-                    hi = a1[bb] * x;
-                }
-                const uint32_t t0 = __shfl_sync(0xffffffffu, t, 0);
-                if (ct != SENT && t0 != ct) {
-                    // the carried run is complete
-                    if (lane == 0) {
-                        if (first_pending) side[warp * 2] = Side{ct, clo, chi};
-                        else { LO[ct] = clo; HI[ct] = chi; }
+            if (q0 + 1 < q1) {
+                if (i0 + 1 < ADJ_SQ) { k1 = stg_k[sb + i0 + 1]; a1 = stg_a[sb + i0 + 1]; c1 = stg_c[sb + i0 + 1]; }
+                else { k1 = K4[q0 + 1]; a1 = A4[q0 + 1]; c1 = C4[q0 + 1]; }
+            }
+            // `dep` is 0 but depends on every register read from the stage, so the
+            // warp barrier below is passed only once those reads have completed.
+            unsigned dep = k0.x ^ k0.y ^ k0.z ^ k0.w ^ k1.x ^ k1.y ^ k1.z ^ k1.w ^ kprev ^
+                           __float_as_uint(a0.x) ^ __float_as_uint(a0.y) ^ __float_as_uint(a0.z) ^
+                           __float_as_uint(a0.w) ^ __float_as_uint(a1.x) ^ __float_as_uint(a1.y) ^
+                           __float_as_uint(a1.z) ^ __float_as_uint(a1.w) ^ __float_as_uint(c0.x) ^
+                           __float_as_uint(c0.y) ^ __float_as_uint(c0.z) ^ __float_as_uint(c0.w) ^
+                           __float_as_uint(c1.x) ^ __float_as_uint(c1.y) ^ __float_as_uint(c1.z) ^
+                           __float_as_uint(c1.w);
+            asm volatile("and.b32 %0, %0, 0;" : "+r"(dep));
+            kprev += dep;
+        }
+        __syncwarp();
+        if (lane == 0 && !late) {
+            par ^= 1u;
+            pending = false;
+            if (v + 1 < v1) {
+                issue(on0, on1);
+                pending = true;
+            }
+        }
+        ob = on0;
+        oe = on1;
+        on0 = on1;
+        on1 = A.off[min(v + 3, A.R)];
+        if (lane != 0 && !late) par ^= 1u;
+
+        // A part that does not start the voxel begins inside the run of the record
+        // before it, with zero partial sums (a zero slot if that run ends there).
+        uint32_t ct = SENT, pt = SENT, st = SENT;
+        bool cont = false;
+        float clo = 0.f, chi = 0.f, ph = 0.f, slo = 0.f, shi = 0.f;
+        if (!late && q0 < q1) {
+            cont = q0 > 0;
+            ct = (cont ? kprev : k0.x) >> 16;
+            auto take = [&](uint32_t k, float wa, float wb) {
+                const uint32_t t = k >> 16;
+                const float x = w_s[k & 0xffffu];
+                if (t != ct) {
+                    if (cont) {   // the continued run ends inside the part
+                        st = ct;
+                        slo = clo;
+                        shi = chi;
+                        cont = false;
+                    } else {      // a complete head run
+                        const float lo = clo + (pt + 1 == ct ? ph : 0.f);
+                        if (pt != SENT && pt + 1 != ct) V[pt + 1] = ph;
+                        V[ct] = lo;
+                        pt = ct;
+                        ph = chi;
                     }
-                    first_pending = false;
-                    ct = SENT;
+                    ct = t;
+                    clo = 0.f;
+                    chi = 0.f;
                 }
-                if (ct != SENT && lane == 0) {
-                    lo += clo;
-                    hi += chi;
-                }
-                // inclusive segmented scan over equal t (records are sorted, runs contiguous)
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const float ylo = __shfl_up_sync(0xffffffffu, lo, o);
-                    const float yhi = __shfl_up_sync(0xffffffffu, hi, o);
-                    const uint32_t yt = __shfl_up_sync(0xffffffffu, t, o);
-                    if (lane >= o && yt == t) {
-                        lo += ylo;
-                        hi += yhi;
-                    }
-                }
-                // the run holding the batch's last valid record may continue into the
-                // next batch: it becomes the carry; every run ending before it is complete
-                const int last = 31 - __clz(__ballot_sync(0xffffffffu, valid));
-                const uint32_t tn = __shfl_down_sync(0xffffffffu, t, 1);
-                const bool run_end = valid && (lane < last) && (tn != t);
-                const unsigned ends = __ballot_sync(0xffffffffu, run_end);
-                if (run_end) {
-                    const bool is_first = first_pending && ((ends & ((1u << lane) - 1u)) == 0);
-                    if (is_first) side[warp * 2] = Side{t, lo, hi};
-                    else { LO[t] = lo; HI[t] = hi; }
-                }
-                if (ends) first_pending = false;
-                ct = __shfl_sync(0xffffffffu, t, last);
-                clo = __shfl_sync(0xffffffffu, lo, last);
-                chi = __shfl_sync(0xffffffffu, hi, last);
+                clo = fmaf(wa, x, clo);
+                chi = fmaf(wb, x, chi);
+            };
+            auto take4 = [&](const uint4 &k, const float4 &a, const float4 &c) {
+                take(k.x, a.x, c.x);
+                take(k.y, a.y, c.y);
+                take(k.z, a.z, c.z);
+                take(k.w, a.w, c.w);
+            };
+            take4(k0, a0, c0);
+            if (q0 + 1 < q1) take4(k1, a1, c1);
+            for (int q = q0 + 2; q < q1; ++q) take4(K4[q], A4[q], C4[q]);
+            if (cont) {      // the whole part continues one run
+                st = ct;
+                slo = clo;
+                shi = chi;
+                ct = SENT;
             }
         }
-        if (lane == 0) {
-            if (ct != SENT && first_pending) {
-                side[warp * 2] = Side{ct, clo, chi};
-                side[warp * 2 + 1] = Side{SENT, 0.f, 0.f};
-            } else {
-                if (first_pending) side[warp * 2] = Side{SENT, 0.f, 0.f};
-                side[warp * 2 + 1] = ct != SENT ? Side{ct, clo, chi} : Side{SENT, 0.f, 0.f};
+        slot_t[tid] = st;
+        slot_lo[tid] = slo;
+        slot_hi[tid] = shi;
+        if (__syncthreads_or(late)) {   // block-uniform decision
+            ok = false;
+            break;
+        }
+        if (ct != SENT) {    // the last head run: add its continuations, in order
+            for (int k = tid + 1; k < ADJ_T && slot_t[k] == ct; ++k) {
+                clo += slot_lo[k];
+                chi += slot_hi[k];
             }
+            float lo = clo;
+            if (pt != SENT) {
+                if (pt + 1 == ct) lo += ph;
+                else V[pt + 1] = ph;
+            }
+            V[ct] = lo;
         }
         __syncthreads();
-        if (warp == 0) {
-            // The side slots, read in warp order, have nondecreasing t once the empty
-            // ones are dropped: compact them (order kept), then sum runs of equal t
-            // with the same carry-based segmented scan and add each run once.
-            int nvalid = 0;
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const Side sd = side[32 * r + lane];
-                const bool val = sd.t != SENT;
-                const unsigned bal = __ballot_sync(0xffffffffu, val);
-                if (val) comp[nvalid + __popc(bal & ((1u << lane) - 1u))] = sd;
-                nvalid += __popc(bal);
-            }
-            __syncwarp();
-            uint32_t mt = SENT;
-            float mlo = 0.f, mhi = 0.f;
-            for (int r = 0; r * 32 < nvalid; ++r) {
-                const int idx = 32 * r + lane;
-                const bool valid = idx < nvalid;
-                uint32_t t = SENT;
-                float lo = 0.f, hi = 0.f;
-                if (valid) {
-                    const Side sd = comp[idx];
-                    t = sd.t;
-                    lo = sd.lo;
-                    hi = sd.hi;
-                }
-                const uint32_t t0 = __shfl_sync(0xffffffffu, t, 0);
-                if (mt != SENT && t0 != mt) {
-                    if (lane == 0) { LO[mt] += mlo; HI[mt] += mhi; }
-                    mt = SENT;
-                }
-                if (mt != SENT && lane == 0) { lo += mlo; hi += mhi; }
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const float ylo = __shfl_up_sync(0xffffffffu, lo, o);
-                    const float yhi = __shfl_up_sync(0xffffffffu, hi, o);
-                    const uint32_t yt = __shfl_up_sync(0xffffffffu, t, o);
-                    if (lane >= o && yt == t) { lo += ylo; hi += yhi; }
-                }
-                const int last = 31 - __clz(__ballot_sync(0xffffffffu, valid));
-                const uint32_t tn = __shfl_down_sync(0xffffffffu, t, 1);
-                if (valid && lane < last && tn != t) { LO[t] += lo; HI[t] += hi; }
-                mt = __shfl_sync(0xffffffffu, t, last);
-                mlo = __shfl_sync(0xffffffffu, lo, last);
-                mhi = __shfl_sync(0xffffffffu, hi, last);
-            }
-            if (mt != SENT && lane == 0) { LO[mt] += mlo; HI[mt] += mhi; }
-        }
+        if (ct != SENT) V[ct + 1] += chi;
         __syncthreads();
+        // write the row (all Bp entries, whole quads) and clear V for the next voxel
         OutT *vrow = Vtab + (int64_t)v * A.Bp;
+        float4 *V4 = reinterpret_cast<float4 *>(V);
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (Vlo) {
             float *lrow = Vlo + (int64_t)v * A.Bp;
-            for (int t = tid; t < A.B; t += RT) {
-                float h, l;
-                tf32_split(LO[t] + (t > 0 ? HI[t - 1] : 0.f), h, l);
-                store_v(vrow + t, h);
-                lrow[t] = l;
+            for (int t4 = tid; t4 < (A.Bp >> 2); t4 += ADJ_T) {
+                const float4 x = V4[t4];
+                float4 h, l;
+                tf32_split(x.x, h.x, l.x);
+                tf32_split(x.y, h.y, l.y);
+                tf32_split(x.z, h.z, l.z);
+                tf32_split(x.w, h.w, l.w);
+                store_v4(vrow + 4 * t4, h);
+                reinterpret_cast<float4 *>(lrow)[t4] = l;
+                V4[t4] = zero4;
             }
         } else {
-            for (int t = tid; t < A.B; t += RT) store_v(vrow + t, LO[t] + (t > 0 ? HI[t - 1] : 0.f));
+            for (int t4 = tid; t4 < (A.Bp >> 2); t4 += ADJ_T) {
+                store_v4(vrow + 4 * t4, V4[t4]);
+                V4[t4] = zero4;
+            }
         }
         __syncthreads();
+    }
+    if (!ok && lane == 0) {
+        // a copy did not land in time: report, drain this warp's copy in flight, stop
+        atomicExch(err, 1);
+        if (pending) mbar_wait(&bar[warp], par);
     }
 }
 
@@ -465,7 +539,8 @@ size_t fwd_rec_smem(int npix, int Bp) {
     return (size_t)((npix + 3) & ~3) * 4 + 2 * (size_t)Bp * 4 + 16;
 }
 size_t adj_rec_smem(int npix, int Bp) {
-    return (size_t)((npix + 3) & ~3) * 4 + 2 * (size_t)Bp * 4 + 128 * sizeof(Side);
+    return (size_t)((npix + 3) & ~3) * 4 + (size_t)Bp * 4 + (size_t)ADJ_W * ADJ_SQ * 48 + ADJ_W * 16 +
+           3 * (size_t)ADJ_T * 4 + ADJ_W * 8;
 }
 
 }  // namespace
@@ -508,13 +583,19 @@ caxsi_status records_build(caxsi_plan *p, TablePath *T) {
         return CAXSI_ERR_CUDA;
     }
     cudaFree(cnt);
+    // every voxel's list is padded to a multiple of 4 records (whole 16-byte quads)
+    int64_t n_real = 0;
     h[0] = 0;
-    for (int v = 0; v < g.R; ++v) h[v + 1] += h[v];
+    for (int v = 0; v < g.R; ++v) {
+        n_real += h[v + 1];
+        h[v + 1] = h[v] + ((h[v + 1] + 3) & ~int64_t(3));
+    }
     const int64_t n = h[g.R];
+    const int64_t npad = n > 0 ? n : 4;
     if (cudaMalloc(&T->rec_off, (size_t)(g.R + 1) * sizeof(int64_t)) != cudaSuccess ||
-        cudaMalloc(&T->rec_key, (size_t)(n > 0 ? n : 1) * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&T->rec_w0, (size_t)(n > 0 ? n : 1) * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&T->rec_w1, (size_t)(n > 0 ? n : 1) * sizeof(float)) != cudaSuccess) {
+        cudaMalloc(&T->rec_key, (size_t)npad * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&T->rec_w0, (size_t)npad * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&T->rec_w1, (size_t)npad * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         records_free(T);
         return CAXSI_OK;
@@ -531,7 +612,7 @@ caxsi_status records_build(caxsi_plan *p, TablePath *T) {
         records_free(T);
         return CAXSI_ERR_CUDA;
     }
-    T->n_rec = n;
+    T->n_rec = n_real;
     T->use_records = true;
     int chunks = 2 * p->num_sms;
     if (chunks > g.R) chunks = g.R;
@@ -557,7 +638,8 @@ cudaError_t launch_adj_rec(const caxsi_plan *p, const TablePath *T, const float 
     const size_t smem = adj_rec_smem(npix, T->Bp);
     cudaError_t e = cudaFuncSetAttribute(k_adj_rec<OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_adj_rec<OutT><<<T->rec_chunks, RT, smem, s>>>(rec_args(p, T), w, out, lo, T->rec_vc);
+    k_adj_rec<OutT><<<T->rec_chunks, ADJ_T, smem, s>>>(rec_args(p, T), w, out, lo, T->rec_vc,
+                                                       p->err_flag + 1);
     return cudaGetLastError();
 }
 
