@@ -312,6 +312,48 @@ def em_iteration(A, At, y, r, f_hat, b1, beta, delta):
 # Ordered subsets (Sec. VI)
 # ---------------------------------------------------------------------------
 
+def os_pixel_mask(M, N, rows, cols):
+    """Boolean [M, N] mask of one subset from its 1-based row and column lists."""
+    m = np.zeros((M, N), dtype=bool)
+    m[np.ix_(np.asarray(rows) - 1, np.asarray(cols) - 1)] = True
+    return m
+
+
+def os_b1(At, in_subset):
+    """b1_p = A_p^T 1 = A^T (indicator of the subset's pixels) (Algorithm 5)."""
+    return At(np.asarray(in_subset, dtype=np.float64))
+
+
+def os_sub_iteration(A, At, y, r, f_hat, in_subset, b1_p, beta_p, delta):
+    """One inner step of the ordered-subset EM-type algorithm (Algorithm 5, Sec. VI).
+
+    A_p is A restricted to the rows (pixels) of subset p, so z_p = (A f + r) on
+    the subset, b2_p = A_p^T (y_p / z_p) = A^T of the ratio with zeros outside
+    the subset, and f is updated by Eq. 10 with b1_p = A_p^T 1 in place of b1.
+    beta_p is the penalty weight used in this step (the OS passes use beta / P:
+    the subset data term stands for 1/P of the full one).  Returns
+    (f_next, L_p(f_hat)) with L_p the likelihood of the subset's counts.
+    """
+    in_subset = np.asarray(in_subset, dtype=bool)
+    z = A(f_hat) + r
+    if np.any(in_subset & (y > 0) & (z <= 0)):
+        raise ValueError("positive count with non-positive mean")
+    ok = in_subset & (z > 0)
+    ratio = np.where(ok, y / np.where(ok, z, 1.0), 0.0)
+    b2 = At(ratio)
+    return em_update(f_hat, b1_p, b2, beta_p, delta), nll(y[in_subset], z[in_subset])
+
+
+def os_em_pass(A, At, y, r, f_hat, masks, b1s, beta, delta):
+    """One pass t -> t+1 of Algorithm 5 over the P subsets in order, each step
+    with penalty weight beta / P."""
+    P = len(masks)
+    f = f_hat
+    for m, b1_p in zip(masks, b1s):
+        f, _ = os_sub_iteration(A, At, y, r, f, m, b1_p, beta / P, delta)
+    return f
+
+
 def os_subsets(M, N, rho_y, rho_z):
     """Symmetry-preserving detector partition of Sec. VI, 1-based as in the paper.
 

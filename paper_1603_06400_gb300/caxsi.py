@@ -130,6 +130,32 @@ def _dev(t, n, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def os_partition(M: int, N: int, rho_y: int, rho_z: int, sigma_y: int | None = None) -> np.ndarray:
+    """Subset index of every detector pixel (int32 [M*N], row-major in (m, n)) for
+    the symmetry-preserving ordered-subset partition of Sec. VI.
+
+    Rows: the top half is split into rho_z classes of step rho_z, and each row's
+    mirror image about the centre line z = 0 joins its class.  Columns: classes of
+    step sigma_y, each joined by its mirror image about y = 0, so sigma_y / 2 column
+    classes.  sigma_y must be even, divide N, and be a multiple of the translation
+    step rho_y (so that translation symmetry is kept); it defaults to rho_y when
+    rho_y is even and to 16 * rho_y otherwise (the paper's example uses 16).
+    Subset index = row class * (sigma_y / 2) + column class.
+    """
+    if sigma_y is None:
+        sigma_y = rho_y if rho_y % 2 == 0 else 16 * rho_y
+    if M % 2 or (M // 2) % rho_z or rho_z < 1:
+        raise ValueError("rho_z must divide M / 2 (M even)")
+    if sigma_y < 2 or sigma_y % 2 or N % sigma_y or sigma_y % rho_y:
+        raise ValueError("sigma_y must be even, divide N and be a multiple of rho_y")
+    m = np.arange(M)
+    row_class = np.where(m < M // 2, m, M - 1 - m) % rho_z
+    n = np.arange(N) % sigma_y
+    col_class = np.minimum(n, sigma_y - 1 - n)
+    sub = row_class[:, None] * (sigma_y // 2) + col_class[None, :]
+    return np.ascontiguousarray(sub.reshape(-1), dtype=np.int32)
+
+
 class Plan:
     """A device plan for one geometry, spectrum and mask (see include/caxsi.h)."""
 

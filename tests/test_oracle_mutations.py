@@ -1,8 +1,9 @@
 """The oracle's pins catch plausible mistakes.
 
 Each case plants one mistake (a dropped factor, a wrong exponent, a swapped
-weight or index, a wrong plane) in a temporary copy of the C oracle, on the
-CPU, and checks that the pin suites fail on it.
+weight or index, a wrong plane, a subset step that leaks outside its subset)
+in a temporary copy of the oracle, on the CPU, and checks that the pin suites
+fail on it.
 """
 import os
 import shutil
@@ -12,38 +13,43 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SRC = os.path.join(ROOT, "oracle", "caxsi_oracle.c")
+C_SRC = "oracle/caxsi_oracle.c"
+PY_SRC = "oracle/__init__.py"
 
 MUTATIONS = {
-    "G_so exponent": ("pow(x * x + y * y, 1.5)", "pow(x * x + y * y, 1.0)"),
-    "G_od power of s": ("(slen * slen * slen)", "(slen * slen)"),
-    "dtheta edge offset": ("double h = 0.5 * g->p_z;", "double h = g->p_z;"),
-    "Bragg half angle": ("o->u = sin(0.5 * o->theta);", "o->u = sin(o->theta);"),
-    "dropped cos(theta/2)": ("* cos(0.5 * o->theta);", ";"),
-    "dropped Jacobian E": ("phi[k] * E * dE / (g->hc * g->hc);\n        acc",
+    "G_so exponent": (C_SRC, "pow(x * x + y * y, 1.5)", "pow(x * x + y * y, 1.0)"),
+    "G_od power of s": (C_SRC, "(slen * slen * slen)", "(slen * slen)"),
+    "dtheta edge offset": (C_SRC, "double h = 0.5 * g->p_z;", "double h = g->p_z;"),
+    "Bragg half angle": (C_SRC, "o->u = sin(0.5 * o->theta);", "o->u = sin(o->theta);"),
+    "dropped cos(theta/2)": (C_SRC, "* cos(0.5 * o->theta);", ";"),
+    "dropped Jacobian E": (C_SRC, "phi[k] * E * dE / (g->hc * g->hc);\n        acc",
                            "phi[k] * dE / (g->hc * g->hc);\n        acc"),
-    "swapped interpolation weights": ("return (1.0 - a) * f0 + a * f1;",
+    "swapped interpolation weights": (C_SRC, "return (1.0 - a) * f0 + a * f1;",
                                       "return a * f0 + (1.0 - a) * f1;"),
-    "mask plane parameter": ("double t = (g->X_mask - x) / (g->X_det - x);",
+    "mask plane parameter": (C_SRC, "double t = (g->X_mask - x) / (g->X_det - x);",
                              "double t = (g->X_det - g->X_mask) / (g->X_det - x);"),
-    "mask row/col transposed": ("mask[(long)rf * g->mask_cols + (long)cf]",
+    "mask row/col transposed": (C_SRC, "mask[(long)rf * g->mask_cols + (long)cf]",
                                 "mask[(long)cf * g->mask_rows + (long)rf]"),
-    "object y pitch": ("* g->rho_y * g->p_y; }", "* g->p_y; }"),
-    "adjoint weight": ("frow[l + 1] += base * ck * a;", "frow[l + 1] += base * ck * (1.0 - a);"),
-    "energy bin centre": ("(k + 0.5) * dE", "(k + 1.0) * dE"),
+    "object y pitch": (C_SRC, "* g->rho_y * g->p_y; }", "* g->p_y; }"),
+    "adjoint weight": (C_SRC, "frow[l + 1] += base * ck * a;", "frow[l + 1] += base * ck * (1.0 - a);"),
+    "energy bin centre": (C_SRC, "(k + 0.5) * dE", "(k + 1.0) * dE"),
+    # ordered subsets (Algorithm 5)
+    "OS ratio outside the subset": (PY_SRC, "ok = in_subset & (z > 0)", "ok = z > 0"),
+    "OS sensitivity of all pixels": (PY_SRC, "return At(np.asarray(in_subset, dtype=np.float64))",
+                                     "return At(np.ones(np.shape(in_subset)))"),
 }
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_pins_catch_planted_mistake(name, tmp_path):
-    before, after = MUTATIONS[name]
-    src = open(SRC).read()
+    rel, before, after = MUTATIONS[name]
+    src = open(os.path.join(ROOT, rel)).read()
     assert before in src
     for d in ("oracle", "synth", "tests"):
         shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
                         ignore=shutil.ignore_patterns("_build", "__pycache__"))
     shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path / "pytest.ini")
-    (tmp_path / "oracle" / "caxsi_oracle.c").write_text(src.replace(before, after, 1))
+    (tmp_path / rel).write_text(src.replace(before, after, 1))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         "tests/test_oracle_pins.py", "tests/test_oracle_recon.py"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=600)

@@ -161,3 +161,60 @@ def test_os_partition_matches_worked_example():
     for rws, cls in subs:
         cover[np.ix_(rws - 1, cls - 1)] += 1
     assert np.all(cover == 1)
+
+
+# ---------------------------------------------------------------------------
+# Ordered subsets (Algorithm 5, Sec. VI)
+# ---------------------------------------------------------------------------
+
+def _os_masks(g, rho_z, sigma_y):
+    return [oracle.os_pixel_mask(g.M, g.N, rows, cols)
+            for rows, cols in oracle.os_subsets(g.M, g.N, sigma_y, rho_z)]
+
+
+def test_os_single_subset_is_the_em_iteration():
+    g, A, At, y, _ = _small_problem(2)
+    r = np.full_like(y, 0.25)
+    b1 = At(np.ones_like(y))
+    f = np.full((g.X, g.J, g.Q), y.sum() / b1.sum())
+    every = np.ones((g.M, g.N), bool)
+    f1, L1 = oracle.os_sub_iteration(A, At, y, r, f, every, oracle.os_b1(At, every), 0.3, 0.05)
+    f2, L2 = oracle.em_iteration(A, At, y, r, f, b1, 0.3, 0.05)
+    np.testing.assert_array_equal(f1, f2)
+    assert L1 == L2
+
+
+def test_os_subset_sensitivities_sum_to_b1():
+    g, A, At, y, _ = _small_problem(3)
+    masks = _os_masks(g, 2, 4)
+    assert len(masks) == 4
+    np.testing.assert_allclose(sum(oracle.os_b1(At, m) for m in masks), At(np.ones_like(y)),
+                               rtol=1e-12, atol=1e-300)
+
+
+def test_os_step_preserves_the_subset_counts():
+    # with beta = 0 and r = 0 each step is MLEM on its subset:
+    # sum_{i in S_p} (A f')_i = sum_j f_j b2_pj = sum_{i in S_p} y_i (exact algebra)
+    g, A, At, y, _ = _small_problem(4)
+    r = np.zeros_like(y)
+    masks = _os_masks(g, 2, 4)
+    b1s = [oracle.os_b1(At, m) for m in masks]
+    f = np.full((g.X, g.J, g.Q), y.sum() / sum(b.sum() for b in b1s))
+    for m, b1p in zip(masks, b1s):
+        f_new, _ = oracle.os_sub_iteration(A, At, y, r, f, m, b1p, 0.0, 0.1)
+        assert A(f_new)[m].sum() == pytest.approx(y[m].sum(), rel=1e-10)
+        # pixels outside the subset do not enter the step
+        y_other = np.where(m, y, y + 7.0)
+        f_alt, _ = oracle.os_sub_iteration(A, At, y_other, r, f, m, b1p, 0.0, 0.1)
+        np.testing.assert_array_equal(f_alt, f_new)
+        f = f_new
+
+
+def test_os_pass_reduces_the_likelihood_from_a_flat_start():
+    g, A, At, y, f_true = _small_problem(5)
+    r = np.zeros_like(y)
+    masks = _os_masks(g, 2, 4)
+    b1s = [oracle.os_b1(At, m) for m in masks]
+    f0 = np.full((g.X, g.J, g.Q), y.sum() / sum(b.sum() for b in b1s))
+    f1 = oracle.os_em_pass(A, At, y, r, f0, masks, b1s, 0.0, 0.1)
+    assert oracle.nll(y, A(f1)) < oracle.nll(y, A(f0))
