@@ -154,6 +154,49 @@ caxsi_status caxsi_recon_step(caxsi_plan *plan, const float *y_dev, const float 
                               float *f_dev, int64_t f_len, float beta, float delta,
                               int path, double *nll_out, void *stream);
 
+/* ---- Ordered subsets (Sec. VI, Algorithm 5) ------------------------------------
+ * The detector is split into P disjoint pixel subsets; A_p is A restricted to
+ * the rows (pixels) of subset p.  The paper's symmetry-preserving choice groups
+ * every pixel with its left-right and up-down mirror images and with the
+ * pixels a multiple of the translation step away; any partition is accepted
+ * here (the Python binding builds the paper's one).  Table paths only: the
+ * subset operators stream only the pairs of the subset's pixels (records
+ * grouped by subset), while the q contractions stay whole-object.
+ */
+#define CAXSI_MAX_SUBSETS 1024
+
+/* Set (or replace) the partition.  subset_of_pixel: host, M*N int32 in
+ * [0, n_subsets), row-major (m, n).  Builds the grouped pair records on the
+ * device (synchronous) and drops the cached subset sensitivities.
+ * Errors: INVALID (sizes, an index out of range, n_subsets outside
+ * [1, min(CAXSI_MAX_SUBSETS, M*N)]), UNSUPPORTED (the geometry has no pair
+ * records: more than 65536 pixels or knots), CUDA, OOM. */
+caxsi_status caxsi_plan_set_subsets(caxsi_plan *plan, int n_subsets, const int32_t *subset_of_pixel);
+
+/* g = A_p f: g_dev (M*N, device) holds the subset's pixels of A f and 0 at every
+ * other pixel.  Same arguments and errors as caxsi_forward, plus subset in
+ * [0, n_subsets) (INVALID otherwise or before caxsi_plan_set_subsets) and
+ * UNSUPPORTED for CAXSI_PATH_DIRECT. */
+caxsi_status caxsi_forward_subset(caxsi_plan *plan, int subset, const float *f_dev, int64_t f_len,
+                                  float *g_dev, int64_t g_len, int path, void *stream);
+
+/* f = A_p^T w: only the subset's pixels of w_dev are read.  Arguments and
+ * errors as caxsi_forward_subset. */
+caxsi_status caxsi_adjoint_subset(caxsi_plan *plan, int subset, const float *w_dev, int64_t w_len,
+                                  float *f_dev, int64_t f_len, int path, void *stream);
+
+/* One inner step of the ordered-subset EM-type algorithm (Algorithm 5):
+ *   z_p = A_p f + r_p;  b2_p = A_p^T (y_p / z_p);  f <- Eq. 10 with b1_p = A_p^T 1
+ *   (computed on first use per subset and path, cached in the plan).
+ * Only the subset's pixels of y_dev and r_dev are read; nll_out receives the
+ * subset's likelihood L_p(f_in).  beta is the penalty weight of this step: the
+ * ordered-subset pass of the Python binding passes beta / P, so that the
+ * subset's data term stands for 1/P of the full one.  Edge rules and errors as
+ * caxsi_recon_step, plus those of caxsi_forward_subset. */
+caxsi_status caxsi_recon_step_subset(caxsi_plan *plan, int subset, const float *y_dev, const float *r_dev,
+                                     float *f_dev, int64_t f_len, float beta, float delta, int path,
+                                     double *nll_out, void *stream);
+
 /* Host-buffer forms: copy the input from host memory to plan-owned device
  * staging buffers, evaluate, copy the result back to host memory, and
  * synchronise before returning.  Pinned host memory gives the fastest copies.

@@ -94,11 +94,19 @@ def load():
             lib.caxsi_profile_enable.argtypes = [P, ctypes.c_int]
             lib.caxsi_profile_read.argtypes = [P, ctypes.POINTER(CKernelStat), ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_int)]
+            lib.caxsi_plan_set_subsets.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]
+            lib.caxsi_forward_subset.argtypes = [P, ctypes.c_int, P, I64, P, I64, ctypes.c_int, P]
+            lib.caxsi_adjoint_subset.argtypes = [P, ctypes.c_int, P, I64, P, I64, ctypes.c_int, P]
+            lib.caxsi_recon_step_subset.argtypes = [P, ctypes.c_int, P, P, P, I64, ctypes.c_float,
+                                                    ctypes.c_float, ctypes.c_int,
+                                                    ctypes.POINTER(ctypes.c_double), P]
             lib.caxsi_status_string.argtypes = [ctypes.c_int]
             lib.caxsi_status_string.restype = ctypes.c_char_p
             for name in ("caxsi_plan_create", "caxsi_forward", "caxsi_adjoint",
                          "caxsi_recon_step", "caxsi_forward_host", "caxsi_adjoint_host",
-                         "caxsi_plan_info", "caxsi_profile_enable", "caxsi_profile_read"):
+                         "caxsi_plan_info", "caxsi_profile_enable", "caxsi_profile_read",
+                         "caxsi_plan_set_subsets", "caxsi_forward_subset", "caxsi_adjoint_subset",
+                         "caxsi_recon_step_subset"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -206,6 +214,56 @@ class Plan:
             float(beta), float(delta), int(path),
             ctypes.byref(nll) if want_nll else None, _stream_handle(stream)), "caxsi_recon_step")
         return nll.value if want_nll else None
+
+    # -- ordered subsets (Sec. VI, Algorithm 5) --------------------------------
+    def set_subsets(self, subset_of_pixel):
+        """Set the detector partition (M*N subset indexes, e.g. from os_partition)."""
+        sub = np.ascontiguousarray(np.asarray(subset_of_pixel).reshape(-1), dtype=np.int32)
+        if sub.size != self.g_len:
+            raise ValueError("subset_of_pixel must have M*N entries")
+        n = int(sub.max()) + 1 if sub.size else 0
+        _check(self.lib.caxsi_plan_set_subsets(self.handle, n, sub.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_int32))), "caxsi_plan_set_subsets")
+        self.n_subsets = n
+
+    def forward_subset(self, subset, f, out=None, path=PATH_TABLE_FP32, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.M, self.N), device=f.device, dtype=torch.float32)
+        _check(self.lib.caxsi_forward_subset(self.handle, int(subset), _dev(f, self.f_len, "f"), self.f_len,
+                                             _dev(out, self.g_len, "g"), self.g_len, int(path),
+                                             _stream_handle(stream)), "caxsi_forward_subset")
+        return out
+
+    def adjoint_subset(self, subset, w, out=None, path=PATH_TABLE_FP32, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.X, self.J, self.Q), device=w.device, dtype=torch.float32)
+        _check(self.lib.caxsi_adjoint_subset(self.handle, int(subset), _dev(w, self.g_len, "w"), self.g_len,
+                                             _dev(out, self.f_len, "f"), self.f_len, int(path),
+                                             _stream_handle(stream)), "caxsi_adjoint_subset")
+        return out
+
+    def recon_step_subset(self, subset, y, f, r=None, beta=0.0, delta=0.0, path=PATH_TABLE_FP32,
+                          want_nll=False, stream=None):
+        nll = ctypes.c_double(0.0)
+        rp = _dev(r, self.g_len, "r") if r is not None else ctypes.c_void_p(None)
+        _check(self.lib.caxsi_recon_step_subset(
+            self.handle, int(subset), _dev(y, self.g_len, "y"), rp, _dev(f, self.f_len, "f"), self.f_len,
+            float(beta), float(delta), int(path), ctypes.byref(nll) if want_nll else None,
+            _stream_handle(stream)), "caxsi_recon_step_subset")
+        return nll.value if want_nll else None
+
+    def os_pass(self, y, f, r=None, beta=0.0, delta=0.0, path=PATH_TABLE_FP32, stream=None):
+        """One pass of Algorithm 5 over the subsets in order, in place on f; each
+        step uses the penalty weight beta / P (the subset's data term stands for
+        1/P of the full one)."""
+        P = getattr(self, "n_subsets", 0)
+        if P < 1:
+            raise CaxsiError("set_subsets has not been called")
+        for p in range(P):
+            self.recon_step_subset(p, y, f, r=r, beta=beta / P, delta=delta, path=path, stream=stream)
+        return f
 
     # -- host-buffer calls ----------------------------------------------------
     def forward_host(self, f, out=None, path=PATH_DIRECT):

@@ -65,6 +65,7 @@ void free_plan(caxsi_plan *p) {
     cudaFree(p->ratio);
     cudaFree(p->ones);
     for (int k = 0; k < 4; ++k) cudaFree(p->b1[k]);
+    for (int k = 0; k < 4; ++k) cudaFree(p->b1_sub[k]);
     cudaFree(p->b2);
     cudaFree(p->fnew);
     cudaFree(p->nll_part);
@@ -107,15 +108,26 @@ caxsi_status alloc_scratch(caxsi_plan *p) {
 
 bool path_ok(int path) { return path >= CAXSI_PATH_DIRECT && path <= CAXSI_PATH_TABLE_FP16; }
 
-caxsi_status run_forward(caxsi_plan *p, const float *f, float *g, int path, cudaStream_t s) {
-    if (path == CAXSI_PATH_DIRECT) return direct_forward(p, f, g, s);
-    return table_forward(p, f, g, path, s);
+// subset < 0: the full operator; else the rows of that detector subset (table paths).
+caxsi_status run_forward(caxsi_plan *p, const float *f, float *g, int path, cudaStream_t s, int subset = -1) {
+    if (path == CAXSI_PATH_DIRECT) return subset < 0 ? direct_forward(p, f, g, s) : CAXSI_ERR_UNSUPPORTED;
+    return table_forward(p, f, g, path, subset, s);
 }
 
-caxsi_status run_adjoint(caxsi_plan *p, const float *w, float *f, int path, cudaStream_t s) {
-    if (path == CAXSI_PATH_DIRECT) return direct_adjoint(p, w, f, s);
-    return table_adjoint(p, w, f, path, s);
+caxsi_status run_adjoint(caxsi_plan *p, const float *w, float *f, int path, cudaStream_t s, int subset = -1) {
+    if (path == CAXSI_PATH_DIRECT) return subset < 0 ? direct_adjoint(p, w, f, s) : CAXSI_ERR_UNSUPPORTED;
+    return table_adjoint(p, w, f, path, subset, s);
 }
+
+void drop_subset_sensitivities(caxsi_plan *p) {
+    for (int k = 0; k < 4; ++k) {
+        cudaFree(p->b1_sub[k]);
+        p->b1_sub[k] = nullptr;
+        p->b1_sub_ok[k].clear();
+    }
+}
+
+bool subset_ok(const caxsi_plan *p, int subset) { return subset >= 0 && subset < p->n_subsets; }
 
 }  // namespace
 
@@ -219,7 +231,7 @@ caxsi_status caxsi_recon_step(caxsi_plan *p, const float *y_dev, const float *r_
     }
     // z = A f + r, ratio = y / z, L(f) in FP64
     if ((st = run_forward(p, f_dev, p->gtmp, path, s)) != CAXSI_OK) return st;
-    if ((st = recon_ratio(p, y_dev, r_dev, s)) != CAXSI_OK) return st;
+    if ((st = recon_ratio(p, y_dev, r_dev, nullptr, -1, s)) != CAXSI_OK) return st;
     if (nll_out) {
         int64_t keep = p->launches;
         st = recon_nll_fetch(p, nll_out, s);
@@ -229,6 +241,83 @@ caxsi_status caxsi_recon_step(caxsi_plan *p, const float *y_dev, const float *r_
     // b2 = A^T (y / z), then the closed-form update
     if ((st = run_adjoint(p, p->ratio, p->b2, path, s)) != CAXSI_OK) return st;
     if ((st = recon_update(p, f_dev, beta, delta, p->b1[path], s)) != CAXSI_OK) return st;
+    CAXSI_CUDA_TRY(cudaMemcpyAsync(f_dev, p->fnew, nf * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return CAXSI_OK;
+}
+
+caxsi_status caxsi_plan_set_subsets(caxsi_plan *p, int n_subsets, const int32_t *subset_of_pixel) {
+    if (!p || !subset_of_pixel) return CAXSI_ERR_INVALID;
+    const int64_t npix = (int64_t)p->dg.M * p->dg.N;
+    if (n_subsets < 1 || n_subsets > CAXSI_MAX_SUBSETS || n_subsets > npix) return CAXSI_ERR_INVALID;
+    for (int64_t k = 0; k < npix; ++k)
+        if (subset_of_pixel[k] < 0 || subset_of_pixel[k] >= n_subsets) return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return CAXSI_ERR_CUDA;
+    p->n_subsets = 0;
+    drop_subset_sensitivities(p);
+    caxsi_status st = table_set_subsets(p, n_subsets, subset_of_pixel);
+    if (st == CAXSI_OK) p->n_subsets = n_subsets;
+    return st;
+}
+
+caxsi_status caxsi_forward_subset(caxsi_plan *p, int subset, const float *f_dev, int64_t f_len, float *g_dev,
+                                  int64_t g_len, int path, void *stream) {
+    if (!p || !f_dev || !g_dev || !path_ok(path) || !subset_ok(p, subset)) return CAXSI_ERR_INVALID;
+    if (f_len != (int64_t)p->dg.R * p->dg.Q || g_len != (int64_t)p->dg.M * p->dg.N)
+        return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return CAXSI_ERR_CUDA;
+    p->launches = 0;
+    return run_forward(p, f_dev, g_dev, path, (cudaStream_t)stream, subset);
+}
+
+caxsi_status caxsi_adjoint_subset(caxsi_plan *p, int subset, const float *w_dev, int64_t w_len, float *f_dev,
+                                  int64_t f_len, int path, void *stream) {
+    if (!p || !f_dev || !w_dev || !path_ok(path) || !subset_ok(p, subset)) return CAXSI_ERR_INVALID;
+    if (f_len != (int64_t)p->dg.R * p->dg.Q || w_len != (int64_t)p->dg.M * p->dg.N)
+        return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return CAXSI_ERR_CUDA;
+    p->launches = 0;
+    return run_adjoint(p, w_dev, f_dev, path, (cudaStream_t)stream, subset);
+}
+
+caxsi_status caxsi_recon_step_subset(caxsi_plan *p, int subset, const float *y_dev, const float *r_dev,
+                                     float *f_dev, int64_t f_len, float beta, float delta, int path,
+                                     double *nll_out, void *stream) {
+    if (!p || !y_dev || !f_dev || !path_ok(path) || !subset_ok(p, subset)) return CAXSI_ERR_INVALID;
+    if (f_len != (int64_t)p->dg.R * p->dg.Q) return CAXSI_ERR_INVALID;
+    if (!isfinite(beta) || beta < 0.f || !isfinite(delta) || delta < 0.f) return CAXSI_ERR_INVALID;
+    if (path == CAXSI_PATH_DIRECT) return CAXSI_ERR_UNSUPPORTED;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return CAXSI_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    p->launches = 0;
+    const int64_t nf = (int64_t)p->dg.R * p->dg.Q;
+    caxsi_status st;
+    if (!p->b1_sub[path]) {
+        CAXSI_CUDA_TRY(cudaMalloc(&p->b1_sub[path], (size_t)p->n_subsets * nf * sizeof(float)));
+        p->b1_sub_ok[path].assign(p->n_subsets, 0);
+        p->table_bytes += p->n_subsets * nf * 4;
+    }
+    float *b1p = p->b1_sub[path] + (int64_t)subset * nf;
+    if (!p->b1_sub_ok[path][subset]) {
+        // b1_p = A_p^T 1: the subset adjoint reads only the subset's pixels of `ones`
+        if ((st = run_adjoint(p, p->ones, b1p, path, s, subset)) != CAXSI_OK) return st;
+        p->b1_sub_ok[path][subset] = 1;
+    }
+    // z_p = A_p f + r_p, ratio on the subset's pixels, L_p(f) in FP64
+    if ((st = run_forward(p, f_dev, p->gtmp, path, s, subset)) != CAXSI_OK) return st;
+    if ((st = recon_ratio(p, y_dev, r_dev, table_subset_of_pixel(p), subset, s)) != CAXSI_OK) return st;
+    if (nll_out) {
+        int64_t keep = p->launches;
+        st = recon_nll_fetch(p, nll_out, s);
+        p->launches = keep;
+        if (st != CAXSI_OK) return st;
+    }
+    // b2_p = A_p^T (y_p / z_p), then the closed-form update with b1_p
+    if ((st = run_adjoint(p, p->ratio, p->b2, path, s, subset)) != CAXSI_OK) return st;
+    if ((st = recon_update(p, f_dev, beta, delta, b1p, s)) != CAXSI_OK) return st;
     CAXSI_CUDA_TRY(cudaMemcpyAsync(f_dev, p->fnew, nf * sizeof(float), cudaMemcpyDeviceToDevice, s));
     return CAXSI_OK;
 }

@@ -66,6 +66,9 @@ struct caxsi_plan {
     float *ratio;       // [M*N]
     float *ones;        // [M*N]
     float *b1[4];       // [R*Q] A^T 1 per path, lazily
+    int n_subsets;      // detector subsets of the ordered-subset operators (0 = none)
+    float *b1_sub[4];   // [n_subsets][R*Q] A_p^T 1 per path, lazily
+    std::vector<unsigned char> b1_sub_ok[4];   // which subsets of b1_sub are computed
     float *b2;          // [R*Q]
     float *fnew;        // [R*Q]
     double *nll_part;   // [nll_blocks]
@@ -94,14 +97,20 @@ void direct_configure(caxsi_plan *p);
 caxsi_status direct_forward_static_scratch(caxsi_plan *p, const float *f, float *g, cudaStream_t s);
 
 // ---- table.cu ----------------------------------------------------------------
-caxsi_status table_forward(caxsi_plan *p, const float *f, float *g, int path, cudaStream_t s);
-caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f, int path, cudaStream_t s);
+// subset < 0: the full operator; else the rows (pixels) of that detector subset.
+caxsi_status table_forward(caxsi_plan *p, const float *f, float *g, int path, int subset, cudaStream_t s);
+caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f, int path, int subset, cudaStream_t s);
+caxsi_status table_set_subsets(caxsi_plan *p, int P, const int32_t *sub_host);
+const int *table_subset_of_pixel(const caxsi_plan *p);
 void table_destroy(caxsi_plan *p);
 int64_t table_breakpoints(const caxsi_plan *p);
 int64_t table_records(const caxsi_plan *p);
 
 // ---- recon.cu ----------------------------------------------------------------
-caxsi_status recon_ratio(caxsi_plan *p, const float *y, const float *r, cudaStream_t s);
+// sub != null: only pixels with sub[i] == subset enter (ratio 0 and no
+// likelihood term elsewhere).
+caxsi_status recon_ratio(caxsi_plan *p, const float *y, const float *r, const int *sub, int subset,
+                         cudaStream_t s);
 caxsi_status recon_update(caxsi_plan *p, const float *f_old, float beta, float delta,
                           const float *b1, cudaStream_t s);
 caxsi_status recon_nll_fetch(caxsi_plan *p, double *out, cudaStream_t s);

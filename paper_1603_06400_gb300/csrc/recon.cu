@@ -15,7 +15,8 @@ constexpr int NLL_THREADS = 256;
 // ratio 0; y_i > 0 with z_i <= 0 raises the plan's error word.
 __global__ void __launch_bounds__(NLL_THREADS)
 k_ratio_nll(const float *__restrict__ g, const float *__restrict__ y, const float *__restrict__ r,
-            float *__restrict__ ratio, double *__restrict__ part, int *err, int64_t n) {
+            const int *__restrict__ sub, int subset, float *__restrict__ ratio, double *__restrict__ part,
+            int *err, int64_t n) {
     __shared__ double sh[NLL_THREADS / 32];
     double local = 0.0;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
@@ -23,7 +24,9 @@ k_ratio_nll(const float *__restrict__ g, const float *__restrict__ y, const floa
         const float z = r ? g[idx] + r[idx] : g[idx];
         const float yy = y[idx];
         float rt = 0.f;
-        if (z > 0.f) {
+        if (sub && sub[idx] != subset) {
+            // outside the subset: no ratio, no likelihood term
+        } else if (z > 0.f) {
             rt = yy / z;
             const double zd = (double)z, yd = (double)yy;
             local += zd - (yd > 0.0 ? yd * log(zd) : 0.0) + lgamma(yd + 1.0);
@@ -98,12 +101,13 @@ __global__ void k_update(DevGeo g, const float *__restrict__ f, const float *__r
 
 }  // namespace
 
-caxsi_status recon_ratio(caxsi_plan *p, const float *y, const float *r, cudaStream_t s) {
+caxsi_status recon_ratio(caxsi_plan *p, const float *y, const float *r, const int *sub, int subset,
+                         cudaStream_t s) {
     const int64_t n = (int64_t)p->dg.M * p->dg.N;
     {
         CAXSI_PROF(p, "ratio_nll", s);
-        k_ratio_nll<<<p->nll_blocks, NLL_THREADS, 0, s>>>(p->gtmp, y, r, p->ratio, p->nll_part,
-                                                          p->err_flag, n);
+        k_ratio_nll<<<p->nll_blocks, NLL_THREADS, 0, s>>>(p->gtmp, y, r, sub, subset, p->ratio,
+                                                          p->nll_part, p->err_flag, n);
     }
     CAXSI_LAUNCH_CHECK(p);
     {

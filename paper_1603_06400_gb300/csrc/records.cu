@@ -38,22 +38,34 @@ constexpr uint32_t WAIT_LIMIT = 1u << 24;
 
 struct RecArgs {
     int R, npix, Bp, B;
+    int ostride, osel;    // voxel v's records: [off[v * ostride + osel], off[v * ostride + osel + 1])
     const int64_t *off;
     const uint32_t *key;
     const float *w0, *w1;
 };
 
-RecArgs rec_args(const caxsi_plan *p, const TablePath *T) {
+// subset < 0: every record of each voxel; else the records of that subset.
+RecArgs rec_args(const caxsi_plan *p, const TablePath *T, int subset) {
+    const RecSet &r = subset < 0 ? T->rec : T->sub;
     RecArgs a;
     a.R = p->dg.R;
     a.npix = p->dg.M * p->dg.N;
     a.Bp = T->Bp;
     a.B = T->B;
-    a.off = T->rec_off;
-    a.key = T->rec_key;
-    a.w0 = T->rec_w0;
-    a.w1 = T->rec_w1;
+    a.ostride = r.P;
+    a.osel = subset < 0 ? 0 : subset;
+    a.off = r.off;
+    a.key = r.key;
+    a.w0 = r.w0;
+    a.w1 = r.w1;
     return a;
+}
+
+__device__ __forceinline__ int64_t rec_begin(const RecArgs &A, int v) {
+    return A.off[(int64_t)v * A.ostride + A.osel];
+}
+__device__ __forceinline__ int64_t rec_end(const RecArgs &A, int v) {
+    return A.off[(int64_t)v * A.ostride + A.osel + 1];
 }
 
 // ---- one pair, as the on-the-fly table kernels evaluate it --------------------
@@ -85,100 +97,113 @@ __device__ __forceinline__ PairRec pair_record(const PairArgs &A, const TabArgs 
     return r;
 }
 
-// Count the records of each voxel (one warp per voxel).
-__global__ void k_rec_count(PairArgs A, TabArgs T, int64_t *cnt) {
+// Count the records of each (voxel, group): one warp per voxel, P counters per
+// warp in shared memory; the group of a pixel is sub[pixel] (group 0 without sub).
+__global__ void k_rec_count(PairArgs A, TabArgs T, const int *sub, int P, int64_t *cnt) {
+    extern __shared__ int cnt_s[];
     const DevGeo &g = A.g;
-    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (v >= g.R) return;
+    if (v >= g.R) return;   // warp-uniform
+    int *c = cnt_s + warp * P;
+    for (int k = lane; k < P; k += 32) c[k] = 0;
+    __syncwarp();
     const float u_first = T.knots[0].x, u_last = T.knots[T.B - 1].x;
     const int i = v / g.J, j = v - i * g.J;
     const float4 vx = A.vox[v];
     const int npix = g.M * g.N;
-    int c = 0;
     for (int p = lane; p < npix; p += 32) {
         const int m = p / g.N, n = p - m * g.N;
-        c += pair_record(A, T, u_first, u_last, v, i, j, vx, m, n).ok ? 1 : 0;
+        if (pair_record(A, T, u_first, u_last, v, i, j, vx, m, n).ok) atomicAdd(&c[sub ? sub[p] : 0], 1);
     }
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-    if (lane == 0) cnt[v] = c;
+    __syncwarp();
+    for (int k = lane; k < P; k += 32) cnt[(int64_t)v * P + k] = c[k];
 }
-
-// Fill the records of each voxel, sorted by (t, pixel): a histogram of t, its
-// exclusive scan, then placement in pixel order with ranks among equal t.
-__global__ void k_rec_fill(PairArgs A, TabArgs T, int wpb, const int64_t *off, uint32_t *key,
-                           float *w0, float *w1) {
+// Fill the records of each (voxel, group), sorted by (t, pixel) within the group:
+// one warp per voxel, a counting sort over t in a per-warp histogram.  Group s
+// holds the pixels sp_pix[sp_off[s] .. sp_off[s+1]) (all pixels when sp_off is
+// null, P = 1).  Each group's list is padded to whole 16-byte quads with
+// zero-weight copies of its last record (same pixel and interval, so the order
+// by t is kept).
+__global__ void k_rec_fill(PairArgs A, TabArgs T, int wpb, int P, const int *sp_off, const int *sp_pix,
+                           const int64_t *off, uint32_t *key, float *w0, float *w1) {
     extern __shared__ __align__(16) int rec_smem[];
     const DevGeo &g = A.g;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int v = blockIdx.x * wpb + warp;
     if (warp >= wpb || v >= g.R) return;
     int *hist = rec_smem + warp * (T.B + 1);
-    for (int t = lane; t <= T.B; t += 32) hist[t] = 0;
-    __syncwarp();
     const float u_first = T.knots[0].x, u_last = T.knots[T.B - 1].x;
     const int i = v / g.J, j = v - i * g.J;
     const float4 vx = A.vox[v];
-    const int npix = g.M * g.N;
-    for (int p = lane; p < npix; p += 32) {
-        const int m = p / g.N, n = p - m * g.N;
-        const PairRec r = pair_record(A, T, u_first, u_last, v, i, j, vx, m, n);
-        if (r.ok) atomicAdd(&hist[r.t], 1);
-    }
-    __syncwarp();
-    // exclusive scan of hist[0..B) by the warp: contiguous chunks per lane
-    const int chunk = (T.B + 31) / 32;
-    const int t0 = min(T.B, lane * chunk), t1 = min(T.B, t0 + chunk);
-    int local = 0;
-    for (int t = t0; t < t1; ++t) local += hist[t];
-    int incl = local;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    int run = incl - local;
-    for (int t = t0; t < t1; ++t) {
-        const int h = hist[t];
-        hist[t] = run;
-        run += h;
-    }
-    __syncwarp();
-    const int64_t base = off[v];
     const unsigned lt = (1u << lane) - 1u;
-    for (int pb = 0; pb < npix; pb += 32) {
-        const int p = pb + lane;
-        PairRec r;
-        r.ok = false;
-        if (p < npix) {
+    for (int s = 0; s < P; ++s) {
+        const int64_t base = off[(int64_t)v * P + s], gend = off[(int64_t)v * P + s + 1];
+        if (gend == base) continue;   // warp-uniform: no records in this group
+        const int np = sp_off ? sp_off[s + 1] - sp_off[s] : g.M * g.N;
+        const int *list = sp_off ? sp_pix + sp_off[s] : nullptr;
+        for (int t = lane; t <= T.B; t += 32) hist[t] = 0;
+        __syncwarp();
+        for (int k = lane; k < np; k += 32) {
+            const int p = list ? list[k] : k;
             const int m = p / g.N, n = p - m * g.N;
-            r = pair_record(A, T, u_first, u_last, v, i, j, vx, m, n);
-        }
-        const unsigned act = __ballot_sync(0xffffffffu, r.ok);
-        unsigned grp = 0;
-        int pos = 0;
-        if (r.ok) {
-            grp = __match_any_sync(act, r.t);
-            pos = hist[r.t] + __popc(grp & lt);
+            const PairRec r = pair_record(A, T, u_first, u_last, v, i, j, vx, m, n);
+            if (r.ok) atomicAdd(&hist[r.t], 1);
         }
         __syncwarp();
-        if (r.ok) {
-            if ((grp & lt) == 0) hist[r.t] += __popc(grp);
-            const int64_t q = base + pos;
-            key[q] = (uint32_t)p | ((uint32_t)r.t << 16);
-            w0[q] = r.w0;
-            w1[q] = r.w1;
+        // exclusive scan of hist[0..B) by the warp: contiguous chunks per lane
+        const int chunk = (T.B + 31) / 32;
+        const int t0 = min(T.B, lane * chunk), t1 = min(T.B, t0 + chunk);
+        int local = 0;
+        for (int t = t0; t < t1; ++t) local += hist[t];
+        int incl = local;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int run = incl - local;
+        for (int t = t0; t < t1; ++t) {
+            const int h = hist[t];
+            hist[t] = run;
+            run += h;
         }
         __syncwarp();
-    }
-    // Pad the voxel's list to whole 16-byte quads with zero-weight copies of its
-    // last record (same pixel and interval, so the order by t is kept).
-    const int creal = __shfl_sync(0xffffffffu, incl, 31);
-    const int npadv = (int)(off[v + 1] - base) - creal;
-    if (lane < npadv) {
-        const int64_t q = base + creal + lane;
-        key[q] = key[base + creal - 1];
-        w0[q] = 0.f;
-        w1[q] = 0.f;
+        for (int kb = 0; kb < np; kb += 32) {
+            const int k = kb + lane;
+            PairRec r;
+            r.ok = false;
+            int p = 0;
+            if (k < np) {
+                p = list ? list[k] : k;
+                const int m = p / g.N, n = p - m * g.N;
+                r = pair_record(A, T, u_first, u_last, v, i, j, vx, m, n);
+            }
+            const unsigned act = __ballot_sync(0xffffffffu, r.ok);
+            unsigned grp = 0;
+            int pos = 0;
+            if (r.ok) {
+                grp = __match_any_sync(act, r.t);
+                pos = hist[r.t] + __popc(grp & lt);
+            }
+            __syncwarp();
+            if (r.ok) {
+                if ((grp & lt) == 0) hist[r.t] += __popc(grp);
+                const int64_t q = base + pos;
+                key[q] = (uint32_t)p | ((uint32_t)r.t << 16);
+                w0[q] = r.w0;
+                w1[q] = r.w1;
+            }
+            __syncwarp();
+        }
+        const int creal = __shfl_sync(0xffffffffu, incl, 31);
+        const int npadv = (int)(gend - base) - creal;
+        if (lane < npadv) {
+            const int64_t q = base + creal + lane;
+            key[q] = key[base + creal - 1];
+            w0[q] = 0.f;
+            w1[q] = 0.f;
+        }
+        __syncwarp();
     }
 }
 
@@ -259,7 +284,7 @@ k_fwd_rec(RecArgs A, const float *__restrict__ Wtab, float *__restrict__ part, i
             break;
         }
         if (buf) ph1 ^= 1u; else ph0 ^= 1u;
-        const int64_t b = A.off[v], e = A.off[v + 1];
+        const int64_t b = rec_begin(A, v), e = rec_end(A, v);
         for (int64_t q = b + tid; q < e; q += RT) {
             const uint32_t k = A.key[q];
             const int t = (int)(k >> 16);
@@ -375,9 +400,10 @@ k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float
     for (int p = tid; p < A.npix; p += ADJ_T) w_s[p] = w[p];
     for (int t = tid; t < A.Bp; t += ADJ_T) V[t] = 0.f;
     __syncthreads();
-    int64_t ob = A.off[v0], oe = A.off[v0 + 1];
+    int64_t ob = rec_begin(A, v0), oe = rec_end(A, v0);
     if (lane == 0) issue(ob, oe);
-    int64_t on0 = oe, on1 = A.off[min(v0 + 2, A.R)];   // the next voxel's list
+    const int vn = min(v0 + 1, A.R - 1);
+    int64_t on0 = rec_begin(A, vn), on1 = rec_end(A, vn);   // the next voxel's list
     uint32_t par = 0u;       // parity of the warp's outstanding phase
     bool pending = true;     // lane 0: a staged copy is in flight
     bool ok = true;
@@ -430,8 +456,11 @@ k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float
         }
         ob = on0;
         oe = on1;
-        on0 = on1;
-        on1 = A.off[min(v + 3, A.R)];
+        {
+            const int vn2 = min(v + 2, A.R - 1);
+            on0 = rec_begin(A, vn2);
+            on1 = rec_end(A, vn2);
+        }
         if (lane != 0 && !late) par ^= 1u;
 
         // A part that does not start the voxel begins inside the run of the record
@@ -545,107 +574,194 @@ size_t adj_rec_smem(int npix, int Bp) {
 
 }  // namespace
 
-void records_free(TablePath *T) {
-    cudaFree(T->rec_off);
-    cudaFree(T->rec_key);
-    cudaFree(T->rec_w0);
-    cudaFree(T->rec_w1);
-    T->rec_off = nullptr;
-    T->rec_key = nullptr;
-    T->rec_w0 = T->rec_w1 = nullptr;
-    T->use_records = false;
+namespace {
+
+void free_set(RecSet &r) {
+    cudaFree(r.off);
+    cudaFree(r.key);
+    cudaFree(r.w0);
+    cudaFree(r.w1);
+    r = RecSet();
 }
 
-// Build the records.  Returns OK without records (use_records stays false) when
-// the sizes do not fit the 16-bit key fields or shared memory, or when the
-// device memory is not available; the on-the-fly table kernels are used then.
-caxsi_status records_build(caxsi_plan *p, TablePath *T) {
+// Count, allocate and fill one record set with P groups per voxel (group of a
+// pixel: sub_dev[pixel], with the pixel lists sp_off_dev / sp_pix_dev; all
+// pixels in one group when sub_dev is null).  Returns OK with r.P = 0 when the
+// device memory is not available.
+caxsi_status build_set(caxsi_plan *p, TablePath *T, RecSet &r, int P, const int *sub_dev,
+                       const int *sp_off_dev, const int *sp_pix_dev, int wpb) {
+    const DevGeo &g = p->dg;
+    const int64_t ng = (int64_t)g.R * P;
+    int64_t *cnt = nullptr;
+    if (cudaMalloc(&cnt, (size_t)ng * sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return CAXSI_OK;
+    }
+    const PairArgs pa = pair_args(p);
+    const TabArgs ta = tab_args(T);
+    k_rec_count<<<(unsigned)ceil_div64((int64_t)g.R * 32, 256), 256, 8 * P * sizeof(int)>>>(pa, ta, sub_dev, P,
+                                                                                          cnt);
+    std::vector<int64_t> h(ng + 1);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpy(h.data() + 1, cnt, (size_t)ng * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaFree(cnt);
+        return CAXSI_ERR_CUDA;
+    }
+    cudaFree(cnt);
+    // every group's list is padded to a multiple of 4 records (whole 16-byte quads)
+    int64_t n_real = 0;
+    h[0] = 0;
+    for (int64_t k = 0; k < ng; ++k) {
+        n_real += h[k + 1];
+        h[k + 1] = h[k] + ((h[k + 1] + 3) & ~int64_t(3));
+    }
+    const int64_t n = h[ng];
+    const int64_t nalloc = n > 0 ? n : 4;
+    if (cudaMalloc(&r.off, (size_t)(ng + 1) * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&r.key, (size_t)nalloc * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&r.w0, (size_t)nalloc * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&r.w1, (size_t)nalloc * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        free_set(r);
+        return CAXSI_OK;
+    }
+    if (cudaMemcpy(r.off, h.data(), (size_t)(ng + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+        free_set(r);
+        return CAXSI_ERR_CUDA;
+    }
+    const size_t smem = (size_t)wpb * (T->B + 1) * sizeof(int);
+    if (cudaFuncSetAttribute(k_rec_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        free_set(r);
+        return CAXSI_ERR_CUDA;
+    }
+    k_rec_fill<<<(unsigned)ceil_div64(g.R, wpb), wpb * 32, smem>>>(pa, ta, wpb, P, sp_off_dev, sp_pix_dev, r.off,
+                                                                 r.key, r.w0, r.w1);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        free_set(r);
+        return CAXSI_ERR_CUDA;
+    }
+    r.P = P;
+    r.n = n_real;
+    p->table_bytes += n * 12 + (ng + 1) * 8;
+    return CAXSI_OK;
+}
+
+// Warps per block of the fill kernel (its histogram of B + 1 ints per warp must
+// fit shared memory), or 0 when records cannot be used: the sizes do not fit the
+// 16-bit key fields or the streaming kernels' shared memory.
+int fill_warps(const caxsi_plan *p, const TablePath *T) {
     const DevGeo &g = p->dg;
     const int npix = g.M * g.N;
-    if (npix > 65536 || T->B > 65535) return CAXSI_OK;
+    if (npix > 65536 || T->B > 65535) return 0;
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
     const size_t need = fwd_rec_smem(npix, T->Bp) > adj_rec_smem(npix, T->Bp)
                             ? fwd_rec_smem(npix, T->Bp) : adj_rec_smem(npix, T->Bp);
     int wpb = (int)((smem_max - 1024) / ((size_t)(T->B + 1) * 4));
     if (wpb > 8) wpb = 8;
-    if ((size_t)smem_max < need || wpb < 1) return CAXSI_OK;
+    if ((size_t)smem_max < need || wpb < 1) return 0;
+    return wpb;
+}
 
-    int64_t *cnt = nullptr;
-    if (cudaMalloc(&cnt, (size_t)g.R * sizeof(int64_t)) != cudaSuccess) return CAXSI_OK;
-    const PairArgs pa = pair_args(p);
-    const TabArgs ta = tab_args(T);
-    k_rec_count<<<(unsigned)ceil_div64((int64_t)g.R * 32, 256), 256>>>(pa, ta, cnt);
-    std::vector<int64_t> h(g.R + 1);
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpy(h.data() + 1, cnt, (size_t)g.R * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
-        cudaFree(cnt);
-        return CAXSI_ERR_CUDA;
-    }
-    cudaFree(cnt);
-    // every voxel's list is padded to a multiple of 4 records (whole 16-byte quads)
-    int64_t n_real = 0;
-    h[0] = 0;
-    for (int v = 0; v < g.R; ++v) {
-        n_real += h[v + 1];
-        h[v + 1] = h[v] + ((h[v + 1] + 3) & ~int64_t(3));
-    }
-    const int64_t n = h[g.R];
-    const int64_t npad = n > 0 ? n : 4;
-    if (cudaMalloc(&T->rec_off, (size_t)(g.R + 1) * sizeof(int64_t)) != cudaSuccess ||
-        cudaMalloc(&T->rec_key, (size_t)npad * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&T->rec_w0, (size_t)npad * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&T->rec_w1, (size_t)npad * sizeof(float)) != cudaSuccess) {
-        cudaGetLastError();
-        records_free(T);
-        return CAXSI_OK;
-    }
-    cudaMemcpy(T->rec_off, h.data(), (size_t)(g.R + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
-    const size_t smem = (size_t)wpb * (T->B + 1) * sizeof(int);
-    if (cudaFuncSetAttribute(k_rec_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        records_free(T);
-        return CAXSI_ERR_CUDA;
-    }
-    k_rec_fill<<<(unsigned)ceil_div64(g.R, wpb), wpb * 32, smem>>>(pa, ta, wpb, T->rec_off, T->rec_key,
-                                                                 T->rec_w0, T->rec_w1);
-    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
-        records_free(T);
-        return CAXSI_ERR_CUDA;
-    }
-    T->n_rec = n_real;
+}  // namespace
+
+void records_free(TablePath *T) {
+    free_set(T->rec);
+    free_set(T->sub);
+    cudaFree(T->sub_of_pix);
+    T->sub_of_pix = nullptr;
+    T->use_records = false;
+}
+
+// Build the records of the full operator.  Returns OK without records
+// (use_records stays false) when the sizes do not fit the 16-bit key fields or
+// shared memory, or when the device memory is not available; the on-the-fly
+// table kernels are used then.
+caxsi_status records_build(caxsi_plan *p, TablePath *T) {
+    const int wpb = fill_warps(p, T);
+    if (wpb < 1) return CAXSI_OK;
+    caxsi_status st = build_set(p, T, T->rec, 1, nullptr, nullptr, nullptr, wpb);
+    if (st != CAXSI_OK || T->rec.P == 0) return st;
     T->use_records = true;
+    const DevGeo &g = p->dg;
     int chunks = 2 * p->num_sms;
     if (chunks > g.R) chunks = g.R;
     T->rec_vc = (int)ceil_div64(g.R, chunks);
     T->rec_chunks = (int)ceil_div64(g.R, T->rec_vc);
-    p->table_bytes += n * 12 + (int64_t)(g.R + 1) * 8;
     return CAXSI_OK;
 }
 
-cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s) {
+// Build the records grouped by detector subset (sub_host[pixel] in [0, P)),
+// replacing an earlier grouping.  Needs the full records (use_records).
+caxsi_status records_build_subsets(caxsi_plan *p, TablePath *T, int P, const int32_t *sub_host) {
+    if (!T->use_records) return CAXSI_ERR_UNSUPPORTED;
+    const DevGeo &g = p->dg;
+    const int npix = g.M * g.N;
+    free_set(T->sub);
+    cudaFree(T->sub_of_pix);
+    T->sub_of_pix = nullptr;
+    // pixel lists of the subsets (counting sort of the pixels by subset)
+    std::vector<int> sp_off(P + 1, 0), sp_pix(npix);
+    for (int k = 0; k < npix; ++k) sp_off[sub_host[k] + 1]++;
+    for (int s = 0; s < P; ++s) sp_off[s + 1] += sp_off[s];
+    {
+        std::vector<int> fill(sp_off.begin(), sp_off.end() - 1);
+        for (int k = 0; k < npix; ++k) sp_pix[fill[sub_host[k]]++] = k;
+    }
+    int *d_sub = nullptr, *d_off = nullptr, *d_pix = nullptr;
+    if (cudaMalloc(&d_sub, npix * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&d_off, (P + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&d_pix, npix * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d_sub);
+        cudaFree(d_off);
+        cudaFree(d_pix);
+        return CAXSI_ERR_OOM;
+    }
+    caxsi_status st = CAXSI_OK;
+    if (cudaMemcpy(d_sub, sub_host, npix * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_off, sp_off.data(), (P + 1) * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_pix, sp_pix.data(), npix * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        st = CAXSI_ERR_CUDA;
+    if (st == CAXSI_OK) st = build_set(p, T, T->sub, P, d_sub, d_off, d_pix, fill_warps(p, T));
+    cudaFree(d_off);
+    cudaFree(d_pix);
+    if (st == CAXSI_OK && T->sub.P == 0) st = CAXSI_ERR_OOM;
+    if (st != CAXSI_OK) {
+        cudaFree(d_sub);
+        return st;
+    }
+    T->sub_of_pix = d_sub;
+    p->table_bytes += (int64_t)npix * 4;
+    return CAXSI_OK;
+}
+
+cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, int subset, float *part, cudaStream_t s) {
     const int npix = p->dg.M * p->dg.N;
     const size_t smem = fwd_rec_smem(npix, T->Bp);
     cudaError_t e = cudaFuncSetAttribute(k_fwd_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_fwd_rec<<<T->rec_chunks, RT, smem, s>>>(rec_args(p, T), T->tab, part, T->rec_vc, p->err_flag + 1);
+    k_fwd_rec<<<T->rec_chunks, RT, smem, s>>>(rec_args(p, T, subset), T->tab, part, T->rec_vc, p->err_flag + 1);
     return cudaGetLastError();
 }
 
 template <typename OutT>
-cudaError_t launch_adj_rec(const caxsi_plan *p, const TablePath *T, const float *w, OutT *out,
+cudaError_t launch_adj_rec(const caxsi_plan *p, const TablePath *T, int subset, const float *w, OutT *out,
                            float *lo, cudaStream_t s) {
     const int npix = p->dg.M * p->dg.N;
     const size_t smem = adj_rec_smem(npix, T->Bp);
     cudaError_t e = cudaFuncSetAttribute(k_adj_rec<OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_adj_rec<OutT><<<T->rec_chunks, ADJ_T, smem, s>>>(rec_args(p, T), w, out, lo, T->rec_vc,
+    k_adj_rec<OutT><<<T->rec_chunks, ADJ_T, smem, s>>>(rec_args(p, T, subset), w, out, lo, T->rec_vc,
                                                        p->err_flag + 1);
     return cudaGetLastError();
 }
 
-cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, const float *w, int out_kind,
+cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, int subset, const float *w, int out_kind,
                             cudaStream_t s) {
-    if (out_kind == 1) return launch_adj_rec(p, T, w, reinterpret_cast<__nv_bfloat16 *>(T->v16), (float *)nullptr, s);
-    if (out_kind == 2) return launch_adj_rec(p, T, w, reinterpret_cast<__half *>(T->v16), (float *)nullptr, s);
-    return launch_adj_rec(p, T, w, T->tab, (float *)nullptr, s);
+    if (out_kind == 1)
+        return launch_adj_rec(p, T, subset, w, reinterpret_cast<__nv_bfloat16 *>(T->v16), (float *)nullptr, s);
+    if (out_kind == 2)
+        return launch_adj_rec(p, T, subset, w, reinterpret_cast<__half *>(T->v16), (float *)nullptr, s);
+    return launch_adj_rec(p, T, subset, w, T->tab, (float *)nullptr, s);
 }

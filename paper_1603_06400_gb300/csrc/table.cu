@@ -441,7 +441,7 @@ caxsi_status build_table(caxsi_plan *p) {
 }  // namespace
 
 int64_t table_breakpoints(const caxsi_plan *p) { return p->table ? p->table->B : 0; }
-int64_t table_records(const caxsi_plan *p) { return p->table ? p->table->n_rec : 0; }
+int64_t table_records(const caxsi_plan *p) { return p->table ? p->table->rec.n : 0; }
 
 namespace {
 
@@ -545,10 +545,11 @@ cudaDataType_t dtype16(int path) { return path == CAXSI_PATH_TABLE_BF16 ? CUDA_R
 
 }  // namespace
 
-caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path, cudaStream_t s) {
+caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path, int subset, cudaStream_t s) {
     caxsi_status st = ensure_table(p, path);
     if (st != CAXSI_OK) return st;
     TablePath *T = p->table;
+    if (subset >= 0 && (!T->use_records || subset >= T->sub.P)) return CAXSI_ERR_UNSUPPORTED;
     const DevGeo &d = p->dg;
     const float one = 1.f, zero = 0.f;
     if (cublasSetStream(T->blas, s) != CUBLAS_STATUS_SUCCESS) return CAXSI_ERR_CUDA;
@@ -600,7 +601,7 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
     }
     if (T->use_records) {
         CAXSI_PROF(p, "rec_pairs_fwd", s);
-        CAXSI_CUDA_TRY(records_forward(p, T, T->fwd_part, s));
+        CAXSI_CUDA_TRY(records_forward(p, T, subset, T->fwd_part, s));
     } else {
         CAXSI_PROF(p, "tab_pairs_fwd", s);
         CAXSI_CUDA_TRY(dispatch_fwd(p, T, T->fwd_part, s));
@@ -616,16 +617,17 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
     return CAXSI_OK;
 }
 
-caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path, cudaStream_t s) {
+caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path, int subset, cudaStream_t s) {
     caxsi_status st = ensure_table(p, path);
     if (st != CAXSI_OK) return st;
     TablePath *T = p->table;
+    if (subset >= 0 && (!T->use_records || subset >= T->sub.P)) return CAXSI_ERR_UNSUPPORTED;
     const DevGeo &d = p->dg;
     const int out_kind = path == CAXSI_PATH_TABLE_FP32 ? 0 : (path == CAXSI_PATH_TABLE_BF16 ? 1 : 2);
     const bool tc = p->gemm_engine == 0 && T->use_records;
     if (T->use_records) {
         CAXSI_PROF(p, "rec_pairs_adj", s);
-        CAXSI_CUDA_TRY(records_adjoint(p, T, w, out_kind, s));
+        CAXSI_CUDA_TRY(records_adjoint(p, T, subset, w, out_kind, s));
     } else {
         CAXSI_PROF(p, "tab_pairs_adj", s);
         CAXSI_CUDA_TRY(dispatch_adj(p, T, w, s));
@@ -662,6 +664,16 @@ caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path
     }
     return CAXSI_OK;
 }
+
+caxsi_status table_set_subsets(caxsi_plan *p, int P, const int32_t *sub_host) {
+    caxsi_status st = ensure_table(p, CAXSI_PATH_TABLE_FP32);
+    if (st != CAXSI_OK) return st;
+    st = records_build_subsets(p, p->table, P, sub_host);
+    if (st == CAXSI_OK) CAXSI_CUDA_TRY(cudaDeviceSynchronize());
+    return st;
+}
+
+const int *table_subset_of_pixel(const caxsi_plan *p) { return p->table ? p->table->sub_of_pix : nullptr; }
 
 void table_destroy(caxsi_plan *p) {
     free_table(p->table);

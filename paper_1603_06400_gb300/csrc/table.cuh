@@ -5,6 +5,16 @@
 
 #include "internal.cuh"
 
+// One set of pair records: P groups per voxel (P = 1 for the full operator).
+struct RecSet {
+    int P = 0;                  // groups per voxel; 0 = not built
+    int64_t n = 0;              // records, without the quad padding
+    int64_t *off = nullptr;     // [R * P + 1] record range of each (voxel, group), whole quads
+    uint32_t *key = nullptr;    // pixel | (t << 16)
+    float *w0 = nullptr;        // c (1 - alpha)
+    float *w1 = nullptr;        // c alpha
+};
+
 struct TablePath {
     int B = 0;          // knots
     int Qp = 0;         // q row length of the 16-bit / TF32-split operand copies (multiple of 8)
@@ -20,14 +30,13 @@ struct TablePath {
     int adj_chunks = 0, adj_vc = 0;
     size_t smem_fwd = 0, smem_adj = 0;
 
-    // Pair records (precomputed per-pair interval and weights), voxel-major,
-    // sorted by (knot interval t, pixel) within each voxel.
+    // Pair records (precomputed per-pair interval and weights), voxel-major.
+    // rec: every open pair, sorted by (knot interval t, pixel) within each voxel.
+    // sub: the same pairs grouped by detector subset within each voxel, then
+    //      sorted by (t, pixel): the ordered-subset operators (built on request).
     bool use_records = false;
-    int64_t n_rec = 0;
-    int64_t *rec_off = nullptr;   // [R + 1] record range of each voxel
-    uint32_t *rec_key = nullptr;  // [n_rec] pixel | (t << 16)
-    float *rec_w0 = nullptr;      // [n_rec] c (1 - alpha)
-    float *rec_w1 = nullptr;      // [n_rec] c alpha
+    RecSet rec, sub;
+    int *sub_of_pix = nullptr;   // [M*N] subset of each pixel (device), when sub is built
     int rec_chunks = 0, rec_vc = 0;
 
     // Contractions over q on tensor cores (cuBLAS): FP32-accurate via the
@@ -98,10 +107,11 @@ inline TabArgs tab_args(const TablePath *T) {
 
 // records.cu
 caxsi_status records_build(caxsi_plan *p, TablePath *T);
-cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s);
+caxsi_status records_build_subsets(caxsi_plan *p, TablePath *T, int P, const int32_t *sub_host);
+cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, int subset, float *part, cudaStream_t s);
 // out_kind: 0 = FP32 rows in tab, 1 = bf16 rows in v16, 2 = fp16 rows in v16
-cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, const float *w, int out_kind,
-                            cudaStream_t s);
+cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, int subset, const float *w,
+                            int out_kind, cudaStream_t s);
 
 // tc_gemm.cu
 cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const void *A2, int64_t lda,

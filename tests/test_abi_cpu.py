@@ -77,4 +77,9 @@ def test_null_and_invalid_arguments_rejected_before_any_cuda_call(lib):
     assert lib.caxsi_forward_host(None, None, 0, None, 0, 0) == 1
     info = caxsi.CPlanInfo()
     assert lib.caxsi_plan_info(None, ctypes.byref(info)) == 1
+    sub = np.zeros(g.M * g.N, np.int32)
+    assert lib.caxsi_plan_set_subsets(None, 1, sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))) == 1
+    assert lib.caxsi_forward_subset(None, 0, None, 0, None, 0, 1, None) == 1
+    assert lib.caxsi_adjoint_subset(None, 0, None, 0, None, 0, 1, None) == 1
+    assert lib.caxsi_recon_step_subset(None, 0, None, None, None, 0, 0.0, 0.0, 1, None, None) == 1
     lib.caxsi_plan_destroy(None)
