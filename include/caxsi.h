@@ -197,6 +197,49 @@ caxsi_status caxsi_recon_step_subset(caxsi_plan *plan, int subset, const float *
                                      float *f_dev, int64_t f_len, float beta, float delta, int path,
                                      double *nll_out, void *stream);
 
+/* ---- Batches of objects ------------------------------------------------------
+ * n_objects objects share the plan's geometry, spectrum and mask; object b is
+ * the voxel range [voxel_ranges[2b], voxel_ranges[2b+1]) of the voxel index
+ * v = i*J + j (depth slabs of uneven extent), with its own f block
+ * f_dev + b*X*J*Q ([X][J][Q], voxels outside its range are not read) and its own
+ * detector image g_dev + b*M*N.  The paper has no batched operator: it serves
+ * training and many-object reconstruction (one launch per stage for the whole
+ * batch).  The q contraction is one GEMM over the packed rows of all objects'
+ * voxels, and the pair streaming runs per voxel chunk of each object, so each
+ * object's result is bit-identical to caxsi_forward / caxsi_adjoint on that
+ * object alone with f = 0 outside its range (the adjoint's f is 0 outside the
+ * range).  CAXSI_PATH_TABLE_FP32 with the tcgen05 engine only (UNSUPPORTED
+ * otherwise).  voxel_ranges is host memory; the call is asynchronous on stream
+ * after a synchronous upload when the layout changes.  Errors: INVALID (sizes,
+ * ranges outside [0, X*J], n_objects outside [1, CAXSI_MAX_BATCH]),
+ * UNSUPPORTED, CUDA, OOM. */
+#define CAXSI_MAX_BATCH 4096
+caxsi_status caxsi_forward_batch(caxsi_plan *plan, int n_objects, const int32_t *voxel_ranges,
+                                 const float *f_dev, int64_t f_len, float *g_dev, int64_t g_len, int path,
+                                 void *stream);
+caxsi_status caxsi_adjoint_batch(caxsi_plan *plan, int n_objects, const int32_t *voxel_ranges,
+                                 const float *w_dev, int64_t w_len, float *f_dev, int64_t f_len, int path,
+                                 void *stream);
+
+/* ---- The update step as a differentiable function ------------------------------
+ * caxsi_em_update: f_out = the closed-form update of Eq. 10 (the Lemma's positive
+ * root with the Huber penalty of caxsi_recon_step) from f, b1 = A^T 1 and
+ * b2 = A^T (y / z), elementwise with the 4-neighbour stencil; f_len is a multiple
+ * of X*J*Q (objects of this geometry back to back, each with its own
+ * neighbourhoods).  All pointers device, f_out must not alias f.
+ * caxsi_em_update_vjp: the reverse mode of caxsi_em_update: given grad_out =
+ * dL/df_out, writes grad_f = dL/df and grad_b2 = dL/db2 (b1 is treated as a
+ * constant), by implicit differentiation of the root
+ * ((2 chi1 x + chi2) dx = dchi3 - x dchi2 - x^2 dchi1) through the Huber terms
+ * (derivatives taken one-sided at |f_j - f_k| = delta).  Used with A and A^T to
+ * unroll the reconstruction under automatic differentiation; the paper has no
+ * such step.  Errors: INVALID, CUDA, OOM. */
+caxsi_status caxsi_em_update(caxsi_plan *plan, const float *f_dev, const float *b1_dev, const float *b2_dev,
+                             float beta, float delta, float *f_out_dev, int64_t f_len, void *stream);
+caxsi_status caxsi_em_update_vjp(caxsi_plan *plan, const float *f_dev, const float *b1_dev,
+                                 const float *b2_dev, float beta, float delta, const float *grad_out_dev,
+                                 float *grad_f_dev, float *grad_b2_dev, int64_t f_len, void *stream);
+
 /* Host-buffer forms: copy the input from host memory to plan-owned device
  * staging buffers, evaluate, copy the result back to host memory, and
  * synchronise before returning.  Pinned host memory gives the fastest copies.

@@ -100,13 +100,19 @@ def load():
             lib.caxsi_recon_step_subset.argtypes = [P, ctypes.c_int, P, P, P, I64, ctypes.c_float,
                                                     ctypes.c_float, ctypes.c_int,
                                                     ctypes.POINTER(ctypes.c_double), P]
+            I32P = ctypes.POINTER(ctypes.c_int32)
+            lib.caxsi_forward_batch.argtypes = [P, ctypes.c_int, I32P, P, I64, P, I64, ctypes.c_int, P]
+            lib.caxsi_adjoint_batch.argtypes = [P, ctypes.c_int, I32P, P, I64, P, I64, ctypes.c_int, P]
+            lib.caxsi_em_update.argtypes = [P, P, P, P, ctypes.c_float, ctypes.c_float, P, I64, P]
+            lib.caxsi_em_update_vjp.argtypes = [P, P, P, P, ctypes.c_float, ctypes.c_float, P, P, P, I64, P]
             lib.caxsi_status_string.argtypes = [ctypes.c_int]
             lib.caxsi_status_string.restype = ctypes.c_char_p
             for name in ("caxsi_plan_create", "caxsi_forward", "caxsi_adjoint",
                          "caxsi_recon_step", "caxsi_forward_host", "caxsi_adjoint_host",
                          "caxsi_plan_info", "caxsi_profile_enable", "caxsi_profile_read",
                          "caxsi_plan_set_subsets", "caxsi_forward_subset", "caxsi_adjoint_subset",
-                         "caxsi_recon_step_subset"):
+                         "caxsi_recon_step_subset", "caxsi_forward_batch", "caxsi_adjoint_batch",
+                         "caxsi_em_update", "caxsi_em_update_vjp"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -264,6 +270,61 @@ class Plan:
         for p in range(P):
             self.recon_step_subset(p, y, f, r=r, beta=beta / P, delta=delta, path=path, stream=stream)
         return f
+
+    # -- batches of objects (voxel ranges of this geometry) ---------------------
+    def _ranges(self, nb, ranges):
+        R = self.X * self.J
+        if ranges is None:
+            ranges = [(0, R)] * nb
+        r = np.ascontiguousarray(np.asarray(ranges, dtype=np.int32).reshape(nb, 2))
+        return r
+
+    def forward_batch(self, f, ranges=None, out=None, path=PATH_TABLE_FP32, stream=None):
+        """g[b] = A f[b] over object b's voxel range (f: [nb, X, J, Q] device)."""
+        import torch
+        nb = f.shape[0]
+        r = self._ranges(nb, ranges)
+        if out is None:
+            out = torch.empty((nb, self.M, self.N), device=f.device, dtype=torch.float32)
+        _check(self.lib.caxsi_forward_batch(self.handle, nb, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                            _dev(f, nb * self.f_len, "f"), nb * self.f_len,
+                                            _dev(out, nb * self.g_len, "g"), nb * self.g_len, int(path),
+                                            _stream_handle(stream)), "caxsi_forward_batch")
+        return out
+
+    def adjoint_batch(self, w, ranges=None, out=None, path=PATH_TABLE_FP32, stream=None):
+        """f[b] = A^T w[b] on object b's voxel range, 0 elsewhere (w: [nb, M, N] device)."""
+        import torch
+        nb = w.shape[0]
+        r = self._ranges(nb, ranges)
+        if out is None:
+            out = torch.empty((nb, self.X, self.J, self.Q), device=w.device, dtype=torch.float32)
+        _check(self.lib.caxsi_adjoint_batch(self.handle, nb, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                            _dev(w, nb * self.g_len, "w"), nb * self.g_len,
+                                            _dev(out, nb * self.f_len, "f"), nb * self.f_len, int(path),
+                                            _stream_handle(stream)), "caxsi_adjoint_batch")
+        return out
+
+    # -- the update step and its reverse mode -------------------------------------
+    def em_update(self, f, b1, b2, beta=0.0, delta=0.0, out=None, stream=None):
+        import torch
+        n = f.numel()
+        if out is None:
+            out = torch.empty_like(f)
+        _check(self.lib.caxsi_em_update(self.handle, _dev(f, n, "f"), _dev(b1, n, "b1"), _dev(b2, n, "b2"),
+                                        float(beta), float(delta), _dev(out, n, "out"), n,
+                                        _stream_handle(stream)), "caxsi_em_update")
+        return out
+
+    def em_update_vjp(self, f, b1, b2, grad_out, beta=0.0, delta=0.0, stream=None):
+        import torch
+        n = f.numel()
+        gf, gb2 = torch.empty_like(f), torch.empty_like(f)
+        _check(self.lib.caxsi_em_update_vjp(self.handle, _dev(f, n, "f"), _dev(b1, n, "b1"), _dev(b2, n, "b2"),
+                                            float(beta), float(delta), _dev(grad_out, n, "grad_out"),
+                                            _dev(gf, n, "grad_f"), _dev(gb2, n, "grad_b2"), n,
+                                            _stream_handle(stream)), "caxsi_em_update_vjp")
+        return gf, gb2
 
     # -- host-buffer calls ----------------------------------------------------
     def forward_host(self, f, out=None, path=PATH_DIRECT):

@@ -66,6 +66,7 @@ void free_plan(caxsi_plan *p) {
     cudaFree(p->ones);
     for (int k = 0; k < 4; ++k) cudaFree(p->b1[k]);
     for (int k = 0; k < 4; ++k) cudaFree(p->b1_sub[k]);
+    cudaFree(p->vjp_scratch);
     cudaFree(p->b2);
     cudaFree(p->fnew);
     cudaFree(p->nll_part);
@@ -320,6 +321,66 @@ caxsi_status caxsi_recon_step_subset(caxsi_plan *p, int subset, const float *y_d
     if ((st = recon_update(p, f_dev, beta, delta, b1p, s)) != CAXSI_OK) return st;
     CAXSI_CUDA_TRY(cudaMemcpyAsync(f_dev, p->fnew, nf * sizeof(float), cudaMemcpyDeviceToDevice, s));
     return CAXSI_OK;
+}
+
+static caxsi_status batch_args(const caxsi_plan *p, int nb, const int32_t *ranges, const void *in, int64_t in_len,
+                               const void *out, int64_t out_len, bool fwd) {
+    if (!p || !ranges || !in || !out || nb < 1 || nb > CAXSI_MAX_BATCH) return CAXSI_ERR_INVALID;
+    const int64_t nf = (int64_t)p->dg.R * p->dg.Q, ng = (int64_t)p->dg.M * p->dg.N;
+    if (in_len != nb * (fwd ? nf : ng) || out_len != nb * (fwd ? ng : nf)) return CAXSI_ERR_INVALID;
+    for (int b = 0; b < nb; ++b)
+        if (ranges[2 * b] < 0 || ranges[2 * b] > ranges[2 * b + 1] || ranges[2 * b + 1] > p->dg.R)
+            return CAXSI_ERR_INVALID;
+    return CAXSI_OK;
+}
+
+caxsi_status caxsi_forward_batch(caxsi_plan *p, int n_objects, const int32_t *voxel_ranges, const float *f_dev,
+                                 int64_t f_len, float *g_dev, int64_t g_len, int path, void *stream) {
+    caxsi_status st = batch_args(p, n_objects, voxel_ranges, f_dev, f_len, g_dev, g_len, true);
+    if (st != CAXSI_OK) return st;
+    if (!path_ok(path)) return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return CAXSI_ERR_CUDA;
+    p->launches = 0;
+    return table_forward_batch(p, n_objects, voxel_ranges, f_dev, g_dev, path, (cudaStream_t)stream);
+}
+
+caxsi_status caxsi_adjoint_batch(caxsi_plan *p, int n_objects, const int32_t *voxel_ranges, const float *w_dev,
+                                 int64_t w_len, float *f_dev, int64_t f_len, int path, void *stream) {
+    caxsi_status st = batch_args(p, n_objects, voxel_ranges, w_dev, w_len, f_dev, f_len, false);
+    if (st != CAXSI_OK) return st;
+    if (!path_ok(path)) return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return CAXSI_ERR_CUDA;
+    p->launches = 0;
+    return table_adjoint_batch(p, n_objects, voxel_ranges, w_dev, f_dev, path, (cudaStream_t)stream);
+}
+
+caxsi_status caxsi_em_update(caxsi_plan *p, const float *f_dev, const float *b1_dev, const float *b2_dev,
+                             float beta, float delta, float *f_out_dev, int64_t f_len, void *stream) {
+    if (!p || !f_dev || !b1_dev || !b2_dev || !f_out_dev) return CAXSI_ERR_INVALID;
+    const int64_t nf = (int64_t)p->dg.R * p->dg.Q;
+    if (f_len < nf || f_len % nf) return CAXSI_ERR_INVALID;
+    if (!isfinite(beta) || beta < 0.f || !isfinite(delta) || delta < 0.f) return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return CAXSI_ERR_CUDA;
+    p->launches = 0;
+    return recon_update_ext(p, f_dev, b1_dev, b2_dev, beta, delta, f_out_dev, f_len, (cudaStream_t)stream);
+}
+
+caxsi_status caxsi_em_update_vjp(caxsi_plan *p, const float *f_dev, const float *b1_dev, const float *b2_dev,
+                                 float beta, float delta, const float *grad_out_dev, float *grad_f_dev,
+                                 float *grad_b2_dev, int64_t f_len, void *stream) {
+    if (!p || !f_dev || !b1_dev || !b2_dev || !grad_out_dev || !grad_f_dev || !grad_b2_dev)
+        return CAXSI_ERR_INVALID;
+    const int64_t nf = (int64_t)p->dg.R * p->dg.Q;
+    if (f_len < nf || f_len % nf) return CAXSI_ERR_INVALID;
+    if (!isfinite(beta) || beta < 0.f || !isfinite(delta) || delta < 0.f) return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return CAXSI_ERR_CUDA;
+    p->launches = 0;
+    return recon_update_vjp(p, f_dev, b1_dev, b2_dev, beta, delta, grad_out_dev, grad_f_dev, grad_b2_dev, f_len,
+                            (cudaStream_t)stream);
 }
 
 static caxsi_status host_call(caxsi_plan *p, const float *in_host, int64_t in_len, float *out_host,

@@ -69,6 +69,8 @@ struct caxsi_plan {
     int n_subsets;      // detector subsets of the ordered-subset operators (0 = none)
     float *b1_sub[4];   // [n_subsets][R*Q] A_p^T 1 per path, lazily
     std::vector<unsigned char> b1_sub_ok[4];   // which subsets of b1_sub are computed
+    float *vjp_scratch;   // [2][vjp_cap] reverse-mode scratch of the update
+    int64_t vjp_cap;
     float *b2;          // [R*Q]
     float *fnew;        // [R*Q]
     double *nll_part;   // [nll_blocks]
@@ -101,6 +103,11 @@ caxsi_status direct_forward_static_scratch(caxsi_plan *p, const float *f, float 
 caxsi_status table_forward(caxsi_plan *p, const float *f, float *g, int path, int subset, cudaStream_t s);
 caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f, int path, int subset, cudaStream_t s);
 caxsi_status table_set_subsets(caxsi_plan *p, int P, const int32_t *sub_host);
+// nb objects = voxel ranges [ranges[2b], ranges[2b+1]) of the shared geometry
+caxsi_status table_forward_batch(caxsi_plan *p, int nb, const int32_t *ranges, const float *f, float *g,
+                                 int path, cudaStream_t s);
+caxsi_status table_adjoint_batch(caxsi_plan *p, int nb, const int32_t *ranges, const float *w, float *f,
+                                 int path, cudaStream_t s);
 const int *table_subset_of_pixel(const caxsi_plan *p);
 void table_destroy(caxsi_plan *p);
 int64_t table_breakpoints(const caxsi_plan *p);
@@ -114,6 +121,11 @@ caxsi_status recon_ratio(caxsi_plan *p, const float *y, const float *r, const in
 caxsi_status recon_update(caxsi_plan *p, const float *f_old, float beta, float delta,
                           const float *b1, cudaStream_t s);
 caxsi_status recon_nll_fetch(caxsi_plan *p, double *out, cudaStream_t s);
+// n = nobj * R * Q elements (objects back to back)
+caxsi_status recon_update_ext(caxsi_plan *p, const float *f, const float *b1, const float *b2, float beta,
+                              float delta, float *out, int64_t n, cudaStream_t s);
+caxsi_status recon_update_vjp(caxsi_plan *p, const float *f, const float *b1, const float *b2, float beta,
+                              float delta, const float *gx, float *gf, float *gb2, int64_t n, cudaStream_t s);
 
 // ---- helpers -----------------------------------------------------------------
 #define CAXSI_CUDA_TRY(expr)                                   \

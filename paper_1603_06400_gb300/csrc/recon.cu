@@ -59,44 +59,136 @@ __global__ void k_sum_nll(const double *__restrict__ part, int nb, double *__res
 // b3 = b4 = 2 sum_k omega(f_j - f_k), b5 = b6 = sum_k psi_dot(f_j - f_k) over the
 // 4 spatial neighbours (symmetric neighbourhood, unit weights); the update is
 // the positive root of chi1 x^2 + chi2 x - chi3 = 0 (the Lemma), written without
-// cancellation for chi2 > 0.
-__global__ void k_update(DevGeo g, const float *__restrict__ f, const float *__restrict__ b1,
-                         const float *__restrict__ b2, float beta, float delta,
-                         float *__restrict__ fnew) {
-    const int64_t n = (int64_t)g.R * g.Q;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n) return;
+// cancellation for chi2 > 0.  n = nobj * R * Q: objects of the same geometry
+// back to back, each with its own neighbourhoods.
+struct UpdTerms {
+    float fh, b3, b5, chi1, chi2, chi3, x;
+    int kind;   // 0: root with chi1 > 0, 1: chi3 / chi2, 2: value kept
+};
+
+__device__ __forceinline__ int64_t nb_index(const DevGeo &g, int64_t idx, int q, bool &ok) {
     const int l = (int)(idx % g.Q);
-    const int v = (int)(idx / g.Q);
+    const int64_t vv = idx / g.Q;
+    const int v = (int)(vv % g.R);
+    const int64_t base = (vv - v) * g.Q;   // the object's first element
     const int i = v / g.J, j = v - i * g.J;
-    const float fh = f[idx];
-    float b3 = 0.f, b5 = 0.f;
+    const int ii = i + (q == 0 ? -1 : q == 1 ? 1 : 0), jj = j + (q == 2 ? -1 : q == 3 ? 1 : 0);
+    ok = ii >= 0 && ii < g.X && jj >= 0 && jj < g.J;
+    return base + ((int64_t)ii * g.J + jj) * g.Q + l;
+}
+
+__device__ __forceinline__ UpdTerms upd_terms(const DevGeo &g, const float *__restrict__ f,
+                                              const float *__restrict__ b1, const float *__restrict__ b2,
+                                              float beta, float delta, int64_t idx) {
+    UpdTerms u;
+    u.fh = f[idx];
+    u.b3 = 0.f;
+    u.b5 = 0.f;
     if (beta != 0.f) {
-        const int di[4] = {-1, 1, 0, 0};
-        const int dj[4] = {0, 0, -1, 1};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int ii = i + di[q], jj = j + dj[q];
-            if (ii < 0 || ii >= g.X || jj < 0 || jj >= g.J) continue;
-            const float d = fh - f[((int64_t)ii * g.J + jj) * g.Q + l];
+            bool ok;
+            const int64_t k = nb_index(g, idx, q, ok);
+            if (!ok) continue;
+            const float d = u.fh - f[k];
             const float ad = fabsf(d);
-            b3 += 2.f * (ad <= delta ? 1.f : delta / ad);
-            b5 += fminf(fmaxf(d, -delta), delta);
+            u.b3 += 2.f * (ad <= delta ? 1.f : delta / ad);
+            u.b5 += fminf(fmaxf(d, -delta), delta);
         }
     }
-    const float chi1 = beta * (2.f * b3);
-    const float chi2 = b1[idx] + beta * (-fh * (2.f * b3) + 2.f * b5);
-    const float chi3 = fh * b2[idx];
-    float x;
-    if (chi1 > 0.f) {
-        const float disc = sqrtf(fmaf(chi2, chi2, 4.f * chi1 * chi3));
-        x = chi2 > 0.f ? (2.f * chi3) / (chi2 + disc) : (disc - chi2) / (2.f * chi1);
-    } else if (chi2 > 0.f) {
-        x = chi3 / chi2;
+    u.chi1 = beta * (2.f * u.b3);
+    u.chi2 = b1[idx] + beta * (-u.fh * (2.f * u.b3) + 2.f * u.b5);
+    u.chi3 = u.fh * b2[idx];
+    if (u.chi1 > 0.f) {
+        const float disc = sqrtf(fmaf(u.chi2, u.chi2, 4.f * u.chi1 * u.chi3));
+        u.x = u.chi2 > 0.f ? (2.f * u.chi3) / (u.chi2 + disc) : (disc - u.chi2) / (2.f * u.chi1);
+        u.kind = 0;
+    } else if (u.chi2 > 0.f) {
+        u.x = u.chi3 / u.chi2;
+        u.kind = 1;
     } else {
-        x = fh;
+        u.x = u.fh;
+        u.kind = 2;
     }
-    fnew[idx] = x;
+    return u;
+}
+
+__global__ void k_update(DevGeo g, const float *__restrict__ f, const float *__restrict__ b1,
+                         const float *__restrict__ b2, float beta, float delta,
+                         float *__restrict__ fnew, int64_t n) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    fnew[idx] = upd_terms(g, f, b1, b2, beta, delta, idx).x;
+}
+
+// Reverse mode of the update.  Implicit differentiation of the root:
+// (2 chi1 x + chi2) dx = dchi3 - x dchi2 - x^2 dchi1.  Pass 1, per element j: the
+// gradients of chi1..3, hence of b2_j, of f_j through chi2 and chi3, and of b3_j
+// and b5_j (kept in gb3, gb5) with their derivatives with respect to f_j itself
+// (omega'(d) = -delta sign(d) / d^2 beyond delta, psi_dot'(d) = 1 within it).
+__global__ void k_update_vjp1(DevGeo g, const float *__restrict__ f, const float *__restrict__ b1,
+                              const float *__restrict__ b2, float beta, float delta,
+                              const float *__restrict__ gx, float *__restrict__ gf, float *__restrict__ gb2,
+                              float *__restrict__ gb3, float *__restrict__ gb5, int64_t n) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const UpdTerms u = upd_terms(g, f, b1, b2, beta, delta, idx);
+    const float gxi = gx[idx];
+    if (u.kind == 2) {
+        gf[idx] = gxi;
+        gb2[idx] = 0.f;
+        gb3[idx] = 0.f;
+        gb5[idx] = 0.f;
+        return;
+    }
+    const float D = 2.f * u.chi1 * u.x + u.chi2;
+    if (!(D > 0.f)) {   // a double root at x = 0 (f = 0 and chi2 = 0): no derivative, taken as 0
+        gf[idx] = 0.f;
+        gb2[idx] = 0.f;
+        gb3[idx] = 0.f;
+        gb5[idx] = 0.f;
+        return;
+    }
+    const float g3 = gxi / D, g2 = -gxi * u.x / D, g1 = -gxi * u.x * u.x / D;
+    const float gB3 = 2.f * beta * g1 - 2.f * beta * u.fh * g2;
+    const float gB5 = 2.f * beta * g2;
+    float own = g3 * b2[idx] + g2 * (-2.f * beta * u.b3);
+    if (beta != 0.f) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            bool ok;
+            const int64_t k = nb_index(g, idx, q, ok);
+            if (!ok) continue;
+            const float d = u.fh - f[k];
+            const float ad = fabsf(d);
+            const float domega = ad <= delta ? 0.f : -delta * copysignf(1.f, d) / (d * d);
+            own += gB3 * 2.f * domega + gB5 * (ad < delta ? 1.f : 0.f);
+        }
+    }
+    gf[idx] = own;
+    gb2[idx] = g3 * u.fh;
+    gb3[idx] = gB3;
+    gb5[idx] = gB5;
+}
+
+// Pass 2: each neighbour k of j adds -(gb3_k 2 omega'(f_k - f_j) + gb5_k psi_dot'(f_k - f_j)).
+__global__ void k_update_vjp2(DevGeo g, const float *__restrict__ f, float delta, const float *__restrict__ gb3,
+                              const float *__restrict__ gb5, float *__restrict__ gf, int64_t n) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const float fj = f[idx];
+    float acc = gf[idx];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        bool ok;
+        const int64_t k = nb_index(g, idx, q, ok);
+        if (!ok) continue;
+        const float d = f[k] - fj;
+        const float ad = fabsf(d);
+        const float domega = ad <= delta ? 0.f : -delta * copysignf(1.f, d) / (d * d);
+        acc -= gb3[k] * 2.f * domega + gb5[k] * (ad < delta ? 1.f : 0.f);
+    }
+    gf[idx] = acc;
 }
 
 }  // namespace
@@ -123,7 +215,7 @@ caxsi_status recon_update(caxsi_plan *p, const float *f_old, float beta, float d
     const int64_t n = (int64_t)p->dg.R * p->dg.Q;
     {
         CAXSI_PROF(p, "em_update", s);
-        k_update<<<(unsigned)ceil_div64(n, 256), 256, 0, s>>>(p->dg, f_old, b1, p->b2, beta, delta, p->fnew);
+        k_update<<<(unsigned)ceil_div64(n, 256), 256, 0, s>>>(p->dg, f_old, b1, p->b2, beta, delta, p->fnew, n);
     }
     CAXSI_LAUNCH_CHECK(p);
     return CAXSI_OK;
@@ -139,5 +231,39 @@ caxsi_status recon_nll_fetch(caxsi_plan *p, double *out, cudaStream_t s) {
         CAXSI_CUDA_TRY(cudaStreamSynchronize(s));
         return err[1] ? CAXSI_ERR_INTERNAL : CAXSI_ERR_NONPOS_MEAN;
     }
+    return CAXSI_OK;
+}
+
+caxsi_status recon_update_ext(caxsi_plan *p, const float *f, const float *b1, const float *b2, float beta,
+                              float delta, float *out, int64_t n, cudaStream_t s) {
+    {
+        CAXSI_PROF(p, "em_update", s);
+        k_update<<<(unsigned)ceil_div64(n, 256), 256, 0, s>>>(p->dg, f, b1, b2, beta, delta, out, n);
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    return CAXSI_OK;
+}
+
+caxsi_status recon_update_vjp(caxsi_plan *p, const float *f, const float *b1, const float *b2, float beta,
+                              float delta, const float *gx, float *gf, float *gb2, int64_t n, cudaStream_t s) {
+    if (n > p->vjp_cap) {
+        cudaFree(p->vjp_scratch);
+        p->vjp_scratch = nullptr;
+        p->vjp_cap = 0;
+        CAXSI_CUDA_TRY(cudaMalloc(&p->vjp_scratch, 2 * (size_t)n * sizeof(float)));
+        p->vjp_cap = n;
+    }
+    float *gb3 = p->vjp_scratch, *gb5 = p->vjp_scratch + n;
+    const unsigned nb = (unsigned)ceil_div64(n, 256);
+    {
+        CAXSI_PROF(p, "em_update_vjp1", s);
+        k_update_vjp1<<<nb, 256, 0, s>>>(p->dg, f, b1, b2, beta, delta, gx, gf, gb2, gb3, gb5, n);
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    {
+        CAXSI_PROF(p, "em_update_vjp2", s);
+        k_update_vjp2<<<nb, 256, 0, s>>>(p->dg, f, delta, gb3, gb5, gf, n);
+    }
+    CAXSI_LAUNCH_CHECK(p);
     return CAXSI_OK;
 }

@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "internal.cuh"
@@ -42,6 +43,12 @@ struct RecArgs {
     const int64_t *off;
     const uint32_t *key;
     const float *w0, *w1;
+    // Work items {obj, v0, v1, row0}: voxels [v0, v1) of object obj, whose table
+    // row (Wtab / Vtab) is row0 + v - v0; the forward's partial image of item k
+    // goes to slot k.  Blocks take items k = blockIdx.x, + gridDim.x, ...
+    const int4 *items;    // null: item k is voxel chunk k, {0, k vc, min(R, (k+1) vc), k vc}
+    int n_items, vc;
+    int64_t w_stride;     // adjoint input image of object obj: w + obj * w_stride
 };
 
 // subset < 0: every record of each voxel; else the records of that subset.
@@ -58,7 +65,18 @@ RecArgs rec_args(const caxsi_plan *p, const TablePath *T, int subset) {
     a.key = r.key;
     a.w0 = r.w0;
     a.w1 = r.w1;
+    a.items = nullptr;
+    a.n_items = T->rec_chunks;
+    a.vc = T->rec_vc;
+    a.w_stride = 0;
     return a;
+}
+
+template <bool ITEMS>
+__device__ __forceinline__ int4 item_at(const RecArgs &A, int k) {
+    if (ITEMS) return A.items[k];
+    const int v0 = k * A.vc;
+    return make_int4(0, v0, min(A.R, v0 + A.vc), v0);
 }
 
 __device__ __forceinline__ int64_t rec_begin(const RecArgs &A, int v) {
@@ -241,11 +259,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     return false;
 }
 
-// Forward streaming kernel.  Block = 1024 threads, a chunk of voxels; the
-// detector image accumulates in shared memory; each voxel's Wtab row arrives
-// by a TMA bulk copy, double-buffered one voxel ahead.
+// Forward streaming kernel.  Block = 1024 threads, work items of voxels (one
+// chunk of an object's voxels each; a single-object call has one item per
+// block); the detector image accumulates in shared memory and is written out per
+// item; each voxel's Wtab row arrives by a TMA bulk copy, double-buffered one
+// voxel ahead.
+template <bool ITEMS>
 __global__ void __launch_bounds__(RT, 1)
-k_fwd_rec(RecArgs A, const float *__restrict__ Wtab, float *__restrict__ part, int vc, int *err) {
+k_fwd_rec(RecArgs A, const float *__restrict__ Wtab, float *__restrict__ part, int *err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int npix_al = (A.npix + 3) & ~3;
     float *g_s = reinterpret_cast<float *>(smem_raw);
@@ -253,57 +274,62 @@ k_fwd_rec(RecArgs A, const float *__restrict__ Wtab, float *__restrict__ part, i
     float *wbuf1 = wbuf0 + A.Bp;
     uint64_t *bar = reinterpret_cast<uint64_t *>(wbuf1 + A.Bp);
     const int tid = threadIdx.x;
-    const int v0 = blockIdx.x * vc;
-    const int v1 = min(v0 + vc, A.R);
+    if (blockIdx.x >= (unsigned)A.n_items) return;   // block-uniform
     const uint32_t row_bytes = (uint32_t)A.Bp * 4u;
-    for (int p = tid; p < A.npix; p += RT) g_s[p] = 0.f;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        if (v0 < v1) {
-            mbar_expect_tx(&bar[0], row_bytes);
-            bulk_g2s(wbuf0, Wtab + (int64_t)v0 * A.Bp, row_bytes, &bar[0]);
-        }
     }
-    __syncthreads();
     bool ok = true;
     uint32_t ph0 = 0u, ph1 = 0u;   // mbarrier phase parity of each buffer
-    for (int v = v0; v < v1; ++v) {
-        const int buf = (v - v0) & 1;
-        float *w_s = buf ? wbuf1 : wbuf0;
-        if (tid == 0 && v + 1 < v1) {
-            // the other buffer was last read by voxel v - 1, finished at the barrier below
+    for (int k = blockIdx.x; k < A.n_items && ok; k += gridDim.x) {
+        const int4 it = item_at<ITEMS>(A, k);
+        const int v0 = it.y, v1 = it.z;
+        const int64_t r0 = (int64_t)it.w - v0;   // table row of voxel v: r0 + v
+        for (int p = tid; p < A.npix; p += RT) g_s[p] = 0.f;
+        if (tid == 0) {
+            // buffer 0 was last read before the barrier that ended the previous item
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(&bar[buf ^ 1], row_bytes);
-            bulk_g2s(buf ? wbuf0 : wbuf1, Wtab + (int64_t)(v + 1) * A.Bp, row_bytes, &bar[buf ^ 1]);
-        }
-        const int late = mbar_wait(&bar[buf], buf ? ph1 : ph0) ? 0 : 1;
-        if (__syncthreads_or(late)) {   // block-uniform decision
-            ok = false;
-            break;
-        }
-        if (buf) ph1 ^= 1u; else ph0 ^= 1u;
-        const int64_t b = rec_begin(A, v), e = rec_end(A, v);
-        for (int64_t q = b + tid; q < e; q += RT) {
-            const uint32_t k = A.key[q];
-            const int t = (int)(k >> 16);
-            const float val = fmaf(A.w0[q], w_s[t], A.w1[q] * w_s[t + 1]);
-            g_s[k & 0xffffu] += val;
+            mbar_expect_tx(&bar[0], row_bytes);
+            bulk_g2s(wbuf0, Wtab + (r0 + v0) * A.Bp, row_bytes, &bar[0]);
         }
         __syncthreads();
-    }
-    if (!ok) {
-        // a copy did not land in time: report, drain the copies this block issued, stop
-        if (tid == 0) {
-            atomicExch(err, 1);
-            mbar_wait(&bar[0], ph0);
-            mbar_wait(&bar[1], ph1);
+        for (int v = v0; v < v1; ++v) {
+            const int buf = (v - v0) & 1;
+            float *w_s = buf ? wbuf1 : wbuf0;
+            if (tid == 0 && v + 1 < v1) {
+                // the other buffer was last read by voxel v - 1, finished at the barrier below
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&bar[buf ^ 1], row_bytes);
+                bulk_g2s(buf ? wbuf0 : wbuf1, Wtab + (r0 + v + 1) * A.Bp, row_bytes, &bar[buf ^ 1]);
+            }
+            const int late = mbar_wait(&bar[buf], buf ? ph1 : ph0) ? 0 : 1;
+            if (__syncthreads_or(late)) {   // block-uniform decision
+                ok = false;
+                break;
+            }
+            if (buf) ph1 ^= 1u; else ph0 ^= 1u;
+            const int64_t b = rec_begin(A, v), e = rec_end(A, v);
+            for (int64_t q = b + tid; q < e; q += RT) {
+                const uint32_t key = A.key[q];
+                const int t = (int)(key >> 16);
+                const float val = fmaf(A.w0[q], w_s[t], A.w1[q] * w_s[t + 1]);
+                g_s[key & 0xffffu] += val;
+            }
+            __syncthreads();
         }
-        return;
+        if (!ok) break;
+        float *dst = part + (int64_t)k * A.npix;
+        for (int p = tid; p < A.npix; p += RT) dst[p] = g_s[p];
+        __syncthreads();
     }
-    float *dst = part + (int64_t)blockIdx.x * A.npix;
-    for (int p = tid; p < A.npix; p += RT) dst[p] = g_s[p];
+    if (!ok && tid == 0) {
+        // a copy did not land in time: report, drain the copies this block issued, stop
+        atomicExch(err, 1);
+        mbar_wait(&bar[0], ph0);
+        mbar_wait(&bar[1], ph1);
+    }
 }
 
 __device__ __forceinline__ void store_v4(float *p, float4 x) { *reinterpret_cast<float4 *>(p) = x; }
@@ -346,10 +372,9 @@ constexpr int ADJ_T = 1024;
 constexpr int ADJ_W = ADJ_T / 32;
 constexpr int ADJ_SQ = 64;
 
-template <typename OutT>
+template <typename OutT, bool ITEMS>
 __global__ void __launch_bounds__(ADJ_T, 1)
-k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float *__restrict__ Vlo, int vc,
-          int *err) {
+k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float *__restrict__ Vlo, int *err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int npix_al = (A.npix + 3) & ~3;
     float *w_s = reinterpret_cast<float *>(smem_raw);
@@ -363,9 +388,7 @@ k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float
     float *slot_hi = slot_lo + ADJ_T;
     uint64_t *bar = reinterpret_cast<uint64_t *>(slot_hi + ADJ_T);    // [ADJ_W]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int v0 = blockIdx.x * vc;
-    const int v1 = min(v0 + vc, A.R);
-    if (v0 >= v1) return;
+    if (blockIdx.x >= (unsigned)A.n_items) return;   // block-uniform
 
     // The warp's quads [ws, we) of the voxel with list [ob, oe): thread parts of perq
     // quads, ADJ_T parts.
@@ -397,16 +420,29 @@ k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float
         for (int k = 0; k < ADJ_W; ++k) mbar_init(&bar[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int p = tid; p < A.npix; p += ADJ_T) w_s[p] = w[p];
     for (int t = tid; t < A.Bp; t += ADJ_T) V[t] = 0.f;
+    uint32_t par = 0u;       // parity of the warp's outstanding phase
+    bool pending = false;    // lane 0: a staged copy is in flight
+    bool ok = true;
+    int staged = -1;         // the object whose w is in w_s
+    for (int k = blockIdx.x; k < A.n_items && ok; k += gridDim.x) {
+    const int4 item = item_at<ITEMS>(A, k);
+    const int v0 = item.y, v1 = item.z;
+    const int64_t r0 = (int64_t)item.w - v0;   // table row of voxel v: r0 + v
+    if (item.x != staged) {
+        // (the previous voxel ended with a barrier: no thread reads w_s any more)
+        const float *wo = w + (int64_t)item.x * A.w_stride;
+        for (int p = tid; p < A.npix; p += ADJ_T) w_s[p] = wo[p];
+        staged = item.x;
+    }
     __syncthreads();
     int64_t ob = rec_begin(A, v0), oe = rec_end(A, v0);
-    if (lane == 0) issue(ob, oe);
-    const int vn = min(v0 + 1, A.R - 1);
+    if (lane == 0) {
+        issue(ob, oe);
+        pending = true;
+    }
+    const int vn = min(v0 + 1, v1 - 1);
     int64_t on0 = rec_begin(A, vn), on1 = rec_end(A, vn);   // the next voxel's list
-    uint32_t par = 0u;       // parity of the warp's outstanding phase
-    bool pending = true;     // lane 0: a staged copy is in flight
-    bool ok = true;
     for (int v = v0; v < v1; ++v) {
         const int late = mbar_wait(&bar[warp], par) ? 0 : 1;
         int ws, we, perq;
@@ -454,10 +490,12 @@ k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float
                 pending = true;
             }
         }
+        // the current voxel's list is no longer needed past this point (pointers
+        // taken above); load the one after the next
         ob = on0;
         oe = on1;
         {
-            const int vn2 = min(v + 2, A.R - 1);
+            const int vn2 = min(v + 2, v1 - 1);
             on0 = rec_begin(A, vn2);
             on1 = rec_end(A, vn2);
         }
@@ -533,11 +571,11 @@ k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float
         if (ct != SENT) V[ct + 1] += chi;
         __syncthreads();
         // write the row (all Bp entries, whole quads) and clear V for the next voxel
-        OutT *vrow = Vtab + (int64_t)v * A.Bp;
+        OutT *vrow = Vtab + (r0 + v) * A.Bp;
         float4 *V4 = reinterpret_cast<float4 *>(V);
         const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (Vlo) {
-            float *lrow = Vlo + (int64_t)v * A.Bp;
+            float *lrow = Vlo + (r0 + v) * A.Bp;
             for (int t4 = tid; t4 < (A.Bp >> 2); t4 += ADJ_T) {
                 const float4 x = V4[t4];
                 float4 h, l;
@@ -556,6 +594,7 @@ k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float
             }
         }
         __syncthreads();
+    }
     }
     if (!ok && lane == 0) {
         // a copy did not land in time: report, drain this warp's copy in flight, stop
@@ -739,9 +778,9 @@ caxsi_status records_build_subsets(caxsi_plan *p, TablePath *T, int P, const int
 cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, int subset, float *part, cudaStream_t s) {
     const int npix = p->dg.M * p->dg.N;
     const size_t smem = fwd_rec_smem(npix, T->Bp);
-    cudaError_t e = cudaFuncSetAttribute(k_fwd_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_fwd_rec<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_fwd_rec<<<T->rec_chunks, RT, smem, s>>>(rec_args(p, T, subset), T->tab, part, T->rec_vc, p->err_flag + 1);
+    k_fwd_rec<false><<<T->rec_chunks, RT, smem, s>>>(rec_args(p, T, subset), T->tab, part, p->err_flag + 1);
     return cudaGetLastError();
 }
 
@@ -750,10 +789,40 @@ cudaError_t launch_adj_rec(const caxsi_plan *p, const TablePath *T, int subset, 
                            float *lo, cudaStream_t s) {
     const int npix = p->dg.M * p->dg.N;
     const size_t smem = adj_rec_smem(npix, T->Bp);
-    cudaError_t e = cudaFuncSetAttribute(k_adj_rec<OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_adj_rec<OutT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    k_adj_rec<OutT><<<T->rec_chunks, ADJ_T, smem, s>>>(rec_args(p, T, subset), w, out, lo, T->rec_vc,
-                                                       p->err_flag + 1);
+    k_adj_rec<OutT, false><<<T->rec_chunks, ADJ_T, smem, s>>>(rec_args(p, T, subset), w, out, lo, p->err_flag + 1);
+    return cudaGetLastError();
+}
+
+// Batched forms: explicit work items (objects' voxel chunks) and table rows.
+cudaError_t records_forward_items(const caxsi_plan *p, const TablePath *T, const int4 *items, int n_items,
+                                  const float *Wtab, float *part, cudaStream_t s) {
+    const int npix = p->dg.M * p->dg.N;
+    const size_t smem = fwd_rec_smem(npix, T->Bp);
+    cudaError_t e = cudaFuncSetAttribute(k_fwd_rec<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    RecArgs a = rec_args(p, T, -1);
+    a.items = items;
+    a.n_items = n_items;
+    k_fwd_rec<true><<<std::min(n_items, T->rec_chunks), RT, smem, s>>>(a, Wtab, part, p->err_flag + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t records_adjoint_items(const caxsi_plan *p, const TablePath *T, const int4 *items, int n_items,
+                                  const float *w, int64_t w_stride, float *Vtab, cudaStream_t s) {
+    const int npix = p->dg.M * p->dg.N;
+    const size_t smem = adj_rec_smem(npix, T->Bp);
+    cudaError_t e = cudaFuncSetAttribute(k_adj_rec<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    RecArgs a = rec_args(p, T, -1);
+    a.items = items;
+    a.n_items = n_items;
+    a.w_stride = w_stride;
+    k_adj_rec<float, true><<<std::min(n_items, T->rec_chunks), ADJ_T, smem, s>>>(a, w, Vtab, (float *)nullptr,
+                                                                                p->err_flag + 1);
     return cudaGetLastError();
 }
 

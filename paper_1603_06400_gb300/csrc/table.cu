@@ -279,6 +279,15 @@ void free_table(TablePath *T) {
     cudaFree(T->S);
     cudaFree(T->tab);
     cudaFree(T->fwd_part);
+    BatchState &bs = T->batch;
+    cudaFree(bs.items);
+    cudaFree(bs.rowmap);
+    cudaFree(bs.obj_items);
+    cudaFree(bs.tab);
+    cudaFree(bs.f_hi);
+    cudaFree(bs.f_lo);
+    cudaFree(bs.fpk);
+    cudaFree(bs.part);
     delete T;
 }
 
@@ -526,6 +535,124 @@ caxsi_status blas_setup(caxsi_plan *p, TablePath *T) {
     return CAXSI_OK;
 }
 
+// Row-mapped TF32 split of the forward input: packed row r takes source row
+// rowmap[r] of x (the batched operators' packing), padded to Qp.
+__global__ void k_pack_split(const float *__restrict__ x, const int64_t *__restrict__ rowmap, int64_t rows, int Q,
+                             int Qp, float *__restrict__ hi, float *__restrict__ lo) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * Qp) return;
+    const int64_t r = i / Qp;
+    const int l = (int)(i - r * Qp);
+    const float v = l < Q ? x[rowmap[r] * Q + l] : 0.f;
+    float h, w;
+    tf32_split(v, h, w);
+    hi[i] = h;
+    lo[i] = w;
+}
+
+// Packed adjoint rows back to each object's [R][Q] block (rows outside an
+// object's range were cleared before).
+__global__ void k_unpack_rows(const float *__restrict__ fpk, const int64_t *__restrict__ rowmap, int64_t rows,
+                              int Q, float *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * Q) return;
+    const int64_t r = i / Q;
+    const int l = (int)(i - r * Q);
+    out[rowmap[r] * Q + l] = fpk[i];
+}
+
+// g_b = sum of object b's partial images, in item (voxel chunk) order.
+__global__ void k_sum_parts_batch(const float *__restrict__ part, const int2 *__restrict__ obj_items, int64_t npix,
+                                  float *__restrict__ g) {
+    const int b = blockIdx.y;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= npix) return;
+    const int2 oi = obj_items[b];
+    float acc = 0.f;
+    for (int c = 0; c < oi.y; ++c) acc += part[(int64_t)(oi.x + c) * npix + idx];
+    g[(int64_t)b * npix + idx] = acc;
+}
+
+template <typename X>
+cudaError_t grow(X *&ptr, int64_t &cap, int64_t need, int64_t elems_per_unit) {
+    if (need <= cap && ptr) return cudaSuccess;
+    cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&ptr, (size_t)(need > 0 ? need : 1) * elems_per_unit * sizeof(X));
+    if (e == cudaSuccess) cap = need;
+    return e;
+}
+
+// Lay out a batch: object b is voxels [ranges[2b], ranges[2b+1]); its rows are
+// packed after those of objects 0..b-1; its work items are the record kernels'
+// voxel chunks cut to its range (so each object's sums run in the same order as
+// a single-object call).  Reuses the device arrays when the layout is unchanged.
+caxsi_status batch_layout(caxsi_plan *p, TablePath *T, int nb, const int32_t *ranges, cudaStream_t s) {
+    BatchState &bs = T->batch;
+    const DevGeo &d = p->dg;
+    if (bs.nb == nb && bs.ranges.size() == (size_t)(2 * nb) &&
+        std::equal(bs.ranges.begin(), bs.ranges.end(), ranges))
+        return CAXSI_OK;
+    std::vector<int4> items;
+    std::vector<int2> oi(nb);
+    std::vector<int64_t> rowmap;
+    int64_t rows = 0;
+    const int vc = T->rec_vc;
+    for (int b = 0; b < nb; ++b) {
+        const int vb = ranges[2 * b], ve = ranges[2 * b + 1];
+        oi[b] = make_int2((int)items.size(), 0);
+        if (ve > vb) {
+            for (int c = vb / vc; c * vc < ve; ++c) {
+                const int v0 = std::max(vb, c * vc), v1 = std::min(ve, (c + 1) * vc);
+                items.push_back(make_int4(b, v0, v1, (int)(rows + (v0 - vb))));
+            }
+            for (int v = vb; v < ve; ++v) rowmap.push_back((int64_t)b * d.R + v);
+            rows += ve - vb;
+        }
+        oi[b].y = (int)items.size() - oi[b].x;
+    }
+    if (rows >= (int64_t)1 << 31) return CAXSI_ERR_INVALID;
+    int64_t icap = bs.items_cap, ncap = bs.nb_cap;
+    CAXSI_CUDA_TRY(grow(bs.items, icap, (int64_t)items.size(), 1));
+    CAXSI_CUDA_TRY(grow(bs.obj_items, ncap, nb, 1));
+    int64_t rcap = bs.rows_cap;
+    if (rows > rcap || !bs.rowmap) {
+        cudaFree(bs.rowmap);
+        cudaFree(bs.tab);
+        cudaFree(bs.f_hi);
+        cudaFree(bs.f_lo);
+        cudaFree(bs.fpk);
+        bs.rowmap = nullptr;
+        bs.tab = bs.f_hi = bs.f_lo = bs.fpk = nullptr;
+        bs.rows_cap = 0;
+        const size_t r = (size_t)(rows > 0 ? rows : 1);
+        CAXSI_CUDA_TRY(cudaMalloc(&bs.rowmap, r * sizeof(int64_t)));
+        CAXSI_CUDA_TRY(cudaMalloc(&bs.tab, r * T->Bp * sizeof(float)));
+        CAXSI_CUDA_TRY(cudaMalloc(&bs.f_hi, r * T->Qp * sizeof(float)));
+        CAXSI_CUDA_TRY(cudaMalloc(&bs.f_lo, r * T->Qp * sizeof(float)));
+        CAXSI_CUDA_TRY(cudaMalloc(&bs.fpk, r * d.Q * sizeof(float)));
+        bs.rows_cap = rows;
+    }
+    const int64_t npix = (int64_t)d.M * d.N;
+    CAXSI_CUDA_TRY(grow(bs.part, bs.part_cap, (int64_t)items.size(), npix));
+    bs.items_cap = (int)icap;
+    bs.nb_cap = (int)ncap;
+    if (!items.empty())
+        CAXSI_CUDA_TRY(cudaMemcpyAsync(bs.items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+    CAXSI_CUDA_TRY(cudaMemcpyAsync(bs.obj_items, oi.data(), nb * sizeof(int2), cudaMemcpyHostToDevice, s));
+    if (rows > 0)
+        CAXSI_CUDA_TRY(cudaMemcpyAsync(bs.rowmap, rowmap.data(), rows * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    // the host vectors are pageable: the copies have been staged when they return,
+    // but keep the device state consistent with the layout only once they are done
+    CAXSI_CUDA_TRY(cudaStreamSynchronize(s));
+    bs.ranges.assign(ranges, ranges + 2 * nb);
+    bs.nb = nb;
+    bs.rows = rows;
+    bs.n_items = (int)items.size();
+    return CAXSI_OK;
+}
+
 caxsi_status ensure_table(caxsi_plan *p, int path) {
     if (path < CAXSI_PATH_TABLE_FP32 || path > CAXSI_PATH_TABLE_FP16) return CAXSI_ERR_UNSUPPORTED;
     if (!p->table) {
@@ -662,6 +789,78 @@ caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path
                          CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
             return CAXSI_ERR_CUDA;
     }
+    return CAXSI_OK;
+}
+
+caxsi_status table_forward_batch(caxsi_plan *p, int nb, const int32_t *ranges, const float *f, float *g_out,
+                                 int path, cudaStream_t s) {
+    if (path != CAXSI_PATH_TABLE_FP32 || p->gemm_engine != 0) return CAXSI_ERR_UNSUPPORTED;
+    caxsi_status st = ensure_table(p, path);
+    if (st != CAXSI_OK) return st;
+    TablePath *T = p->table;
+    if (!T->use_records) return CAXSI_ERR_UNSUPPORTED;
+    if ((st = batch_layout(p, T, nb, ranges, s)) != CAXSI_OK) return st;
+    BatchState &bs = T->batch;
+    const DevGeo &d = p->dg;
+    const int64_t npix = (int64_t)d.M * d.N;
+    if (bs.rows > 0) {
+        {
+            CAXSI_PROF(p, "split_tf32", s);
+            k_pack_split<<<(unsigned)ceil_div64(bs.rows * T->Qp, 256), 256, 0, s>>>(f, bs.rowmap, bs.rows, d.Q,
+                                                                                 T->Qp, bs.f_hi, bs.f_lo);
+        }
+        CAXSI_LAUNCH_CHECK(p);
+        {
+            CAXSI_PROF(p, "tc_gemm_fwd_3xtf32", s);
+            CAXSI_CUDA_TRY(tc_gemm(0, 256, bs.rows, T->B, d.Q, bs.f_hi, bs.f_lo, T->Qp, T->S_hi, T->S_lo, T->Qp,
+                                   bs.tab, T->Bp, p->err_flag + 1, p->num_sms, s));
+        }
+        CAXSI_LAUNCH_CHECK(p);
+        {
+            CAXSI_PROF(p, "rec_pairs_fwd", s);
+            CAXSI_CUDA_TRY(records_forward_items(p, T, bs.items, bs.n_items, bs.tab, bs.part, s));
+        }
+        CAXSI_LAUNCH_CHECK(p);
+    }
+    {
+        CAXSI_PROF(p, "sum_parts", s);
+        k_sum_parts_batch<<<dim3((unsigned)ceil_div64(npix, 256), (unsigned)nb), 256, 0, s>>>(bs.part, bs.obj_items,
+                                                                                          npix, g_out);
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    return CAXSI_OK;
+}
+
+caxsi_status table_adjoint_batch(caxsi_plan *p, int nb, const int32_t *ranges, const float *w, float *f_out,
+                                 int path, cudaStream_t s) {
+    if (path != CAXSI_PATH_TABLE_FP32 || p->gemm_engine != 0) return CAXSI_ERR_UNSUPPORTED;
+    caxsi_status st = ensure_table(p, path);
+    if (st != CAXSI_OK) return st;
+    TablePath *T = p->table;
+    if (!T->use_records) return CAXSI_ERR_UNSUPPORTED;
+    if ((st = batch_layout(p, T, nb, ranges, s)) != CAXSI_OK) return st;
+    BatchState &bs = T->batch;
+    const DevGeo &d = p->dg;
+    const int64_t nf = (int64_t)d.R * d.Q;
+    CAXSI_CUDA_TRY(cudaMemsetAsync(f_out, 0, (size_t)nb * nf * sizeof(float), s));
+    if (bs.rows == 0) return CAXSI_OK;
+    {
+        CAXSI_PROF(p, "rec_pairs_adj", s);
+        CAXSI_CUDA_TRY(records_adjoint_items(p, T, bs.items, bs.n_items, w, (int64_t)d.M * d.N, bs.tab, s));
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    {
+        CAXSI_PROF(p, "tc_gemm_adj_3xtf32", s);
+        CAXSI_CUDA_TRY(tc_gemm(3, 128, bs.rows, d.Q, T->B, bs.tab, nullptr, T->Bp, T->St_hi, T->St_lo, T->Bp,
+                               bs.fpk, d.Q, p->err_flag + 1, p->num_sms, s));
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    {
+        CAXSI_PROF(p, "unpack_rows", s);
+        k_unpack_rows<<<(unsigned)ceil_div64(bs.rows * d.Q, 256), 256, 0, s>>>(bs.fpk, bs.rowmap, bs.rows, d.Q,
+                                                                            f_out);
+    }
+    CAXSI_LAUNCH_CHECK(p);
     return CAXSI_OK;
 }
 

@@ -3,6 +3,8 @@
 
 #include <cublas_v2.h>
 
+#include <vector>
+
 #include "internal.cuh"
 
 // One set of pair records: P groups per voxel (P = 1 for the full operator).
@@ -13,6 +15,23 @@ struct RecSet {
     uint32_t *key = nullptr;    // pixel | (t << 16)
     float *w0 = nullptr;        // c (1 - alpha)
     float *w1 = nullptr;        // c alpha
+};
+
+// Buffers and layout of the batched operators (objects = voxel ranges of the
+// shared geometry; the rows of all objects' voxels are packed).
+struct BatchState {
+    std::vector<int32_t> ranges;   // the layout the device arrays below describe
+    int nb = 0, n_items = 0;
+    int64_t rows = 0;
+    int4 *items = nullptr;         // [n_items] {obj, v0, v1, packed row of v0}
+    int64_t *rowmap = nullptr;     // [rows] source row obj * R + v of each packed row
+    int2 *obj_items = nullptr;     // [nb] {first item, items} of each object (chunk order)
+    int items_cap = 0, nb_cap = 0;
+    int64_t rows_cap = 0, part_cap = 0;
+    float *tab = nullptr;          // [rows][Bp] W / V rows
+    float *f_hi = nullptr, *f_lo = nullptr;   // [rows][Qp]
+    float *fpk = nullptr;          // [rows][Q] adjoint output rows
+    float *part = nullptr;         // [n_items][M*N] forward partial images
 };
 
 struct TablePath {
@@ -37,6 +56,7 @@ struct TablePath {
     bool use_records = false;
     RecSet rec, sub;
     int *sub_of_pix = nullptr;   // [M*N] subset of each pixel (device), when sub is built
+    BatchState batch;
     int rec_chunks = 0, rec_vc = 0;
 
     // Contractions over q on tensor cores (cuBLAS): FP32-accurate via the
@@ -126,3 +146,7 @@ static __device__ __forceinline__ void tf32_split(float x, float &hi, float &lo)
     lo = x - hi;
 }
 void records_free(TablePath *T);
+cudaError_t records_forward_items(const caxsi_plan *p, const TablePath *T, const int4 *items, int n_items,
+                                  const float *Wtab, float *part, cudaStream_t s);
+cudaError_t records_adjoint_items(const caxsi_plan *p, const TablePath *T, const int4 *items, int n_items,
+                                  const float *w, int64_t w_stride, float *Vtab, cudaStream_t s);
