@@ -81,6 +81,15 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         "l"((uint64_t)map), "r"(x), "r"(y), "r"(s_addr(bar))
         : "memory");
 }
+// Tile store from shared memory (bulk async group); rows / columns outside the
+// tensor are not written.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     (uint64_t)map),
+                 "r"(src), "r"(x), "r"(y)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
 // K-major operand, 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t sw128_desc(const void *p) {
     const uint32_t a = s_addr(p);
@@ -140,13 +149,17 @@ struct TcArgs {
     int64_t ldc;
     int *err;
     int ntn, ntiles, nk;
-    int vec_ok;  // rows of C start on 16-byte boundaries (vector stores allowed)
+    int vec_ok;     // rows of C start on 16-byte boundaries (vector stores allowed)
+    int tma_store;  // C is written by TMA tensor stores through shared memory
 };
+
+constexpr uint32_t TCG_STG = 4096;   // per epilogue warp: one 32 x 32 FP32 chunk, 128-byte swizzled
 
 template <int BN, int KIND, int NS, int NT>
 __global__ void __launch_bounds__(NT, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tA2,
-          const __grid_constant__ CUtensorMap tB, const __grid_constant__ CUtensorMap tB2, TcArgs a) {
+          const __grid_constant__ CUtensorMap tB, const __grid_constant__ CUtensorMap tB2,
+          const __grid_constant__ CUtensorMap tC, TcArgs a) {
     constexpr bool X3 = KIND == 0 || KIND == 3;
     constexpr bool SPLIT_A = KIND == 3;   // converter warps 10..13 split A in shared memory
     constexpr uint32_t A_BYTES = 128 * 128;
@@ -162,7 +175,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
     extern __shared__ unsigned char smem_raw[];
     // operand tiles need 1024-byte alignment of their shared-memory address (swizzle atoms)
     unsigned char *base = smem_raw + ((1024u - (s_addr(smem_raw) & 1023u)) & 1023u);
-    uint64_t *full = reinterpret_cast<uint64_t *>(base + NS * STAGE);
+    unsigned char *stg_base = base + NS * STAGE;   // [8 epilogue warps][TCG_STG]
+    uint64_t *full = reinterpret_cast<uint64_t *>(stg_base + 8 * TCG_STG);
     uint64_t *empty = full + NS;
     uint64_t *accf = empty + NS;
     uint64_t *acce = accf + 2;
@@ -312,7 +326,24 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                 mb_arrive(&acce[b]);
             }
             if (!ok) break;
-            if (row < a.M) {
+            if (a.tma_store) {
+                // chunk c0: lane = row, its 32 columns as 8 float4 at 16-byte slot j ^ (row & 7)
+                float4 *stg = reinterpret_cast<float4 *>(stg_base + (warp - 2) * TCG_STG);
+#pragma unroll
+                for (int c0 = 0; c0 < CW; c0 += 32) {
+                    const int col = n0 + c0;
+                    if (col >= a.N) break;   // warp-uniform
+                    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                    __syncwarp();
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        stg[lane * 8 + (j ^ (lane & 7))] = make_float4(run[c0 + 4 * j], run[c0 + 4 * j + 1],
+                                                                       run[c0 + 4 * j + 2], run[c0 + 4 * j + 3]);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) tma_store_2d(&tC, s_addr(stg), col, m0 + q * 32);
+                }
+            } else if (row < a.M) {
 #pragma unroll
                 for (int c0 = 0; c0 < CW; c0 += 32) {
                     const int col = n0 + c0;
@@ -332,6 +363,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
             }
         }
     }
+    // the tile stores must have completed before the block exits
+    if (warp >= 2 && lane == 0 && a.tma_store) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     fence_before();
     __syncthreads();
     fence_after();
@@ -378,15 +411,16 @@ bool make_map(CUtensorMap *m, const void *ptr, int elem_bytes, int64_t rows, int
 
 template <int BN, int KIND, int NS>
 cudaError_t launch_tc(const CUtensorMap &tA, const CUtensorMap &tA2, const CUtensorMap &tB,
-                      const CUtensorMap &tB2, TcArgs a, int num_sms, cudaStream_t s) {
+                      const CUtensorMap &tB2, const CUtensorMap &tC, TcArgs a, int num_sms, cudaStream_t s) {
     constexpr uint32_t STAGE = (KIND == 0 || KIND == 3 ? 2 : 1) * (128 * 128 + BN * 128);
     constexpr int NT = KIND == 3 ? TCG_THREADS + 128 : TCG_THREADS;
-    const size_t smem = 1024 + (size_t)NS * STAGE + (3 * NS + 4) * 8 + 16;
+    const size_t smem = 1024 + (size_t)NS * STAGE + 8 * TCG_STG + (3 * NS + 4) * 8 + 16;
+    static_assert(1024 + NS * STAGE + 8 * TCG_STG + (3 * NS + 4) * 8 + 16 <= 232448, "shared memory");
     auto kfn = k_tc_gemm<BN, KIND, NS, NT>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = a.ntiles < num_sms ? a.ntiles : num_sms;
-    kfn<<<grid, NT, smem, s>>>(tA, tA2, tB, tB2, a);
+    kfn<<<grid, NT, smem, s>>>(tA, tA2, tB, tB2, tC, a);
     return cudaGetLastError();
 }
 
@@ -422,17 +456,21 @@ cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const 
     a.ldc = ldc;
     a.err = err;
     a.vec_ok = ((ldc & 3) == 0) && (((uintptr_t)C & 15) == 0);
+    // C by TMA tensor stores: 32 x 32 boxes with the 128-byte swizzle of the staging buffer
+    CUtensorMap tC;
+    a.tma_store = a.vec_ok && make_map(&tC, C, 4, M, N, ldc, 32) ? 1 : 0;
+    if (!a.tma_store) tC = tA;
     a.ntn = (N + bn - 1) / bn;
     a.ntiles = ((M + 127) / 128) * a.ntn;
     a.nk = (K * eb + 127) / 128;
     if (bn == 256) {
         if (kind == 3) return cudaErrorInvalidValue;   // the on-chip A split is built for bn = 128
-        if (kind == 0) return launch_tc<256, 0, 2>(tA, tA2, tB, tB2, a, num_sms, s);
-        if (kind == 1) return launch_tc<256, 1, 4>(tA, tA2, tB, tB2, a, num_sms, s);
-        return launch_tc<256, 2, 4>(tA, tA2, tB, tB2, a, num_sms, s);
+        if (kind == 0) return launch_tc<256, 0, 2>(tA, tA2, tB, tB2, tC, a, num_sms, s);
+        if (kind == 1) return launch_tc<256, 1, 4>(tA, tA2, tB, tB2, tC, a, num_sms, s);
+        return launch_tc<256, 2, 4>(tA, tA2, tB, tB2, tC, a, num_sms, s);
     }
-    if (kind == 0) return launch_tc<128, 0, 3>(tA, tA2, tB, tB2, a, num_sms, s);
-    if (kind == 3) return launch_tc<128, 3, 3>(tA, tA2, tB, tB2, a, num_sms, s);
-    if (kind == 1) return launch_tc<128, 1, 6>(tA, tA2, tB, tB2, a, num_sms, s);
-    return launch_tc<128, 2, 6>(tA, tA2, tB, tB2, a, num_sms, s);
+    if (kind == 0) return launch_tc<128, 0, 3>(tA, tA2, tB, tB2, tC, a, num_sms, s);
+    if (kind == 3) return launch_tc<128, 3, 3>(tA, tA2, tB, tB2, tC, a, num_sms, s);
+    if (kind == 1) return launch_tc<128, 1, 6>(tA, tA2, tB, tB2, tC, a, num_sms, s);
+    return launch_tc<128, 2, 6>(tA, tA2, tB, tB2, tC, a, num_sms, s);
 }
