@@ -14,6 +14,12 @@ states (10 x 16.8 MB) exceed the 129 MB L2 together with the operator tables.
 Multi-GPU: the phantoms are independent problems; ranks take disjoint
 phantoms and run without any data-path collective (weak scaling).
 
+Reconstruction experiment (the "recon" key, rank 0): the wall time of the
+plain FP32 iterations to a fixed NMSE, and the time of each alternative to
+reach the same NMSE: bf16 / fp16 table paths, ordered subsets (8 and 64
+subsets), and the learned warm start (a U-Net trained here for --unet-steps
+objects, its training time reported apart).
+
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload per step.
 """
@@ -53,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-recon", action="store_true")
+    ap.add_argument("--unet-steps", type=int, default=1000,
+                    help="training objects of the learned warm start in the recon experiment (0: skip)")
     return ap.parse_args()
 
 
@@ -303,7 +311,7 @@ def max_over_ranks(value, dist, device=None):
 # reconstruction: time to the plain FP32 method's final NMSE
 # ---------------------------------------------------------------------------
 
-def recon_experiment(caxsi, plan, g, dev, phantom, iters=100, max_iters=300):
+def recon_experiment(caxsi, plan, g, dev, phantom, iters=100, max_iters=300, unet_steps=1000):
     """Penalised EM (Huber on the spatial neighbours) on one phantom: the plain
     FP32 table path for `iters` iterations gives the target NMSE; each
     reduced-precision path, and the ordered-subset algorithm with 8 and 64
@@ -375,8 +383,58 @@ def recon_experiment(caxsi, plan, g, dev, phantom, iters=100, max_iters=300):
                 break
         r["speedup_vs_plain"] = plain["seconds"] / r["seconds"] if r["reached"] else None
         res[f"os_em_{n_sub}"] = r
-    res["learned"] = None
+    res["learned"] = learned_experiment(plan, g, y, f_ref, plain, unet_steps) if unet_steps > 0 else None
     return res
+
+
+def learned_experiment(plan, g, y, f_ref, plain, steps):
+    """The learned warm start: a U-Net (hand-written kernels, bf16 tensor-core
+    convolutions) trained for `steps` objects of the input recipe (seeds 100000+,
+    disjoint from the benchmark phantoms); then, timed: the first EM-type iterate
+    from the flat start, the network's f^0, and EM-type iterations from f^0 until
+    the plain FP32 target NMSE.  Training time is reported apart (done once)."""
+    import torch
+    from paper_1603_06400_gb300 import warmstart
+    P = caxsi_paths()
+    maker = warmstart.PairMaker(plan, g)
+    net = warmstart.UNet(channels=g.Q, base=32, seed=0)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    losses = warmstart.train(net, maker, steps, lr=1e-3, log=max(1, steps // 10))
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    nref = float(torch.sum(f_ref.double() ** 2))
+    nmse = lambda f: float(torch.sum((f.double() - f_ref.double()) ** 2)) / nref
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    f1, _, _, beta, delta, f_init = maker.make(0, y=y, f_ref=f_ref)
+    s = float(f1.mean())
+    f = net.predict(f1, s, 1e-3 * s)
+    e1.record()
+    torch.cuda.synchronize()
+    start_s = e0.elapsed_time(e1) / 1e3
+    total, n_em = start_s, 0
+    cur = nmse(f)
+    f0_nmse = cur
+    while cur > plain["nmse"] and n_em < 300:
+        e0.record()
+        plan.recon_step(y, f, beta=beta, delta=delta, path=P["table_fp32"])
+        e1.record()
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1) / 1e3
+        n_em += 1
+        cur = nmse(f)
+    reached = cur <= plain["nmse"]
+    return {"network": "U-Net, 4 levels, base width 32, 3x3 convs (bf16 tensor-core GEMMs, FP32 accumulation)",
+            "train_steps": steps, "train_seconds": train_s, "train_loss": losses,
+            "first_iterate_and_inference_seconds": start_s, "f0_nmse": f0_nmse, "em_iterations": n_em,
+            "seconds": total, "nmse": cur, "reached": reached,
+            "speedup_vs_plain": plain["seconds"] / total if reached else None}
+
+
+def caxsi_paths():
+    from paper_1603_06400_gb300 import caxsi
+    return caxsi.PATHS
 
 
 # ---------------------------------------------------------------------------
@@ -544,7 +602,7 @@ def run_ours(args):
         "kernels": kernels,
     }
     if world == 1 and args.workload != "small" and not args.no_recon:
-        line["recon"] = recon_experiment(caxsi, plan, g, dev, phantom=0)
+        line["recon"] = recon_experiment(caxsi, plan, g, dev, phantom=0, unet_steps=args.unet_steps)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g)
     print(json.dumps(line), flush=True)

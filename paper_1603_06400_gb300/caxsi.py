@@ -105,6 +105,30 @@ def load():
             lib.caxsi_adjoint_batch.argtypes = [P, ctypes.c_int, I32P, P, I64, P, I64, ctypes.c_int, P]
             lib.caxsi_em_update.argtypes = [P, P, P, P, ctypes.c_float, ctypes.c_float, P, I64, P]
             lib.caxsi_em_update_vjp.argtypes = [P, P, P, P, ctypes.c_float, ctypes.c_float, P, P, P, I64, P]
+            V, U16 = ctypes.c_void_p, ctypes.c_void_p
+            I, F32, I64_ = ctypes.c_int, ctypes.c_float, ctypes.c_int64
+            nn = {
+                "caxsi_nn_im2col3x3": [V, I, I, I, I, U16, V],
+                "caxsi_nn_col2im3x3": [V, I, I, I, I, V, V],
+                "caxsi_nn_gemm_bf16": [I, I, I, U16, U16, V, V, V],
+                "caxsi_nn_to_bf16": [V, U16, I64_, V],
+                "caxsi_nn_transpose_bf16": [V, I, I, I, U16, V],
+                "caxsi_nn_bias_act": [V, V, I64_, I, I, V],
+                "caxsi_nn_relu_bwd": [V, V, I64_, V],
+                "caxsi_nn_bias_grad": [V, I64_, I, V, V],
+                "caxsi_nn_pool2": [V, I, I, I, I, V, V],
+                "caxsi_nn_pool2_bwd": [V, I, I, I, I, V, V],
+                "caxsi_nn_up2": [V, I, I, I, I, V, V],
+                "caxsi_nn_up2_bwd": [V, I, I, I, I, V, V],
+                "caxsi_nn_copy_channels": [V, I64_, I, I, I, V, I, I, V],
+                "caxsi_nn_scale_clamp": [V, F32, F32, V, I64_, V],
+                "caxsi_nn_adam": [V, V, V, V, I64_, F32, F32, F32, F32, I, V],
+                "caxsi_nn_axpy": [F32, V, V, I64_, V],
+                "caxsi_nn_mse": [V, V, I64_, V, V, V],
+            }
+            for name, at in nn.items():
+                getattr(lib, name).argtypes = at
+                getattr(lib, name).restype = ctypes.c_int
             lib.caxsi_status_string.argtypes = [ctypes.c_int]
             lib.caxsi_status_string.restype = ctypes.c_char_p
             for name in ("caxsi_plan_create", "caxsi_forward", "caxsi_adjoint",

@@ -201,6 +201,31 @@ def phantom(g: Geometry, seed: int, n_ellipses: int | None = None,
     return f
 
 
+def phantom_torch(g: Geometry, seed: int, device, n_ellipses: int | None = None, max_ellipses: int = 8):
+    """The phantom of `phantom` (the same random draws, ellipse tests in float64)
+    rasterised on a torch device as float32 [X][J][Q], for generating many
+    training objects quickly."""
+    import torch
+    rng = np.random.default_rng(seed)
+    if n_ellipses is None:
+        n_ellipses = int(rng.integers(1, max_ellipses + 1))
+    q = np.linspace(g.q_min, g.q_max, g.Q)
+    f = torch.zeros((g.X, g.J, g.Q), dtype=torch.float32, device=device)
+    ii = ((torch.arange(g.X, dtype=torch.float64, device=device) + 0.5) / g.X)[:, None]
+    jj = ((torch.arange(g.J, dtype=torch.float64, device=device) + 0.5) / g.J)[None, :]
+    for _ in range(n_ellipses):
+        ci, cj = rng.uniform(0.2, 0.8, size=2)
+        ai, aj = rng.uniform(0.1, 0.3, size=2)
+        rot = rng.uniform(0.0, math.pi)
+        di, dj = ii - ci, jj - cj
+        u = (math.cos(rot) * di + math.sin(rot) * dj) / ai
+        v = (-math.sin(rot) * di + math.cos(rot) * dj) / aj
+        inside = u * u + v * v <= 1.0
+        prof = torch.tensor(_profile(rng, q), dtype=torch.float32, device=device)
+        f[inside] = prof
+    return f
+
+
 def uniform_random(shape, seed: int, lo=0.0, hi=1.0) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, size=shape)
