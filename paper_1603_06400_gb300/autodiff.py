@@ -95,9 +95,10 @@ def em_step(op: Operator, y, f, b1, r=None, beta=0.0, delta=0.0):
 
 
 def unrolled_em(op: Operator, y, f0, n_iter: int = 10, r=None, beta=0.0, delta=0.0,
-                checkpoint: bool = True, relax=None):
+                checkpoint: bool = True, relax=None, floor=None):
     """n_iter EM-type iterations from f0, differentiable with respect to f0 and to
-    `relax` (optional per-iteration step scalings s_t: f <- f + s_t (U(f) - f)).
+    `relax` (optional per-iteration step scalings s_t: f <- f + s_t (U(f) - f),
+    then max(f, floor) when floor is given, so that f stays positive).
     With checkpoint=True each iteration keeps only its input for the backward
     pass and recomputes the rest."""
     with torch.no_grad():
@@ -108,6 +109,8 @@ def unrolled_em(op: Operator, y, f0, n_iter: int = 10, r=None, beta=0.0, delta=0
             fn = em_step(op, y, fc, b1, r, beta, delta)
             if relax is not None:
                 fn = fc + relax[t] * (fn - fc)
+                if floor is not None:
+                    fn = torch.clamp(fn, min=floor)
             return fn
         f = _checkpoint(step, f, use_reentrant=False) if checkpoint else step(f)
     return f

@@ -269,3 +269,35 @@ def train(net: UNet, maker: PairMaker, steps: int, lr: float = 1e-3, first_seed:
         if log is not None and (k % log == 0 or k == steps - 1):
             losses.append((k, float(loss)))
     return losses
+
+
+def train_step_scalings(net: UNet, maker: PairMaker, T: int = 10, samples: int = 40, lr: float = 2e-2,
+                        first_seed: int = 200000):
+    """Per-iteration relaxation factors s_1..s_T of the EM-type iterations that
+    follow the warm start (f <- max(f + s_t (U(f) - f), floor)), learned by
+    differentiating T unrolled, checkpointed iterations (autodiff.unrolled_em) of
+    the normalised error ||f_T - f_ref||^2 / ||f_ref||^2 over training objects."""
+    from . import autodiff
+    op = autodiff.Operator(maker.plan)
+    relax = torch.ones(T, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([relax], lr=lr)
+    for k in range(samples):
+        f1, f_ref, y, beta, delta, _ = maker.make(first_seed + k)
+        s = float(f1.mean())
+        with torch.no_grad():
+            f0 = net.predict(f1, s, 1e-3 * s)
+        out = autodiff.unrolled_em(op, y, f0, T, beta=beta, delta=delta, checkpoint=True, relax=relax,
+                                   floor=1e-3 * s)
+        loss = torch.sum((out.double() - f_ref.double()) ** 2) / torch.sum(f_ref.double() ** 2)
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+    return relax.detach()
+
+
+def relaxed_iterations(maker: PairMaker, y, f0, relax, beta, delta, floor):
+    """The EM-type iterations from f0 with step scalings `relax` (no gradients)."""
+    from . import autodiff
+    with torch.no_grad():
+        return autodiff.unrolled_em(autodiff.Operator(maker.plan), y, f0, len(relax), beta=beta, delta=delta,
+                                    checkpoint=False, relax=relax, floor=floor)

@@ -181,3 +181,21 @@ def test_warm_start_training_lowers_the_loss(ws, tiny):
     assert bool(torch.isfinite(f0).all()) and float(f0.min()) >= 1e-6 * s * (1 - 1e-6)
     assert int(net.K.err[0]) == 0
     plan.close()
+
+
+def test_step_scalings_train_and_unit_scalings_are_plain_iterations(ws, tiny):
+    torch, caxsi, warmstart = ws
+    g, phi, mask = tiny
+    plan = caxsi.Plan(g, phi, mask)
+    maker = warmstart.PairMaker(plan, g)
+    net = warmstart.UNet(channels=g.Q, base=8, seed=3)
+    relax = warmstart.train_step_scalings(net, maker, T=3, samples=3)
+    assert relax.shape == (3,) and bool(torch.isfinite(relax).all())
+    # unit scalings are the plain EM-type iterations of caxsi_recon_step
+    f1, f_ref, y, beta, delta, _ = maker.make(7)
+    f_a = warmstart.relaxed_iterations(maker, y, f1.clone(), torch.ones(3, device="cuda"), beta, delta, 0.0)
+    f_b = f1.clone()
+    for _ in range(3):
+        plan.recon_step(y, f_b, beta=beta, delta=delta, path=caxsi.PATHS["table_fp32"])
+    assert torch.allclose(f_a, f_b, rtol=1e-5, atol=1e-6 * float(f_b.abs().max()))
+    plan.close()
