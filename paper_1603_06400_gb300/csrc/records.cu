@@ -310,12 +310,25 @@ k_fwd_rec(RecArgs A, const float *__restrict__ Wtab, float *__restrict__ part, i
                 break;
             }
             if (buf) ph1 ^= 1u; else ph0 ^= 1u;
-            const int64_t b = rec_begin(A, v), e = rec_end(A, v);
-            for (int64_t q = b + tid; q < e; q += RT) {
-                const uint32_t key = A.key[q];
+            // Whole 16-byte quads per thread: a pixel occurs once per voxel, except the
+            // zero-weight pad records, which share the last record's pixel and sit in
+            // its quad, so they are accumulated by the same thread, in order.
+            const int64_t b = rec_begin(A, v);
+            const int nq = (int)((rec_end(A, v) - b) >> 2);
+            const uint4 *K4 = reinterpret_cast<const uint4 *>(A.key + b);
+            const float4 *A4 = reinterpret_cast<const float4 *>(A.w0 + b);
+            const float4 *C4 = reinterpret_cast<const float4 *>(A.w1 + b);
+            auto one = [&](uint32_t key, float a0, float a1) {
                 const int t = (int)(key >> 16);
-                const float val = fmaf(A.w0[q], w_s[t], A.w1[q] * w_s[t + 1]);
-                g_s[key & 0xffffu] += val;
+                g_s[key & 0xffffu] += fmaf(a0, w_s[t], a1 * w_s[t + 1]);
+            };
+            for (int q = tid; q < nq; q += RT) {
+                const uint4 k4 = K4[q];
+                const float4 a4 = A4[q], c4 = C4[q];
+                one(k4.x, a4.x, c4.x);
+                one(k4.y, a4.y, c4.y);
+                one(k4.z, a4.z, c4.z);
+                one(k4.w, a4.w, c4.w);
             }
             __syncthreads();
         }
