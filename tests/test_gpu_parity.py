@@ -272,3 +272,30 @@ def test_reduced_precision_error(cx, path):
     rhs = torch.sum(x.double() * plan.adjoint(y, path=p).double()).item()
     assert abs(lhs - rhs) <= 4 * RED_BOUND[path] * abs(lhs)
     plan.close()
+
+
+# --------------------------------------------------------------------------
+# Detectors beyond the pair records' 16-bit pixel field: the table paths fall
+# back to the on-the-fly interpolation kernels (FP32 only)
+# --------------------------------------------------------------------------
+
+def test_large_detector_uses_on_the_fly_table_kernels(cx):
+    caxsi, torch = cx
+    g = synth.make_geometry(X=2, J=3, Q=12, M=260, N=260, K=6, rho_y=1, p_y=0.75, p_z=0.375, dx=20.0)
+    assert g.M * g.N > 65536
+    phi = synth.tungsten_spectrum(g)
+    mask = synth.random_mask(g, 31)
+    f = synth.uniform_random((g.X, g.J, g.Q), 32) + 0.1
+    w = synth.uniform_random((g.M, g.N), 33) + 0.1
+    plan = caxsi.Plan(g, phi, mask)
+    p = caxsi.PATHS["table_fp32"]
+    gg = plan.forward(_t(torch, f), path=p).cpu().numpy()
+    fa = plan.adjoint(_t(torch, w), path=p).cpu().numpy()
+    assert plan.info()["n_records"] == 0
+    assert rel_l2(gg, oracle.forward(g, phi, mask, _f32(f))) <= REL_L2_TOL
+    assert rel_l2(fa, oracle.adjoint(g, phi, mask, _f32(w))) <= REL_L2_TOL
+    with pytest.raises(caxsi.CaxsiError) as e:     # the 16-bit paths need the records
+        plan.forward(_t(torch, f), path=caxsi.PATHS["table_bf16"])
+    assert e.value.status == 6
+    assert plan.info()["device_error"] == 0
+    plan.close()
