@@ -113,13 +113,49 @@ __device__ __forceinline__ UpdTerms upd_terms(const DevGeo &g, const float *__re
     return u;
 }
 
+// One block per voxel (blockIdx.x over nobj * R voxels), the q channels across
+// the threads: the neighbours are +-Q and +-J*Q away, no index divisions per element.
 __global__ void k_update(DevGeo g, const float *__restrict__ f, const float *__restrict__ b1,
                          const float *__restrict__ b2, float beta, float delta,
-                         float *__restrict__ fnew, int64_t n) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n) return;
-    fnew[idx] = upd_terms(g, f, b1, b2, beta, delta, idx).x;
+                         float *__restrict__ fnew) {
+    const int vv = blockIdx.x;
+    const int v = vv % g.R;
+    const int i = v / g.J, j = v - i * g.J;
+    const int64_t JQ = (int64_t)g.J * g.Q;
+    for (int l = threadIdx.x; l < g.Q; l += blockDim.x) {
+        const int64_t idx = (int64_t)vv * g.Q + l;
+        const float fh = f[idx];
+        float b3 = 0.f, b5 = 0.f;
+        if (beta != 0.f) {
+            const float nbv[4] = {i > 0 ? f[idx - JQ] : 0.f, i + 1 < g.X ? f[idx + JQ] : 0.f,
+                                  j > 0 ? f[idx - g.Q] : 0.f, j + 1 < g.J ? f[idx + g.Q] : 0.f};
+            const bool ok[4] = {i > 0, i + 1 < g.X, j > 0, j + 1 < g.J};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (!ok[q]) continue;
+                const float d = fh - nbv[q];
+                const float ad = fabsf(d);
+                b3 += 2.f * (ad <= delta ? 1.f : delta / ad);
+                b5 += fminf(fmaxf(d, -delta), delta);
+            }
+        }
+        const float chi1 = beta * (2.f * b3);
+        const float chi2 = b1[idx] + beta * (-fh * (2.f * b3) + 2.f * b5);
+        const float chi3 = fh * b2[idx];
+        float x;
+        if (chi1 > 0.f) {
+            const float disc = sqrtf(fmaf(chi2, chi2, 4.f * chi1 * chi3));
+            x = chi2 > 0.f ? (2.f * chi3) / (chi2 + disc) : (disc - chi2) / (2.f * chi1);
+        } else if (chi2 > 0.f) {
+            x = chi3 / chi2;
+        } else {
+            x = fh;
+        }
+        fnew[idx] = x;
+    }
 }
+
+inline unsigned update_threads(int Q) { return (unsigned)(Q >= 128 ? 128 : (Q + 31) / 32 * 32); }
 
 // Reverse mode of the update.  Implicit differentiation of the root:
 // (2 chi1 x + chi2) dx = dchi3 - x dchi2 - x^2 dchi1.  Pass 1, per element j: the
@@ -215,7 +251,8 @@ caxsi_status recon_update(caxsi_plan *p, const float *f_old, float beta, float d
     const int64_t n = (int64_t)p->dg.R * p->dg.Q;
     {
         CAXSI_PROF(p, "em_update", s);
-        k_update<<<(unsigned)ceil_div64(n, 256), 256, 0, s>>>(p->dg, f_old, b1, p->b2, beta, delta, p->fnew, n);
+        k_update<<<(unsigned)(n / p->dg.Q), update_threads(p->dg.Q), 0, s>>>(p->dg, f_old, b1, p->b2, beta, delta,
+                                                                            p->fnew);
     }
     CAXSI_LAUNCH_CHECK(p);
     return CAXSI_OK;
@@ -238,7 +275,7 @@ caxsi_status recon_update_ext(caxsi_plan *p, const float *f, const float *b1, co
                               float delta, float *out, int64_t n, cudaStream_t s) {
     {
         CAXSI_PROF(p, "em_update", s);
-        k_update<<<(unsigned)ceil_div64(n, 256), 256, 0, s>>>(p->dg, f, b1, b2, beta, delta, out, n);
+        k_update<<<(unsigned)(n / p->dg.Q), update_threads(p->dg.Q), 0, s>>>(p->dg, f, b1, b2, beta, delta, out);
     }
     CAXSI_LAUNCH_CHECK(p);
     return CAXSI_OK;
