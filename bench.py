@@ -164,7 +164,8 @@ def measured_peaks():
 def kernel_work(name, g, info, path, nsm):
     """Algorithmic work of one launch of the named kernel: (unit, amount, bound).
 
-    The amounts are the minimum bytes or flops the kernel's job needs (formulas in the design doc)."""
+    The amounts are the minimum bytes or flops the kernel's job needs: 12-byte records, one table row
+    per voxel, partial images; 2 R B Q flop per product pass of a contraction."""
     open_pairs = info["n_open_pairs"]
     B = info["n_breakpoints"]
     Bp = (B + 1 + 7) // 8 * 8

@@ -242,7 +242,7 @@ def test_paper_scale_sampled(cx, path):
 # --------------------------------------------------------------------------
 # Reduced precision (bf16 / fp16 operands, FP32 accumulation): the error
 # against the FP64 oracle is measured and reported; the bounds below only
-# catch a broken path (the measured values are in the test output and the design doc)
+# catch a broken path (the measured values are printed by the tests)
 # --------------------------------------------------------------------------
 
 RED_BOUND = {"table_bf16": 2e-2, "table_fp16": 5e-3, "table_bf16@cublas": 2e-2,
