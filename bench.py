@@ -18,7 +18,8 @@ Reconstruction experiment (the "recon" key, rank 0): the wall time of the
 plain FP32 iterations to a fixed NMSE, and the time of each alternative to
 reach the same NMSE: bf16 / fp16 table paths, ordered subsets (8 and 64
 subsets), and the learned warm start (a U-Net trained here for --unet-steps
-objects, its training time reported apart).
+objects, its training time reported apart).  The "batch" key times the
+batched operators on 32 objects of uneven size against one call per object.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload per step.
@@ -447,6 +448,55 @@ def learned_experiment(plan, g, y, f_ref, plain, steps):
             "speedup_vs_plain": plain["seconds"] / total if reached else None}
 
 
+def batch_experiment(plan, g, n_objects=32, reps=5):
+    """Batched operators (caxsi_forward_batch / caxsi_adjoint_batch) over
+    n_objects objects of uneven size: seeded depth slabs [v0, v1) of the voxel
+    index, extents uniform in [R/8, R].  Timed (CUDA events, after warm-up): one
+    batched forward + adjoint of all objects, against the same objects one call
+    each (full-size operators on the object's f with zeros outside its slab)."""
+    import torch
+    from paper_1603_06400_gb300 import caxsi
+    R = g.X * g.J
+    rng = np.random.default_rng(2024)
+    ranges = []
+    for _ in range(n_objects):
+        n = int(rng.integers(R // 8, R + 1))
+        v0 = int(rng.integers(0, R - n + 1))
+        ranges.append((v0, v0 + n))
+    ranges = np.array(ranges, np.int32)
+    f = torch.rand((n_objects, g.X, g.J, g.Q), device="cuda")
+    w = torch.rand((n_objects, g.M, g.N), device="cuda") + 0.5
+    fm = torch.zeros_like(f)
+    for b, (v0, v1) in enumerate(ranges):
+        fm[b].view(R, g.Q)[v0:v1] = f[b].view(R, g.Q)[v0:v1]
+    P = caxsi.PATHS["table_fp32"]
+
+    def batched():
+        plan.forward_batch(f, ranges=ranges)
+        plan.adjoint_batch(w, ranges=ranges)
+
+    def single():
+        for b in range(n_objects):
+            plan.forward(fm[b], path=P)
+            plan.adjoint(w[b], path=P)
+    out = {"objects": n_objects, "voxel_rows": int(sum(v1 - v0 for v0, v1 in ranges)),
+           "extents": "uniform in [R/8, R], R = %d voxels" % R}
+    for name, fn in (("batched", batched), ("single_calls", single)):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        out[name] = {"seconds": sec, "objects_per_s": n_objects / sec}
+    out["speedup"] = out["single_calls"]["seconds"] / out["batched"]["seconds"]
+    return out
+
+
 def caxsi_paths():
     from paper_1603_06400_gb300 import caxsi
     return caxsi.PATHS
@@ -618,6 +668,8 @@ def run_ours(args):
     }
     if world == 1 and args.workload != "small" and not args.no_recon:
         line["recon"] = recon_experiment(caxsi, plan, g, dev, phantom=0, unet_steps=args.unet_steps)
+    if world == 1 and args.workload == "paper" and not args.no_recon:
+        line["batch"] = batch_experiment(plan, g)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g)
     print(json.dumps(line), flush=True)
