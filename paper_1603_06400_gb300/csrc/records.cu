@@ -12,12 +12,15 @@
 //   adjoint:  V[v][t] += w0 w[pix],  V[v][t+1] += w1 w[pix]
 //
 // Records are voxel-major and sorted by (t, pixel) inside each voxel (a stable
-// counting sort, one warp per voxel, deterministic).  The forward accumulates
-// one voxel at a time into a shared-memory detector image (a pixel occurs at
-// most once per voxel, so there are no conflicts).  The adjoint reduces runs
-// of equal t with a warp-level segmented scan; only the runs at warp-segment
-// boundaries are combined afterwards, in a fixed order.  Neither kernel uses
-// atomics; both are deterministic.
+// counting sort, one warp per voxel, deterministic); each voxel's list is
+// padded to whole 16-byte quads with zero-weight copies of its last record.  A
+// second set groups each voxel's records by detector subset first (ordered
+// subsets, Sec. VI).  The forward accumulates one voxel at a time into a
+// shared-memory detector image, one quad per thread (a pixel occurs once per
+// voxel, and its pad copies are in the same quad).  The adjoint gives each
+// thread an equal part of the voxel's list and the runs of equal t that start
+// in it; runs that cross parts are combined through per-thread slots in a fixed
+// order.  Neither kernel uses atomics; both are deterministic.
 //
 // Record layout (structure of arrays, 12 bytes per record):
 //   key = pixel | (t << 16) (uint32), w0 (float), w1 (float).

@@ -24,6 +24,13 @@
 // knots.  Only knots inside the range of u over the open pairs, plus one
 // bracketing knot on each side, are kept.  The interval search uses a uniform
 // bucket grid over the knot range followed by a short scan.
+//
+// The per-pair stages run on the precomputed pair records (records.cu, the
+// default; deterministic) or, when the detector or the knot count exceeds the
+// records' 16-bit fields, on the on-the-fly kernels below, which find each
+// pair's interval per call (the adjoint's shared-memory row then accumulates
+// with float atomics: reproducible to rounding, not bitwise).  The
+// contractions run on the tcgen05 GEMM (tc_gemm.cu) or cuBLAS.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
