@@ -177,6 +177,11 @@ def kernel_work(name, g, info, path, nsm):
         # per open (voxel, pixel) pair: K energy terms of 8 flop (tau FMA, floor,
         # fraction, lerp FMA, accumulate FMA) plus 30 flop of scatter geometry
         return "TFLOP/s", open_pairs * (8.0 * g.K + 30.0), "alu"
+    if name == "sym_pairs_fwd":
+        # one 21-byte record per voxel pair and quadrant pixel (8 pairs), two W rows
+        # per voxel pair, one partial image per block
+        recs = (g.X * (g.J // 2)) * ((g.M // 2) * (g.N // 2))
+        return "GB/s", 21.0 * recs + 4.0 * R * Bp + 4.0 * chunks * npix, "hbm"
     if name == "rec_pairs_fwd":
         # 12-byte records, one W row per voxel, one partial image per block
         return "GB/s", 12.0 * n_rec + 4.0 * R * Bp + 4.0 * chunks * npix, "hbm"

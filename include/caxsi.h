@@ -208,7 +208,8 @@ caxsi_status caxsi_recon_step_subset(caxsi_plan *plan, int subset, const float *
  * voxels, and the pair streaming runs per voxel chunk of each object, so each
  * object's result is bit-identical to caxsi_forward / caxsi_adjoint on that
  * object alone with f = 0 outside its range (the adjoint's f is 0 outside the
- * range).  CAXSI_PATH_TABLE_FP32 with the tcgen05 engine only (UNSUPPORTED
+ * range; the single forward with CAXSI_OPT_SYMMETRY 0, since batches stream one
+ * record per open pair).  CAXSI_PATH_TABLE_FP32 with the tcgen05 engine only (UNSUPPORTED
  * otherwise).  voxel_ranges is host memory; the call is asynchronous on stream
  * after a synchronous upload when the layout changes.  Errors: INVALID (sizes,
  * ranges outside [0, X*J], n_objects outside [1, CAXSI_MAX_BATCH]),
@@ -266,7 +267,7 @@ typedef struct {
 
 caxsi_status caxsi_plan_info(caxsi_plan *plan, caxsi_plan_info_t *info);
 
-/* Plan options.
+/* Plan options (CAXSI_OPT_SYMMETRY below).
  *   CAXSI_OPT_GEMM_ENGINE: how the table paths evaluate their contractions
  *     over q: CAXSI_GEMM_TCGEN05 (default; this library's tcgen05 tensor-core
  *     kernel, 3xTF32 for TABLE_FP32, single pass for TABLE_BF16/FP16) or
@@ -275,6 +276,12 @@ caxsi_status caxsi_plan_info(caxsi_plan *plan, caxsi_plan_info_t *info);
 #define CAXSI_OPT_GEMM_ENGINE 1
 #define CAXSI_GEMM_TCGEN05 0
 #define CAXSI_GEMM_CUBLAS 1
+/*   CAXSI_OPT_SYMMETRY: 1 (default) or 0.  With 1, the table paths' forward
+ *     model uses the left-right and up-down mirror symmetries of the geometry
+ *     (Sec. III-A) when J, M and N are even: one precomputed record serves a
+ *     pair and its three mirror images (each with its own mask factor), which
+ *     halves the bytes streamed per call.  0 streams one record per open pair. */
+#define CAXSI_OPT_SYMMETRY 2
 caxsi_status caxsi_plan_set_option(caxsi_plan *plan, int key, int value);
 
 /* Kernel timing (tracing).  When enabled, every kernel the plan launches is

@@ -374,6 +374,10 @@ class Plan:
         _check(self.lib.caxsi_plan_info(self.handle, ctypes.byref(i)), "caxsi_plan_info")
         return {k: getattr(i, k) for k, _ in CPlanInfo._fields_}
 
+    def set_symmetry(self, on: bool = True):
+        """Mirror-symmetric records for the table forward (default on when the geometry allows)."""
+        _check(self.lib.caxsi_plan_set_option(self.handle, 2, int(bool(on))), "caxsi_plan_set_option")
+
     def set_gemm_engine(self, engine: str):
         """'tcgen05' (default) or 'cublas' for the table paths' contractions."""
         _check(self.lib.caxsi_plan_set_option(self.handle, 1, {"tcgen05": 0, "cublas": 1}[engine]),

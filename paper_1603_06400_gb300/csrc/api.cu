@@ -452,6 +452,10 @@ caxsi_status caxsi_plan_set_option(caxsi_plan *p, int key, int value) {
         p->gemm_engine = value;
         return CAXSI_OK;
     }
+    if (key == CAXSI_OPT_SYMMETRY && (value == 0 || value == 1)) {
+        p->no_symmetry = !value;
+        return CAXSI_OK;
+    }
     return CAXSI_ERR_INVALID;
 }
 

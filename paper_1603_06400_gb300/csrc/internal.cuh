@@ -86,6 +86,7 @@ struct caxsi_plan {
     int64_t open_pairs; // (voxel, pixel) pairs with mask factor 1
     std::vector<double> phi;  // host copy of the spectrum Phi_k
     int gemm_engine;          // table-path contractions: 0 = tcgen05 kernel, 1 = cuBLAS
+    int no_symmetry;          // 1: the table forward streams the ordinary records, not the mirror-symmetric ones
     KernelProfiler prof;
 };
 

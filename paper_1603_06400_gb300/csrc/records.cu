@@ -96,6 +96,33 @@ struct PairRec {
     float w0, w1;
 };
 
+__device__ __forceinline__ bool pair_open(const PairArgs &A, int v, int m, int n) {
+    const DevGeo &g = A.g;
+    const uint32_t word = A.tbits[((int64_t)v * g.M + m) * g.Nw + (n >> 5)];
+    return (word >> (n & 31)) & 1u;
+}
+
+// The interval and weights of pair (voxel v = (i, j), pixel (m, n)), mask factor
+// aside (ok = false when u lies outside the knot range).
+__device__ __forceinline__ PairRec pair_geometry(const PairArgs &A, const TabArgs &T, float u_first,
+                                                 float u_last, int i, int j, float4 vx, int m, int n) {
+    const DevGeo &g = A.g;
+    PairRec r;
+    r.ok = false;
+    float u, ang;
+    pair_u_angular(vx.x, vx.y, vx.w, (float)n - g.cN, A.zrow[m], g.p_y, g.Xd, u, ang);
+    if (!(u >= u_first && u <= u_last)) return r;
+    const int t = find_interval(u, T.knots, T.bstart, T.B, T.NB, T.u0, T.inv_h);
+    const float2 kn = T.knots[t];
+    const float al = (u - kn.x) * kn.y;
+    const float c = vx.z * A.god[((int64_t)i * g.M + m) * g.ND + (n - g.rho_y * j - g.d_min)] * ang;
+    r.ok = true;
+    r.t = t;
+    r.w1 = c * al;
+    r.w0 = c - r.w1;
+    return r;
+}
+
 __device__ __forceinline__ PairRec pair_record(const PairArgs &A, const TabArgs &T, float u_first,
                                                float u_last, int v, int i, int j, float4 vx, int m,
                                                int n) {
@@ -619,6 +646,143 @@ k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float
     }
 }
 
+// ---- mirror-symmetric records (forward) ------------------------------------------
+struct SymArgs {
+    int R2, J2, J, M, N, NH, npix, Bp, nrec, vc;
+    const uint32_t *tt;
+    const uint8_t *tb;
+    const float4 *w;
+};
+
+SymArgs sym_args(const caxsi_plan *p, const TablePath *T) {
+    SymArgs a;
+    a.R2 = T->sym.R2;
+    a.J = p->dg.J;
+    a.J2 = p->dg.J / 2;
+    a.M = p->dg.M;
+    a.N = p->dg.N;
+    a.NH = p->dg.N / 2;
+    a.npix = p->dg.M * p->dg.N;
+    a.Bp = T->Bp;
+    a.nrec = T->sym.nrec;
+    a.vc = T->sym.vc;
+    a.tt = T->sym.tt;
+    a.tb = T->sym.tb;
+    a.w = T->sym.w;
+    return a;
+}
+
+// Record (s, r): voxel pair s = (i, jq), v = (i, jq), v' = (i, J-1-jq); quadrant
+// pixel r = (m, n), m < M/2, n < N/2.  Mask bits: 0 (v, m, n), 1 (v, M-1-m, n),
+// 2 (v', m, N-1-n), 3 (v', M-1-m, N-1-n) [class A]; 4 (v, m, N-1-n),
+// 5 (v, M-1-m, N-1-n), 6 (v', m, n), 7 (v', M-1-m, n) [class B].
+__global__ void k_sym_build(PairArgs A, TabArgs T, int R2, int nrec, uint32_t *__restrict__ tt,
+                            uint8_t *__restrict__ tb, float4 *__restrict__ w) {
+    const DevGeo &g = A.g;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)R2 * nrec) return;
+    const int s = (int)(idx / nrec), r = (int)(idx - (int64_t)s * nrec);
+    const int J2 = g.J / 2, NH = g.N / 2;
+    const int i = s / J2, jq = s - i * J2;
+    const int v = i * g.J + jq, vp = i * g.J + (g.J - 1 - jq);
+    const int m = r / NH, n = r - m * NH;
+    const int mm = g.M - 1 - m, nn = g.N - 1 - n;
+    const float u_first = T.knots[0].x, u_last = T.knots[T.B - 1].x;
+    const float4 vx = A.vox[v];
+    const PairRec a = pair_geometry(A, T, u_first, u_last, i, jq, vx, m, n);
+    const PairRec b = pair_geometry(A, T, u_first, u_last, i, jq, vx, m, nn);
+    uint32_t bits = 0;
+    bits |= pair_open(A, v, m, n) ? 1u : 0u;
+    bits |= pair_open(A, v, mm, n) ? 2u : 0u;
+    bits |= pair_open(A, vp, m, nn) ? 4u : 0u;
+    bits |= pair_open(A, vp, mm, nn) ? 8u : 0u;
+    bits |= pair_open(A, v, m, nn) ? 16u : 0u;
+    bits |= pair_open(A, v, mm, nn) ? 32u : 0u;
+    bits |= pair_open(A, vp, m, n) ? 64u : 0u;
+    bits |= pair_open(A, vp, mm, n) ? 128u : 0u;
+    if (!a.ok) bits &= ~15u;
+    if (!b.ok) bits &= ~240u;
+    tt[idx] = (uint32_t)(a.ok ? a.t : 0) | ((uint32_t)(b.ok ? b.t : 0) << 16);
+    tb[idx] = (uint8_t)bits;
+    w[idx] = make_float4(a.ok ? a.w0 : 0.f, a.ok ? a.w1 : 0.f, b.ok ? b.w0 : 0.f, b.ok ? b.w1 : 0.f);
+}
+
+// Forward over the symmetric records: a block takes a chunk of voxel pairs; the
+// two W rows of each pair arrive by TMA bulk copies, double-buffered one pair
+// ahead; each record adds its 8 pairs' contributions to its 4 pixels (owned by
+// the record within the pair: no conflicts, no atomics).
+__global__ void __launch_bounds__(RT, 1)
+k_fwd_sym(SymArgs S, const float *__restrict__ Wtab, float *__restrict__ part, int *err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int npix_al = (S.npix + 3) & ~3;
+    float *g_s = reinterpret_cast<float *>(smem_raw);
+    float *wb = g_s + npix_al;                                  // [2 buffers][2 rows][Bp]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(wb + 4 * S.Bp);
+    const int tid = threadIdx.x;
+    const int s0 = blockIdx.x * S.vc, s1 = min(s0 + S.vc, S.R2);
+    if (s0 >= s1) return;   // block-uniform
+    const uint32_t row_bytes = (uint32_t)S.Bp * 4u;
+    auto issue = [&](int s, int buf) {
+        const int i = s / S.J2, jq = s - i * S.J2;
+        const int64_t v = (int64_t)i * S.J + jq, vp = (int64_t)i * S.J + (S.J - 1 - jq);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar[buf], 2u * row_bytes);
+        bulk_g2s(wb + (2 * buf) * S.Bp, Wtab + v * S.Bp, row_bytes, &bar[buf]);
+        bulk_g2s(wb + (2 * buf + 1) * S.Bp, Wtab + vp * S.Bp, row_bytes, &bar[buf]);
+    };
+    for (int p = tid; p < S.npix; p += RT) g_s[p] = 0.f;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        issue(s0, 0);
+    }
+    __syncthreads();
+    bool ok = true;
+    uint32_t ph0 = 0u, ph1 = 0u;
+    for (int s = s0; s < s1; ++s) {
+        const int buf = (s - s0) & 1;
+        if (tid == 0 && s + 1 < s1) issue(s + 1, buf ^ 1);   // its buffer was last read by pair s - 1
+        const int late = mbar_wait(&bar[buf], buf ? ph1 : ph0) ? 0 : 1;
+        if (__syncthreads_or(late)) {
+            ok = false;
+            break;
+        }
+        if (buf) ph1 ^= 1u; else ph0 ^= 1u;
+        const float *Wv = wb + (2 * buf) * S.Bp, *Wp = Wv + S.Bp;
+        const int64_t base = (int64_t)s * S.nrec;
+        for (int r = tid; r < S.nrec; r += RT) {
+            const uint32_t t2 = S.tt[base + r];
+            const uint32_t bits = S.tb[base + r];
+            const float4 ww = S.w[base + r];
+            const int ta = (int)(t2 & 0xffffu), tbb = (int)(t2 >> 16);
+            const float xav = fmaf(ww.x, Wv[ta], ww.y * Wv[ta + 1]);
+            const float xap = fmaf(ww.x, Wp[ta], ww.y * Wp[ta + 1]);
+            const float xbv = fmaf(ww.z, Wv[tbb], ww.w * Wv[tbb + 1]);
+            const float xbp = fmaf(ww.z, Wp[tbb], ww.w * Wp[tbb + 1]);
+            const int m = r / S.NH, n = r - m * S.NH;
+            const int mm = S.M - 1 - m, nn = S.N - 1 - n;
+            g_s[m * S.N + n] += ((bits & 1u) ? xav : 0.f) + ((bits & 64u) ? xbp : 0.f);
+            g_s[mm * S.N + n] += ((bits & 2u) ? xav : 0.f) + ((bits & 128u) ? xbp : 0.f);
+            g_s[m * S.N + nn] += ((bits & 4u) ? xap : 0.f) + ((bits & 16u) ? xbv : 0.f);
+            g_s[mm * S.N + nn] += ((bits & 8u) ? xap : 0.f) + ((bits & 32u) ? xbv : 0.f);
+        }
+        __syncthreads();
+    }
+    if (!ok) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            mbar_wait(&bar[0], ph0);
+            mbar_wait(&bar[1], ph1);
+        }
+        return;
+    }
+    float *dst = part + (int64_t)blockIdx.x * S.npix;
+    for (int p = tid; p < S.npix; p += RT) dst[p] = g_s[p];
+}
+
+size_t fwd_sym_smem(int npix, int Bp) { return (size_t)((npix + 3) & ~3) * 4 + 4 * (size_t)Bp * 4 + 16; }
+
 size_t fwd_rec_smem(int npix, int Bp) {
     return (size_t)((npix + 3) & ~3) * 4 + 2 * (size_t)Bp * 4 + 16;
 }
@@ -725,6 +889,10 @@ void records_free(TablePath *T) {
     free_set(T->sub);
     cudaFree(T->sub_of_pix);
     T->sub_of_pix = nullptr;
+    cudaFree(T->sym.tt);
+    cudaFree(T->sym.tb);
+    cudaFree(T->sym.w);
+    T->sym = SymSet();
     T->use_records = false;
 }
 
@@ -789,6 +957,54 @@ caxsi_status records_build_subsets(caxsi_plan *p, TablePath *T, int P, const int
     T->sub_of_pix = d_sub;
     p->table_bytes += (int64_t)npix * 4;
     return CAXSI_OK;
+}
+
+// Build the mirror-symmetric records when the geometry allows them (J, M, N
+// even, knots within 16 bits, shared memory for the forward); otherwise leave
+// sym.ok false (the forward then streams the ordinary records).
+caxsi_status sym_build(caxsi_plan *p, TablePath *T) {
+    const DevGeo &g = p->dg;
+    if (!T->use_records || g.J % 2 || g.M % 2 || g.N % 2 || T->B > 65535) return CAXSI_OK;
+    int smem_max = 0;
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    if ((size_t)smem_max < fwd_sym_smem(g.M * g.N, T->Bp)) return CAXSI_OK;
+    SymSet &y = T->sym;
+    y.R2 = g.X * (g.J / 2);
+    y.nrec = (g.M / 2) * (g.N / 2);
+    const int64_t n = (int64_t)y.R2 * y.nrec;
+    if (cudaMalloc(&y.tt, n * sizeof(uint32_t)) != cudaSuccess || cudaMalloc(&y.tb, n) != cudaSuccess ||
+        cudaMalloc(&y.w, n * sizeof(float4)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(y.tt);
+        cudaFree(y.tb);
+        cudaFree(y.w);
+        y = SymSet();
+        return CAXSI_OK;
+    }
+    k_sym_build<<<(unsigned)ceil_div64(n, 256), 256>>>(pair_args(p), tab_args(T), y.R2, y.nrec, y.tt, y.tb, y.w);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        cudaFree(y.tt);
+        cudaFree(y.tb);
+        cudaFree(y.w);
+        y = SymSet();
+        return CAXSI_ERR_CUDA;
+    }
+    int chunks = T->rec_chunks;   // the forward's partial images fit its buffer
+    if (chunks > y.R2) chunks = y.R2;
+    y.vc = (int)ceil_div64(y.R2, chunks);
+    y.chunks = (int)ceil_div64(y.R2, y.vc);
+    y.ok = true;
+    p->table_bytes += n * 21;
+    return CAXSI_OK;
+}
+
+cudaError_t sym_forward(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s) {
+    const int npix = p->dg.M * p->dg.N;
+    const size_t smem = fwd_sym_smem(npix, T->Bp);
+    cudaError_t e = cudaFuncSetAttribute(k_fwd_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_fwd_sym<<<T->sym.chunks, RT, smem, s>>>(sym_args(p, T), T->tab, part, p->err_flag + 1);
+    return cudaGetLastError();
 }
 
 cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, int subset, float *part, cudaStream_t s) {

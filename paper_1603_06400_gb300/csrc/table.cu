@@ -434,6 +434,8 @@ caxsi_status build_table(caxsi_plan *p) {
                           (int64_t)T->fwd_chunks * npix * 4;
         // 5. per-pair records (precomputed intervals and weights), when they fit
         if ((st = records_build(p, T)) != CAXSI_OK) break;
+        // 6. mirror-symmetric records for the forward, when the geometry allows them
+        if ((st = sym_build(p, T)) != CAXSI_OK) break;
         if (T->use_records && T->rec_chunks > T->fwd_chunks) {
             cudaFree(T->fwd_part);
             T->fwd_part = nullptr;
@@ -733,9 +735,15 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
                          CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
             return CAXSI_ERR_CUDA;
     }
-    if (T->use_records) {
+    int nparts = T->fwd_chunks;
+    if (T->use_records && subset < 0 && T->sym.ok && !p->no_symmetry) {
+        CAXSI_PROF(p, "sym_pairs_fwd", s);
+        CAXSI_CUDA_TRY(sym_forward(p, T, T->fwd_part, s));
+        nparts = T->sym.chunks;
+    } else if (T->use_records) {
         CAXSI_PROF(p, "rec_pairs_fwd", s);
         CAXSI_CUDA_TRY(records_forward(p, T, subset, T->fwd_part, s));
+        nparts = T->rec_chunks;
     } else {
         CAXSI_PROF(p, "tab_pairs_fwd", s);
         CAXSI_CUDA_TRY(dispatch_fwd(p, T, T->fwd_part, s));
@@ -744,8 +752,7 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
     const int64_t npix = (int64_t)d.M * d.N;
     {
         CAXSI_PROF(p, "sum_parts", s);
-        CAXSI_CUDA_TRY(launch_sum_parts(T->fwd_part, T->use_records ? T->rec_chunks : T->fwd_chunks,
-                                        npix, g_out, npix, s));
+        CAXSI_CUDA_TRY(launch_sum_parts(T->fwd_part, nparts, npix, g_out, npix, s));
     }
     CAXSI_LAUNCH_CHECK(p);
     return CAXSI_OK;

@@ -34,6 +34,23 @@ struct BatchState {
     float *part = nullptr;         // [n_items][M*N] forward partial images
 };
 
+// Mirror-symmetric records for the forward model.  The geometry is symmetric
+// under the left-right mirror (j, n) -> (J-1-j, N-1-n) and the up-down mirror
+// m -> M-1-m (Sec. III-A): mirrored pairs share u, the interval, alpha and c;
+// only their mask factors differ.  One record per voxel pair (j, J-1-j) and
+// quadrant pixel (m < M/2, n < N/2) holds the two geometry classes of its 8
+// pairs -- A: (v, m, n) and its mirrors, B: (v, m, N-1-n) and its mirrors --
+// and the 8 mask bits, so that the record owns its 4 pixels for both voxels.
+struct SymSet {
+    bool ok = false;
+    int R2 = 0;                // voxel pairs X * J/2
+    int nrec = 0;              // records per voxel pair (M/2)(N/2)
+    uint32_t *tt = nullptr;    // [R2 * nrec] interval of class A | class B << 16
+    uint8_t *tb = nullptr;     // [R2 * nrec] mask bits (see k_sym_build)
+    float4 *w = nullptr;       // [R2 * nrec] {w0 A, w1 A, w0 B, w1 B}
+    int chunks = 0, vc = 0;    // forward blocks, voxel pairs per block
+};
+
 struct TablePath {
     int B = 0;          // knots
     int Qp = 0;         // q row length of the 16-bit / TF32-split operand copies (multiple of 8)
@@ -55,6 +72,7 @@ struct TablePath {
     //      sorted by (t, pixel): the ordered-subset operators (built on request).
     bool use_records = false;
     RecSet rec, sub;
+    SymSet sym;
     int *sub_of_pix = nullptr;   // [M*N] subset of each pixel (device), when sub is built
     BatchState batch;
     int rec_chunks = 0, rec_vc = 0;
@@ -128,6 +146,8 @@ inline TabArgs tab_args(const TablePath *T) {
 // records.cu
 caxsi_status records_build(caxsi_plan *p, TablePath *T);
 caxsi_status records_build_subsets(caxsi_plan *p, TablePath *T, int P, const int32_t *sub_host);
+caxsi_status sym_build(caxsi_plan *p, TablePath *T);
+cudaError_t sym_forward(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s);
 cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, int subset, float *part, cudaStream_t s);
 // out_kind: 0 = FP32 rows in tab, 1 = bf16 rows in v16, 2 = fp16 rows in v16
 cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, int subset, const float *w,
