@@ -263,6 +263,9 @@ typedef struct {
     int64_t device_error;     /* 1 if a kernel of this plan gave up a bounded wait (copy or
                                  tensor-core pipeline); reading it synchronises the device
                                  and clears it */
+    int64_t n_sym_records;    /* records of the mirror-symmetric adjoint, each serving up to
+                                 four pairs (0 until built, or when the geometry has no
+                                 mirror symmetry) */
 } caxsi_plan_info_t;
 
 caxsi_status caxsi_plan_info(caxsi_plan *plan, caxsi_plan_info_t *info);
@@ -276,11 +279,13 @@ caxsi_status caxsi_plan_info(caxsi_plan *plan, caxsi_plan_info_t *info);
 #define CAXSI_OPT_GEMM_ENGINE 1
 #define CAXSI_GEMM_TCGEN05 0
 #define CAXSI_GEMM_CUBLAS 1
-/*   CAXSI_OPT_SYMMETRY: 1 (default) or 0.  With 1, the table paths' forward
- *     model uses the left-right and up-down mirror symmetries of the geometry
- *     (Sec. III-A) when J, M and N are even: one precomputed record serves a
- *     pair and its three mirror images (each with its own mask factor), which
- *     halves the bytes streamed per call.  0 streams one record per open pair. */
+/*   CAXSI_OPT_SYMMETRY: 1 (default) or 0.  With 1, the table paths' full
+ *     forward and adjoint use the left-right and up-down mirror symmetries of
+ *     the geometry (Sec. III-A) when J, M and N are even: one precomputed record
+ *     serves a pair and its mirror images (each with its own mask factor), which
+ *     about halves the bytes streamed per call.  0 streams one record per open
+ *     pair.  The subset and batched operators always stream one record per open
+ *     pair. */
 #define CAXSI_OPT_SYMMETRY 2
 caxsi_status caxsi_plan_set_option(caxsi_plan *plan, int key, int value);
 

@@ -45,7 +45,7 @@ class CPlanInfo(ctypes.Structure):
     _fields_ = [("n_offsets", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
                 ("n_breakpoints", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("n_open_pairs", ctypes.c_int64), ("n_records", ctypes.c_int64),
-                ("device_error", ctypes.c_int64)]
+                ("device_error", ctypes.c_int64), ("n_sym_records", ctypes.c_int64)]
 
 
 class CKernelStat(ctypes.Structure):
@@ -375,7 +375,8 @@ class Plan:
         return {k: getattr(i, k) for k, _ in CPlanInfo._fields_}
 
     def set_symmetry(self, on: bool = True):
-        """Mirror-symmetric records for the table forward (default on when the geometry allows)."""
+        """Mirror-symmetric records for the table paths' full forward and adjoint
+        (default on when the geometry allows)."""
         _check(self.lib.caxsi_plan_set_option(self.handle, 2, int(bool(on))), "caxsi_plan_set_option")
 
     def set_gemm_engine(self, engine: str):

@@ -432,6 +432,7 @@ caxsi_status caxsi_plan_info(caxsi_plan *p, caxsi_plan_info_t *info) {
     info->kernel_launches = p->launches;
     info->n_open_pairs = p->open_pairs;
     info->n_records = table_records(p);
+    info->n_sym_records = table_sym_records(p);
     return CAXSI_OK;
 }
 

@@ -113,6 +113,7 @@ const int *table_subset_of_pixel(const caxsi_plan *p);
 void table_destroy(caxsi_plan *p);
 int64_t table_breakpoints(const caxsi_plan *p);
 int64_t table_records(const caxsi_plan *p);
+int64_t table_sym_records(const caxsi_plan *p);
 
 // ---- recon.cu ----------------------------------------------------------------
 // sub != null: only pixels with sub[i] == subset enter (ratio 0 and no

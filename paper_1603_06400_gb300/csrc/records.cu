@@ -282,6 +282,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Bulk prefetch of [src, src + bytes) into L2, trimmed inwards to whole 16-byte
+// units (the copy's alignment rule); the trimmed edges are left to the loads.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, size_t bytes) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(src);
+    const uintptr_t b = (a + 15) & ~(uintptr_t)15, e = (a + bytes) & ~(uintptr_t)15;
+    if (e > b)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b), "r"((uint32_t)(e - b)) : "memory");
+}
 // Bounded wait: false if the phase did not complete within WAIT_LIMIT polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     for (uint32_t k = 0; k < WAIT_LIMIT; ++k)
@@ -293,7 +301,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 // chunk of an object's voxels each; a single-object call has one item per
 // block); the detector image accumulates in shared memory and is written out per
 // item; each voxel's Wtab row arrives by a TMA bulk copy, double-buffered one
-// voxel ahead.
+// voxel ahead, and the next voxel's records are prefetched into L2 meanwhile.
+constexpr int FWD_U = 2;   // quads a thread loads before it uses the first
 template <bool ITEMS>
 __global__ void __launch_bounds__(RT, 1)
 k_fwd_rec(RecArgs A, const float *__restrict__ Wtab, float *__restrict__ part, int *err) {
@@ -334,6 +343,12 @@ k_fwd_rec(RecArgs A, const float *__restrict__ Wtab, float *__restrict__ part, i
                 mbar_expect_tx(&bar[buf ^ 1], row_bytes);
                 bulk_g2s(buf ? wbuf0 : wbuf1, Wtab + (r0 + v + 1) * A.Bp, row_bytes, &bar[buf ^ 1]);
             }
+            if (tid == 32 && v + 1 < v1) {
+                const int64_t nb = rec_begin(A, v + 1), nbytes = 4 * (rec_end(A, v + 1) - nb);
+                bulk_prefetch_l2(A.key + nb, (size_t)nbytes);
+                bulk_prefetch_l2(A.w0 + nb, (size_t)nbytes);
+                bulk_prefetch_l2(A.w1 + nb, (size_t)nbytes);
+            }
             const int late = mbar_wait(&bar[buf], buf ? ph1 : ph0) ? 0 : 1;
             if (__syncthreads_or(late)) {   // block-uniform decision
                 ok = false;
@@ -352,13 +367,26 @@ k_fwd_rec(RecArgs A, const float *__restrict__ Wtab, float *__restrict__ part, i
                 const int t = (int)(key >> 16);
                 g_s[key & 0xffffu] += fmaf(a0, w_s[t], a1 * w_s[t + 1]);
             };
-            for (int q = tid; q < nq; q += RT) {
-                const uint4 k4 = K4[q];
-                const float4 a4 = A4[q], c4 = C4[q];
-                one(k4.x, a4.x, c4.x);
-                one(k4.y, a4.y, c4.y);
-                one(k4.z, a4.z, c4.z);
-                one(k4.w, a4.w, c4.w);
+            for (int q0 = tid; q0 < nq; q0 += FWD_U * RT) {
+                uint4 k4[FWD_U];
+                float4 a4[FWD_U], c4[FWD_U];
+#pragma unroll
+                for (int u = 0; u < FWD_U; ++u) {
+                    const int q = q0 + u * RT;
+                    if (q < nq) {
+                        k4[u] = K4[q];
+                        a4[u] = A4[q];
+                        c4[u] = C4[q];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < FWD_U; ++u) {
+                    if (q0 + u * RT >= nq) break;
+                    one(k4[u].x, a4[u].x, c4[u].x);
+                    one(k4[u].y, a4[u].y, c4[u].y);
+                    one(k4[u].z, a4[u].z, c4[u].z);
+                    one(k4[u].w, a4[u].w, c4[u].w);
+                }
             }
             __syncthreads();
         }
@@ -707,10 +735,13 @@ __global__ void k_sym_build(PairArgs A, TabArgs T, int R2, int nrec, uint32_t *_
     w[idx] = make_float4(a.ok ? a.w0 : 0.f, a.ok ? a.w1 : 0.f, b.ok ? b.w0 : 0.f, b.ok ? b.w1 : 0.f);
 }
 
-// Forward over the symmetric records: a block takes a chunk of voxel pairs; the
-// two W rows of each pair arrive by TMA bulk copies, double-buffered one pair
-// ahead; each record adds its 8 pairs' contributions to its 4 pixels (owned by
-// the record within the pair: no conflicts, no atomics).
+// Forward over the symmetric records: a block takes a chunk of voxel pairs;
+// the two W rows of each pair arrive by TMA bulk copies, double-buffered one
+// pair ahead, and the next pair's records are prefetched into L2 meanwhile; each
+// record adds its 8 pairs' contributions to its 4 pixels (owned by the record
+// within the pair: no conflicts, no atomics).  A thread loads SYM_U records
+// before it uses the first, so that their loads overlap.
+constexpr int SYM_U = 4;
 __global__ void __launch_bounds__(RT, 1)
 k_fwd_sym(SymArgs S, const float *__restrict__ Wtab, float *__restrict__ part, int *err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -730,6 +761,12 @@ k_fwd_sym(SymArgs S, const float *__restrict__ Wtab, float *__restrict__ part, i
         bulk_g2s(wb + (2 * buf) * S.Bp, Wtab + v * S.Bp, row_bytes, &bar[buf]);
         bulk_g2s(wb + (2 * buf + 1) * S.Bp, Wtab + vp * S.Bp, row_bytes, &bar[buf]);
     };
+    auto prefetch = [&](int s) {
+        const int64_t b = (int64_t)s * S.nrec;
+        bulk_prefetch_l2(S.tt + b, (size_t)S.nrec * 4);
+        bulk_prefetch_l2(S.tb + b, (size_t)S.nrec);
+        bulk_prefetch_l2(S.w + b, (size_t)S.nrec * 16);
+    };
     for (int p = tid; p < S.npix; p += RT) g_s[p] = 0.f;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -743,6 +780,7 @@ k_fwd_sym(SymArgs S, const float *__restrict__ Wtab, float *__restrict__ part, i
     for (int s = s0; s < s1; ++s) {
         const int buf = (s - s0) & 1;
         if (tid == 0 && s + 1 < s1) issue(s + 1, buf ^ 1);   // its buffer was last read by pair s - 1
+        if (tid == 32 && s + 1 < s1) prefetch(s + 1);
         const int late = mbar_wait(&bar[buf], buf ? ph1 : ph0) ? 0 : 1;
         if (__syncthreads_or(late)) {
             ok = false;
@@ -751,21 +789,38 @@ k_fwd_sym(SymArgs S, const float *__restrict__ Wtab, float *__restrict__ part, i
         if (buf) ph1 ^= 1u; else ph0 ^= 1u;
         const float *Wv = wb + (2 * buf) * S.Bp, *Wp = Wv + S.Bp;
         const int64_t base = (int64_t)s * S.nrec;
-        for (int r = tid; r < S.nrec; r += RT) {
-            const uint32_t t2 = S.tt[base + r];
-            const uint32_t bits = S.tb[base + r];
-            const float4 ww = S.w[base + r];
-            const int ta = (int)(t2 & 0xffffu), tbb = (int)(t2 >> 16);
-            const float xav = fmaf(ww.x, Wv[ta], ww.y * Wv[ta + 1]);
-            const float xap = fmaf(ww.x, Wp[ta], ww.y * Wp[ta + 1]);
-            const float xbv = fmaf(ww.z, Wv[tbb], ww.w * Wv[tbb + 1]);
-            const float xbp = fmaf(ww.z, Wp[tbb], ww.w * Wp[tbb + 1]);
-            const int m = r / S.NH, n = r - m * S.NH;
-            const int mm = S.M - 1 - m, nn = S.N - 1 - n;
-            g_s[m * S.N + n] += ((bits & 1u) ? xav : 0.f) + ((bits & 64u) ? xbp : 0.f);
-            g_s[mm * S.N + n] += ((bits & 2u) ? xav : 0.f) + ((bits & 128u) ? xbp : 0.f);
-            g_s[m * S.N + nn] += ((bits & 4u) ? xap : 0.f) + ((bits & 16u) ? xbv : 0.f);
-            g_s[mm * S.N + nn] += ((bits & 8u) ? xap : 0.f) + ((bits & 32u) ? xbv : 0.f);
+        for (int r0 = tid; r0 < S.nrec; r0 += SYM_U * RT) {
+            uint32_t t2[SYM_U], bits[SYM_U];
+            float4 ww[SYM_U];
+#pragma unroll
+            for (int u = 0; u < SYM_U; ++u) {
+                const int r = r0 + u * RT;
+                t2[u] = 0u;
+                bits[u] = 0u;
+                ww[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (r < S.nrec) {
+                    t2[u] = S.tt[base + r];
+                    bits[u] = S.tb[base + r];
+                    ww[u] = S.w[base + r];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < SYM_U; ++u) {
+                const int r = r0 + u * RT;
+                if (r >= S.nrec) break;
+                const int ta = (int)(t2[u] & 0xffffu), tbb = (int)(t2[u] >> 16);
+                const float xav = fmaf(ww[u].x, Wv[ta], ww[u].y * Wv[ta + 1]);
+                const float xap = fmaf(ww[u].x, Wp[ta], ww[u].y * Wp[ta + 1]);
+                const float xbv = fmaf(ww[u].z, Wv[tbb], ww[u].w * Wv[tbb + 1]);
+                const float xbp = fmaf(ww[u].z, Wp[tbb], ww[u].w * Wp[tbb + 1]);
+                const uint32_t bt = bits[u];
+                const int m = r / S.NH, n = r - m * S.NH;
+                const int mm = S.M - 1 - m, nn = S.N - 1 - n;
+                g_s[m * S.N + n] += ((bt & 1u) ? xav : 0.f) + ((bt & 64u) ? xbp : 0.f);
+                g_s[mm * S.N + n] += ((bt & 2u) ? xav : 0.f) + ((bt & 128u) ? xbp : 0.f);
+                g_s[m * S.N + nn] += ((bt & 4u) ? xap : 0.f) + ((bt & 16u) ? xbv : 0.f);
+                g_s[mm * S.N + nn] += ((bt & 8u) ? xap : 0.f) + ((bt & 32u) ? xbv : 0.f);
+            }
         }
         __syncthreads();
     }
@@ -779,6 +834,386 @@ k_fwd_sym(SymArgs S, const float *__restrict__ Wtab, float *__restrict__ part, i
     }
     float *dst = part + (int64_t)blockIdx.x * S.npix;
     for (int p = tid; p < S.npix; p += RT) dst[p] = g_s[p];
+}
+
+// ---- mirror-symmetric records (adjoint) -------------------------------------------
+// Candidate k of voxel pair (i, jq) (v = (i, jq), v' = (i, J-1-jq)): class c = k /
+// ((M/2)(N/2)), quadrant pixel r = k mod (M/2)(N/2) = (m, n0); its column is n = n0
+// for class 0 and N-1-n0 for class 1.  The record stands for the four pairs (v, m, n),
+// (v, M-1-m, n), (v', m, N-1-n), (v', M-1-m, N-1-n), which share the interval and the
+// weights of (v, m, n); ok is false when all four are closed or u is out of range.
+struct SymRec {
+    bool ok;
+    int t, m, n;
+    uint32_t bits;
+    float w0, w1;
+};
+
+__device__ __forceinline__ SymRec sym_adj_record(const PairArgs &A, const TabArgs &T, float u_first,
+                                                 float u_last, int i, int jq, float4 vx, int k) {
+    const DevGeo &g = A.g;
+    const int NH = g.N / 2, nq = (g.M / 2) * NH;
+    const int c = k >= nq ? 1 : 0, r = k - c * nq;
+    const int m = r / NH, n0 = r - m * NH;
+    const int n = c ? g.N - 1 - n0 : n0;
+    const int mm = g.M - 1 - m, nn = g.N - 1 - n;
+    const int v = i * g.J + jq, vp = i * g.J + (g.J - 1 - jq);
+    SymRec s;
+    s.ok = false;
+    s.m = m;
+    s.n = n;
+    s.bits = (pair_open(A, v, m, n) ? 1u : 0u) | (pair_open(A, v, mm, n) ? 2u : 0u) |
+             (pair_open(A, vp, m, nn) ? 4u : 0u) | (pair_open(A, vp, mm, nn) ? 8u : 0u);
+    if (!s.bits) return s;
+    const PairRec pr = pair_geometry(A, T, u_first, u_last, i, jq, vx, m, n);
+    if (!pr.ok) return s;
+    s.ok = true;
+    s.t = pr.t;
+    s.w0 = pr.w0;
+    s.w1 = pr.w1;
+    return s;
+}
+
+// Count the records of each voxel pair: one warp per pair.
+__global__ void k_sadj_count(PairArgs A, TabArgs T, int R2, int64_t *cnt) {
+    const DevGeo &g = A.g;
+    const int lane = threadIdx.x & 31;
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= R2) return;   // warp-uniform
+    const int J2 = g.J / 2, i = s / J2, jq = s - i * J2;
+    const float4 vx = A.vox[i * g.J + jq];
+    const float u_first = T.knots[0].x, u_last = T.knots[T.B - 1].x;
+    const int nk = (g.M / 2) * g.N;
+    int c = 0;
+    for (int k = lane; k < nk; k += 32) c += sym_adj_record(A, T, u_first, u_last, i, jq, vx, k).ok ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) cnt[s] = c;
+}
+
+// Fill each voxel pair's list sorted by (t, candidate index): one warp per pair, a
+// counting sort over t in a per-warp histogram; the list is padded to whole quads
+// with zero-weight copies of its last record.  Key: mask bits | (m << nbits | n) << 4
+// | t << 18, nbits the bits of a column index.
+__global__ void k_sadj_fill(PairArgs A, TabArgs T, int R2, int wpb, int nbits, const int64_t *off,
+                            uint32_t *key, float *w0, float *w1) {
+    extern __shared__ __align__(16) int rec_smem[];
+    const DevGeo &g = A.g;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = blockIdx.x * wpb + warp;
+    if (warp >= wpb || s >= R2) return;   // warp-uniform
+    int *hist = rec_smem + warp * (T.B + 1);
+    const int J2 = g.J / 2, i = s / J2, jq = s - i * J2;
+    const float4 vx = A.vox[i * g.J + jq];
+    const float u_first = T.knots[0].x, u_last = T.knots[T.B - 1].x;
+    const unsigned lt = (1u << lane) - 1u;
+    const int nk = (g.M / 2) * g.N;
+    const int64_t base = off[s], lend = off[s + 1];
+    if (lend == base) return;
+    for (int t = lane; t <= T.B; t += 32) hist[t] = 0;
+    __syncwarp();
+    for (int k = lane; k < nk; k += 32) {
+        const SymRec r = sym_adj_record(A, T, u_first, u_last, i, jq, vx, k);
+        if (r.ok) atomicAdd(&hist[r.t], 1);
+    }
+    __syncwarp();
+    const int chunk = (T.B + 31) / 32;
+    const int t0 = min(T.B, lane * chunk), t1 = min(T.B, t0 + chunk);
+    int local = 0;
+    for (int t = t0; t < t1; ++t) local += hist[t];
+    int incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    int run = incl - local;
+    for (int t = t0; t < t1; ++t) {
+        const int h = hist[t];
+        hist[t] = run;
+        run += h;
+    }
+    __syncwarp();
+    for (int kb = 0; kb < nk; kb += 32) {
+        const int k = kb + lane;
+        SymRec r;
+        r.ok = false;
+        if (k < nk) r = sym_adj_record(A, T, u_first, u_last, i, jq, vx, k);
+        const unsigned act = __ballot_sync(0xffffffffu, r.ok);
+        unsigned grp = 0;
+        int pos = 0;
+        if (r.ok) {
+            grp = __match_any_sync(act, r.t);
+            pos = hist[r.t] + __popc(grp & lt);
+        }
+        __syncwarp();
+        if (r.ok) {
+            if ((grp & lt) == 0) hist[r.t] += __popc(grp);
+            const int64_t q = base + pos;
+            key[q] = r.bits | ((((uint32_t)r.m << nbits) | (uint32_t)r.n) << 4) | ((uint32_t)r.t << 18);
+            w0[q] = r.w0;
+            w1[q] = r.w1;
+        }
+        __syncwarp();
+    }
+    const int creal = __shfl_sync(0xffffffffu, incl, 31);
+    const int npadv = (int)(lend - base) - creal;
+    if (lane < npadv) {
+        const int64_t q = base + creal + lane;
+        key[q] = key[base + creal - 1];
+        w0[q] = 0.f;
+        w1[q] = 0.f;
+    }
+}
+
+// Adjoint over the symmetric lists: the run-ownership reduction of k_adj_rec, with
+// two sums per run (voxels v and v' of the pair) and the two V rows interleaved in
+// shared memory as float2 {row v, row v'}.  A record adds w0 x and w1 x to knots t
+// and t + 1, x = w[m, n] b0 + w[M-1-m, n] b1 for v and w[m, N-1-n] b2 +
+// w[M-1-m, N-1-n] b3 for v' (b the mask bits).  The input image is held as rows
+// m < M/2 of float2 {w[m, n], w[M-1-m, n]}, so a record reads two of them.  Each
+// warp stages up to SADJ_SQ quads of its segment of the next pair's list by TMA
+// and prefetches the rest of the segment into L2.
+constexpr int SADJ_SQ = 48;
+
+struct SymAdjArgs {
+    int R2, J, J2, M, N, npix, Bp, vc, nbits;
+    const int64_t *off;
+    const uint32_t *key;
+    const float *w0, *w1;
+};
+
+__device__ __forceinline__ float2 f2fma(float a, float2 x, float2 y) {
+    return make_float2(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y));
+}
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+
+template <typename OutT>
+__global__ void __launch_bounds__(ADJ_T, 1)
+k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, int *err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int npix_al = (A.npix + 3) & ~3;
+    float2 *w2 = reinterpret_cast<float2 *>(smem_raw);                // [M/2][N] {w[m,n], w[M-1-m,n]}
+    float2 *V = reinterpret_cast<float2 *>(smem_raw + 4 * (size_t)npix_al);   // [Bp] {row v, row v'}
+    uint4 *stg_k = reinterpret_cast<uint4 *>(V + A.Bp);               // [ADJ_W][SADJ_SQ]
+    float4 *stg_a = reinterpret_cast<float4 *>(stg_k + ADJ_W * SADJ_SQ);
+    float4 *stg_c = stg_a + ADJ_W * SADJ_SQ;
+    uint4 *stg_p = reinterpret_cast<uint4 *>(stg_c + ADJ_W * SADJ_SQ);   // [ADJ_W]
+    uint32_t *slot_t = reinterpret_cast<uint32_t *>(stg_p + ADJ_W);
+    float2 *slot_lo = reinterpret_cast<float2 *>(slot_t + ADJ_T);
+    float2 *slot_hi = slot_lo + ADJ_T;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(slot_hi + ADJ_T);    // [ADJ_W]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int s0 = blockIdx.x * A.vc, s1 = min(s0 + A.vc, A.R2);
+    if (s0 >= s1) return;   // block-uniform
+
+    auto segment = [&](int64_t ob, int64_t oe, int &ws, int &we, int &perq) {
+        const int nq = (int)((oe - ob) >> 2);
+        perq = (nq + ADJ_T - 1) / ADJ_T;
+        ws = min(nq, warp * 32 * perq);
+        we = min(nq, ws + 32 * perq);
+    };
+    // Lane 0: stage the warp's segment of the list [ob, oe) (the stage was last read
+    // through the generic proxy, hence the proxy fence) and prefetch its unstaged tail.
+    auto issue = [&](int64_t ob, int64_t oe) {
+        int ws, we, perq;
+        segment(ob, oe, ws, we, perq);
+        const int ns = min(we, ws + SADJ_SQ) - ws;
+        const bool kp = ws > 0 && ws < we;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar[warp], 48u * (uint32_t)ns + (kp ? 16u : 0u));
+        if (ns > 0) {
+            const int64_t r = ob + 4 * (int64_t)ws;
+            bulk_g2s(stg_k + warp * SADJ_SQ, A.key + r, 16u * ns, &bar[warp]);
+            bulk_g2s(stg_a + warp * SADJ_SQ, A.w0 + r, 16u * ns, &bar[warp]);
+            bulk_g2s(stg_c + warp * SADJ_SQ, A.w1 + r, 16u * ns, &bar[warp]);
+        }
+        if (kp) bulk_g2s(stg_p + warp, A.key + ob + 4 * (int64_t)(ws - 1), 16u, &bar[warp]);
+        if (we > ws + ns) {
+            const int64_t r = ob + 4 * (int64_t)(ws + ns);
+            const size_t nb = 16 * (size_t)(we - ws - ns);
+            bulk_prefetch_l2(A.key + r, nb);
+            bulk_prefetch_l2(A.w0 + r, nb);
+            bulk_prefetch_l2(A.w1 + r, nb);
+        }
+    };
+
+    if (tid == 0) {
+        for (int k = 0; k < ADJ_W; ++k) mbar_init(&bar[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int t = tid; t < A.Bp; t += ADJ_T) V[t] = make_float2(0.f, 0.f);
+    {
+        const int nh = (A.M / 2) * A.N, mrow = (A.M - 1) * A.N;
+        for (int e = tid; e < nh; e += ADJ_T) {
+            const int n = e % A.N;
+            w2[e] = make_float2(w[e], w[mrow - (e - n) + n]);
+        }
+    }
+    __syncthreads();
+    uint32_t par = 0u;       // parity of the warp's outstanding phase
+    bool pending = false;    // lane 0: a staged copy is in flight
+    bool ok = true;
+    int64_t ob = A.off[s0], oe = A.off[s0 + 1];
+    if (lane == 0) {
+        issue(ob, oe);
+        pending = true;
+    }
+    const int sn = min(s0 + 1, s1 - 1);
+    int64_t on0 = A.off[sn], on1 = A.off[sn + 1];   // the next pair's list
+    const float2 zero2 = make_float2(0.f, 0.f);
+    for (int s = s0; s < s1; ++s) {
+        const int late = mbar_wait(&bar[warp], par) ? 0 : 1;
+        int ws, we, perq;
+        segment(ob, oe, ws, we, perq);
+        const int q0 = min(we, ws + lane * perq), q1 = min(we, q0 + perq);
+        const int i0 = q0 - ws, sb = warp * SADJ_SQ;
+        const uint4 *K4 = reinterpret_cast<const uint4 *>(A.key + ob);
+        const float4 *A4 = reinterpret_cast<const float4 *>(A.w0 + ob);
+        const float4 *C4 = reinterpret_cast<const float4 *>(A.w1 + ob);
+        uint4 k0 = make_uint4(0u, 0u, 0u, 0u), k1 = k0;
+        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, c0 = a0, c1 = a0;
+        uint32_t kprev = 0u;
+        if (!late) {
+            if (q0 < q1) {
+                if (i0 < SADJ_SQ) { k0 = stg_k[sb + i0]; a0 = stg_a[sb + i0]; c0 = stg_c[sb + i0]; }
+                else { k0 = K4[q0]; a0 = A4[q0]; c0 = C4[q0]; }
+                if (q0 > 0) {
+                    if (lane == 0) kprev = stg_p[warp].w;
+                    else if (i0 - 1 < SADJ_SQ) kprev = stg_k[sb + i0 - 1].w;
+                    else kprev = A.key[ob + 4 * (int64_t)q0 - 1];
+                }
+            }
+            if (q0 + 1 < q1) {
+                if (i0 + 1 < SADJ_SQ) { k1 = stg_k[sb + i0 + 1]; a1 = stg_a[sb + i0 + 1]; c1 = stg_c[sb + i0 + 1]; }
+                else { k1 = K4[q0 + 1]; a1 = A4[q0 + 1]; c1 = C4[q0 + 1]; }
+            }
+            // `dep` is 0 but depends on every register read from the stage, so the
+            // warp barrier below is passed only once those reads have completed.
+            unsigned dep = k0.x ^ k0.y ^ k0.z ^ k0.w ^ k1.x ^ k1.y ^ k1.z ^ k1.w ^ kprev ^
+                           __float_as_uint(a0.x) ^ __float_as_uint(a0.y) ^ __float_as_uint(a0.z) ^
+                           __float_as_uint(a0.w) ^ __float_as_uint(a1.x) ^ __float_as_uint(a1.y) ^
+                           __float_as_uint(a1.z) ^ __float_as_uint(a1.w) ^ __float_as_uint(c0.x) ^
+                           __float_as_uint(c0.y) ^ __float_as_uint(c0.z) ^ __float_as_uint(c0.w) ^
+                           __float_as_uint(c1.x) ^ __float_as_uint(c1.y) ^ __float_as_uint(c1.z) ^
+                           __float_as_uint(c1.w);
+            asm volatile("and.b32 %0, %0, 0;" : "+r"(dep));
+            kprev += dep;
+        }
+        __syncwarp();
+        if (lane == 0 && !late) {
+            par ^= 1u;
+            pending = false;
+            if (s + 1 < s1) {
+                issue(on0, on1);
+                pending = true;
+            }
+        }
+        ob = on0;
+        oe = on1;
+        {
+            const int sn2 = min(s + 2, s1 - 1);
+            on0 = A.off[sn2];
+            on1 = A.off[sn2 + 1];
+        }
+        if (lane != 0 && !late) par ^= 1u;
+
+        uint32_t ct = SENT, pt = SENT, st = SENT;
+        bool cont = false;
+        float2 clo = zero2, chi = zero2, ph = zero2, slo = zero2, shi = zero2;
+        if (!late && q0 < q1) {
+            cont = q0 > 0;
+            ct = (cont ? kprev : k0.x) >> 18;
+            const uint32_t nmask = (1u << A.nbits) - 1u;
+            auto take = [&](uint32_t k, float wa, float wb) {
+                const uint32_t t = k >> 18;
+                const int n = (int)((k >> 4) & nmask), m = (int)((k & 0x3ffffu) >> (4 + A.nbits));
+                const int ra = m * A.N;
+                const float2 pa = w2[ra + n], pb = w2[ra + (A.N - 1 - n)];
+                float2 x;
+                x.x = ((k & 1u) ? pa.x : 0.f) + ((k & 2u) ? pa.y : 0.f);
+                x.y = ((k & 4u) ? pb.x : 0.f) + ((k & 8u) ? pb.y : 0.f);
+                if (t != ct) {
+                    if (cont) {   // the continued run ends inside the part
+                        st = ct;
+                        slo = clo;
+                        shi = chi;
+                        cont = false;
+                    } else {      // a complete head run
+                        const float2 lo = pt + 1 == ct ? f2add(clo, ph) : clo;
+                        if (pt != SENT && pt + 1 != ct) V[pt + 1] = ph;
+                        V[ct] = lo;
+                        pt = ct;
+                        ph = chi;
+                    }
+                    ct = t;
+                    clo = zero2;
+                    chi = zero2;
+                }
+                clo = f2fma(wa, x, clo);
+                chi = f2fma(wb, x, chi);
+            };
+            auto take4 = [&](const uint4 &k, const float4 &a, const float4 &c) {
+                take(k.x, a.x, c.x);
+                take(k.y, a.y, c.y);
+                take(k.z, a.z, c.z);
+                take(k.w, a.w, c.w);
+            };
+            take4(k0, a0, c0);
+            if (q0 + 1 < q1) take4(k1, a1, c1);
+            for (int q = q0 + 2; q < q1; ++q) take4(K4[q], A4[q], C4[q]);
+            if (cont) {      // the whole part continues one run
+                st = ct;
+                slo = clo;
+                shi = chi;
+                ct = SENT;
+            }
+        }
+        slot_t[tid] = st;
+        slot_lo[tid] = slo;
+        slot_hi[tid] = shi;
+        if (__syncthreads_or(late)) {   // block-uniform decision
+            ok = false;
+            break;
+        }
+        if (ct != SENT) {    // the last head run: add its continuations, in order
+            for (int k = tid + 1; k < ADJ_T && slot_t[k] == ct; ++k) {
+                clo = f2add(clo, slot_lo[k]);
+                chi = f2add(chi, slot_hi[k]);
+            }
+            float2 lo = clo;
+            if (pt != SENT) {
+                if (pt + 1 == ct) lo = f2add(lo, ph);
+                else V[pt + 1] = ph;
+            }
+            V[ct] = lo;
+        }
+        __syncthreads();
+        if (ct != SENT) V[ct + 1] = f2add(V[ct + 1], chi);
+        __syncthreads();
+        // write rows v and v' (whole quads) and clear V for the next pair
+        const int i = s / A.J2, jq = s - i * A.J2;
+        OutT *rv = Vtab + ((int64_t)i * A.J + jq) * A.Bp;
+        OutT *rp = Vtab + ((int64_t)i * A.J + (A.J - 1 - jq)) * A.Bp;
+        float4 *V4 = reinterpret_cast<float4 *>(V);
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int t4 = tid; t4 < (A.Bp >> 2); t4 += ADJ_T) {
+            const float4 x = V4[2 * t4], y = V4[2 * t4 + 1];
+            store_v4(rv + 4 * t4, make_float4(x.x, x.z, y.x, y.z));
+            store_v4(rp + 4 * t4, make_float4(x.y, x.w, y.y, y.w));
+            V4[2 * t4] = zero4;
+            V4[2 * t4 + 1] = zero4;
+        }
+        __syncthreads();
+    }
+    if (!ok && lane == 0) {
+        // a copy did not land in time: report, drain this warp's copy in flight, stop
+        atomicExch(err, 1);
+        if (pending) mbar_wait(&bar[warp], par);
+    }
+}
+
+size_t adj_sym_smem(int npix, int Bp) {
+    return (size_t)((npix + 3) & ~3) * 4 + (size_t)Bp * 8 + (size_t)ADJ_W * SADJ_SQ * 48 + ADJ_W * 16 +
+           (size_t)ADJ_T * 20 + ADJ_W * 8;
 }
 
 size_t fwd_sym_smem(int npix, int Bp) { return (size_t)((npix + 3) & ~3) * 4 + 4 * (size_t)Bp * 4 + 16; }
@@ -892,6 +1327,7 @@ void records_free(TablePath *T) {
     cudaFree(T->sym.tt);
     cudaFree(T->sym.tb);
     cudaFree(T->sym.w);
+    free_set(T->sym.adj);
     T->sym = SymSet();
     T->use_records = false;
 }
@@ -959,6 +1395,81 @@ caxsi_status records_build_subsets(caxsi_plan *p, TablePath *T, int P, const int
     return CAXSI_OK;
 }
 
+// The adjoint's symmetric lists (SymSet::adj): count, pad to quads, fill sorted by
+// t.  Leaves adj.P = 0 (the adjoint then streams the ordinary records) when the
+// sizes do not fit the key or shared memory, or the device memory is not there.
+caxsi_status sym_adj_build(caxsi_plan *p, TablePath *T) {
+    const DevGeo &g = p->dg;
+    SymSet &y = T->sym;
+    int nbits = 0;
+    while ((1 << nbits) < g.N) ++nbits;
+    int mbits = 0;
+    while ((1 << mbits) < g.M / 2) ++mbits;
+    if (nbits + mbits > 14 || T->B > 16383) return CAXSI_OK;
+    int smem_max = 0;
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    if ((size_t)smem_max < adj_sym_smem(g.M * g.N, T->Bp)) return CAXSI_OK;
+    const int wpb = fill_warps(p, T);
+    if (wpb < 1) return CAXSI_OK;
+    const PairArgs pa = pair_args(p);
+    const TabArgs ta = tab_args(T);
+    const int64_t ng = y.R2;
+    int64_t *cnt = nullptr;
+    if (cudaMalloc(&cnt, (size_t)ng * sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return CAXSI_OK;
+    }
+    k_sadj_count<<<(unsigned)ceil_div64(ng * 32, 256), 256>>>(pa, ta, y.R2, cnt);
+    std::vector<int64_t> h(ng + 1);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpy(h.data() + 1, cnt, (size_t)ng * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaFree(cnt);
+        return CAXSI_ERR_CUDA;
+    }
+    cudaFree(cnt);
+    int64_t n_real = 0;
+    h[0] = 0;
+    for (int64_t k = 0; k < ng; ++k) {
+        n_real += h[k + 1];
+        h[k + 1] = h[k] + ((h[k + 1] + 3) & ~int64_t(3));
+    }
+    const int64_t n = h[ng];
+    const int64_t nalloc = n > 0 ? n : 4;
+    RecSet &r = y.adj;
+    if (cudaMalloc(&r.off, (size_t)(ng + 1) * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&r.key, (size_t)nalloc * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&r.w0, (size_t)nalloc * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&r.w1, (size_t)nalloc * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        free_set(r);
+        return CAXSI_OK;
+    }
+    if (cudaMemcpy(r.off, h.data(), (size_t)(ng + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+        free_set(r);
+        return CAXSI_ERR_CUDA;
+    }
+    const size_t smem = (size_t)wpb * (T->B + 1) * sizeof(int);
+    if (cudaFuncSetAttribute(k_sadj_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        free_set(r);
+        return CAXSI_ERR_CUDA;
+    }
+    k_sadj_fill<<<(unsigned)ceil_div64(ng, wpb), wpb * 32, smem>>>(pa, ta, y.R2, wpb, nbits, r.off, r.key, r.w0,
+                                                                 r.w1);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        free_set(r);
+        return CAXSI_ERR_CUDA;
+    }
+    r.P = 1;
+    r.n = n_real;
+    y.adj_nbits = nbits;
+    p->table_bytes += n * 12 + (ng + 1) * 8;
+    // one block per SM (its shared memory allows one)
+    int chunks = p->num_sms < y.R2 ? p->num_sms : y.R2;
+    y.adj_vc = (int)ceil_div64(y.R2, chunks);
+    y.adj_chunks = (int)ceil_div64(y.R2, y.adj_vc);
+    return CAXSI_OK;
+}
+
 // Build the mirror-symmetric records when the geometry allows them (J, M, N
 // even, knots within 16 bits, shared memory for the forward); otherwise leave
 // sym.ok false (the forward then streams the ordinary records).
@@ -989,13 +1500,15 @@ caxsi_status sym_build(caxsi_plan *p, TablePath *T) {
         y = SymSet();
         return CAXSI_ERR_CUDA;
     }
-    int chunks = T->rec_chunks;   // the forward's partial images fit its buffer
+    // one block per SM (the kernel's shared memory allows one); the partial
+    // images fit the forward's buffer, which holds rec_chunks of them
+    int chunks = p->num_sms < T->rec_chunks ? p->num_sms : T->rec_chunks;
     if (chunks > y.R2) chunks = y.R2;
     y.vc = (int)ceil_div64(y.R2, chunks);
     y.chunks = (int)ceil_div64(y.R2, y.vc);
     y.ok = true;
     p->table_bytes += n * 21;
-    return CAXSI_OK;
+    return sym_adj_build(p, T);
 }
 
 cudaError_t sym_forward(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s) {
@@ -1005,6 +1518,37 @@ cudaError_t sym_forward(const caxsi_plan *p, const TablePath *T, float *part, cu
     if (e != cudaSuccess) return e;
     k_fwd_sym<<<T->sym.chunks, RT, smem, s>>>(sym_args(p, T), T->tab, part, p->err_flag + 1);
     return cudaGetLastError();
+}
+
+template <typename OutT>
+cudaError_t launch_adj_sym(const caxsi_plan *p, const TablePath *T, const float *w, OutT *out, cudaStream_t s) {
+    const DevGeo &g = p->dg;
+    const size_t smem = adj_sym_smem(g.M * g.N, T->Bp);
+    cudaError_t e = cudaFuncSetAttribute(k_adj_sym<OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const SymSet &y = T->sym;
+    SymAdjArgs a;
+    a.R2 = y.R2;
+    a.J = g.J;
+    a.J2 = g.J / 2;
+    a.M = g.M;
+    a.N = g.N;
+    a.npix = g.M * g.N;
+    a.Bp = T->Bp;
+    a.vc = y.adj_vc;
+    a.nbits = y.adj_nbits;
+    a.off = y.adj.off;
+    a.key = y.adj.key;
+    a.w0 = y.adj.w0;
+    a.w1 = y.adj.w1;
+    k_adj_sym<OutT><<<y.adj_chunks, ADJ_T, smem, s>>>(a, w, out, p->err_flag + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t sym_adjoint(const caxsi_plan *p, const TablePath *T, const float *w, int out_kind, cudaStream_t s) {
+    if (out_kind == 1) return launch_adj_sym(p, T, w, reinterpret_cast<__nv_bfloat16 *>(T->v16), s);
+    if (out_kind == 2) return launch_adj_sym(p, T, w, reinterpret_cast<__half *>(T->v16), s);
+    return launch_adj_sym(p, T, w, T->tab, s);
 }
 
 cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, int subset, float *part, cudaStream_t s) {

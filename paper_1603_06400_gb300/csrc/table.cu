@@ -460,6 +460,7 @@ caxsi_status build_table(caxsi_plan *p) {
 
 int64_t table_breakpoints(const caxsi_plan *p) { return p->table ? p->table->B : 0; }
 int64_t table_records(const caxsi_plan *p) { return p->table ? p->table->rec.n : 0; }
+int64_t table_sym_records(const caxsi_plan *p) { return p->table ? p->table->sym.adj.n : 0; }
 
 namespace {
 
@@ -766,7 +767,10 @@ caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path
     const DevGeo &d = p->dg;
     const int out_kind = path == CAXSI_PATH_TABLE_FP32 ? 0 : (path == CAXSI_PATH_TABLE_BF16 ? 1 : 2);
     const bool tc = p->gemm_engine == 0 && T->use_records;
-    if (T->use_records) {
+    if (T->use_records && subset < 0 && T->sym.adj.P > 0 && !p->no_symmetry) {
+        CAXSI_PROF(p, "sym_pairs_adj", s);
+        CAXSI_CUDA_TRY(sym_adjoint(p, T, w, out_kind, s));
+    } else if (T->use_records) {
         CAXSI_PROF(p, "rec_pairs_adj", s);
         CAXSI_CUDA_TRY(records_adjoint(p, T, subset, w, out_kind, s));
     } else {

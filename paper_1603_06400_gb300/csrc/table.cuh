@@ -49,6 +49,17 @@ struct SymSet {
     uint8_t *tb = nullptr;     // [R2 * nrec] mask bits (see k_sym_build)
     float4 *w = nullptr;       // [R2 * nrec] {w0 A, w1 A, w0 B, w1 B}
     int chunks = 0, vc = 0;    // forward blocks, voxel pairs per block
+    // The adjoint's lists, one per voxel pair s (group 0 of "voxel" s), sorted by
+    // t: a record stands for the four pairs (v, m, n), (v, M-1-m, n),
+    // (v', m, N-1-n), (v', M-1-m, N-1-n) of one quadrant row m < M/2 and any
+    // column n, which share the interval and the weights; key = mask bits of the
+    // four pairs (bits 0-3, in that order) | (m << adj_nbits | n) << 4 | t << 18.
+    // Records whose four pairs are all closed are left out.  adj.P = 0 when the
+    // sizes do not fit the key (bits of m and n above 14, or B > 16383) or shared
+    // memory.
+    RecSet adj;
+    int adj_chunks = 0, adj_vc = 0;   // adjoint blocks, voxel pairs per block
+    int adj_nbits = 0;                // bits of a column index in the key
 };
 
 struct TablePath {
@@ -148,6 +159,8 @@ caxsi_status records_build(caxsi_plan *p, TablePath *T);
 caxsi_status records_build_subsets(caxsi_plan *p, TablePath *T, int P, const int32_t *sub_host);
 caxsi_status sym_build(caxsi_plan *p, TablePath *T);
 cudaError_t sym_forward(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s);
+// out_kind as for records_adjoint
+cudaError_t sym_adjoint(const caxsi_plan *p, const TablePath *T, const float *w, int out_kind, cudaStream_t s);
 cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, int subset, float *part, cudaStream_t s);
 // out_kind: 0 = FP32 rows in tab, 1 = bf16 rows in v16, 2 = fp16 rows in v16
 cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, int subset, const float *w,

@@ -302,10 +302,10 @@ def test_large_detector_uses_on_the_fly_table_kernels(cx):
 
 
 @pytest.mark.parametrize("name", ["tiny", "even_small"])
-def test_mirror_symmetric_forward_equals_the_plain_records(cx, name):
-    """The forward over mirror-symmetric records (one record per pair and its
-    three mirror images) against one record per open pair, and both against the
-    oracle."""
+def test_mirror_symmetric_operators_equal_the_plain_records(cx, name):
+    """The forward and the adjoint over mirror-symmetric records (a record serves a
+    pair and its mirror images) against one record per open pair, and both
+    against the oracle."""
     caxsi, torch = cx
     g = synth.tiny_geometry() if name == "tiny" else synth.make_geometry(
         X=3, J=6, Q=20, M=10, N=24, K=9, rho_y=2, p_y=3.0, p_z=5.0, dx=9.0)
@@ -314,10 +314,15 @@ def test_mirror_symmetric_forward_equals_the_plain_records(cx, name):
     f = synth.phantom(g, 6, n_ellipses=3) + 0.05 * synth.uniform_random((g.X, g.J, g.Q), 7)
     plan = caxsi.Plan(g, phi, mask)
     p = caxsi.PATHS["table_fp32"]
+    w = synth.uniform_random((g.M, g.N), 8) + 0.1
     sym = plan.forward(_t(torch, f), path=p).cpu().numpy()
+    sym_t = plan.adjoint(_t(torch, w), path=p).cpu().numpy()
     plan.set_symmetry(False)
     plain = plan.forward(_t(torch, f), path=p).cpu().numpy()
+    plain_t = plan.adjoint(_t(torch, w), path=p).cpu().numpy()
     assert rel_l2(sym, plain) <= 1e-6
+    assert rel_l2(sym_t, plain_t) <= 1e-6
     assert rel_l2(sym, oracle.forward(g, phi, mask, _f32(f))) <= REL_L2_TOL
+    assert rel_l2(sym_t, oracle.adjoint(g, phi, mask, _f32(w))) <= REL_L2_TOL
     assert plan.info()["device_error"] == 0
     plan.close()
