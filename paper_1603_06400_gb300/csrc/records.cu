@@ -842,9 +842,12 @@ k_fwd_sym(SymArgs S, const float *__restrict__ Wtab, float *__restrict__ part, i
 // for class 0 and N-1-n0 for class 1.  The record stands for the four pairs (v, m, n),
 // (v, M-1-m, n), (v', m, N-1-n), (v', M-1-m, N-1-n), which share the interval and the
 // weights of (v, m, n); ok is false when all four are closed or u is out of range.
+// The mask bits are in the order of the quadrant's pixels (m, n0), (M-1-m, n0),
+// (m, N-1-n0), (M-1-m, N-1-n0): for class 0 the first two pairs are v's, for class 1
+// the last two.
 struct SymRec {
     bool ok;
-    int t, m, n;
+    int t, r, c;
     uint32_t bits;
     float w0, w1;
 };
@@ -860,10 +863,11 @@ __device__ __forceinline__ SymRec sym_adj_record(const PairArgs &A, const TabArg
     const int v = i * g.J + jq, vp = i * g.J + (g.J - 1 - jq);
     SymRec s;
     s.ok = false;
-    s.m = m;
-    s.n = n;
-    s.bits = (pair_open(A, v, m, n) ? 1u : 0u) | (pair_open(A, v, mm, n) ? 2u : 0u) |
-             (pair_open(A, vp, m, nn) ? 4u : 0u) | (pair_open(A, vp, mm, nn) ? 8u : 0u);
+    s.r = r;
+    s.c = c;
+    const uint32_t b = (pair_open(A, v, m, n) ? 1u : 0u) | (pair_open(A, v, mm, n) ? 2u : 0u) |
+                       (pair_open(A, vp, m, nn) ? 4u : 0u) | (pair_open(A, vp, mm, nn) ? 8u : 0u);
+    s.bits = c ? ((b & 3u) << 2) | (b >> 2) : b;
     if (!s.bits) return s;
     const PairRec pr = pair_geometry(A, T, u_first, u_last, i, jq, vx, m, n);
     if (!pr.ok) return s;
@@ -892,10 +896,10 @@ __global__ void k_sadj_count(PairArgs A, TabArgs T, int R2, int64_t *cnt) {
 
 // Fill each voxel pair's list sorted by (t, candidate index): one warp per pair, a
 // counting sort over t in a per-warp histogram; the list is padded to whole quads
-// with zero-weight copies of its last record.  Key: mask bits | (m << nbits | n) << 4
-// | t << 18, nbits the bits of a column index.
-__global__ void k_sadj_fill(PairArgs A, TabArgs T, int R2, int wpb, int nbits, const int64_t *off,
-                            uint32_t *key, float *w0, float *w1) {
+// with zero-weight copies of its last record.  Key: mask bits | class << 4 | quadrant
+// pixel << 5 | t << 18.
+__global__ void k_sadj_fill(PairArgs A, TabArgs T, int R2, int wpb, const int64_t *off, uint32_t *key,
+                            float *w0, float *w1) {
     extern __shared__ __align__(16) int rec_smem[];
     const DevGeo &g = A.g;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -948,7 +952,7 @@ __global__ void k_sadj_fill(PairArgs A, TabArgs T, int R2, int wpb, int nbits, c
         if (r.ok) {
             if ((grp & lt) == 0) hist[r.t] += __popc(grp);
             const int64_t q = base + pos;
-            key[q] = r.bits | ((((uint32_t)r.m << nbits) | (uint32_t)r.n) << 4) | ((uint32_t)r.t << 18);
+            key[q] = r.bits | ((uint32_t)r.c << 4) | ((uint32_t)r.r << 5) | ((uint32_t)r.t << 18);
             w0[q] = r.w0;
             w1[q] = r.w1;
         }
@@ -968,14 +972,16 @@ __global__ void k_sadj_fill(PairArgs A, TabArgs T, int R2, int wpb, int nbits, c
 // two sums per run (voxels v and v' of the pair) and the two V rows interleaved in
 // shared memory as float2 {row v, row v'}.  A record adds w0 x and w1 x to knots t
 // and t + 1, x = w[m, n] b0 + w[M-1-m, n] b1 for v and w[m, N-1-n] b2 +
-// w[M-1-m, N-1-n] b3 for v' (b the mask bits).  The input image is held as rows
-// m < M/2 of float2 {w[m, n], w[M-1-m, n]}, so a record reads two of them.  Each
-// warp stages up to SADJ_SQ quads of its segment of the next pair's list by TMA
-// and prefetches the rest of the segment into L2.
+// w[M-1-m, N-1-n] b3 for v' (b the mask bits).  The input image is held per
+// quadrant pixel (m, n0) as float4 {w[m, n0], w[M-1-m, n0], w[m, N-1-n0],
+// w[M-1-m, N-1-n0]}, so a record reads one of them and its class says which half
+// is v's.  Each warp stages up to SADJ_SQ quads of its segment of the next pair's
+// list by TMA; the rest of the segment is read from global memory (an L2 prefetch
+// of it measured slower: the warp waits while its lane issues the prefetches).
 constexpr int SADJ_SQ = 48;
 
 struct SymAdjArgs {
-    int R2, J, J2, M, N, npix, Bp, vc, nbits;
+    int R2, J, J2, M, N, npix, Bp, vc;
     const int64_t *off;
     const uint32_t *key;
     const float *w0, *w1;
@@ -991,7 +997,7 @@ __global__ void __launch_bounds__(ADJ_T, 1)
 k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, int *err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int npix_al = (A.npix + 3) & ~3;
-    float2 *w2 = reinterpret_cast<float2 *>(smem_raw);                // [M/2][N] {w[m,n], w[M-1-m,n]}
+    float4 *w4 = reinterpret_cast<float4 *>(smem_raw);                // [M/2][N/2] quadrant pixels
     float2 *V = reinterpret_cast<float2 *>(smem_raw + 4 * (size_t)npix_al);   // [Bp] {row v, row v'}
     uint4 *stg_k = reinterpret_cast<uint4 *>(V + A.Bp);               // [ADJ_W][SADJ_SQ]
     float4 *stg_a = reinterpret_cast<float4 *>(stg_k + ADJ_W * SADJ_SQ);
@@ -1001,9 +1007,11 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, in
     float2 *slot_lo = reinterpret_cast<float2 *>(slot_t + ADJ_T);
     float2 *slot_hi = slot_lo + ADJ_T;
     uint64_t *bar = reinterpret_cast<uint64_t *>(slot_hi + ADJ_T);    // [ADJ_W]
+    int *offr = reinterpret_cast<int *>(bar + ADJ_W);                  // [vc + 1] list starts - off[s0]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int s0 = blockIdx.x * A.vc, s1 = min(s0 + A.vc, A.R2);
     if (s0 >= s1) return;   // block-uniform
+    const int64_t base = A.off[s0];   // the block's lists are contiguous from here
 
     auto segment = [&](int64_t ob, int64_t oe, int &ws, int &we, int &perq) {
         const int nq = (int)((oe - ob) >> 2);
@@ -1011,29 +1019,22 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, in
         ws = min(nq, warp * 32 * perq);
         we = min(nq, ws + 32 * perq);
     };
-    // Lane 0: stage the warp's segment of the list [ob, oe) (the stage was last read
-    // through the generic proxy, hence the proxy fence) and prefetch its unstaged tail.
+    // The whole warp: stage the warp's segment of the list [ob, oe), one copy per
+    // lane 0-3 after lane 0 has set the expected bytes (the stage was last read
+    // through the generic proxy, hence the proxy fences).
     auto issue = [&](int64_t ob, int64_t oe) {
         int ws, we, perq;
         segment(ob, oe, ws, we, perq);
         const int ns = min(we, ws + SADJ_SQ) - ws;
         const bool kp = ws > 0 && ws < we;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&bar[warp], 48u * (uint32_t)ns + (kp ? 16u : 0u));
-        if (ns > 0) {
-            const int64_t r = ob + 4 * (int64_t)ws;
-            bulk_g2s(stg_k + warp * SADJ_SQ, A.key + r, 16u * ns, &bar[warp]);
-            bulk_g2s(stg_a + warp * SADJ_SQ, A.w0 + r, 16u * ns, &bar[warp]);
-            bulk_g2s(stg_c + warp * SADJ_SQ, A.w1 + r, 16u * ns, &bar[warp]);
-        }
-        if (kp) bulk_g2s(stg_p + warp, A.key + ob + 4 * (int64_t)(ws - 1), 16u, &bar[warp]);
-        if (we > ws + ns) {
-            const int64_t r = ob + 4 * (int64_t)(ws + ns);
-            const size_t nb = 16 * (size_t)(we - ws - ns);
-            bulk_prefetch_l2(A.key + r, nb);
-            bulk_prefetch_l2(A.w0 + r, nb);
-            bulk_prefetch_l2(A.w1 + r, nb);
-        }
+        if (lane == 0) mbar_expect_tx(&bar[warp], 48u * (uint32_t)ns + (kp ? 16u : 0u));
+        __syncwarp();
+        if (lane < 4) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const int64_t r = ob + 4 * (int64_t)ws;
+        if (lane == 0 && ns > 0) bulk_g2s(stg_k + warp * SADJ_SQ, A.key + r, 16u * ns, &bar[warp]);
+        if (lane == 1 && ns > 0) bulk_g2s(stg_a + warp * SADJ_SQ, A.w0 + r, 16u * ns, &bar[warp]);
+        if (lane == 2 && ns > 0) bulk_g2s(stg_c + warp * SADJ_SQ, A.w1 + r, 16u * ns, &bar[warp]);
+        if (lane == 3 && kp) bulk_g2s(stg_p + warp, A.key + ob + 4 * (int64_t)(ws - 1), 16u, &bar[warp]);
     };
 
     if (tid == 0) {
@@ -1041,27 +1042,25 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, in
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int t = tid; t < A.Bp; t += ADJ_T) V[t] = make_float2(0.f, 0.f);
+    for (int k = tid; k <= s1 - s0; k += ADJ_T) offr[k] = (int)(A.off[s0 + k] - base);
     {
-        const int nh = (A.M / 2) * A.N, mrow = (A.M - 1) * A.N;
-        for (int e = tid; e < nh; e += ADJ_T) {
-            const int n = e % A.N;
-            w2[e] = make_float2(w[e], w[mrow - (e - n) + n]);
+        const int NH = A.N / 2, nq = (A.M / 2) * NH;
+        for (int e = tid; e < nq; e += ADJ_T) {
+            const int m = e / NH, n0 = e - m * NH;
+            const float *ra = w + (int64_t)m * A.N, *rb = w + (int64_t)(A.M - 1 - m) * A.N;
+            w4[e] = make_float4(ra[n0], rb[n0], ra[A.N - 1 - n0], rb[A.N - 1 - n0]);
         }
     }
     __syncthreads();
     uint32_t par = 0u;       // parity of the warp's outstanding phase
-    bool pending = false;    // lane 0: a staged copy is in flight
+    bool pending = false;    // the warp has staged copies in flight
     bool ok = true;
-    int64_t ob = A.off[s0], oe = A.off[s0 + 1];
-    if (lane == 0) {
-        issue(ob, oe);
-        pending = true;
-    }
-    const int sn = min(s0 + 1, s1 - 1);
-    int64_t on0 = A.off[sn], on1 = A.off[sn + 1];   // the next pair's list
+    issue(base, base + offr[1]);
+    pending = true;
     const float2 zero2 = make_float2(0.f, 0.f);
     for (int s = s0; s < s1; ++s) {
-        const int late = mbar_wait(&bar[warp], par) ? 0 : 1;
+        const int late = __any_sync(0xffffffffu, !mbar_wait(&bar[warp], par)) ? 1 : 0;
+        const int64_t ob = base + offr[s - s0], oe = base + offr[s - s0 + 1];
         int ws, we, perq;
         segment(ob, oe, ws, we, perq);
         const int q0 = min(we, ws + lane * perq), q1 = min(we, q0 + perq);
@@ -1069,6 +1068,8 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, in
         const uint4 *K4 = reinterpret_cast<const uint4 *>(A.key + ob);
         const float4 *A4 = reinterpret_cast<const float4 *>(A.w0 + ob);
         const float4 *C4 = reinterpret_cast<const float4 *>(A.w1 + ob);
+        // The part's first two quads come to registers (from the stage, or from
+        // global memory past it), so that the stage can be refilled at once.
         uint4 k0 = make_uint4(0u, 0u, 0u, 0u), k1 = k0;
         float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, c0 = a0, c1 = a0;
         uint32_t kprev = 0u;
@@ -1099,22 +1100,14 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, in
             kprev += dep;
         }
         __syncwarp();
-        if (lane == 0 && !late) {
+        if (!late) {   // warp-uniform
             par ^= 1u;
             pending = false;
             if (s + 1 < s1) {
-                issue(on0, on1);
+                issue(base + offr[s + 1 - s0], base + offr[s + 2 - s0]);
                 pending = true;
             }
         }
-        ob = on0;
-        oe = on1;
-        {
-            const int sn2 = min(s + 2, s1 - 1);
-            on0 = A.off[sn2];
-            on1 = A.off[sn2 + 1];
-        }
-        if (lane != 0 && !late) par ^= 1u;
 
         uint32_t ct = SENT, pt = SENT, st = SENT;
         bool cont = false;
@@ -1122,15 +1115,13 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, in
         if (!late && q0 < q1) {
             cont = q0 > 0;
             ct = (cont ? kprev : k0.x) >> 18;
-            const uint32_t nmask = (1u << A.nbits) - 1u;
             auto take = [&](uint32_t k, float wa, float wb) {
                 const uint32_t t = k >> 18;
-                const int n = (int)((k >> 4) & nmask), m = (int)((k & 0x3ffffu) >> (4 + A.nbits));
-                const int ra = m * A.N;
-                const float2 pa = w2[ra + n], pb = w2[ra + (A.N - 1 - n)];
-                float2 x;
-                x.x = ((k & 1u) ? pa.x : 0.f) + ((k & 2u) ? pa.y : 0.f);
-                x.y = ((k & 4u) ? pb.x : 0.f) + ((k & 8u) ? pb.y : 0.f);
+                const float4 c = w4[(k >> 5) & 0x1fffu];
+                const float s01 = ((k & 1u) ? c.x : 0.f) + ((k & 2u) ? c.y : 0.f);
+                const float s23 = ((k & 4u) ? c.z : 0.f) + ((k & 8u) ? c.w : 0.f);
+                const bool cls = (k & 16u) != 0u;
+                const float2 x = make_float2(cls ? s23 : s01, cls ? s01 : s23);
                 if (t != ct) {
                     if (cont) {   // the continued run ends inside the part
                         st = ct;
@@ -1205,15 +1196,15 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, in
         __syncthreads();
     }
     if (!ok && lane == 0) {
-        // a copy did not land in time: report, drain this warp's copy in flight, stop
+        // a copy did not land in time: report, drain this warp's copies in flight, stop
         atomicExch(err, 1);
         if (pending) mbar_wait(&bar[warp], par);
     }
 }
 
-size_t adj_sym_smem(int npix, int Bp) {
+size_t adj_sym_smem(int npix, int Bp, int vc) {
     return (size_t)((npix + 3) & ~3) * 4 + (size_t)Bp * 8 + (size_t)ADJ_W * SADJ_SQ * 48 + ADJ_W * 16 +
-           (size_t)ADJ_T * 20 + ADJ_W * 8;
+           (size_t)ADJ_T * 20 + ADJ_W * 8 + 4 * (size_t)(vc + 1);
 }
 
 size_t fwd_sym_smem(int npix, int Bp) { return (size_t)((npix + 3) & ~3) * 4 + 4 * (size_t)Bp * 4 + 16; }
@@ -1401,14 +1392,14 @@ caxsi_status records_build_subsets(caxsi_plan *p, TablePath *T, int P, const int
 caxsi_status sym_adj_build(caxsi_plan *p, TablePath *T) {
     const DevGeo &g = p->dg;
     SymSet &y = T->sym;
-    int nbits = 0;
-    while ((1 << nbits) < g.N) ++nbits;
-    int mbits = 0;
-    while ((1 << mbits) < g.M / 2) ++mbits;
-    if (nbits + mbits > 14 || T->B > 16383) return CAXSI_OK;
+    if ((g.M / 2) * (g.N / 2) > 8192 || T->B > 16383) return CAXSI_OK;
+    // one block per SM (its shared memory allows one)
+    const int chunks = p->num_sms < y.R2 ? p->num_sms : y.R2;
+    const int vc = (int)ceil_div64(y.R2, chunks);
+    if ((int64_t)vc * (g.M / 2) * g.N + 4 * (int64_t)vc > INT32_MAX) return CAXSI_OK;   // 32-bit list offsets
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
-    if ((size_t)smem_max < adj_sym_smem(g.M * g.N, T->Bp)) return CAXSI_OK;
+    if ((size_t)smem_max < adj_sym_smem(g.M * g.N, T->Bp, vc)) return CAXSI_OK;
     const int wpb = fill_warps(p, T);
     if (wpb < 1) return CAXSI_OK;
     const PairArgs pa = pair_args(p);
@@ -1453,20 +1444,16 @@ caxsi_status sym_adj_build(caxsi_plan *p, TablePath *T) {
         free_set(r);
         return CAXSI_ERR_CUDA;
     }
-    k_sadj_fill<<<(unsigned)ceil_div64(ng, wpb), wpb * 32, smem>>>(pa, ta, y.R2, wpb, nbits, r.off, r.key, r.w0,
-                                                                 r.w1);
+    k_sadj_fill<<<(unsigned)ceil_div64(ng, wpb), wpb * 32, smem>>>(pa, ta, y.R2, wpb, r.off, r.key, r.w0, r.w1);
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
         free_set(r);
         return CAXSI_ERR_CUDA;
     }
     r.P = 1;
     r.n = n_real;
-    y.adj_nbits = nbits;
     p->table_bytes += n * 12 + (ng + 1) * 8;
-    // one block per SM (its shared memory allows one)
-    int chunks = p->num_sms < y.R2 ? p->num_sms : y.R2;
-    y.adj_vc = (int)ceil_div64(y.R2, chunks);
-    y.adj_chunks = (int)ceil_div64(y.R2, y.adj_vc);
+    y.adj_vc = vc;
+    y.adj_chunks = (int)ceil_div64(y.R2, vc);
     return CAXSI_OK;
 }
 
@@ -1523,7 +1510,7 @@ cudaError_t sym_forward(const caxsi_plan *p, const TablePath *T, float *part, cu
 template <typename OutT>
 cudaError_t launch_adj_sym(const caxsi_plan *p, const TablePath *T, const float *w, OutT *out, cudaStream_t s) {
     const DevGeo &g = p->dg;
-    const size_t smem = adj_sym_smem(g.M * g.N, T->Bp);
+    const size_t smem = adj_sym_smem(g.M * g.N, T->Bp, T->sym.adj_vc);
     cudaError_t e = cudaFuncSetAttribute(k_adj_sym<OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const SymSet &y = T->sym;
@@ -1536,7 +1523,6 @@ cudaError_t launch_adj_sym(const caxsi_plan *p, const TablePath *T, const float 
     a.npix = g.M * g.N;
     a.Bp = T->Bp;
     a.vc = y.adj_vc;
-    a.nbits = y.adj_nbits;
     a.off = y.adj.off;
     a.key = y.adj.key;
     a.w0 = y.adj.w0;

@@ -52,14 +52,14 @@ struct SymSet {
     // The adjoint's lists, one per voxel pair s (group 0 of "voxel" s), sorted by
     // t: a record stands for the four pairs (v, m, n), (v, M-1-m, n),
     // (v', m, N-1-n), (v', M-1-m, N-1-n) of one quadrant row m < M/2 and any
-    // column n, which share the interval and the weights; key = mask bits of the
-    // four pairs (bits 0-3, in that order) | (m << adj_nbits | n) << 4 | t << 18.
-    // Records whose four pairs are all closed are left out.  adj.P = 0 when the
-    // sizes do not fit the key (bits of m and n above 14, or B > 16383) or shared
-    // memory.
+    // column n, which share the interval and the weights; key = the four mask
+    // bits in the order of the quadrant pixel (m, n0)'s images (m, n0),
+    // (M-1-m, n0), (m, N-1-n0), (M-1-m, N-1-n0) | class << 4 (0: n = n0, 1: n =
+    // N-1-n0) | quadrant pixel m (N/2) + n0 << 5 | t << 18.  Records whose four
+    // pairs are all closed are left out.  adj.P = 0 when the sizes do not fit the
+    // key ((M/2)(N/2) > 8192 or B > 16383) or shared memory.
     RecSet adj;
     int adj_chunks = 0, adj_vc = 0;   // adjoint blocks, voxel pairs per block
-    int adj_nbits = 0;                // bits of a column index in the key
 };
 
 struct TablePath {
