@@ -469,22 +469,22 @@ k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float
         ws = min(nq, warp * 32 * perq);
         we = min(nq, ws + 32 * perq);
     };
-    // Lane 0: stage the warp's segment of the voxel [ob, oe).  The stage was last
-    // read through the generic proxy, hence the proxy fence.
+    // The whole warp: stage the warp's segment of the voxel [ob, oe), one copy per
+    // lane 0-3 after lane 0 has set the expected bytes (the stage was last read
+    // through the generic proxy, hence the proxy fences).
     auto issue = [&](int64_t ob, int64_t oe) {
         int ws, we, perq;
         segment(ob, oe, ws, we, perq);
         const int ns = min(we, ws + ADJ_SQ) - ws;
         const bool kp = ws > 0 && ws < we;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&bar[warp], 48u * (uint32_t)ns + (kp ? 16u : 0u));
-        if (ns > 0) {
-            const int64_t r = ob + 4 * (int64_t)ws;
-            bulk_g2s(stg_k + warp * ADJ_SQ, A.key + r, 16u * ns, &bar[warp]);
-            bulk_g2s(stg_a + warp * ADJ_SQ, A.w0 + r, 16u * ns, &bar[warp]);
-            bulk_g2s(stg_c + warp * ADJ_SQ, A.w1 + r, 16u * ns, &bar[warp]);
-        }
-        if (kp) bulk_g2s(stg_p + warp, A.key + ob + 4 * (int64_t)(ws - 1), 16u, &bar[warp]);
+        if (lane == 0) mbar_expect_tx(&bar[warp], 48u * (uint32_t)ns + (kp ? 16u : 0u));
+        __syncwarp();
+        if (lane < 4) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const int64_t r = ob + 4 * (int64_t)ws;
+        if (lane == 0 && ns > 0) bulk_g2s(stg_k + warp * ADJ_SQ, A.key + r, 16u * ns, &bar[warp]);
+        if (lane == 1 && ns > 0) bulk_g2s(stg_a + warp * ADJ_SQ, A.w0 + r, 16u * ns, &bar[warp]);
+        if (lane == 2 && ns > 0) bulk_g2s(stg_c + warp * ADJ_SQ, A.w1 + r, 16u * ns, &bar[warp]);
+        if (lane == 3 && kp) bulk_g2s(stg_p + warp, A.key + ob + 4 * (int64_t)(ws - 1), 16u, &bar[warp]);
     };
 
     if (tid == 0) {
@@ -493,7 +493,7 @@ k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float
     }
     for (int t = tid; t < A.Bp; t += ADJ_T) V[t] = 0.f;
     uint32_t par = 0u;       // parity of the warp's outstanding phase
-    bool pending = false;    // lane 0: a staged copy is in flight
+    bool pending = false;    // the warp has staged copies in flight
     bool ok = true;
     int staged = -1;         // the object whose w is in w_s
     for (int k = blockIdx.x; k < A.n_items && ok; k += gridDim.x) {
@@ -508,14 +508,12 @@ k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float
     }
     __syncthreads();
     int64_t ob = rec_begin(A, v0), oe = rec_end(A, v0);
-    if (lane == 0) {
-        issue(ob, oe);
-        pending = true;
-    }
+    issue(ob, oe);
+    pending = true;
     const int vn = min(v0 + 1, v1 - 1);
     int64_t on0 = rec_begin(A, vn), on1 = rec_end(A, vn);   // the next voxel's list
     for (int v = v0; v < v1; ++v) {
-        const int late = mbar_wait(&bar[warp], par) ? 0 : 1;
+        const int late = __any_sync(0xffffffffu, !mbar_wait(&bar[warp], par)) ? 1 : 0;
         int ws, we, perq;
         segment(ob, oe, ws, we, perq);
         const int q0 = min(we, ws + lane * perq), q1 = min(we, q0 + perq);
@@ -553,7 +551,7 @@ k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float
             kprev += dep;
         }
         __syncwarp();
-        if (lane == 0 && !late) {
+        if (!late) {   // warp-uniform
             par ^= 1u;
             pending = false;
             if (v + 1 < v1) {
@@ -570,7 +568,6 @@ k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float
             on0 = rec_begin(A, vn2);
             on1 = rec_end(A, vn2);
         }
-        if (lane != 0 && !late) par ^= 1u;
 
         // A part that does not start the voxel begins inside the run of the record
         // before it, with zero partial sums (a zero slot if that run ends there).
