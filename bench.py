@@ -16,10 +16,13 @@ phantoms and run without any data-path collective (weak scaling).
 
 Reconstruction experiment (the "recon" key, rank 0): the wall time of the
 plain FP32 iterations to a fixed NMSE, and the time of each alternative to
-reach the same NMSE: bf16 / fp16 table paths, ordered subsets (8 and 64
-subsets), and the learned warm start (a U-Net trained here for --unet-steps
-objects, its training time reported apart).  The "batch" key times the
-batched operators on 32 objects of uneven size against one call per object.
+reach the same NMSE: bf16 / fp16 table paths, a 2048-sample u table (FP32 and
+bf16), ordered subsets (8 and 64 subsets), and the learned warm start (a U-Net
+trained here for --unet-steps objects, its training time reported apart).  The
+"precision" key gives the throughput and the error (against the exact FP32
+path) of the 16-bit contractions and of u tables of 1024-4096 samples.  The
+"batch" key times the batched operators on 32 objects of uneven size against
+one call per object.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload per step.
@@ -324,13 +327,15 @@ def max_over_ranks(value, dist, device=None):
 # reconstruction: time to the plain FP32 method's final NMSE
 # ---------------------------------------------------------------------------
 
-def recon_experiment(caxsi, plan, g, dev, phantom, iters=100, max_iters=300, unet_steps=1000):
+def recon_experiment(caxsi, plan, g, dev, phantom, iters=100, max_iters=300, unet_steps=1000,
+                     make_plan=None):
     """Penalised EM (Huber on the spatial neighbours) on one phantom: the plain
     FP32 table path for `iters` iterations gives the target NMSE; each
-    reduced-precision path, and the ordered-subset algorithm with 8 and 64
-    subsets (FP32 table path, penalty beta / P per step), is run until it
-    reaches that NMSE.  Device time of
-    the iterations only (CUDA events); NMSE = |f - f_true|^2 / |f_true|^2."""
+    reduced-precision path (16-bit contractions; a 2048-sample u table, in FP32
+    and bf16, on a plan from make_plan(2048)), and the ordered-subset algorithm
+    with 8 and 64 subsets (FP32 table path, penalty beta / P per step), is run
+    until it reaches that NMSE.  Device time of the iterations only (CUDA
+    events); NMSE = |f - f_true|^2 / |f_true|^2."""
     import torch
     f_true = torch.tensor(synth.phantom(g, phantom), dtype=torch.float32, device=dev)
     P = caxsi.PATHS
@@ -346,13 +351,14 @@ def recon_experiment(caxsi, plan, g, dev, phantom, iters=100, max_iters=300, une
     delta = 0.01 * f_init
     nref = float(torch.sum(f_ref.double() ** 2))
 
-    def run(path, target=None, n=iters):
+    def run(path, target=None, n=iters, on=None):
+        on = on or plan
         f = torch.full((g.X, g.J, g.Q), f_init, device=dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         total, hist = 0.0, []
         for it in range(n):
             e0.record()
-            plan.recon_step(y, f, beta=beta, delta=delta, path=P[path])
+            on.recon_step(y, f, beta=beta, delta=delta, path=P[path])
             e1.record()
             torch.cuda.synchronize()
             total += e0.elapsed_time(e1) / 1e3
@@ -372,6 +378,17 @@ def recon_experiment(caxsi, plan, g, dev, phantom, iters=100, max_iters=300, une
         r = run(path, target=plain["nmse"], n=max_iters)
         r["speedup_vs_plain"] = plain["seconds"] / r["seconds"] if r["reached"] else None
         res[path] = r
+    if make_plan is not None:
+        # the sampled table is another operator: its sensitivity b1 and first
+        # iteration are computed once before the timed iterations
+        sp = make_plan(2048)
+        for path in ("table_fp32", "table_bf16"):
+            sp.recon_step(y, torch.full((g.X, g.J, g.Q), f_init, device=dev), beta=beta, delta=delta,
+                          path=P[path])
+            r = run(path, target=plain["nmse"], n=max_iters, on=sp)
+            r["speedup_vs_plain"] = plain["seconds"] / r["seconds"] if r["reached"] else None
+            res["utable_2048_" + path.split("_")[1]] = r
+        sp.close()
     # ordered subsets (Algorithm 5): passes over the P subsets until the plain
     # target NMSE; the subset sensitivities b1_p are precomputed outside the
     # timing, as b1 is for the plain iterations
@@ -505,6 +522,54 @@ def batch_experiment(plan, g, n_objects=32, reps=5):
         sec = e0.elapsed_time(e1) / 1e3 / reps
         out[name] = {"seconds": sec, "objects_per_s": n_objects / sec}
     out["speedup"] = out["single_calls"]["seconds"] / out["batched"]["seconds"]
+    return out
+
+
+def precision_experiment(caxsi, plan, g, dev, make_plan, reps=20):
+    """Throughput and error of the reduced-cost operators at full size: 16-bit
+    contractions (bf16, fp16) on the exact knots, and u tables of 1024, 2048 and
+    4096 uniform samples (FP32 and bf16 contractions).  One evaluation = one
+    forward + one adjoint (CUDA events over `reps` after 3 warm-ups, inputs
+    resident); errors are relative L2 against the exact FP32 table path, which
+    is itself within 1e-6 of the FP64 oracle."""
+    import torch
+    P = caxsi.PATHS
+    f = torch.tensor(synth.phantom(g, 0), dtype=torch.float32, device=dev)
+    w = torch.rand((g.M, g.N), device=dev, generator=torch.Generator(device=dev).manual_seed(7)) + 0.5
+
+    def measure(pl, path):
+        for _ in range(3):
+            pl.forward(f, path=P[path])
+            pl.adjoint(w, path=P[path])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            pl.forward(f, path=P[path])
+            pl.adjoint(w, path=P[path])
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        return sec, pl.forward(f, path=P[path]).double(), pl.adjoint(w, path=P[path]).double()
+
+    def rel(a, b):
+        return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+    t_ref, g_ref, f_ref = measure(plan, "table_fp32")
+    out = {"table_fp32": {"evals_per_s": 1.0 / t_ref, "u_samples": "exact knots"}}
+    for path in ("table_bf16", "table_fp16"):
+        t, gg, ff = measure(plan, path)
+        out[path] = {"evals_per_s": 1.0 / t, "speedup": t_ref / t, "u_samples": "exact knots",
+                     "fwd_rel_l2": rel(gg, g_ref), "adj_rel_l2": rel(ff, f_ref)}
+    for n in (1024, 2048, 4096):
+        sp = make_plan(n)
+        for path in ("table_fp32", "table_bf16"):
+            t, gg, ff = measure(sp, path)
+            out[f"utable_{n}_{path.split('_')[1]}"] = {
+                "evals_per_s": 1.0 / t, "speedup": t_ref / t, "u_samples": n,
+                "fwd_rel_l2": rel(gg, g_ref), "adj_rel_l2": rel(ff, f_ref)}
+        sp.close()
+    out["reference"] = "exact FP32 table path (forward and adjoint of phantom 0 and a random image)"
     return out
 
 
@@ -678,8 +743,15 @@ def run_ours(args):
         "gpu_launches": launches,
         "kernels": kernels,
     }
+    def make_plan(n):
+        sp = caxsi.Plan(g, phi, mask)
+        sp.set_u_samples(n)
+        return sp
+
     if world == 1 and args.workload != "small" and not args.no_recon:
-        line["recon"] = recon_experiment(caxsi, plan, g, dev, phantom=0, unet_steps=args.unet_steps)
+        line["precision"] = precision_experiment(caxsi, plan, g, dev, make_plan)
+        line["recon"] = recon_experiment(caxsi, plan, g, dev, phantom=0, unet_steps=args.unet_steps,
+                                         make_plan=make_plan)
     if world == 1 and args.workload == "paper" and not args.no_recon:
         line["batch"] = batch_experiment(plan, g)
     if world == 1 and not args.no_cpu_baseline:

@@ -287,6 +287,17 @@ caxsi_status caxsi_plan_info(caxsi_plan *plan, caxsi_plan_info_t *info);
  *     pair.  The subset and batched operators always stream one record per open
  *     pair. */
 #define CAXSI_OPT_SYMMETRY 2
+/*   CAXSI_OPT_U_SAMPLES: 0 (default) or N in [2, CAXSI_MAX_U_SAMPLES].  With 0
+ *     the table paths interpolate W(r, u) between the exact knots, where it is
+ *     piecewise linear (exact up to rounding).  With N they sample it at N
+ *     uniformly spaced u over the same range and interpolate linearly between
+ *     the samples: an approximation of A (and the exact transpose of that
+ *     approximation as the adjoint), the table-path counterpart of the paper's
+ *     scatter-angle interpolation (Sec. III-B), with N/B of the table bytes and
+ *     of the contraction work.  It must be set before the first table-path call
+ *     of the plan (INVALID afterwards, unless the value is unchanged). */
+#define CAXSI_OPT_U_SAMPLES 3
+#define CAXSI_MAX_U_SAMPLES 8192
 caxsi_status caxsi_plan_set_option(caxsi_plan *plan, int key, int value);
 
 /* Kernel timing (tracing).  When enabled, every kernel the plan launches is

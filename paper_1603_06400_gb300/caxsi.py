@@ -374,6 +374,12 @@ class Plan:
         _check(self.lib.caxsi_plan_info(self.handle, ctypes.byref(i)), "caxsi_plan_info")
         return {k: getattr(i, k) for k, _ in CPlanInfo._fields_}
 
+    def set_u_samples(self, n: int = 0):
+        """Table paths: 0 (default) interpolates W between the exact knots; n >= 2
+        samples it at n uniform u and interpolates between them (an approximation
+        of A, cheaper by B/n).  Set it before the first table-path call."""
+        _check(self.lib.caxsi_plan_set_option(self.handle, 3, int(n)), "caxsi_plan_set_option")
+
     def set_symmetry(self, on: bool = True):
         """Mirror-symmetric records for the table paths' full forward and adjoint
         (default on when the geometry allows)."""

@@ -87,6 +87,7 @@ struct caxsi_plan {
     std::vector<double> phi;  // host copy of the spectrum Phi_k
     int gemm_engine;          // table-path contractions: 0 = tcgen05 kernel, 1 = cuBLAS
     int no_symmetry;          // 1: the table forward streams the ordinary records, not the mirror-symmetric ones
+    int u_samples;            // table paths: 0 = the exact knots; N >= 2: N uniform samples of u (approximate)
     KernelProfiler prof;
 };
 

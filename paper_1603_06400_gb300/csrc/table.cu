@@ -353,6 +353,16 @@ caxsi_status build_table(caxsi_plan *p) {
         }
         if (hi - lo + 1 < 2) { if (hi + 1 < (int)kn.size()) ++hi; else if (lo > 0) --lo; }
         std::vector<float> knots(kn.begin() + lo, kn.begin() + hi + 1);
+        if (p->u_samples >= 2) {
+            // N uniform samples over the same range instead of the exact knots: W is
+            // then interpolated between samples (an approximation of A)
+            const int N = p->u_samples;
+            const double u_a = knots.front(), u_b = knots.back();
+            knots.resize(N);
+            for (int j = 0; j < N; ++j) knots[j] = (float)(u_a + (u_b - u_a) * j / (N - 1));
+            knots.back() = (float)u_b;
+            knots.erase(std::unique(knots.begin(), knots.end()), knots.end());
+        }
         const int B = (int)knots.size();
         if (B < 2 || B > 65535) { st = CAXSI_ERR_UNSUPPORTED; break; }
         T->B = B;
