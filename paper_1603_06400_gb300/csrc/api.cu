@@ -93,12 +93,13 @@ caxsi_status alloc_scratch(caxsi_plan *p) {
     CAXSI_CUDA_TRY(cudaMalloc(&p->ones, npix * sizeof(float)));
     CAXSI_CUDA_TRY(cudaMalloc(&p->b2, nf * sizeof(float)));
     CAXSI_CUDA_TRY(cudaMalloc(&p->fnew, nf * sizeof(float)));
-    p->nll_blocks = (int)(ceil_div64(npix, 256) < 2 * p->num_sms ? ceil_div64(npix, 256) : 2 * p->num_sms);
+    p->nll_blocks = (int)(ceil_div64(npix, NLL_THREADS) < 2 * p->num_sms ? ceil_div64(npix, NLL_THREADS)
+                                                                         : 2 * p->num_sms);
     if (p->nll_blocks < 1) p->nll_blocks = 1;
     CAXSI_CUDA_TRY(cudaMalloc(&p->nll_part, p->nll_blocks * sizeof(double)));
     CAXSI_CUDA_TRY(cudaMalloc(&p->nll_dev, sizeof(double)));
-    CAXSI_CUDA_TRY(cudaMalloc(&p->err_flag, 2 * sizeof(int)));
-    CAXSI_CUDA_TRY(cudaMemset(p->err_flag, 0, 2 * sizeof(int)));
+    CAXSI_CUDA_TRY(cudaMalloc(&p->err_flag, 3 * sizeof(int)));
+    CAXSI_CUDA_TRY(cudaMemset(p->err_flag, 0, 3 * sizeof(int)));
     k_fill<<<(unsigned)ceil_div64(npix, 256), 256>>>(p->ones, 1.f, npix);
     CAXSI_CUDA_TRY(cudaGetLastError());
     CAXSI_CUDA_TRY(cudaDeviceSynchronize());

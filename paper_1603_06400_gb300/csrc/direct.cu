@@ -97,13 +97,22 @@ k_fwd_direct(Tables T, const float *__restrict__ f, float *__restrict__ part, in
     if (valid) part[(int64_t)blockIdx.y * g.M * g.N + (int64_t)m * g.N + n] = acc;
 }
 
-// out[idx] = sum_c part[c * stride + idx], c ascending.
+// out[idx] = sum_c part[c * stride + idx], c ascending (the loads of 32 terms are
+// issued before they are added, in the same order).
 __global__ void k_sum_parts(const float *__restrict__ part, int nparts, int64_t stride,
                             float *__restrict__ out, int64_t n) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
     float s = 0.f;
-    for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * stride + idx];
+    int c = 0;
+    for (; c + 32 <= nparts; c += 32) {
+        float v[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = part[(int64_t)(c + k) * stride + idx];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) s += v[k];
+    }
+    for (; c < nparts; ++c) s += part[(int64_t)c * stride + idx];
     out[idx] = s;
 }
 

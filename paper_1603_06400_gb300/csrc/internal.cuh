@@ -40,6 +40,10 @@ struct KernelProfiler {
     }
 };
 
+// Threads per block of the likelihood-ratio kernel (recon.cu); the plan sizes
+// its per-block partial sums with it.
+constexpr int NLL_THREADS = 64;
+
 // Table-path data (piecewise-linear structure of W in u); built on first use.
 struct TablePath;
 
@@ -76,7 +80,8 @@ struct caxsi_plan {
     double *nll_part;   // [nll_blocks]
     double *nll_dev;    // [1]
     int nll_blocks;
-    int *err_flag;      // [2] device error words: [0] non-positive mean, [1] copy wait timed out
+    int *err_flag;      // [3] device words: [0] non-positive mean, [1] copy wait timed out,
+                        // [2] completion counter of the likelihood blocks
     float *stage_in, *stage_out;  // host-API staging, lazily
 
     TablePath *table;

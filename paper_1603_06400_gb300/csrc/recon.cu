@@ -8,16 +8,18 @@
 
 namespace {
 
-constexpr int NLL_THREADS = 256;
-
 // ratio_i = y_i / z_i with z = g + r (FP32); per-block FP64 partial sums of
-// d_i = z_i - y_i ln z_i + ln y_i!.  y_i = 0 with z_i <= 0 contributes 0 and
-// ratio 0; y_i > 0 with z_i <= 0 raises the plan's error word.
+// d_i = z_i - y_i ln z_i + ln y_i!, and their sum in block order by the block
+// that finishes last (a completion counter, reset by that block), so the total
+// is deterministic.  y_i = 0 with z_i <= 0 contributes 0 and ratio 0; y_i > 0
+// with z_i <= 0 raises the plan's error word.  Small blocks spread the FP64
+// log / lgamma work over every SM.
 __global__ void __launch_bounds__(NLL_THREADS)
 k_ratio_nll(const float *__restrict__ g, const float *__restrict__ y, const float *__restrict__ r,
             const int *__restrict__ sub, int subset, float *__restrict__ ratio, double *__restrict__ part,
-            int *err, int64_t n) {
-    __shared__ double sh[NLL_THREADS / 32];
+            unsigned *done, double *__restrict__ total, int *err, int64_t n) {
+    __shared__ double sh[NLL_THREADS];
+    __shared__ bool last;
     double local = 0.0;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -43,15 +45,25 @@ k_ratio_nll(const float *__restrict__ g, const float *__restrict__ y, const floa
         double s = 0.0;
         for (int w = 0; w < NLL_THREADS / 32; ++w) s += sh[w];
         part[blockIdx.x] = s;
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;   // every partial is written
     }
-}
-
-// Fixed-order sum of the block partials (deterministic).
-__global__ void k_sum_nll(const double *__restrict__ part, int nb, double *__restrict__ out) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += part[b];
-        *out = s;
+    __syncthreads();
+    if (!last) return;   // block-uniform
+    // the last block: thread t sums partials t, t + NLL_THREADS, ... in order (read
+    // through L2), then a fixed tree over the threads
+    __threadfence();
+    double t = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += NLL_THREADS) t += __ldcg(part + b);
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int h = NLL_THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *total = sh[0];
+        *done = 0u;
     }
 }
 
@@ -113,6 +125,32 @@ __device__ __forceinline__ UpdTerms upd_terms(const DevGeo &g, const float *__re
     return u;
 }
 
+// The update of one element from its value fh, its 4 neighbours nb (ok: inside
+// the object), b1 and b2 (the same arithmetic as upd_terms).
+__device__ __forceinline__ float update_value(float fh, const float (&nb)[4], const bool (&ok)[4], float b1v,
+                                              float b2v, float beta, float delta) {
+    float b3 = 0.f, b5 = 0.f;
+    if (beta != 0.f) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!ok[q]) continue;
+            const float d = fh - nb[q];
+            const float ad = fabsf(d);
+            b3 += 2.f * (ad <= delta ? 1.f : delta / ad);
+            b5 += fminf(fmaxf(d, -delta), delta);
+        }
+    }
+    const float chi1 = beta * (2.f * b3);
+    const float chi2 = b1v + beta * (-fh * (2.f * b3) + 2.f * b5);
+    const float chi3 = fh * b2v;
+    if (chi1 > 0.f) {
+        const float disc = sqrtf(fmaf(chi2, chi2, 4.f * chi1 * chi3));
+        return chi2 > 0.f ? (2.f * chi3) / (chi2 + disc) : (disc - chi2) / (2.f * chi1);
+    }
+    if (chi2 > 0.f) return chi3 / chi2;
+    return fh;
+}
+
 // One block per voxel (blockIdx.x over nobj * R voxels), the q channels across
 // the threads: the neighbours are +-Q and +-J*Q away, no index divisions per element.
 __global__ void k_update(DevGeo g, const float *__restrict__ f, const float *__restrict__ b1,
@@ -122,40 +160,82 @@ __global__ void k_update(DevGeo g, const float *__restrict__ f, const float *__r
     const int v = vv % g.R;
     const int i = v / g.J, j = v - i * g.J;
     const int64_t JQ = (int64_t)g.J * g.Q;
+    const bool ok[4] = {i > 0, i + 1 < g.X, j > 0, j + 1 < g.J};
     for (int l = threadIdx.x; l < g.Q; l += blockDim.x) {
         const int64_t idx = (int64_t)vv * g.Q + l;
-        const float fh = f[idx];
-        float b3 = 0.f, b5 = 0.f;
+        float nb[4] = {0.f, 0.f, 0.f, 0.f};
         if (beta != 0.f) {
-            const float nbv[4] = {i > 0 ? f[idx - JQ] : 0.f, i + 1 < g.X ? f[idx + JQ] : 0.f,
-                                  j > 0 ? f[idx - g.Q] : 0.f, j + 1 < g.J ? f[idx + g.Q] : 0.f};
-            const bool ok[4] = {i > 0, i + 1 < g.X, j > 0, j + 1 < g.J};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (!ok[q]) continue;
-                const float d = fh - nbv[q];
-                const float ad = fabsf(d);
-                b3 += 2.f * (ad <= delta ? 1.f : delta / ad);
-                b5 += fminf(fmaxf(d, -delta), delta);
-            }
+            nb[0] = ok[0] ? f[idx - JQ] : 0.f;
+            nb[1] = ok[1] ? f[idx + JQ] : 0.f;
+            nb[2] = ok[2] ? f[idx - g.Q] : 0.f;
+            nb[3] = ok[3] ? f[idx + g.Q] : 0.f;
         }
-        const float chi1 = beta * (2.f * b3);
-        const float chi2 = b1[idx] + beta * (-fh * (2.f * b3) + 2.f * b5);
-        const float chi3 = fh * b2[idx];
-        float x;
-        if (chi1 > 0.f) {
-            const float disc = sqrtf(fmaf(chi2, chi2, 4.f * chi1 * chi3));
-            x = chi2 > 0.f ? (2.f * chi3) / (chi2 + disc) : (disc - chi2) / (2.f * chi1);
-        } else if (chi2 > 0.f) {
-            x = chi3 / chi2;
-        } else {
-            x = fh;
-        }
-        fnew[idx] = x;
+        fnew[idx] = update_value(f[idx], nb, ok, b1[idx], b2[idx], beta, delta);
     }
 }
 
-inline unsigned update_threads(int Q) { return (unsigned)(Q >= 128 ? 128 : (Q + 31) / 32 * 32); }
+// The same with four q channels per thread and 16-byte accesses (Q % 4 == 0 and
+// 16-byte aligned arrays): block (Q/4, voxels per block); thread (x, y) takes
+// channels 4x .. 4x + 3 of voxel blockIdx.x * blockDim.y + y, nv voxels in all.
+__global__ void k_update4(DevGeo g, const float4 *__restrict__ f, const float4 *__restrict__ b1,
+                          const float4 *__restrict__ b2, float beta, float delta, float4 *__restrict__ fnew,
+                          int nv) {
+    const int QV = (int)blockDim.x;
+    const int vv = (int)(blockIdx.x * blockDim.y + threadIdx.y);
+    if (vv >= nv) return;
+    const int64_t e = (int64_t)vv * QV + threadIdx.x;
+    const int v = vv % g.R;
+    const int i = v / g.J, j = v - i * g.J;
+    const int64_t JQ = (int64_t)g.J * QV;
+    const bool ok[4] = {i > 0, i + 1 < g.X, j > 0, j + 1 < g.J};
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 n4[4] = {z4, z4, z4, z4};
+    if (beta != 0.f) {
+        n4[0] = ok[0] ? f[e - JQ] : z4;
+        n4[1] = ok[1] ? f[e + JQ] : z4;
+        n4[2] = ok[2] ? f[e - QV] : z4;
+        n4[3] = ok[3] ? f[e + QV] : z4;
+    }
+    const float4 fh = f[e], c1 = b1[e], c2 = b2[e];
+    float4 out;
+    {
+        const float nb[4] = {n4[0].x, n4[1].x, n4[2].x, n4[3].x};
+        out.x = update_value(fh.x, nb, ok, c1.x, c2.x, beta, delta);
+    }
+    {
+        const float nb[4] = {n4[0].y, n4[1].y, n4[2].y, n4[3].y};
+        out.y = update_value(fh.y, nb, ok, c1.y, c2.y, beta, delta);
+    }
+    {
+        const float nb[4] = {n4[0].z, n4[1].z, n4[2].z, n4[3].z};
+        out.z = update_value(fh.z, nb, ok, c1.z, c2.z, beta, delta);
+    }
+    {
+        const float nb[4] = {n4[0].w, n4[1].w, n4[2].w, n4[3].w};
+        out.w = update_value(fh.w, nb, ok, c1.w, c2.w, beta, delta);
+    }
+    fnew[e] = out;
+}
+
+// Launch the update over n elements (n / Q voxels, objects back to back).
+cudaError_t launch_update(const DevGeo &g, const float *f, const float *b1, const float *b2, float beta,
+                          float delta, float *out, int64_t n, cudaStream_t s) {
+    const int64_t nv = n / g.Q;
+    const bool v4 = g.Q % 4 == 0 && g.Q / 4 <= 1024 && nv < INT32_MAX &&
+                    ((reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(b1) |
+                      reinterpret_cast<uintptr_t>(b2) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+    if (v4) {
+        const int qv = g.Q / 4, vpb = qv >= 256 ? 1 : 256 / qv;
+        k_update4<<<(unsigned)ceil_div64(nv, vpb), dim3((unsigned)qv, (unsigned)vpb), 0, s>>>(
+            g, reinterpret_cast<const float4 *>(f), reinterpret_cast<const float4 *>(b1),
+            reinterpret_cast<const float4 *>(b2), beta, delta, reinterpret_cast<float4 *>(out), (int)nv);
+    } else {
+        const unsigned thr = (unsigned)(g.Q >= 128 ? 128 : (g.Q + 31) / 32 * 32);
+        k_update<<<(unsigned)(n / g.Q), thr, 0, s>>>(g, f, b1, b2, beta, delta, out);
+    }
+    return cudaGetLastError();
+}
+
 
 // Reverse mode of the update.  Implicit differentiation of the root:
 // (2 chi1 x + chi2) dx = dchi3 - x dchi2 - x^2 dchi1.  Pass 1, per element j: the
@@ -234,13 +314,9 @@ caxsi_status recon_ratio(caxsi_plan *p, const float *y, const float *r, const in
     const int64_t n = (int64_t)p->dg.M * p->dg.N;
     {
         CAXSI_PROF(p, "ratio_nll", s);
-        k_ratio_nll<<<p->nll_blocks, NLL_THREADS, 0, s>>>(p->gtmp, y, r, sub, subset, p->ratio,
-                                                          p->nll_part, p->err_flag, n);
-    }
-    CAXSI_LAUNCH_CHECK(p);
-    {
-        CAXSI_PROF(p, "sum_nll", s);
-        k_sum_nll<<<1, 32, 0, s>>>(p->nll_part, p->nll_blocks, p->nll_dev);
+        k_ratio_nll<<<p->nll_blocks, NLL_THREADS, 0, s>>>(p->gtmp, y, r, sub, subset, p->ratio, p->nll_part,
+                                                          reinterpret_cast<unsigned *>(p->err_flag + 2),
+                                                          p->nll_dev, p->err_flag, n);
     }
     CAXSI_LAUNCH_CHECK(p);
     return CAXSI_OK;
@@ -251,8 +327,7 @@ caxsi_status recon_update(caxsi_plan *p, const float *f_old, float beta, float d
     const int64_t n = (int64_t)p->dg.R * p->dg.Q;
     {
         CAXSI_PROF(p, "em_update", s);
-        k_update<<<(unsigned)(n / p->dg.Q), update_threads(p->dg.Q), 0, s>>>(p->dg, f_old, b1, p->b2, beta, delta,
-                                                                            p->fnew);
+        CAXSI_CUDA_TRY(launch_update(p->dg, f_old, b1, p->b2, beta, delta, p->fnew, n, s));
     }
     CAXSI_LAUNCH_CHECK(p);
     return CAXSI_OK;
@@ -275,7 +350,7 @@ caxsi_status recon_update_ext(caxsi_plan *p, const float *f, const float *b1, co
                               float delta, float *out, int64_t n, cudaStream_t s) {
     {
         CAXSI_PROF(p, "em_update", s);
-        k_update<<<(unsigned)(n / p->dg.Q), update_threads(p->dg.Q), 0, s>>>(p->dg, f, b1, b2, beta, delta, out);
+        CAXSI_CUDA_TRY(launch_update(p->dg, f, b1, b2, beta, delta, out, n, s));
     }
     CAXSI_LAUNCH_CHECK(p);
     return CAXSI_OK;

@@ -495,9 +495,32 @@ __global__ void k_pad_convert(const float *__restrict__ x, int64_t rows, int Q, 
     }
 }
 
+// The TF32 split with Q == Qp and Q % 4 == 0 (no padding): four elements per
+// thread with 16-byte loads and stores.
+__global__ void k_split4(const float4 *__restrict__ x, int64_t n4, float4 *__restrict__ hi,
+                         float4 *__restrict__ lo) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n4) return;
+    const float4 v = x[i];
+    float4 h, l;
+    tf32_split(v.x, h.x, l.x);
+    tf32_split(v.y, h.y, l.y);
+    tf32_split(v.z, h.z, l.z);
+    tf32_split(v.w, h.w, l.w);
+    hi[i] = h;
+    lo[i] = l;
+}
+
 cudaError_t pad_convert(const float *x, int64_t rows, int Q, int Qp, int kind, void *y, float *ylo,
                         cudaStream_t s) {
     const int64_t n = rows * Qp;
+    if (kind == 0 && Q == Qp && Q % 4 == 0 && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) |
+                                                reinterpret_cast<uintptr_t>(ylo)) & 15) == 0) {
+        k_split4<<<(unsigned)ceil_div64(n / 4, 256), 256, 0, s>>>(
+            reinterpret_cast<const float4 *>(x), n / 4, reinterpret_cast<float4 *>(y),
+            reinterpret_cast<float4 *>(ylo));
+        return cudaGetLastError();
+    }
     k_pad_convert<<<(unsigned)ceil_div64(n, 256), 256, 0, s>>>(x, rows, Q, Qp, kind, y, ylo);
     return cudaGetLastError();
 }
@@ -588,8 +611,18 @@ __global__ void k_sum_parts_batch(const float *__restrict__ part, const int2 *__
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= npix) return;
     const int2 oi = obj_items[b];
+    // the same order and grouping of loads as k_sum_parts (equal results)
+    const float *pp = part + (int64_t)oi.x * npix + idx;
     float acc = 0.f;
-    for (int c = 0; c < oi.y; ++c) acc += part[(int64_t)(oi.x + c) * npix + idx];
+    int c = 0;
+    for (; c + 32 <= oi.y; c += 32) {
+        float v[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = pp[(int64_t)(c + k) * npix];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) acc += v[k];
+    }
+    for (; c < oi.y; ++c) acc += pp[(int64_t)c * npix];
     g[(int64_t)b * npix + idx] = acc;
 }
 

@@ -324,5 +324,22 @@ def test_mirror_symmetric_operators_equal_the_plain_records(cx, name):
     assert rel_l2(sym_t, plain_t) <= 1e-6
     assert rel_l2(sym, oracle.forward(g, phi, mask, _f32(f))) <= REL_L2_TOL
     assert rel_l2(sym_t, oracle.adjoint(g, phi, mask, _f32(w))) <= REL_L2_TOL
-    assert plan.info()["device_error"] == 0
+    info = plan.info()
+    assert info["device_error"] == 0
+    assert 0 < info["n_sym_records"] <= info["n_records"]   # a record serves up to 4 pairs
+    plan.close()
+
+
+def test_odd_sizes_have_no_mirror_symmetric_records(cx):
+    """J, M or N odd: there are no mirror pairs to share a record; the operators
+    stream one record per open pair (and still match the oracle)."""
+    caxsi, torch = cx
+    g = GEOMS["ragged"]()                        # J = 7, M = 9
+    phi = synth.tungsten_spectrum(g)
+    mask = synth.random_mask(g, 12)
+    plan = caxsi.Plan(g, phi, mask)
+    f = synth.uniform_random((g.X, g.J, g.Q), 13)
+    gg = plan.forward(_t(torch, f), path=caxsi.PATHS["table_fp32"]).cpu().numpy()
+    assert plan.info()["n_sym_records"] == 0 and plan.info()["n_records"] > 0
+    assert rel_l2(gg, oracle.forward(g, phi, mask, _f32(f))) <= REL_L2_TOL
     plan.close()
