@@ -298,6 +298,12 @@ caxsi_status caxsi_plan_info(caxsi_plan *plan, caxsi_plan_info_t *info);
  *     of the plan (INVALID afterwards, unless the value is unchanged). */
 #define CAXSI_OPT_U_SAMPLES 3
 #define CAXSI_MAX_U_SAMPLES 8192
+/*   CAXSI_OPT_GEMM_BANDS: 1 (default) or 0.  The spectral matrix S~ that the
+ *     table paths contract with is zero outside a band (a knot's energies reach
+ *     only a range of q bins); with 1 the tcgen05 contractions skip the product
+ *     blocks that meet only those zeros.  The skipped products are exact zeros:
+ *     results are unchanged, only the work shrinks.  0 multiplies everything. */
+#define CAXSI_OPT_GEMM_BANDS 4
 caxsi_status caxsi_plan_set_option(caxsi_plan *plan, int key, int value);
 
 /* Kernel timing (tracing).  When enabled, every kernel the plan launches is

@@ -380,6 +380,11 @@ class Plan:
         of A, cheaper by B/n).  Set it before the first table-path call."""
         _check(self.lib.caxsi_plan_set_option(self.handle, 3, int(n)), "caxsi_plan_set_option")
 
+    def set_gemm_bands(self, on: bool = True):
+        """Skip the product blocks of the tcgen05 contractions that meet only
+        zeros of the band-limited spectral matrix (default on; results unchanged)."""
+        _check(self.lib.caxsi_plan_set_option(self.handle, 4, int(bool(on))), "caxsi_plan_set_option")
+
     def set_symmetry(self, on: bool = True):
         """Mirror-symmetric records for the table paths' full forward and adjoint
         (default on when the geometry allows)."""

@@ -93,6 +93,7 @@ struct caxsi_plan {
     int gemm_engine;          // table-path contractions: 0 = tcgen05 kernel, 1 = cuBLAS
     int no_symmetry;          // 1: the table forward streams the ordinary records, not the mirror-symmetric ones
     int u_samples;            // table paths: 0 = the exact knots; N >= 2: N uniform samples of u (approximate)
+    int no_bands;             // 1: the tcgen05 contractions multiply the zeros outside the band of S~ too
     KernelProfiler prof;
 };
 

@@ -273,6 +273,10 @@ void free_table(TablePath *T) {
     cudaFree(T->St_lo);
     cudaFree(T->St16[0]);
     cudaFree(T->St16[1]);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(T->kband[k]);
+        cudaFree(T->nband[k]);
+    }
     cudaFree(T->f_hi);
     cudaFree(T->f_lo);
     if (T->blas) cublasDestroy(T->blas);
@@ -575,6 +579,31 @@ caxsi_status blas_setup(caxsi_plan *p, TablePath *T) {
                                                           (__nv_bfloat16 *)T->St16[0], (__half *)T->St16[1]);
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return CAXSI_ERR_CUDA;
     p->table_bytes += 2 * nS * 4 + nSt * 12 + 2 * nf * 4;
+    // the q band of each knot's row of S~ (first and last nonzero), and the GEMMs'
+    // band tables from it
+    std::vector<float> hS((size_t)T->B * d.Q);
+    if (cudaMemcpy(hS.data(), T->S, hS.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return CAXSI_ERR_CUDA;
+    std::vector<int2> nz(T->B);
+    for (int t = 0; t < T->B; ++t) {
+        int lo = d.Q, hi = -1;
+        for (int l = 0; l < d.Q; ++l)
+            if (hS[(size_t)t * d.Q + l] != 0.f) {
+                lo = std::min(lo, l);
+                hi = l;
+            }
+        nz[t] = make_int2(lo, hi);
+    }
+    for (int k = 0; k < 2; ++k) {
+        const int eb = k == 0 ? 4 : 2;
+        const std::vector<int2> kb = tc_kband(nz, T->B, 256, d.Q, eb);
+        const std::vector<int2> nb = tc_nband(nz, d.Q, 128, T->B, eb);
+        if (cudaMalloc(&T->kband[k], kb.size() * sizeof(int2)) != cudaSuccess ||
+            cudaMalloc(&T->nband[k], nb.size() * sizeof(int2)) != cudaSuccess)
+            return CAXSI_ERR_OOM;
+        if (cudaMemcpy(T->kband[k], kb.data(), kb.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(T->nband[k], nb.data(), nb.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+            return CAXSI_ERR_CUDA;
+    }
     return CAXSI_OK;
 }
 
@@ -723,6 +752,11 @@ caxsi_status ensure_table(caxsi_plan *p, int path) {
 
 cudaDataType_t dtype16(int path) { return path == CAXSI_PATH_TABLE_BF16 ? CUDA_R_16BF : CUDA_R_16F; }
 
+// The band tables of the tcgen05 contractions (k = 0: TF32 operands, 1: 16-bit),
+// or null when the plan has band skipping off.
+const int2 *kband_of(const caxsi_plan *p, int k) { return p->no_bands ? nullptr : p->table->kband[k]; }
+const int2 *nband_of(const caxsi_plan *p, int k) { return p->no_bands ? nullptr : p->table->nband[k]; }
+
 }  // namespace
 
 caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path, int subset, cudaStream_t s) {
@@ -743,7 +777,7 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
         {
             CAXSI_PROF(p, "tc_gemm_fwd_3xtf32", s);
             CAXSI_CUDA_TRY(tc_gemm(0, 256, d.R, T->B, d.Q, T->f_hi, T->f_lo, T->Qp, T->S_hi, T->S_lo, T->Qp,
-                                   T->tab, T->Bp, p->err_flag + 1, p->num_sms, s));
+                                   T->tab, T->Bp, p->err_flag + 1, p->num_sms, s, kband_of(p, 0)));
         }
         CAXSI_LAUNCH_CHECK(p);
     } else if (p->gemm_engine == 0) {
@@ -756,7 +790,7 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
         {
             CAXSI_PROF(p, k == 0 ? "tc_gemm_fwd_bf16" : "tc_gemm_fwd_fp16", s);
             CAXSI_CUDA_TRY(tc_gemm(1 + k, 256, d.R, T->B, d.Q, T->f16, nullptr, T->Qp, T->S16[k], nullptr, T->Qp,
-                                   T->tab, T->Bp, p->err_flag + 1, p->num_sms, s));
+                                   T->tab, T->Bp, p->err_flag + 1, p->num_sms, s, kband_of(p, 1)));
         }
         CAXSI_LAUNCH_CHECK(p);
     } else if (path == CAXSI_PATH_TABLE_FP32) {
@@ -828,10 +862,10 @@ caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path
         CAXSI_PROF(p, k == 0 ? "tc_gemm_adj_3xtf32" : (k == 1 ? "tc_gemm_adj_bf16" : "tc_gemm_adj_fp16"), s);
         if (k == 0)
             CAXSI_CUDA_TRY(tc_gemm(3, 128, d.R, d.Q, T->B, T->tab, nullptr, T->Bp, T->St_hi, T->St_lo, T->Bp,
-                                   f_out, d.Q, p->err_flag + 1, p->num_sms, s));
+                                   f_out, d.Q, p->err_flag + 1, p->num_sms, s, nullptr, nband_of(p, 0)));
         else
             CAXSI_CUDA_TRY(tc_gemm(k, 128, d.R, d.Q, T->B, T->v16, nullptr, T->Bp, T->St16[k - 1], nullptr,
-                                   T->Bp, f_out, d.Q, p->err_flag + 1, p->num_sms, s));
+                                   T->Bp, f_out, d.Q, p->err_flag + 1, p->num_sms, s, nullptr, nband_of(p, 1)));
         return CAXSI_OK;
     }
     if (cublasSetStream(T->blas, s) != CUBLAS_STATUS_SUCCESS) return CAXSI_ERR_CUDA;
@@ -874,7 +908,7 @@ caxsi_status table_forward_batch(caxsi_plan *p, int nb, const int32_t *ranges, c
         {
             CAXSI_PROF(p, "tc_gemm_fwd_3xtf32", s);
             CAXSI_CUDA_TRY(tc_gemm(0, 256, bs.rows, T->B, d.Q, bs.f_hi, bs.f_lo, T->Qp, T->S_hi, T->S_lo, T->Qp,
-                                   bs.tab, T->Bp, p->err_flag + 1, p->num_sms, s));
+                                   bs.tab, T->Bp, p->err_flag + 1, p->num_sms, s, kband_of(p, 0)));
         }
         CAXSI_LAUNCH_CHECK(p);
         {
@@ -913,7 +947,7 @@ caxsi_status table_adjoint_batch(caxsi_plan *p, int nb, const int32_t *ranges, c
     {
         CAXSI_PROF(p, "tc_gemm_adj_3xtf32", s);
         CAXSI_CUDA_TRY(tc_gemm(3, 128, bs.rows, d.Q, T->B, bs.tab, nullptr, T->Bp, T->St_hi, T->St_lo, T->Bp,
-                               bs.fpk, d.Q, p->err_flag + 1, p->num_sms, s));
+                               bs.fpk, d.Q, p->err_flag + 1, p->num_sms, s, nullptr, nband_of(p, 0)));
     }
     CAXSI_LAUNCH_CHECK(p);
     {

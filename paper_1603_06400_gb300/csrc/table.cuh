@@ -103,6 +103,11 @@ struct TablePath {
     float *St_hi = nullptr, *St_lo = nullptr;   // [Q][Bp]
     void *St16[2] = {nullptr, nullptr};         // [Q][Bp] bf16 / fp16
     float *f_hi = nullptr, *f_lo = nullptr;     // [R][Qp] per-call split of the forward input
+    // Band tables of S~ for those GEMMs (device): per n-tile of the forward the
+    // q k-blocks to keep, per K-chunk of the adjoint the q quarters to keep;
+    // [0] for the TF32 operands, [1] for the 16-bit ones.
+    int2 *kband[2] = {nullptr, nullptr};
+    int2 *nband[2] = {nullptr, nullptr};
 };
 
 
@@ -167,9 +172,15 @@ cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, int subset,
                             int out_kind, cudaStream_t s);
 
 // tc_gemm.cu
+// kband / nband (device, or null): B is zero outside bands; see tc_gemm.cu.
 cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const void *A2, int64_t lda,
                     const void *B, const void *B2, int64_t ldb, float *C, int64_t ldc, int *err,
-                    int num_sms, cudaStream_t s);
+                    int num_sms, cudaStream_t s, const int2 *kband = nullptr, const int2 *nband = nullptr);
+// Band tables from the nonzero range of each row of B[N][K] along K (kband: per
+// n-tile of bn rows, the k-blocks to keep) or of each column along N (nband: per
+// K-chunk, the 32-column quarters to keep); eb = operand element bytes.
+std::vector<int2> tc_kband(const std::vector<int2> &row_nz, int N, int bn, int K, int eb);
+std::vector<int2> tc_nband(const std::vector<int2> &col_nz, int N, int bn, int K, int eb);
 
 // TF32 split: hi = x rounded to TF32 (nearest), lo = x - hi (exact in FP32)
 static __device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {

@@ -29,12 +29,23 @@
 // tensor-core accumulation is longer than one chunk; the accumulation inside
 // the tensor core is not IEEE FP32 round-to-nearest and its error grows with
 // the chain length.
+// Band-limited B: the contractions' B operand (the spectral basis S~) is zero
+// outside a band, so a product block that meets only zeros of B is skipped.
+// kband (per n-tile): the k-blocks outside [x, y] are neither loaded nor
+// multiplied.  nband (per K-chunk): the chunk's MMAs cover only the 32-column
+// quarters [x, y] of the tile (N set in the instruction descriptor, the TMEM and
+// B operand addresses offset), and the epilogue adds only those quarters; an
+// empty chunk (x > y) issues no MMA.  The skipped products are exact zeros, so
+// the results are those of the full products.
 // Every mbarrier wait is bounded; on timeout the kernel records an error in
 // err[0] and every role stops.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -43,6 +54,7 @@ namespace {
 constexpr int TCG_THREADS = 320;   // producer, MMA, 8 epilogue warps
 constexpr int TCG_EPI = 256;       // epilogue threads
 constexpr int KCHUNK = 4;  // k-stages (128 bytes of K each) per tensor-core accumulation chain
+constexpr int A_PF = 8;    // k-blocks of A prefetched into L2 ahead of its stage loads (long K)
 constexpr uint32_t TCG_WAIT_LIMIT = 1u << 22;
 
 __device__ __forceinline__ uint32_t s_addr(const void *p) {
@@ -80,6 +92,12 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
             s_addr(dst)),
         "l"((uint64_t)map), "r"(x), "r"(y), "r"(s_addr(bar))
         : "memory");
+}
+// L2 prefetch of the tile a tma_load_2d at (x, y) would read (no completion to wait for).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"((uint64_t)map), "r"(x),
+                 "r"(y)
+                 : "memory");
 }
 // Tile store from shared memory (bulk async group); rows / columns outside the
 // tensor are not written.
@@ -149,6 +167,8 @@ struct TcArgs {
     int64_t ldc;
     int *err;
     int ntn, ntiles, nk;
+    const int2 *kband;   // [ntn] k-block range of each n-tile, or null (all)
+    const int2 *nband;   // [chunks] column-quarter range of each K-chunk, or null (all)
     int vec_ok;     // rows of C start on 16-byte boundaries (vector stores allowed)
     int tma_store;  // C is written by TMA tensor stores through shared memory
 };
@@ -169,8 +189,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
     constexpr uint32_t TMEM_COLS = 2 * BN;
     // idesc: D = F32, A/B = TF32 (2) or BF16 (1) or F16 (0), both K-major, N >> 3, M >> 4
     constexpr uint32_t AB = X3 ? 2u : (KIND == 1 ? 1u : 0u);
-    constexpr uint32_t IDESC = (1u << 4) | (AB << 7) | (AB << 10) | ((uint32_t)(BN >> 3) << 17) |
-                               ((uint32_t)(128 >> 4) << 24);
+    constexpr uint32_t IDESC0 = (1u << 4) | (AB << 7) | (AB << 10) | ((uint32_t)(128 >> 4) << 24);
+    constexpr int NQ = BN / 32;   // 32-column quarters of a tile
 
     extern __shared__ unsigned char smem_raw[];
     // operand tiles need 1024-byte alignment of their shared-memory address (swizzle atoms)
@@ -214,7 +234,19 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
             uint32_t it = 0;
             for (int tile = blockIdx.x; tile < a.ntiles && !*abort; tile += gridDim.x) {
                 const int m0 = (tile / a.ntn) * 128, n0 = (tile % a.ntn) * BN;
-                for (int kt = 0; kt < a.nk; ++kt, ++it) {
+                const int2 kr = a.kband ? a.kband[tile % a.ntn] : make_int2(0, a.nk - 1);
+                // a long contraction streams A from DRAM with only NS stages in flight:
+                // A's k-blocks A_PF ahead go to L2 first (the next tile's at the end)
+                const bool pf = a.nk > 2 * A_PF;
+                const int nxt = tile + (int)gridDim.x;
+                if (pf && tile == (int)blockIdx.x)   // later tiles were prefetched at the end of the previous one
+                    for (int kt = kr.x; kt < kr.x + A_PF && kt <= kr.y; ++kt) tma_prefetch_2d(&tA, kt * KE, m0);
+                for (int kt = kr.x; kt <= kr.y; ++kt, ++it) {
+                    if (pf) {
+                        const int kp = kt + A_PF;
+                        if (kp <= kr.y) tma_prefetch_2d(&tA, kp * KE, m0);
+                        else if (nxt < a.ntiles && !a.kband) tma_prefetch_2d(&tA, (kp - kr.y - 1) * KE, (nxt / a.ntn) * 128);
+                    }
                     const uint32_t s = it % NS, ph = (it / NS) & 1u;
                     if (!mb_wait(&empty[s], ph ^ 1u, abort)) { *abort = 1; break; }
                     unsigned char *st = base + s * STAGE;
@@ -232,31 +264,38 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
     } else if (warp == 1) {
         if (lane == 0) {
             uint32_t it = 0, cc = 0;
-            const int nch = (a.nk + KCHUNK - 1) / KCHUNK;
             bool ok = true;
             for (int tile = blockIdx.x; tile < a.ntiles && ok && !*abort; tile += gridDim.x) {
+                const int2 kr = a.kband ? a.kband[tile % a.ntn] : make_int2(0, a.nk - 1);
+                const int nch = (kr.y - kr.x + KCHUNK) / KCHUNK;
                 for (int c = 0; c < nch && ok; ++c, ++cc) {
                     const uint32_t b = cc & 1u, aph = (cc >> 1) & 1u;
                     if (!mb_wait(&acce[b], aph ^ 1u, abort)) { *abort = 1; ok = false; break; }
                     fence_after();
-                    const uint32_t d = tmem + b * BN;
-                    const int k0 = c * KCHUNK, k1 = min(a.nk, k0 + KCHUNK);
+                    // the chunk's column quarters [qr.x, qr.y]: N and the TMEM / B offsets
+                    const int2 qr = a.nband ? a.nband[c] : make_int2(0, NQ - 1);
+                    const uint32_t idesc = IDESC0 | ((uint32_t)(((qr.y - qr.x + 1) * 32) >> 3) << 17);
+                    const uint32_t d = tmem + b * BN + (uint32_t)(qr.x * 32);
+                    const uint64_t boff = (uint64_t)(qr.x * 32 * 128 / 16);   // 32 rows of 128 bytes, 16-byte units
+                    const int k0 = kr.x + c * KCHUNK, k1 = min(kr.y + 1, k0 + KCHUNK);
                     for (int kt = k0; kt < k1; ++kt, ++it) {
                         const uint32_t s = it % NS, ph = (it / NS) & 1u;
                         if (!mb_wait(SPLIT_A ? &conv[s] : &full[s], ph, abort)) { *abort = 1; ok = false; break; }
                         fence_after();
-                        unsigned char *st = base + s * STAGE;
-                        const uint64_t da = sw128_desc(st), db = sw128_desc(st + A_BYTES);
-                        const uint64_t dal = sw128_desc(st + A_BYTES + B_BYTES);
-                        const uint64_t dbl = sw128_desc(st + 2 * A_BYTES + B_BYTES);
+                        if (qr.x <= qr.y) {
+                            unsigned char *st = base + s * STAGE;
+                            const uint64_t da = sw128_desc(st), db = sw128_desc(st + A_BYTES) + boff;
+                            const uint64_t dal = sw128_desc(st + A_BYTES + B_BYTES);
+                            const uint64_t dbl = sw128_desc(st + 2 * A_BYTES + B_BYTES) + boff;
 #pragma unroll
-                        for (int ks = 0; ks < 4; ++ks) {
-                            const uint64_t adv = (uint64_t)(ks * 2);  // 32 bytes per instruction, 16-byte units
-                            const uint32_t acc = (kt > k0 || ks > 0) ? 1u : 0u;
-                            mma<KIND>(d, da + adv, db + adv, IDESC, acc);
-                            if (X3) {
-                                mma<KIND>(d, da + adv, dbl + adv, IDESC, 1u);
-                                mma<KIND>(d, dal + adv, db + adv, IDESC, 1u);
+                            for (int ks = 0; ks < 4; ++ks) {
+                                const uint64_t adv = (uint64_t)(ks * 2);  // 32 bytes per instruction, 16-byte units
+                                const uint32_t acc = (kt > k0 || ks > 0) ? 1u : 0u;
+                                mma<KIND>(d, da + adv, db + adv, idesc, acc);
+                                if (X3) {
+                                    mma<KIND>(d, da + adv, dbl + adv, idesc, 1u);
+                                    mma<KIND>(d, dal + adv, db + adv, idesc, 1u);
+                                }
                             }
                         }
                         mma_commit(&empty[s]);
@@ -274,7 +313,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
         uint32_t it = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < a.ntiles && ok && !*abort; tile += gridDim.x) {
-            for (int kt = 0; kt < a.nk; ++kt, ++it) {
+            const int2 kr = a.kband ? a.kband[tile % a.ntn] : make_int2(0, a.nk - 1);
+            for (int kt = kr.x; kt <= kr.y; ++kt, ++it) {
                 const uint32_t s = it % NS, ph = (it / NS) & 1u;
                 if (!mb_wait(&full[s], ph, abort)) { *abort = 1; ok = false; break; }
                 unsigned char *st = base + s * STAGE;
@@ -301,10 +341,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
         // column half of the tile
         constexpr int CW = BN / 2;   // columns per epilogue warp
         const int q = warp & 3, h = (warp - 2) >> 2;
-        const int nch = (a.nk + KCHUNK - 1) / KCHUNK;
         uint32_t cc = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+            const int2 kr = a.kband ? a.kband[tile % a.ntn] : make_int2(0, a.nk - 1);
+            const int nch = (kr.y - kr.x + KCHUNK) / KCHUNK;
             const int m0 = (tile / a.ntn) * 128, n0 = (tile % a.ntn) * BN + h * CW;
             const int row = m0 + q * 32 + lane;
             float *crow = a.C + (int64_t)row * a.ldc;
@@ -315,8 +356,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                 const uint32_t b = cc & 1u, aph = (cc >> 1) & 1u;
                 if (!mb_wait(&accf[b], aph, abort)) { *abort = 1; ok = false; break; }
                 fence_after();
+                const int2 qr = a.nband ? a.nband[c] : make_int2(0, NQ - 1);
 #pragma unroll
                 for (int c0 = 0; c0 < CW; c0 += 32) {
+                    const int qq = (h * CW + c0) >> 5;   // warp-uniform
+                    if (qq < qr.x || qq > qr.y) continue;   // columns the chunk did not touch: zero
                     float r[32];
                     tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * BN + h * CW + c0, r);
 #pragma unroll
@@ -433,8 +477,10 @@ cudaError_t launch_tc(const CUtensorMap &tA, const CUtensorMap &tA2, const CUten
 // elements must make 16-byte multiples; base pointers 16-byte aligned.
 cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const void *A2, int64_t lda,
                     const void *B, const void *B2, int64_t ldb, float *C, int64_t ldc, int *err,
-                    int num_sms, cudaStream_t s) {
+                    int num_sms, cudaStream_t s, const int2 *kband, const int2 *nband) {
     const int eb = (kind == 0 || kind == 3) ? 4 : 2;
+    if (kband && nband) return cudaErrorInvalidValue;              // one kind of band at a time
+    if (nband && (N + bn - 1) / bn != 1) return cudaErrorInvalidValue;   // quarters of the only n-tile
     CUtensorMap tA, tA2, tB, tB2;
     if (!make_map(&tA, A, eb, M, K, lda, 128) || !make_map(&tB, B, eb, N, K, ldb, bn))
         return cudaErrorInvalidValue;
@@ -463,6 +509,8 @@ cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const 
     a.ntn = (N + bn - 1) / bn;
     a.ntiles = ((M + 127) / 128) * a.ntn;
     a.nk = (K * eb + 127) / 128;
+    a.kband = kband;
+    a.nband = nband;
     if (bn == 256) {
         if (kind == 3) return cudaErrorInvalidValue;   // the on-chip A split is built for bn = 128
         if (kind == 0) return launch_tc<256, 0, 2>(tA, tA2, tB, tB2, tC, a, num_sms, s);
@@ -473,4 +521,35 @@ cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const 
     if (kind == 3) return launch_tc<128, 3, 3>(tA, tA2, tB, tB2, tC, a, num_sms, s);
     if (kind == 1) return launch_tc<128, 1, 6>(tA, tA2, tB, tB2, tC, a, num_sms, s);
     return launch_tc<128, 2, 6>(tA, tA2, tB, tB2, tC, a, num_sms, s);
+}
+
+std::vector<int2> tc_kband(const std::vector<int2> &row_nz, int N, int bn, int K, int eb) {
+    const int ntn = (N + bn - 1) / bn, ke = 128 / eb, nk = (K * eb + 127) / 128;
+    std::vector<int2> out(ntn);
+    for (int nt = 0; nt < ntn; ++nt) {
+        int lo = K, hi = -1;
+        for (int i = nt * bn; i < std::min(N, (nt + 1) * bn); ++i)
+            if (row_nz[i].x <= row_nz[i].y) {
+                lo = std::min(lo, row_nz[i].x);
+                hi = std::max(hi, row_nz[i].y);
+            }
+        out[nt] = hi < 0 ? make_int2(0, 0) : make_int2(lo / ke, std::min(nk - 1, hi / ke));
+    }
+    return out;
+}
+
+std::vector<int2> tc_nband(const std::vector<int2> &col_nz, int N, int bn, int K, int eb) {
+    const int ke = 128 / eb, nk = (K * eb + 127) / 128, nch = (nk + KCHUNK - 1) / KCHUNK;
+    const int nq = std::min(bn, N + 31 - (N + 31) % 32) / 32;
+    std::vector<int2> out(nch);
+    for (int c = 0; c < nch; ++c) {
+        int lo = N, hi = -1;
+        for (int k = c * KCHUNK * ke; k < std::min(K, (c + 1) * KCHUNK * ke); ++k)
+            if (col_nz[k].x <= col_nz[k].y) {
+                lo = std::min(lo, col_nz[k].x);
+                hi = std::max(hi, col_nz[k].y);
+            }
+        out[c] = hi < 0 ? make_int2(1, 0) : make_int2(lo / 32, std::min(nq - 1, hi / 32));
+    }
+    return out;
 }
