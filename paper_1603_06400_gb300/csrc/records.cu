@@ -411,6 +411,13 @@ __device__ __forceinline__ void store_v4(__nv_bfloat16 *p, float4 x) {
     u.y = *reinterpret_cast<uint32_t *>(&hi);
     *reinterpret_cast<uint2 *>(p) = u;
 }
+__device__ __forceinline__ void store_v2(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
+__device__ __forceinline__ void store_v2(__nv_bfloat16 *p, float a, float b) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+}
+__device__ __forceinline__ void store_v2(__half *p, float a, float b) {
+    *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
+}
 __device__ __forceinline__ void store_v4(__half *p, float4 x) {
     __half2 lo = __floats2half2_rn(x.x, x.y), hi = __floats2half2_rn(x.z, x.w);
     uint2 u;
@@ -1004,7 +1011,8 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, in
     float2 *slot_lo = reinterpret_cast<float2 *>(slot_t + ADJ_T);
     float2 *slot_hi = slot_lo + ADJ_T;
     uint64_t *bar = reinterpret_cast<uint64_t *>(slot_hi + ADJ_T);    // [ADJ_W]
-    int *offr = reinterpret_cast<int *>(bar + ADJ_W);                  // [vc + 1] list starts - off[s0]
+    int *trange = reinterpret_cast<int *>(bar + ADJ_W);                // [2] the pair's first and last t
+    int *offr = trange + 2;                                            // [vc + 1] list starts - off[s0]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int s0 = blockIdx.x * A.vc, s1 = min(s0 + A.vc, A.R2);
     if (s0 >= s1) return;   // block-uniform
@@ -1058,6 +1066,10 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, in
     for (int s = s0; s < s1; ++s) {
         const int late = __any_sync(0xffffffffu, !mbar_wait(&bar[warp], par)) ? 1 : 0;
         const int64_t ob = base + offr[s - s0], oe = base + offr[s - s0 + 1];
+        if (tid == 0) {   // read after the barriers below, rewritten after the last of them
+            trange[0] = oe > ob ? (int)(A.key[ob] >> 18) : 1;
+            trange[1] = oe > ob ? (int)(A.key[oe - 1] >> 18) : 0;
+        }
         int ws, we, perq;
         segment(ob, oe, ws, we, perq);
         const int q0 = min(we, ws + lane * perq), q1 = min(we, q0 + perq);
@@ -1177,18 +1189,23 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, in
         __syncthreads();
         if (ct != SENT) V[ct + 1] = f2add(V[ct + 1], chi);
         __syncthreads();
-        // write rows v and v' (whole quads) and clear V for the next pair
+        // write rows v and v' and clear V for the next pair: knots 2e, 2e + 1 per
+        // float4 e of V; only [first t, last t + 1] can have been written (the rest
+        // of V is zero and is written as zeros without reading it)
         const int i = s / A.J2, jq = s - i * A.J2;
         OutT *rv = Vtab + ((int64_t)i * A.J + jq) * A.Bp;
         OutT *rp = Vtab + ((int64_t)i * A.J + (A.J - 1 - jq)) * A.Bp;
         float4 *V4 = reinterpret_cast<float4 *>(V);
         const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int t4 = tid; t4 < (A.Bp >> 2); t4 += ADJ_T) {
-            const float4 x = V4[2 * t4], y = V4[2 * t4 + 1];
-            store_v4(rv + 4 * t4, make_float4(x.x, x.z, y.x, y.z));
-            store_v4(rp + 4 * t4, make_float4(x.y, x.w, y.y, y.w));
-            V4[2 * t4] = zero4;
-            V4[2 * t4 + 1] = zero4;
+        const int tl = trange[0], th = trange[1] + 1;
+        for (int e = tid; e < (A.Bp >> 1); e += ADJ_T) {
+            float4 x = zero4;
+            if (2 * e + 1 >= tl && 2 * e <= th) {
+                x = V4[e];
+                V4[e] = zero4;
+            }
+            store_v2(rv + 2 * e, x.x, x.z);
+            store_v2(rp + 2 * e, x.y, x.w);
         }
         __syncthreads();
     }
@@ -1201,7 +1218,7 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, in
 
 size_t adj_sym_smem(int npix, int Bp, int vc) {
     return (size_t)((npix + 3) & ~3) * 4 + (size_t)Bp * 8 + (size_t)ADJ_W * SADJ_SQ * 48 + ADJ_W * 16 +
-           (size_t)ADJ_T * 20 + ADJ_W * 8 + 4 * (size_t)(vc + 1);
+           (size_t)ADJ_T * 20 + ADJ_W * 8 + 8 + 4 * (size_t)(vc + 1);
 }
 
 size_t fwd_sym_smem(int npix, int Bp) { return (size_t)((npix + 3) & ~3) * 4 + 4 * (size_t)Bp * 4 + 16; }
