@@ -479,7 +479,8 @@ int64_t table_sym_records(const caxsi_plan *p) { return p->table ? p->table->sym
 namespace {
 
 // Row-padded operand copies: x [rows][Q] -> y [rows][Qp] (zeros beyond Q), as
-// bf16 (kind 1), fp16 (kind 2) or a TF32 high/low split (kind 0).
+// bf16 (kind 1), fp16 (kind 2), a TF32 high/low split rounded to nearest (kind
+// 0, the B operands) or truncated (kind 3, the A operands).
 __global__ void k_pad_convert(const float *__restrict__ x, int64_t rows, int Q, int Qp, int kind,
                               void *__restrict__ y, float *__restrict__ ylo) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -493,38 +494,36 @@ __global__ void k_pad_convert(const float *__restrict__ x, int64_t rows, int Q, 
         reinterpret_cast<__half *>(y)[i] = __float2half_rn(v);
     } else {
         float h, lo;
-        tf32_split(v, h, lo);
+        if (kind == 3) tf32_split_trunc(v, h, lo);
+        else tf32_split(v, h, lo);
         reinterpret_cast<float *>(y)[i] = h;
         ylo[i] = lo;
     }
 }
 
-// The TF32 split with Q == Qp and Q % 4 == 0 (no padding): four elements per
-// thread with 16-byte loads and stores.
-__global__ void k_split4(const float4 *__restrict__ x, int64_t n4, float4 *__restrict__ hi,
-                         float4 *__restrict__ lo) {
+// lo = x - (x with its low 13 mantissa bits cleared), n elements (n % 4 == 0,
+// 16-byte aligned): the remainder of the TF32 value a tensor core reads from x.
+__global__ void k_trunc_lo4(const float4 *__restrict__ x, int64_t n4, float4 *__restrict__ lo) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n4) return;
     const float4 v = x[i];
-    float4 h, l;
-    tf32_split(v.x, h.x, l.x);
-    tf32_split(v.y, h.y, l.y);
-    tf32_split(v.z, h.z, l.z);
-    tf32_split(v.w, h.w, l.w);
-    hi[i] = h;
+    float4 l;
+    l.x = v.x - __uint_as_float(__float_as_uint(v.x) & 0xffffe000u);
+    l.y = v.y - __uint_as_float(__float_as_uint(v.y) & 0xffffe000u);
+    l.z = v.z - __uint_as_float(__float_as_uint(v.z) & 0xffffe000u);
+    l.w = v.w - __uint_as_float(__float_as_uint(v.w) & 0xffffe000u);
     lo[i] = l;
+}
+
+cudaError_t trunc_remainder(const float *x, int64_t n, float *lo, cudaStream_t s) {
+    k_trunc_lo4<<<(unsigned)ceil_div64(n / 4, 256), 256, 0, s>>>(reinterpret_cast<const float4 *>(x), n / 4,
+                                                                  reinterpret_cast<float4 *>(lo));
+    return cudaGetLastError();
 }
 
 cudaError_t pad_convert(const float *x, int64_t rows, int Q, int Qp, int kind, void *y, float *ylo,
                         cudaStream_t s) {
     const int64_t n = rows * Qp;
-    if (kind == 0 && Q == Qp && Q % 4 == 0 && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) |
-                                                reinterpret_cast<uintptr_t>(ylo)) & 15) == 0) {
-        k_split4<<<(unsigned)ceil_div64(n / 4, 256), 256, 0, s>>>(
-            reinterpret_cast<const float4 *>(x), n / 4, reinterpret_cast<float4 *>(y),
-            reinterpret_cast<float4 *>(ylo));
-        return cudaGetLastError();
-    }
     k_pad_convert<<<(unsigned)ceil_div64(n, 256), 256, 0, s>>>(x, rows, Q, Qp, kind, y, ylo);
     return cudaGetLastError();
 }
@@ -617,7 +616,7 @@ __global__ void k_pack_split(const float *__restrict__ x, const int64_t *__restr
     const int l = (int)(i - r * Qp);
     const float v = l < Q ? x[rowmap[r] * Q + l] : 0.f;
     float h, w;
-    tf32_split(v, h, w);
+    tf32_split_trunc(v, h, w);
     hi[i] = h;
     lo[i] = w;
 }
@@ -768,16 +767,21 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
     const float one = 1.f, zero = 0.f;
     if (cublasSetStream(T->blas, s) != CUBLAS_STATUS_SUCCESS) return CAXSI_ERR_CUDA;
     if (p->gemm_engine == 0 && path == CAXSI_PATH_TABLE_FP32) {
-        // Wtab[r][t] = sum_l f[r][l] S~[t][l] by the tcgen05 GEMM, 3xTF32
+        // Wtab[r][t] = sum_l f[r][l] S~[t][l] by the tcgen05 GEMM, 3xTF32.  With
+        // unpadded aligned rows f itself is the high part (the tensor core reads
+        // FP32 as TF32 by dropping the low 13 mantissa bits) and only the
+        // remainder is written; otherwise both parts go to padded copies.
+        const bool raw_hi = d.Q == T->Qp && (reinterpret_cast<uintptr_t>(f) & 15) == 0;
         {
             CAXSI_PROF(p, "split_tf32", s);
-            CAXSI_CUDA_TRY(pad_convert(f, d.R, d.Q, T->Qp, 0, T->f_hi, T->f_lo, s));
+            if (raw_hi) CAXSI_CUDA_TRY(trunc_remainder(f, (int64_t)d.R * d.Q, T->f_lo, s));
+            else CAXSI_CUDA_TRY(pad_convert(f, d.R, d.Q, T->Qp, 3, T->f_hi, T->f_lo, s));
         }
         CAXSI_LAUNCH_CHECK(p);
         {
             CAXSI_PROF(p, "tc_gemm_fwd_3xtf32", s);
-            CAXSI_CUDA_TRY(tc_gemm(0, 256, d.R, T->B, d.Q, T->f_hi, T->f_lo, T->Qp, T->S_hi, T->S_lo, T->Qp,
-                                   T->tab, T->Bp, p->err_flag + 1, p->num_sms, s, kband_of(p, 0)));
+            CAXSI_CUDA_TRY(tc_gemm(0, 256, d.R, T->B, d.Q, raw_hi ? f : T->f_hi, T->f_lo, T->Qp, T->S_hi, T->S_lo,
+                                   T->Qp, T->tab, T->Bp, p->err_flag + 1, p->num_sms, s, kband_of(p, 0)));
         }
         CAXSI_LAUNCH_CHECK(p);
     } else if (p->gemm_engine == 0) {

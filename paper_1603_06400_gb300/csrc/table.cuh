@@ -189,6 +189,13 @@ static __device__ __forceinline__ void tf32_split(float x, float &hi, float &lo)
     hi = __uint_as_float(h);
     lo = x - hi;
 }
+// The split of an A operand of the 3xTF32 contractions: hi = x with its low 13
+// mantissa bits cleared (what the tensor core reads from an FP32 operand, so x
+// itself can stand for hi) and the exact remainder.
+static __device__ __forceinline__ void tf32_split_trunc(float x, float &hi, float &lo) {
+    hi = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+    lo = x - hi;
+}
 void records_free(TablePath *T);
 cudaError_t records_forward_items(const caxsi_plan *p, const TablePath *T, const int4 *items, int n_items,
                                   const float *Wtab, float *part, cudaStream_t s);

@@ -9,8 +9,10 @@
 // part and an FP32 remainder (x = hi + lo, both read as TF32 by the tensor
 // core); the product is accumulated as hi*hi + hi*lo + lo*hi in FP32, an error
 // of about 2^-21 relative per product (FP32-level accuracy).  KIND 3 = the same
-// with A given once in FP32 and split in shared memory by four converter warps
-// (half the A traffic).  KIND 1 / 2 = single-pass bf16 / fp16 operands with
+// with A given once in FP32: the tile as loaded is its own high part (the tensor
+// core reads an FP32 operand as TF32 by dropping the low 13 mantissa bits) and
+// four converter warps write the exact remainder x - hi(x) next to it (half the
+// A traffic; the products with A_hi start before the remainder is written).  KIND 1 / 2 = single-pass bf16 / fp16 operands with
 // FP32 accumulation.
 //
 // Structure (one CTA per SM, persistent over 128 x BN output tiles):
@@ -135,12 +137,6 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uin
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_addr(bar))
                  : "memory");
-}
-__device__ __forceinline__ void tf32_split_dev(float x, float &hi, float &lo) {
-    uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-    hi = __uint_as_float(h);
-    lo = x - hi;
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -280,13 +276,13 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                     const int k0 = kr.x + c * KCHUNK, k1 = min(kr.y + 1, k0 + KCHUNK);
                     for (int kt = k0; kt < k1; ++kt, ++it) {
                         const uint32_t s = it % NS, ph = (it / NS) & 1u;
-                        if (!mb_wait(SPLIT_A ? &conv[s] : &full[s], ph, abort)) { *abort = 1; ok = false; break; }
+                        if (!mb_wait(&full[s], ph, abort)) { *abort = 1; ok = false; break; }
                         fence_after();
+                        unsigned char *st = base + s * STAGE;
+                        const uint64_t da = sw128_desc(st), db = sw128_desc(st + A_BYTES) + boff;
+                        const uint64_t dal = sw128_desc(st + A_BYTES + B_BYTES);
+                        const uint64_t dbl = sw128_desc(st + 2 * A_BYTES + B_BYTES) + boff;
                         if (qr.x <= qr.y) {
-                            unsigned char *st = base + s * STAGE;
-                            const uint64_t da = sw128_desc(st), db = sw128_desc(st + A_BYTES) + boff;
-                            const uint64_t dal = sw128_desc(st + A_BYTES + B_BYTES);
-                            const uint64_t dbl = sw128_desc(st + 2 * A_BYTES + B_BYTES) + boff;
 #pragma unroll
                             for (int ks = 0; ks < 4; ++ks) {
                                 const uint64_t adv = (uint64_t)(ks * 2);  // 32 bytes per instruction, 16-byte units
@@ -294,6 +290,18 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                                 mma<KIND>(d, da + adv, db + adv, idesc, acc);
                                 if (X3) {
                                     mma<KIND>(d, da + adv, dbl + adv, idesc, 1u);
+                                    if (!SPLIT_A) mma<KIND>(d, dal + adv, db + adv, idesc, 1u);
+                                }
+                            }
+                        }
+                        if (SPLIT_A) {
+                            // the A_lo x B_hi products once the converters have written A_lo
+                            if (!mb_wait(&conv[s], ph, abort)) { *abort = 1; ok = false; break; }
+                            fence_after();
+                            if (qr.x <= qr.y) {
+#pragma unroll
+                                for (int ks = 0; ks < 4; ++ks) {
+                                    const uint64_t adv = (uint64_t)(ks * 2);
                                     mma<KIND>(d, dal + adv, db + adv, idesc, 1u);
                                 }
                             }
@@ -306,9 +314,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
             }
         }
     } else if (SPLIT_A && warp >= 10) {
-        // converters: split each landed A tile into its TF32 high part (in place)
-        // and the FP32 remainder (the A_lo slot); element-wise, so the 128-byte
-        // swizzle of the tile is kept as is
+        // converters: for each landed A tile write the remainder A_lo = x - hi(x)
+        // into the A_lo slot, hi(x) = x with its low 13 mantissa bits cleared, the
+        // TF32 value the tensor core reads from an FP32 operand (so the tile itself
+        // serves as A_hi unchanged, and the A_hi products need not wait for this);
+        // element-wise, so the 128-byte swizzle of the tile is kept as is
         const int ct = threadIdx.x - 320;
         uint32_t it = 0;
         bool ok = true;
@@ -318,17 +328,16 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                 const uint32_t s = it % NS, ph = (it / NS) & 1u;
                 if (!mb_wait(&full[s], ph, abort)) { *abort = 1; ok = false; break; }
                 unsigned char *st = base + s * STAGE;
-                float4 *hi = reinterpret_cast<float4 *>(st);
+                const float4 *hi = reinterpret_cast<const float4 *>(st);
                 float4 *lo = reinterpret_cast<float4 *>(st + A_BYTES + B_BYTES);
 #pragma unroll
                 for (int e = ct; e < (int)(A_BYTES / 16); e += 128) {
                     const float4 x = hi[e];
-                    float4 h, l;
-                    tf32_split_dev(x.x, h.x, l.x);
-                    tf32_split_dev(x.y, h.y, l.y);
-                    tf32_split_dev(x.z, h.z, l.z);
-                    tf32_split_dev(x.w, h.w, l.w);
-                    hi[e] = h;
+                    float4 l;
+                    l.x = x.x - __uint_as_float(__float_as_uint(x.x) & 0xffffe000u);
+                    l.y = x.y - __uint_as_float(__float_as_uint(x.y) & 0xffffe000u);
+                    l.z = x.z - __uint_as_float(__float_as_uint(x.z) & 0xffffe000u);
+                    l.w = x.w - __uint_as_float(__float_as_uint(x.w) & 0xffffe000u);
                     lo[e] = l;
                 }
                 // make the generic-proxy writes visible to the tensor core (async proxy)
