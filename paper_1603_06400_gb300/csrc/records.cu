@@ -991,10 +991,9 @@ struct SymAdjArgs {
     const float *w0, *w1;
 };
 
-__device__ __forceinline__ float2 f2fma(float a, float2 x, float2 y) {
-    return make_float2(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y));
-}
-__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+// Two-lane FP32 arithmetic in one packed instruction (each lane rounded as fmaf / +).
+__device__ __forceinline__ float2 f2fma(float a, float2 x, float2 y) { return __ffma2_rn(make_float2(a, a), x, y); }
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
 template <typename OutT>
 __global__ void __launch_bounds__(ADJ_T, 1)
@@ -1127,10 +1126,12 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, in
             auto take = [&](uint32_t k, float wa, float wb) {
                 const uint32_t t = k >> 18;
                 const float4 c = w4[(k >> 5) & 0x1fffu];
-                const float s01 = ((k & 1u) ? c.x : 0.f) + ((k & 2u) ? c.y : 0.f);
-                const float s23 = ((k & 4u) ? c.z : 0.f) + ((k & 8u) ? c.w : 0.f);
+                // {image pixels 0 + 1, pixels 2 + 3} of the open pairs; the class says
+                // which of the two is voxel v's
+                const float2 sp = __fadd2_rn(make_float2((k & 1u) ? c.x : 0.f, (k & 4u) ? c.z : 0.f),
+                                             make_float2((k & 2u) ? c.y : 0.f, (k & 8u) ? c.w : 0.f));
                 const bool cls = (k & 16u) != 0u;
-                const float2 x = make_float2(cls ? s23 : s01, cls ? s01 : s23);
+                const float2 x = make_float2(cls ? sp.y : sp.x, cls ? sp.x : sp.y);
                 if (t != ct) {
                     if (cont) {   // the continued run ends inside the part
                         st = ct;
