@@ -1010,8 +1010,7 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, in
     float2 *slot_lo = reinterpret_cast<float2 *>(slot_t + ADJ_T);
     float2 *slot_hi = slot_lo + ADJ_T;
     uint64_t *bar = reinterpret_cast<uint64_t *>(slot_hi + ADJ_T);    // [ADJ_W]
-    int *trange = reinterpret_cast<int *>(bar + ADJ_W);                // [2] the pair's first and last t
-    int *offr = trange + 2;                                            // [vc + 1] list starts - off[s0]
+    int *offr = reinterpret_cast<int *>(bar + ADJ_W);                  // [vc + 1] list starts - off[s0]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int s0 = blockIdx.x * A.vc, s1 = min(s0 + A.vc, A.R2);
     if (s0 >= s1) return;   // block-uniform
@@ -1065,10 +1064,7 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, in
     for (int s = s0; s < s1; ++s) {
         const int late = __any_sync(0xffffffffu, !mbar_wait(&bar[warp], par)) ? 1 : 0;
         const int64_t ob = base + offr[s - s0], oe = base + offr[s - s0 + 1];
-        if (tid == 0) {   // read after the barriers below, rewritten after the last of them
-            trange[0] = oe > ob ? (int)(A.key[ob] >> 18) : 1;
-            trange[1] = oe > ob ? (int)(A.key[oe - 1] >> 18) : 0;
-        }
+
         int ws, we, perq;
         segment(ob, oe, ws, we, perq);
         const int q0 = min(we, ws + lane * perq), q1 = min(we, q0 + perq);
@@ -1191,20 +1187,15 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, in
         if (ct != SENT) V[ct + 1] = f2add(V[ct + 1], chi);
         __syncthreads();
         // write rows v and v' and clear V for the next pair: knots 2e, 2e + 1 per
-        // float4 e of V; only [first t, last t + 1] can have been written (the rest
-        // of V is zero and is written as zeros without reading it)
+        // float4 e of V (consecutive lanes, consecutive 16 bytes: no bank conflicts)
         const int i = s / A.J2, jq = s - i * A.J2;
         OutT *rv = Vtab + ((int64_t)i * A.J + jq) * A.Bp;
         OutT *rp = Vtab + ((int64_t)i * A.J + (A.J - 1 - jq)) * A.Bp;
         float4 *V4 = reinterpret_cast<float4 *>(V);
         const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int tl = trange[0], th = trange[1] + 1;
         for (int e = tid; e < (A.Bp >> 1); e += ADJ_T) {
-            float4 x = zero4;
-            if (2 * e + 1 >= tl && 2 * e <= th) {
-                x = V4[e];
-                V4[e] = zero4;
-            }
+            const float4 x = V4[e];
+            V4[e] = zero4;
             store_v2(rv + 2 * e, x.x, x.z);
             store_v2(rp + 2 * e, x.y, x.w);
         }
@@ -1219,7 +1210,7 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, in
 
 size_t adj_sym_smem(int npix, int Bp, int vc) {
     return (size_t)((npix + 3) & ~3) * 4 + (size_t)Bp * 8 + (size_t)ADJ_W * SADJ_SQ * 48 + ADJ_W * 16 +
-           (size_t)ADJ_T * 20 + ADJ_W * 8 + 8 + 4 * (size_t)(vc + 1);
+           (size_t)ADJ_T * 20 + ADJ_W * 8 + 4 * (size_t)(vc + 1);
 }
 
 size_t fwd_sym_smem(int npix, int Bp) { return (size_t)((npix + 3) & ~3) * 4 + 4 * (size_t)Bp * 4 + 16; }
