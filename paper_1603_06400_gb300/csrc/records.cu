@@ -24,6 +24,14 @@
 //
 // Record layout (structure of arrays, 12 bytes per record):
 //   key = pixel | (t << 16) (uint32), w0 (float), w1 (float).
+//
+// Mirror-symmetric records (Sec. III-A, when J, M and N are even) serve a pair
+// and its left-right / up-down mirror images, which share the interval and the
+// weights: the full forward streams one 21-byte record per voxel pair and
+// quadrant pixel (8 pairs, k_fwd_sym), the full adjoint t-sorted lists per voxel
+// pair of 12-byte records that stand for 4 pairs each (k_adj_sym, the same
+// run-ownership reduction with two sums per run).  The subset and batched
+// operators stream the one-pair records.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -452,7 +460,7 @@ constexpr int ADJ_SQ = 64;
 
 template <typename OutT, bool ITEMS>
 __global__ void __launch_bounds__(ADJ_T, 1)
-k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float *__restrict__ Vlo, int *err) {
+k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, int *err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int npix_al = (A.npix + 3) & ~3;
     float *w_s = reinterpret_cast<float *>(smem_raw);
@@ -649,24 +657,9 @@ k_adj_rec(RecArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, float
         OutT *vrow = Vtab + (r0 + v) * A.Bp;
         float4 *V4 = reinterpret_cast<float4 *>(V);
         const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (Vlo) {
-            float *lrow = Vlo + (r0 + v) * A.Bp;
-            for (int t4 = tid; t4 < (A.Bp >> 2); t4 += ADJ_T) {
-                const float4 x = V4[t4];
-                float4 h, l;
-                tf32_split(x.x, h.x, l.x);
-                tf32_split(x.y, h.y, l.y);
-                tf32_split(x.z, h.z, l.z);
-                tf32_split(x.w, h.w, l.w);
-                store_v4(vrow + 4 * t4, h);
-                reinterpret_cast<float4 *>(lrow)[t4] = l;
-                V4[t4] = zero4;
-            }
-        } else {
-            for (int t4 = tid; t4 < (A.Bp >> 2); t4 += ADJ_T) {
-                store_v4(vrow + 4 * t4, V4[t4]);
-                V4[t4] = zero4;
-            }
+        for (int t4 = tid; t4 < (A.Bp >> 2); t4 += ADJ_T) {
+            store_v4(vrow + 4 * t4, V4[t4]);
+            V4[t4] = zero4;
         }
         __syncthreads();
     }
@@ -1554,13 +1547,13 @@ cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, int subset,
 
 template <typename OutT>
 cudaError_t launch_adj_rec(const caxsi_plan *p, const TablePath *T, int subset, const float *w, OutT *out,
-                           float *lo, cudaStream_t s) {
+                           cudaStream_t s) {
     const int npix = p->dg.M * p->dg.N;
     const size_t smem = adj_rec_smem(npix, T->Bp);
     cudaError_t e = cudaFuncSetAttribute(k_adj_rec<OutT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_adj_rec<OutT, false><<<T->rec_chunks, ADJ_T, smem, s>>>(rec_args(p, T, subset), w, out, lo, p->err_flag + 1);
+    k_adj_rec<OutT, false><<<T->rec_chunks, ADJ_T, smem, s>>>(rec_args(p, T, subset), w, out, p->err_flag + 1);
     return cudaGetLastError();
 }
 
@@ -1589,7 +1582,7 @@ cudaError_t records_adjoint_items(const caxsi_plan *p, const TablePath *T, const
     a.items = items;
     a.n_items = n_items;
     a.w_stride = w_stride;
-    k_adj_rec<float, true><<<std::min(n_items, T->rec_chunks), ADJ_T, smem, s>>>(a, w, Vtab, (float *)nullptr,
+    k_adj_rec<float, true><<<std::min(n_items, T->rec_chunks), ADJ_T, smem, s>>>(a, w, Vtab,
                                                                                 p->err_flag + 1);
     return cudaGetLastError();
 }
@@ -1597,8 +1590,8 @@ cudaError_t records_adjoint_items(const caxsi_plan *p, const TablePath *T, const
 cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, int subset, const float *w, int out_kind,
                             cudaStream_t s) {
     if (out_kind == 1)
-        return launch_adj_rec(p, T, subset, w, reinterpret_cast<__nv_bfloat16 *>(T->v16), (float *)nullptr, s);
+        return launch_adj_rec(p, T, subset, w, reinterpret_cast<__nv_bfloat16 *>(T->v16), s);
     if (out_kind == 2)
-        return launch_adj_rec(p, T, subset, w, reinterpret_cast<__half *>(T->v16), (float *)nullptr, s);
-    return launch_adj_rec(p, T, subset, w, T->tab, (float *)nullptr, s);
+        return launch_adj_rec(p, T, subset, w, reinterpret_cast<__half *>(T->v16), s);
+    return launch_adj_rec(p, T, subset, w, T->tab, s);
 }
