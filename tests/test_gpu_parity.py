@@ -241,12 +241,14 @@ def test_paper_scale_sampled(cx, path):
 
 # --------------------------------------------------------------------------
 # Reduced precision (bf16 / fp16 operands, FP32 accumulation): the error
-# against the FP64 oracle is measured and reported; the bounds below only
-# catch a broken path (the measured values are printed by the tests)
+# against the FP64 oracle is measured and reported (printed by the tests).
+# Measured on this case: bf16 about 4e-5 forward and 2e-4 adjoint (the adjoint
+# rows are rounded to bf16 too), fp16 about 5e-6 and 3e-5; the bounds leave
+# about 10x for other seeds and the cuBLAS engine.
 # --------------------------------------------------------------------------
 
-RED_BOUND = {"table_bf16": 2e-2, "table_fp16": 5e-3, "table_bf16@cublas": 2e-2,
-             "table_fp16@cublas": 5e-3}
+RED_BOUND = {"table_bf16": 2e-3, "table_fp16": 3e-4, "table_bf16@cublas": 2e-3,
+             "table_fp16@cublas": 3e-4}
 
 
 @pytest.mark.parametrize("path", sorted(RED_BOUND))
