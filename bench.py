@@ -17,7 +17,9 @@ phantoms and run without any data-path collective (weak scaling).
 Reconstruction experiment (the "recon" key, rank 0): the wall time of the
 plain FP32 iterations to a fixed NMSE, and the time of each alternative to
 reach the same NMSE: bf16 / fp16 table paths, a 2048-sample u table (FP32 and
-bf16), ordered subsets (8 and 64 subsets), and the learned warm start (a U-Net
+bf16), ordered subsets (8 and 64 subsets, with the FP32 table operators and
+with the direct ones, whose subset operators cost ~1/P of a full one), and the
+learned warm start (a U-Net
 trained here for --unet-steps objects, its training time reported apart).  The
 "precision" key gives the throughput and the error (against the exact FP32
 path) of the 16-bit contractions and of u tables of 1024-4096 samples.  The
@@ -391,28 +393,32 @@ def recon_experiment(caxsi, plan, g, dev, phantom, iters=100, max_iters=300, une
         sp.close()
     # ordered subsets (Algorithm 5): passes over the P subsets until the plain
     # target NMSE; the subset sensitivities b1_p are precomputed outside the
-    # timing, as b1 is for the plain iterations
+    # timing, as b1 is for the plain iterations.  On the direct path a subset
+    # operator evaluates only its pixels' pairs (cost ~ 1/P of a full one); on
+    # the FP32 table path it still pays the whole-object q contractions.
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for rho_z, sigma_y, max_passes in ((8, 2, 30), (8, 16, 12)):
         plan.set_subsets(caxsi.os_partition(g.M, g.N, g.rho_y, rho_z, sigma_y))
         n_sub = plan.n_subsets
-        plan.os_pass(y, torch.full((g.X, g.J, g.Q), f_init, device=dev), beta=beta, delta=delta)
-        f = torch.full((g.X, g.J, g.Q), f_init, device=dev)
-        total, r = 0.0, None
-        for k in range(max_passes):
-            e0.record()
-            plan.os_pass(y, f, beta=beta, delta=delta)
-            e1.record()
-            torch.cuda.synchronize()
-            total += e0.elapsed_time(e1) / 1e3
-            nmse = float(torch.sum((f.double() - f_ref.double()) ** 2)) / nref
-            r = {"subsets": n_sub, "rho_z": rho_z, "sigma_y": sigma_y, "passes": k + 1,
-                 "sub_iterations": (k + 1) * n_sub, "seconds": total, "nmse": nmse,
-                 "reached": nmse <= plain["nmse"]}
-            if r["reached"]:
-                break
-        r["speedup_vs_plain"] = plain["seconds"] / r["seconds"] if r["reached"] else None
-        res[f"os_em_{n_sub}"] = r
+        for path, tag in (("table_fp32", ""), ("direct", "_direct")):
+            plan.os_pass(y, torch.full((g.X, g.J, g.Q), f_init, device=dev), beta=beta, delta=delta,
+                         path=P[path])
+            f = torch.full((g.X, g.J, g.Q), f_init, device=dev)
+            total, r = 0.0, None
+            for k in range(max_passes):
+                e0.record()
+                plan.os_pass(y, f, beta=beta, delta=delta, path=P[path])
+                e1.record()
+                torch.cuda.synchronize()
+                total += e0.elapsed_time(e1) / 1e3
+                nmse = float(torch.sum((f.double() - f_ref.double()) ** 2)) / nref
+                r = {"subsets": n_sub, "rho_z": rho_z, "sigma_y": sigma_y, "path": path, "passes": k + 1,
+                     "sub_iterations": (k + 1) * n_sub, "seconds": total, "nmse": nmse,
+                     "reached": nmse <= plain["nmse"]}
+                if r["reached"]:
+                    break
+            r["speedup_vs_plain"] = plain["seconds"] / r["seconds"] if r["reached"] else None
+            res[f"os_em_{n_sub}{tag}"] = r
     res["learned"] = learned_experiment(plan, g, y, f_ref, plain, unet_steps) if unet_steps > 0 else None
     return res
 

@@ -159,24 +159,29 @@ caxsi_status caxsi_recon_step(caxsi_plan *plan, const float *y_dev, const float 
  * the rows (pixels) of subset p.  The paper's symmetry-preserving choice groups
  * every pixel with its left-right and up-down mirror images and with the
  * pixels a multiple of the translation step away; any partition is accepted
- * here (the Python binding builds the paper's one).  Table paths only: the
- * subset operators stream only the pairs of the subset's pixels (records
- * grouped by subset), while the q contractions stay whole-object.
+ * here (the Python binding builds the paper's one).  CAXSI_PATH_DIRECT
+ * evaluates only the pairs of the subset's pixels, so a subset operator costs
+ * about 1/P of the full one (the point of the algorithm).  The table paths
+ * stream only the subset's pair records (records grouped by subset), but their
+ * q contractions stay whole-object, so a subset operator there costs most of a
+ * full one.
  */
 #define CAXSI_MAX_SUBSETS 1024
 
 /* Set (or replace) the partition.  subset_of_pixel: host, M*N int32 in
- * [0, n_subsets), row-major (m, n).  Builds the grouped pair records on the
- * device (synchronous) and drops the cached subset sensitivities.
+ * [0, n_subsets), row-major (m, n).  Uploads the subsets' pixel lists, drops
+ * the cached subset sensitivities and (synchronously) builds the table paths'
+ * records grouped by subset if the plan's tables exist already; otherwise the
+ * first table-path subset call builds them (that call then synchronises).
  * Errors: INVALID (sizes, an index out of range, n_subsets outside
- * [1, min(CAXSI_MAX_SUBSETS, M*N)]), UNSUPPORTED (the geometry has no pair
- * records: more than 65536 pixels or knots), CUDA, OOM. */
+ * [1, min(CAXSI_MAX_SUBSETS, M*N)]), UNSUPPORTED (the table paths' subset
+ * calls, when the geometry has no pair records: more than 65536 pixels or
+ * knots), CUDA, OOM. */
 caxsi_status caxsi_plan_set_subsets(caxsi_plan *plan, int n_subsets, const int32_t *subset_of_pixel);
 
 /* g = A_p f: g_dev (M*N, device) holds the subset's pixels of A f and 0 at every
  * other pixel.  Same arguments and errors as caxsi_forward, plus subset in
- * [0, n_subsets) (INVALID otherwise or before caxsi_plan_set_subsets) and
- * UNSUPPORTED for CAXSI_PATH_DIRECT. */
+ * [0, n_subsets) (INVALID otherwise or before caxsi_plan_set_subsets). */
 caxsi_status caxsi_forward_subset(caxsi_plan *plan, int subset, const float *f_dev, int64_t f_len,
                                   float *g_dev, int64_t g_len, int path, void *stream);
 

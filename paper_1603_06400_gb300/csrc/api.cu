@@ -66,6 +66,8 @@ void free_plan(caxsi_plan *p) {
     cudaFree(p->ones);
     for (int k = 0; k < 4; ++k) cudaFree(p->b1[k]);
     for (int k = 0; k < 4; ++k) cudaFree(p->b1_sub[k]);
+    cudaFree(p->sub_pix);
+    cudaFree(p->sub_of_pix);
     cudaFree(p->vjp_scratch);
     cudaFree(p->b2);
     cudaFree(p->fnew);
@@ -112,12 +114,12 @@ bool path_ok(int path) { return path >= CAXSI_PATH_DIRECT && path <= CAXSI_PATH_
 
 // subset < 0: the full operator; else the rows of that detector subset (table paths).
 caxsi_status run_forward(caxsi_plan *p, const float *f, float *g, int path, cudaStream_t s, int subset = -1) {
-    if (path == CAXSI_PATH_DIRECT) return subset < 0 ? direct_forward(p, f, g, s) : CAXSI_ERR_UNSUPPORTED;
+    if (path == CAXSI_PATH_DIRECT) return subset < 0 ? direct_forward(p, f, g, s) : direct_forward_subset(p, f, g, subset, s);
     return table_forward(p, f, g, path, subset, s);
 }
 
 caxsi_status run_adjoint(caxsi_plan *p, const float *w, float *f, int path, cudaStream_t s, int subset = -1) {
-    if (path == CAXSI_PATH_DIRECT) return subset < 0 ? direct_adjoint(p, w, f, s) : CAXSI_ERR_UNSUPPORTED;
+    if (path == CAXSI_PATH_DIRECT) return subset < 0 ? direct_adjoint(p, w, f, s) : direct_adjoint_subset(p, w, f, subset, s);
     return table_adjoint(p, w, f, path, subset, s);
 }
 
@@ -257,8 +259,27 @@ caxsi_status caxsi_plan_set_subsets(caxsi_plan *p, int n_subsets, const int32_t 
     if (!dg.ok) return CAXSI_ERR_CUDA;
     p->n_subsets = 0;
     drop_subset_sensitivities(p);
-    caxsi_status st = table_set_subsets(p, n_subsets, subset_of_pixel);
-    if (st == CAXSI_OK) p->n_subsets = n_subsets;
+    // the partition and its pixel lists (counting sort of the pixels by subset)
+    p->sub_host.assign(subset_of_pixel, subset_of_pixel + npix);
+    p->sub_off.assign(n_subsets + 1, 0);
+    std::vector<int> pix(npix);
+    for (int64_t k = 0; k < npix; ++k) p->sub_off[subset_of_pixel[k] + 1]++;
+    for (int s = 0; s < n_subsets; ++s) p->sub_off[s + 1] += p->sub_off[s];
+    {
+        std::vector<int> fill(p->sub_off.begin(), p->sub_off.end() - 1);
+        for (int64_t k = 0; k < npix; ++k) pix[fill[subset_of_pixel[k]]++] = (int)k;
+    }
+    if (!p->sub_pix) {
+        CAXSI_CUDA_TRY(cudaMalloc(&p->sub_pix, npix * sizeof(int)));
+        CAXSI_CUDA_TRY(cudaMalloc(&p->sub_of_pix, npix * sizeof(int)));
+    }
+    CAXSI_CUDA_TRY(cudaMemcpy(p->sub_pix, pix.data(), npix * sizeof(int), cudaMemcpyHostToDevice));
+    CAXSI_CUDA_TRY(cudaMemcpy(p->sub_of_pix, subset_of_pixel, npix * sizeof(int), cudaMemcpyHostToDevice));
+    ++p->sub_gen;
+    p->n_subsets = n_subsets;
+    // the table paths' grouped records now if the table exists, else on first use
+    caxsi_status st = p->table ? table_set_subsets(p) : CAXSI_OK;
+    if (st != CAXSI_OK) p->n_subsets = 0;
     return st;
 }
 
@@ -290,7 +311,6 @@ caxsi_status caxsi_recon_step_subset(caxsi_plan *p, int subset, const float *y_d
     if (!p || !y_dev || !f_dev || !path_ok(path) || !subset_ok(p, subset)) return CAXSI_ERR_INVALID;
     if (f_len != (int64_t)p->dg.R * p->dg.Q) return CAXSI_ERR_INVALID;
     if (!isfinite(beta) || beta < 0.f || !isfinite(delta) || delta < 0.f) return CAXSI_ERR_INVALID;
-    if (path == CAXSI_PATH_DIRECT) return CAXSI_ERR_UNSUPPORTED;
     DeviceGuard dg(p->device);
     if (!dg.ok) return CAXSI_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
@@ -310,7 +330,7 @@ caxsi_status caxsi_recon_step_subset(caxsi_plan *p, int subset, const float *y_d
     }
     // z_p = A_p f + r_p, ratio on the subset's pixels, L_p(f) in FP64
     if ((st = run_forward(p, f_dev, p->gtmp, path, s, subset)) != CAXSI_OK) return st;
-    if ((st = recon_ratio(p, y_dev, r_dev, table_subset_of_pixel(p), subset, s)) != CAXSI_OK) return st;
+    if ((st = recon_ratio(p, y_dev, r_dev, p->sub_of_pix, subset, s)) != CAXSI_OK) return st;
     if (nll_out) {
         int64_t keep = p->launches;
         st = recon_nll_fetch(p, nll_out, s);

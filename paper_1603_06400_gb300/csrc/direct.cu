@@ -14,6 +14,12 @@
 // lane-private row of Q+3 q bins in shared memory laid out [bin][lane] (bank
 // = lane, so the scatter is conflict-free), and the 32 private rows are
 // summed at the end with a rotated read (also conflict-free).  No atomics.
+//
+// Subset operators (ordered subsets, Sec. VI): both kernels take a list of
+// detector pixels instead of the whole detector (LIST): the forward gives one
+// thread to each listed pixel and writes compact partial sums, which are summed
+// and scattered to the listed pixels; the adjoint's lanes walk the list.  The
+// cost of a subset operator is then that of its pairs.
 #include <mutex>
 
 #include "internal.cuh"
@@ -35,8 +41,10 @@ struct Tables {
     const float2 *energy;
 };
 
+template <bool LIST>
 __global__ void __launch_bounds__(FWD_THREADS)
-k_fwd_direct(Tables T, const float *__restrict__ f, float *__restrict__ part, int vc, int tiles_n) {
+k_fwd_direct(Tables T, const float *__restrict__ f, float *__restrict__ part, int vc, int tiles_n,
+             const int *__restrict__ list, int np) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DevGeo &g = T.g;
     const int QP = g.Q + 2;
@@ -45,9 +53,20 @@ k_fwd_direct(Tables T, const float *__restrict__ f, float *__restrict__ part, in
     float2 *s_f = reinterpret_cast<float2 *>(s_vox + FWD_VS);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
-    const int m = tm * FWD_WARPS + warp, n = tn * 32 + lane;
-    const bool valid = (m < g.M) && (n < g.N);
+    int m, n, e = 0;
+    bool valid;
+    if (LIST) {   // listed pixel e
+        e = blockIdx.x * FWD_THREADS + tid;
+        valid = e < np;
+        const int p = valid ? list[e] : 0;
+        m = p / g.N;
+        n = p - m * g.N;
+    } else {      // 8 x 32 tile of the detector
+        const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
+        m = tm * FWD_WARPS + warp;
+        n = tn * 32 + lane;
+        valid = (m < g.M) && (n < g.N);
+    }
     const int v0 = blockIdx.y * vc;
     const int v1 = min(v0 + vc, g.R);
 
@@ -94,7 +113,21 @@ k_fwd_direct(Tables T, const float *__restrict__ f, float *__restrict__ part, in
             acc = fmaf(vx.z * gd * ang, e_acc, acc);
         }
     }
-    if (valid) part[(int64_t)blockIdx.y * g.M * g.N + (int64_t)m * g.N + n] = acc;
+    if (valid) {
+        if (LIST) part[(int64_t)blockIdx.y * np + e] = acc;
+        else part[(int64_t)blockIdx.y * g.M * g.N + (int64_t)m * g.N + n] = acc;
+    }
+}
+
+// out[list[e]] = sum_c part[c * np + e], c ascending: the listed pixels' sums of
+// the compact partial images.
+__global__ void k_sum_list(const float *__restrict__ part, int nparts, int np, const int *__restrict__ list,
+                           float *__restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= np) return;
+    float s = 0.f;
+    for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * np + e];
+    out[list[e]] = s;
 }
 
 // out[idx] = sum_c part[c * stride + idx], c ascending (the loads of 32 terms are
@@ -116,9 +149,10 @@ __global__ void k_sum_parts(const float *__restrict__ part, int nparts, int64_t 
     out[idx] = s;
 }
 
+template <bool LIST>
 __global__ void __launch_bounds__(ADJ_WARPS * 32)
 k_adj_direct(Tables T, const float *__restrict__ w, float *__restrict__ out, int split,
-             int rows_per_split) {
+             int rows_per_split, const int *__restrict__ list, int np) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DevGeo &g = T.g;
     const int QB = g.Q + 3;  // bins l' = l + 1 in [0, Q + 2]; 1..Q are real
@@ -136,35 +170,44 @@ k_adj_direct(Tables T, const float *__restrict__ w, float *__restrict__ out, int
 
     const int i = v / g.J, j = v - i * g.J;
     const float4 vx = T.vox[v];
-    const int m0 = sp * rows_per_split, m1 = min(g.M, m0 + rows_per_split);
     float *my = acc + lane;
-    for (int m = m0; m < m1; ++m) {
-        const float sz = T.zrow[m];
-        const uint32_t *trow = T.tbits + ((int64_t)v * g.M + m) * g.Nw;
-        const float *god_row = T.god + ((int64_t)i * g.M + m) * g.ND - g.d_min - g.rho_y * j;
-        for (int nb = 0; nb < g.N; nb += 32) {
-            const int n = nb + lane;
-            if (n >= g.N) break;
-            if (!((trow[nb >> 5] >> lane) & 1u)) continue;
-            const float wv = w[(int64_t)m * g.N + n];
-            if (wv == 0.f) continue;
-            float u, ang;
-            pair_u_angular(vx.x, vx.y, vx.w, (float)n - g.cN, sz, g.p_y, g.Xd, u, ang);
-            const float base = vx.z * god_row[n] * ang * wv;
+    // one pair (pixel (m, n)) scattered into the lane's q row
+    auto pair = [&](int m, int n) {
+        const uint32_t word = T.tbits[((int64_t)v * g.M + m) * g.Nw + (n >> 5)];
+        if (!((word >> (n & 31)) & 1u)) return;
+        const float wv = w[(int64_t)m * g.N + n];
+        if (wv == 0.f) return;
+        float u, ang;
+        pair_u_angular(vx.x, vx.y, vx.w, (float)n - g.cN, T.zrow[m], g.p_y, g.Xd, u, ang);
+        const float base = vx.z * T.god[((int64_t)i * g.M + m) * g.ND + (n - g.rho_y * j - g.d_min)] * ang * wv;
 #pragma unroll 4
-            for (int k = 0; k < g.K; ++k) {
-                const float2 ak = s_en[k];
-                float tau = fmaf(ak.x, u, -g.b);
-                tau = fminf(fmaxf(tau, -1.f), g.Qf);
-                const float fl = floorf(tau);
-                const float al = tau - fl;
-                const int lp = (int)fl + 1;
-                const float cb = ak.y * base;
-                const float hi = cb * al;
-                my[lp * 32] += cb - hi;
-                my[(lp + 1) * 32] += hi;
-            }
+        for (int k = 0; k < g.K; ++k) {
+            const float2 ak = s_en[k];
+            float tau = fmaf(ak.x, u, -g.b);
+            tau = fminf(fmaxf(tau, -1.f), g.Qf);
+            const float fl = floorf(tau);
+            const float al = tau - fl;
+            const int lp = (int)fl + 1;
+            const float cb = ak.y * base;
+            const float hi = cb * al;
+            my[lp * 32] += cb - hi;
+            my[(lp + 1) * 32] += hi;
         }
+    };
+    if (LIST) {
+        for (int e = lane; e < np; e += 32) {
+            const int p = list[e];
+            const int m = p / g.N;
+            pair(m, p - m * g.N);
+        }
+    } else {
+        const int m0 = sp * rows_per_split, m1 = min(g.M, m0 + rows_per_split);
+        for (int m = m0; m < m1; ++m)
+            for (int nb = 0; nb < g.N; nb += 32) {
+                const int n = nb + lane;
+                if (n >= g.N) break;
+                pair(m, n);
+            }
     }
     __syncwarp();
     float *dst = out + ((int64_t)sp * g.R + v) * g.Q;
@@ -228,11 +271,11 @@ caxsi_status direct_forward(caxsi_plan *p, const float *f, float *g_out, cudaStr
     const int tiles_n = (int)ceil_div64(g.N, 32);
     const int tiles = (int)ceil_div64(g.M, FWD_WARPS) * tiles_n;
     const size_t sm = fwd_smem(g);
-    CAXSI_CUDA_TRY(cudaFuncSetAttribute(k_fwd_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    CAXSI_CUDA_TRY(cudaFuncSetAttribute(k_fwd_direct<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     dim3 grid(tiles, p->fwd_chunks);
     {
         CAXSI_PROF(p, "fwd_direct", s);
-        k_fwd_direct<<<grid, FWD_THREADS, sm, s>>>(tables_of(p), f, p->fwd_part, p->fwd_vc, tiles_n);
+        k_fwd_direct<false><<<grid, FWD_THREADS, sm, s>>>(tables_of(p), f, p->fwd_part, p->fwd_vc, tiles_n, nullptr, 0);
     }
     CAXSI_LAUNCH_CHECK(p);
     const int64_t npix = (int64_t)g.M * g.N;
@@ -247,14 +290,15 @@ caxsi_status direct_forward(caxsi_plan *p, const float *f, float *g_out, cudaStr
 caxsi_status direct_adjoint(caxsi_plan *p, const float *w, float *f_out, cudaStream_t s) {
     const DevGeo &g = p->dg;
     const size_t sm = adj_smem(g);
-    CAXSI_CUDA_TRY(cudaFuncSetAttribute(k_adj_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    CAXSI_CUDA_TRY(cudaFuncSetAttribute(k_adj_direct<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int split = p->adj_split;
     const int rps = (int)ceil_div64(g.M, split);
     const int64_t items = (int64_t)g.R * split;
     float *dst = split > 1 ? p->adj_part : f_out;
     {
         CAXSI_PROF(p, "adj_direct", s);
-        k_adj_direct<<<(unsigned)ceil_div64(items, ADJ_WARPS), ADJ_WARPS * 32, sm, s>>>(tables_of(p), w, dst, split, rps);
+        k_adj_direct<false><<<(unsigned)ceil_div64(items, ADJ_WARPS), ADJ_WARPS * 32, sm, s>>>(tables_of(p), w, dst,
+                                                                                          split, rps, nullptr, 0);
     }
     CAXSI_LAUNCH_CHECK(p);
     if (split > 1) {
@@ -265,6 +309,52 @@ caxsi_status direct_adjoint(caxsi_plan *p, const float *w, float *f_out, cudaStr
         }
         CAXSI_LAUNCH_CHECK(p);
     }
+    return CAXSI_OK;
+}
+
+// Subset operators: the pixels sub_pix[sub_off[subset] .. sub_off[subset + 1]).
+caxsi_status direct_forward_subset(caxsi_plan *p, const float *f, float *g_out, int subset, cudaStream_t s) {
+    const DevGeo &g = p->dg;
+    const int np = p->sub_off[subset + 1] - p->sub_off[subset];
+    const int *list = p->sub_pix + p->sub_off[subset];
+    const int64_t npix = (int64_t)g.M * g.N;
+    CAXSI_CUDA_TRY(cudaMemsetAsync(g_out, 0, npix * sizeof(float), s));
+    if (np == 0) return CAXSI_OK;
+    // voxel chunks so that about 4 blocks per SM run; their compact partial
+    // images fit the plan's forward scratch (fwd_chunks full images)
+    const int xb = (int)ceil_div64(np, FWD_THREADS);
+    int chunks = (int)ceil_div64(4 * p->num_sms, xb);
+    if (chunks > g.R) chunks = g.R;
+    if ((int64_t)chunks * np > (int64_t)p->fwd_chunks * npix) chunks = (int)((int64_t)p->fwd_chunks * npix / np);
+    const int vc = (int)ceil_div64(g.R, chunks);
+    chunks = (int)ceil_div64(g.R, vc);
+    const size_t sm = fwd_smem(g);
+    CAXSI_CUDA_TRY(cudaFuncSetAttribute(k_fwd_direct<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    {
+        CAXSI_PROF(p, "fwd_direct_subset", s);
+        k_fwd_direct<true><<<dim3(xb, chunks), FWD_THREADS, sm, s>>>(tables_of(p), f, p->fwd_part, vc, 0, list, np);
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    {
+        CAXSI_PROF(p, "sum_list", s);
+        k_sum_list<<<(unsigned)ceil_div64(np, 256), 256, 0, s>>>(p->fwd_part, chunks, np, list, g_out);
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    return CAXSI_OK;
+}
+
+caxsi_status direct_adjoint_subset(caxsi_plan *p, const float *w, float *f_out, int subset, cudaStream_t s) {
+    const DevGeo &g = p->dg;
+    const int np = p->sub_off[subset + 1] - p->sub_off[subset];
+    const int *list = p->sub_pix + p->sub_off[subset];
+    const size_t sm = adj_smem(g);
+    CAXSI_CUDA_TRY(cudaFuncSetAttribute(k_adj_direct<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    {
+        CAXSI_PROF(p, "adj_direct_subset", s);
+        k_adj_direct<true><<<(unsigned)ceil_div64(g.R, ADJ_WARPS), ADJ_WARPS * 32, sm, s>>>(tables_of(p), w, f_out, 1,
+                                                                                         g.M, list, np);
+    }
+    CAXSI_LAUNCH_CHECK(p);
     return CAXSI_OK;
 }
 
@@ -319,9 +409,9 @@ caxsi_status direct_forward_static_scratch(caxsi_plan *p, const float *f, float 
     const int tiles_n = (int)ceil_div64(g.N, 32);
     const int tiles = (int)ceil_div64(g.M, FWD_WARPS) * tiles_n;
     const size_t sm = fwd_smem(g);
-    CAXSI_CUDA_TRY(cudaFuncSetAttribute(k_fwd_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    CAXSI_CUDA_TRY(cudaFuncSetAttribute(k_fwd_direct<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     // every chunk overwrites its whole partial image, so nothing needs clearing
-    k_fwd_direct<<<dim3(tiles, chunks), FWD_THREADS, sm, s>>>(tables_of(p), f, part, vc, tiles_n);
+    k_fwd_direct<false><<<dim3(tiles, chunks), FWD_THREADS, sm, s>>>(tables_of(p), f, part, vc, tiles_n, nullptr, 0);
     CAXSI_LAUNCH_CHECK(p);
     k_sum_parts<<<(unsigned)ceil_div64(npix, 256), 256, 0, s>>>(part, chunks, npix, g_out, npix);
     CAXSI_LAUNCH_CHECK(p);

@@ -71,6 +71,11 @@ struct caxsi_plan {
     float *ones;        // [M*N]
     float *b1[4];       // [R*Q] A^T 1 per path, lazily
     int n_subsets;      // detector subsets of the ordered-subset operators (0 = none)
+    std::vector<int32_t> sub_host;  // [M*N] subset of each pixel (host copy of the partition)
+    std::vector<int> sub_off;   // [n_subsets + 1] each subset's range in sub_pix (host)
+    int *sub_pix;       // [M*N] the pixels grouped by subset, ascending within a subset (device)
+    int *sub_of_pix;    // [M*N] subset of each pixel (device)
+    int sub_gen;        // incremented by every new partition
     float *b1_sub[4];   // [n_subsets][R*Q] A_p^T 1 per path, lazily
     std::vector<unsigned char> b1_sub_ok[4];   // which subsets of b1_sub are computed
     float *vjp_scratch;   // [2][vjp_cap] reverse-mode scratch of the update
@@ -105,18 +110,23 @@ caxsi_status direct_forward(caxsi_plan *p, const float *f, float *g, cudaStream_
 caxsi_status direct_adjoint(caxsi_plan *p, const float *w, float *f, cudaStream_t s);
 void direct_configure(caxsi_plan *p);
 caxsi_status direct_forward_static_scratch(caxsi_plan *p, const float *f, float *g, cudaStream_t s);
+// subset operators over the pixel lists of caxsi_plan_set_subsets
+caxsi_status direct_forward_subset(caxsi_plan *p, const float *f, float *g, int subset, cudaStream_t s);
+caxsi_status direct_adjoint_subset(caxsi_plan *p, const float *w, float *f, int subset, cudaStream_t s);
 
 // ---- table.cu ----------------------------------------------------------------
 // subset < 0: the full operator; else the rows (pixels) of that detector subset.
 caxsi_status table_forward(caxsi_plan *p, const float *f, float *g, int path, int subset, cudaStream_t s);
 caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f, int path, int subset, cudaStream_t s);
-caxsi_status table_set_subsets(caxsi_plan *p, int P, const int32_t *sub_host);
+// the table paths' records grouped by the plan's current partition (no-op when
+// they are up to date; synchronous when it builds them)
+caxsi_status table_set_subsets(caxsi_plan *p);
 // nb objects = voxel ranges [ranges[2b], ranges[2b+1]) of the shared geometry
 caxsi_status table_forward_batch(caxsi_plan *p, int nb, const int32_t *ranges, const float *f, float *g,
                                  int path, cudaStream_t s);
 caxsi_status table_adjoint_batch(caxsi_plan *p, int nb, const int32_t *ranges, const float *w, float *f,
                                  int path, cudaStream_t s);
-const int *table_subset_of_pixel(const caxsi_plan *p);
+
 void table_destroy(caxsi_plan *p);
 int64_t table_breakpoints(const caxsi_plan *p);
 int64_t table_records(const caxsi_plan *p);

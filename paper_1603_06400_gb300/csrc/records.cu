@@ -1312,8 +1312,6 @@ int fill_warps(const caxsi_plan *p, const TablePath *T) {
 void records_free(TablePath *T) {
     free_set(T->rec);
     free_set(T->sub);
-    cudaFree(T->sub_of_pix);
-    T->sub_of_pix = nullptr;
     cudaFree(T->sym.tt);
     cudaFree(T->sym.tb);
     cudaFree(T->sym.w);
@@ -1347,8 +1345,7 @@ caxsi_status records_build_subsets(caxsi_plan *p, TablePath *T, int P, const int
     const DevGeo &g = p->dg;
     const int npix = g.M * g.N;
     free_set(T->sub);
-    cudaFree(T->sub_of_pix);
-    T->sub_of_pix = nullptr;
+    T->sub_gen = 0;
     // pixel lists of the subsets (counting sort of the pixels by subset)
     std::vector<int> sp_off(P + 1, 0), sp_pix(npix);
     for (int k = 0; k < npix; ++k) sp_off[sub_host[k] + 1]++;
@@ -1375,14 +1372,9 @@ caxsi_status records_build_subsets(caxsi_plan *p, TablePath *T, int P, const int
     if (st == CAXSI_OK) st = build_set(p, T, T->sub, P, d_sub, d_off, d_pix, fill_warps(p, T));
     cudaFree(d_off);
     cudaFree(d_pix);
+    cudaFree(d_sub);
     if (st == CAXSI_OK && T->sub.P == 0) st = CAXSI_ERR_OOM;
-    if (st != CAXSI_OK) {
-        cudaFree(d_sub);
-        return st;
-    }
-    T->sub_of_pix = d_sub;
-    p->table_bytes += (int64_t)npix * 4;
-    return CAXSI_OK;
+    return st;
 }
 
 // The adjoint's symmetric lists (SymSet::adj): count, pad to quads, fill sorted by

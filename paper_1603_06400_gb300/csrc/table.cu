@@ -762,7 +762,11 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
     caxsi_status st = ensure_table(p, path);
     if (st != CAXSI_OK) return st;
     TablePath *T = p->table;
-    if (subset >= 0 && (!T->use_records || subset >= T->sub.P)) return CAXSI_ERR_UNSUPPORTED;
+    if (subset >= 0) {   // the records grouped by the current partition (built on first use)
+        if (!T->use_records) return CAXSI_ERR_UNSUPPORTED;
+        if ((st = table_set_subsets(p)) != CAXSI_OK) return st;
+        if (subset >= T->sub.P) return CAXSI_ERR_UNSUPPORTED;
+    }
     const DevGeo &d = p->dg;
     const float one = 1.f, zero = 0.f;
     if (cublasSetStream(T->blas, s) != CUBLAS_STATUS_SUCCESS) return CAXSI_ERR_CUDA;
@@ -844,7 +848,11 @@ caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path
     caxsi_status st = ensure_table(p, path);
     if (st != CAXSI_OK) return st;
     TablePath *T = p->table;
-    if (subset >= 0 && (!T->use_records || subset >= T->sub.P)) return CAXSI_ERR_UNSUPPORTED;
+    if (subset >= 0) {   // the records grouped by the current partition (built on first use)
+        if (!T->use_records) return CAXSI_ERR_UNSUPPORTED;
+        if ((st = table_set_subsets(p)) != CAXSI_OK) return st;
+        if (subset >= T->sub.P) return CAXSI_ERR_UNSUPPORTED;
+    }
     const DevGeo &d = p->dg;
     const int out_kind = path == CAXSI_PATH_TABLE_FP32 ? 0 : (path == CAXSI_PATH_TABLE_BF16 ? 1 : 2);
     const bool tc = p->gemm_engine == 0 && T->use_records;
@@ -963,15 +971,17 @@ caxsi_status table_adjoint_batch(caxsi_plan *p, int nb, const int32_t *ranges, c
     return CAXSI_OK;
 }
 
-caxsi_status table_set_subsets(caxsi_plan *p, int P, const int32_t *sub_host) {
+caxsi_status table_set_subsets(caxsi_plan *p) {
     caxsi_status st = ensure_table(p, CAXSI_PATH_TABLE_FP32);
     if (st != CAXSI_OK) return st;
-    st = records_build_subsets(p, p->table, P, sub_host);
-    if (st == CAXSI_OK) CAXSI_CUDA_TRY(cudaDeviceSynchronize());
+    if (p->table->sub_gen == p->sub_gen) return CAXSI_OK;
+    st = records_build_subsets(p, p->table, p->n_subsets, p->sub_host.data());
+    if (st == CAXSI_OK) {
+        CAXSI_CUDA_TRY(cudaDeviceSynchronize());
+        p->table->sub_gen = p->sub_gen;
+    }
     return st;
 }
-
-const int *table_subset_of_pixel(const caxsi_plan *p) { return p->table ? p->table->sub_of_pix : nullptr; }
 
 void table_destroy(caxsi_plan *p) {
     free_table(p->table);

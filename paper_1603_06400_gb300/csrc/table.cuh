@@ -84,7 +84,7 @@ struct TablePath {
     bool use_records = false;
     RecSet rec, sub;
     SymSet sym;
-    int *sub_of_pix = nullptr;   // [M*N] subset of each pixel (device), when sub is built
+    int sub_gen = 0;             // the plan partition sub was built for (plan sub_gen)
     BatchState batch;
     int rec_chunks = 0, rec_vc = 0;
 

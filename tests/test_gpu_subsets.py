@@ -14,7 +14,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 REL_L2_TOL = 1e-5
-OS_PATHS = ["table_fp32", "table_fp32@cublas"]
+OS_PATHS = ["direct", "table_fp32", "table_fp32@cublas"]
 
 
 def rel_l2(a, b):
@@ -170,9 +170,35 @@ def test_subset_errors(cx):
     with pytest.raises(caxsi.CaxsiError) as e:      # subset out of range
         plan.forward_subset(plan.n_subsets, f)
     assert e.value.status == 1
-    with pytest.raises(caxsi.CaxsiError) as e:      # the direct path has no subset form
-        plan.forward_subset(0, f, path=caxsi.PATHS["direct"])
-    assert e.value.status == 6
+    with pytest.raises(caxsi.CaxsiError) as e:      # out of range on the direct path too
+        plan.forward_subset(plan.n_subsets, f, path=caxsi.PATHS["direct"])
+    assert e.value.status == 1
+    assert plan.info()["device_error"] == 0
+    plan.close()
+
+
+def test_direct_and_table_subsets_agree_and_replace_partitions(cx):
+    """The direct subset operators (pixel lists) and the table ones (records
+    grouped by subset) compute the same A_p; a new partition replaces the old
+    one for both (the table records are rebuilt on first use)."""
+    caxsi, torch = cx
+    g = synth.tiny_geometry()
+    phi = synth.tungsten_spectrum(g)
+    mask = synth.random_mask(g, 41)
+    plan = caxsi.Plan(g, phi, mask)
+    f = _t(torch, synth.uniform_random((g.X, g.J, g.Q), 42))
+    w = _t(torch, synth.uniform_random((g.M, g.N), 43) + 0.1)
+    D, T = caxsi.PATHS["direct"], caxsi.PATHS["table_fp32"]
+    for part in _partitions(caxsi, g).values():
+        plan.set_subsets(part)
+        for s in range(plan.n_subsets):
+            gd = plan.forward_subset(s, f, path=D).cpu().numpy()
+            gt = plan.forward_subset(s, f, path=T).cpu().numpy()
+            assert rel_l2(gd, gt) <= 1e-5
+            assert np.all(gd.ravel()[part != s] == 0)
+            fd = plan.adjoint_subset(s, w, path=D).cpu().numpy()
+            ft = plan.adjoint_subset(s, w, path=T).cpu().numpy()
+            assert rel_l2(fd, ft) <= 1e-5
     assert plan.info()["device_error"] == 0
     plan.close()
 
