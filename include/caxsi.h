@@ -309,6 +309,12 @@ caxsi_status caxsi_plan_info(caxsi_plan *plan, caxsi_plan_info_t *info);
  *     blocks that meet only those zeros.  The skipped products are exact zeros:
  *     results are unchanged, only the work shrinks.  0 multiplies everything. */
 #define CAXSI_OPT_GEMM_BANDS 4
+/*   CAXSI_OPT_SPARSE_SUBSETS: 1 (default) or 0.  With 1 the FP32 table path's
+ *     subset operators contract only at the knots of the subset's pairs, per
+ *     pair record against the rows of S~ (a subset operator then costs about
+ *     1/P of a full one); 0 runs the whole-object contractions as the full
+ *     operators do.  Equal up to FP32 rounding. */
+#define CAXSI_OPT_SPARSE_SUBSETS 5
 caxsi_status caxsi_plan_set_option(caxsi_plan *plan, int key, int value);
 
 /* Kernel timing (tracing).  When enabled, every kernel the plan launches is

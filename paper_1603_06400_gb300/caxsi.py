@@ -380,6 +380,11 @@ class Plan:
         of A, cheaper by B/n).  Set it before the first table-path call."""
         _check(self.lib.caxsi_plan_set_option(self.handle, 3, int(n)), "caxsi_plan_set_option")
 
+    def set_sparse_subsets(self, on: bool = True):
+        """FP32 subset operators contracted per record at the subset's knots only
+        (default on) instead of by the whole-object contractions."""
+        _check(self.lib.caxsi_plan_set_option(self.handle, 5, int(bool(on))), "caxsi_plan_set_option")
+
     def set_gemm_bands(self, on: bool = True):
         """Skip the product blocks of the tcgen05 contractions that meet only
         zeros of the band-limited spectral matrix (default on; results unchanged)."""

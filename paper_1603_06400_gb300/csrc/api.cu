@@ -68,6 +68,7 @@ void free_plan(caxsi_plan *p) {
     for (int k = 0; k < 4; ++k) cudaFree(p->b1_sub[k]);
     cudaFree(p->sub_pix);
     cudaFree(p->sub_of_pix);
+    cudaFree(p->sub_pos);
     cudaFree(p->vjp_scratch);
     cudaFree(p->b2);
     cudaFree(p->fnew);
@@ -262,19 +263,25 @@ caxsi_status caxsi_plan_set_subsets(caxsi_plan *p, int n_subsets, const int32_t 
     // the partition and its pixel lists (counting sort of the pixels by subset)
     p->sub_host.assign(subset_of_pixel, subset_of_pixel + npix);
     p->sub_off.assign(n_subsets + 1, 0);
-    std::vector<int> pix(npix);
+    std::vector<int> pix(npix), pos(npix);
     for (int64_t k = 0; k < npix; ++k) p->sub_off[subset_of_pixel[k] + 1]++;
     for (int s = 0; s < n_subsets; ++s) p->sub_off[s + 1] += p->sub_off[s];
     {
         std::vector<int> fill(p->sub_off.begin(), p->sub_off.end() - 1);
-        for (int64_t k = 0; k < npix; ++k) pix[fill[subset_of_pixel[k]]++] = (int)k;
+        for (int64_t k = 0; k < npix; ++k) {
+            const int s = subset_of_pixel[k];
+            pos[k] = fill[s] - p->sub_off[s];
+            pix[fill[s]++] = (int)k;
+        }
     }
     if (!p->sub_pix) {
         CAXSI_CUDA_TRY(cudaMalloc(&p->sub_pix, npix * sizeof(int)));
         CAXSI_CUDA_TRY(cudaMalloc(&p->sub_of_pix, npix * sizeof(int)));
+        CAXSI_CUDA_TRY(cudaMalloc(&p->sub_pos, npix * sizeof(int)));
     }
     CAXSI_CUDA_TRY(cudaMemcpy(p->sub_pix, pix.data(), npix * sizeof(int), cudaMemcpyHostToDevice));
     CAXSI_CUDA_TRY(cudaMemcpy(p->sub_of_pix, subset_of_pixel, npix * sizeof(int), cudaMemcpyHostToDevice));
+    CAXSI_CUDA_TRY(cudaMemcpy(p->sub_pos, pos.data(), npix * sizeof(int), cudaMemcpyHostToDevice));
     ++p->sub_gen;
     p->n_subsets = n_subsets;
     // the table paths' grouped records now if the table exists, else on first use
@@ -476,6 +483,10 @@ caxsi_status caxsi_plan_set_option(caxsi_plan *p, int key, int value) {
     }
     if (key == CAXSI_OPT_SYMMETRY && (value == 0 || value == 1)) {
         p->no_symmetry = !value;
+        return CAXSI_OK;
+    }
+    if (key == CAXSI_OPT_SPARSE_SUBSETS && (value == 0 || value == 1)) {
+        p->no_sparse_subsets = !value;
         return CAXSI_OK;
     }
     if (key == CAXSI_OPT_GEMM_BANDS && (value == 0 || value == 1)) {

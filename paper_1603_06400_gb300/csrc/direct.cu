@@ -240,6 +240,11 @@ size_t adj_smem(const DevGeo &g) {
 
 }  // namespace
 
+cudaError_t launch_sum_list(const float *part, int nparts, int np, const int *list, float *g, cudaStream_t s) {
+    k_sum_list<<<(unsigned)ceil_div64(np, 256), 256, 0, s>>>(part, nparts, np, list, g);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sum_parts(const float *part, int nparts, int64_t stride, float *out,
                              int64_t n, cudaStream_t s) {
     k_sum_parts<<<(unsigned)ceil_div64(n, 256), 256, 0, s>>>(part, nparts, stride, out, n);

@@ -75,6 +75,7 @@ struct caxsi_plan {
     std::vector<int> sub_off;   // [n_subsets + 1] each subset's range in sub_pix (host)
     int *sub_pix;       // [M*N] the pixels grouped by subset, ascending within a subset (device)
     int *sub_of_pix;    // [M*N] subset of each pixel (device)
+    int *sub_pos;       // [M*N] position of each pixel in its subset's list (device)
     int sub_gen;        // incremented by every new partition
     float *b1_sub[4];   // [n_subsets][R*Q] A_p^T 1 per path, lazily
     std::vector<unsigned char> b1_sub_ok[4];   // which subsets of b1_sub are computed
@@ -99,6 +100,7 @@ struct caxsi_plan {
     int no_symmetry;          // 1: the table forward streams the ordinary records, not the mirror-symmetric ones
     int u_samples;            // table paths: 0 = the exact knots; N >= 2: N uniform samples of u (approximate)
     int no_bands;             // 1: the tcgen05 contractions multiply the zeros outside the band of S~ too
+    int no_sparse_subsets;    // 1: the FP32 subset operators use the whole-object contractions too
     KernelProfiler prof;
 };
 
@@ -110,6 +112,8 @@ caxsi_status direct_forward(caxsi_plan *p, const float *f, float *g, cudaStream_
 caxsi_status direct_adjoint(caxsi_plan *p, const float *w, float *f, cudaStream_t s);
 void direct_configure(caxsi_plan *p);
 caxsi_status direct_forward_static_scratch(caxsi_plan *p, const float *f, float *g, cudaStream_t s);
+// g[list[e]] = sum over the nparts compact partial images part[c * np + e], c ascending
+cudaError_t launch_sum_list(const float *part, int nparts, int np, const int *list, float *g, cudaStream_t s);
 // subset operators over the pixel lists of caxsi_plan_set_subsets
 caxsi_status direct_forward_subset(caxsi_plan *p, const float *f, float *g, int subset, cudaStream_t s);
 caxsi_status direct_adjoint_subset(caxsi_plan *p, const float *w, float *f, int subset, cudaStream_t s);

@@ -1206,6 +1206,144 @@ size_t adj_sym_smem(int npix, int Bp, int vc) {
            (size_t)ADJ_T * 20 + ADJ_W * 8 + 4 * (size_t)(vc + 1);
 }
 
+// ---- sparse subset operators (ordered subsets) -----------------------------------
+// A subset operator needs W = f S~^T (and V) only at the knots of its own pairs:
+// about 1/P of each voxel's records.  These kernels contract record by record on
+// the CUDA cores against the rows of S~ ([B][Q] FP32, L2-resident) instead of
+// running the whole-object contractions: one warp per voxel, lane l holding the
+// q bins 4l .. 4l + 3 (Q <= 128, Q % 4 == 0).  The pad records (zero weights)
+// are skipped.  Both are deterministic (fixed orders, no atomics).
+struct SubArgs {
+    int R, Q, P, subset, np;
+    const int64_t *off;        // records of (voxel v, subset s): [off[v P + s], off[v P + s + 1])
+    const uint32_t *key;       // pixel | t << 16
+    const float *w0, *w1;
+    const float *S;            // [B][Q]
+    const int *pos;            // [M*N] position of a pixel in its subset's list
+};
+
+__device__ __forceinline__ float warp_sum(float x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Forward: W at a record's two knots as dot products of the voxel's f row with
+// two rows of S~ (computed once per run of equal t, the upper one reused by the
+// next run when adjacent); each warp adds w0 W_t + w1 W_t+1 of its records into
+// its own compact image (np floats, by list position), and the block sums its
+// warps' images in warp order into its partial image part[blockIdx.x][np].
+__global__ void k_fwd_sub(SubArgs A, const float *__restrict__ f, float *__restrict__ part) {
+    extern __shared__ __align__(16) float img[];   // [warps][np]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    float *mine = img + (size_t)warp * A.np;
+    for (int e = lane; e < A.np; e += 32) mine[e] = 0.f;
+    __syncwarp();
+    const bool ql = 4 * lane < A.Q;
+    for (int v = blockIdx.x * nw + warp; v < A.R; v += gridDim.x * nw) {
+        const int64_t b = A.off[(int64_t)v * A.P + A.subset], e = A.off[(int64_t)v * A.P + A.subset + 1];
+        if (b == e) continue;   // warp-uniform
+        const float4 fq = ql ? *reinterpret_cast<const float4 *>(f + (int64_t)v * A.Q + 4 * lane)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+        auto dot_s = [&](int t) {
+            float x = 0.f;
+            if (ql) {
+                const float4 s = *reinterpret_cast<const float4 *>(A.S + (int64_t)t * A.Q + 4 * lane);
+                x = fmaf(fq.x, s.x, fmaf(fq.y, s.y, fmaf(fq.z, s.z, fq.w * s.w)));
+            }
+            return warp_sum(x);
+        };
+        int ct = -2;
+        float wt = 0.f, wt1 = 0.f;
+        for (int64_t r0 = b; r0 < e; r0 += 32) {
+            const int n = (int)min((int64_t)32, e - r0);
+            uint32_t k = 0u;
+            float a = 0.f, c = 0.f;
+            if (lane < n) {
+                k = A.key[r0 + lane];
+                a = A.w0[r0 + lane];
+                c = A.w1[r0 + lane];
+            }
+            float val = 0.f;
+            for (int j = 0; j < n; ++j) {
+                const int t = (int)(__shfl_sync(0xffffffffu, k, j) >> 16);
+                if (t != ct) {   // warp-uniform
+                    wt = t == ct + 1 ? wt1 : dot_s(t);
+                    wt1 = dot_s(t + 1);
+                    ct = t;
+                }
+                if (lane == j) val = fmaf(a, wt, c * wt1);
+            }
+            if (lane < n && a != 0.f) mine[A.pos[k & 0xffffu]] += val;   // distinct pixels within a voxel
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < A.np; e += blockDim.x) {
+        float s = 0.f;
+        for (int w = 0; w < nw; ++w) s += img[(size_t)w * A.np + e];
+        part[(int64_t)blockIdx.x * A.np + e] = s;
+    }
+}
+
+// Adjoint: per voxel, the records' coefficients w[pixel] w0 and w[pixel] w1 are
+// summed over each run of equal t; a run adds its lower sum times S~[t] and
+// leaves its upper sum pending for knot t + 1 (merged with the next run's lower
+// sum when that run is t + 1).  out[v][4l .. 4l + 3] = the lane's sums.
+__global__ void k_adj_sub(SubArgs A, const float *__restrict__ w, float *__restrict__ out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int v = blockIdx.x * nw + warp;
+    if (v >= A.R) return;   // warp-uniform
+    const bool ql = 4 * lane < A.Q;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto add_row = [&](int t, float c) {
+        if (ql && t >= 0 && c != 0.f) {
+            const float4 s = *reinterpret_cast<const float4 *>(A.S + (int64_t)t * A.Q + 4 * lane);
+            acc.x = fmaf(c, s.x, acc.x);
+            acc.y = fmaf(c, s.y, acc.y);
+            acc.z = fmaf(c, s.z, acc.z);
+            acc.w = fmaf(c, s.w, acc.w);
+        }
+    };
+    int pt = -1, ct = -1;
+    float pc = 0.f, c0 = 0.f, c1 = 0.f;
+    auto end_run = [&]() {   // run ct with sums (c0, c1)
+        if (ct < 0) return;
+        float lo = c0;
+        if (pt == ct) lo += pc;
+        else add_row(pt, pc);
+        add_row(ct, lo);
+        pt = ct + 1;
+        pc = c1;
+    };
+    const int64_t b = A.off[(int64_t)v * A.P + A.subset], e = A.off[(int64_t)v * A.P + A.subset + 1];
+    for (int64_t r0 = b; r0 < e; r0 += 32) {
+        const int n = (int)min((int64_t)32, e - r0);
+        uint32_t k = 0u;
+        float a = 0.f, c = 0.f;
+        if (lane < n) {
+            k = A.key[r0 + lane];
+            const float wv = w[k & 0xffffu];
+            a = wv * A.w0[r0 + lane];
+            c = wv * A.w1[r0 + lane];
+        }
+        for (int j = 0; j < n; ++j) {
+            const int t = (int)(__shfl_sync(0xffffffffu, k, j) >> 16);
+            const float aj = __shfl_sync(0xffffffffu, a, j), cj = __shfl_sync(0xffffffffu, c, j);
+            if (t != ct) {   // warp-uniform
+                end_run();
+                ct = t;
+                c0 = 0.f;
+                c1 = 0.f;
+            }
+            c0 += aj;
+            c1 += cj;
+        }
+    }
+    end_run();
+    add_row(pt, pc);
+    if (ql) *reinterpret_cast<float4 *>(out + (int64_t)v * A.Q + 4 * lane) = acc;
+}
+
 size_t fwd_sym_smem(int npix, int Bp) { return (size_t)((npix + 3) & ~3) * 4 + 4 * (size_t)Bp * 4 + 16; }
 
 size_t fwd_rec_smem(int npix, int Bp) {
@@ -1586,4 +1724,71 @@ cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, int subset,
     if (out_kind == 2)
         return launch_adj_rec(p, T, subset, w, reinterpret_cast<__half *>(T->v16), s);
     return launch_adj_rec(p, T, subset, w, T->tab, s);
+}
+
+// The sparse subset operators (k_fwd_sub / k_adj_sub) and when they pay: their
+// runs of equal t each wait for rows of S~ from L2, so they win only while a
+// subset has few records per voxel (measured at paper scale, 64 subsets, 125
+// records per voxel and subset: adjoint 0.24 ms, forward 0.52 ms, a pass 15%
+// faster than with the contractions; 8 subsets, 1 000 records: both several
+// times slower than the contractions).  max_per_voxel: the average records per
+// voxel and subset up to which the sparse form is used.  False also when they do not apply (q rows
+// over 128 or not whole float4s, unaligned arrays), and the caller contracts.
+bool sub_sparse_ok(const caxsi_plan *p, const void *a, const void *b, int max_per_voxel) {
+    const int Q = p->dg.Q;
+    const TablePath *T = p->table;
+    if (!(Q <= 128 && Q % 4 == 0 && T && T->sub.P > 0)) return false;
+    if (T->sub.n > (int64_t)max_per_voxel * p->dg.R * T->sub.P) return false;
+    return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0;
+}
+
+static SubArgs sub_args(const caxsi_plan *p, const TablePath *T, int subset) {
+    SubArgs a;
+    a.R = p->dg.R;
+    a.Q = p->dg.Q;
+    a.P = T->sub.P;
+    a.subset = subset;
+    a.np = p->sub_off[subset + 1] - p->sub_off[subset];
+    a.off = T->sub.off;
+    a.key = T->sub.key;
+    a.w0 = T->sub.w0;
+    a.w1 = T->sub.w1;
+    a.S = T->S;
+    a.pos = p->sub_pos;
+    return a;
+}
+
+cudaError_t sub_forward_sparse(const caxsi_plan *p, const TablePath *T, int subset, const float *f, float *g,
+                               cudaStream_t s, bool &done) {
+    done = false;
+    const SubArgs a = sub_args(p, T, subset);
+    const int64_t npix = (int64_t)p->dg.M * p->dg.N;
+    int warps = 8;
+    while (warps > 1 && (size_t)warps * a.np * 4 > (size_t)160 * 1024) warps /= 2;
+    if ((size_t)warps * a.np * 4 > (size_t)160 * 1024) return cudaSuccess;   // too large: not done
+    cudaError_t e = cudaMemsetAsync(g, 0, npix * sizeof(float), s);
+    if (e != cudaSuccess || a.np == 0) {
+        done = e == cudaSuccess;
+        return e;
+    }
+    // blocks: about 4 per SM, their partial images within the forward scratch
+    int blocks = (int)ceil_div64(a.R, warps);
+    if (blocks > 4 * p->num_sms) blocks = 4 * p->num_sms;
+    const int64_t cap = (int64_t)std::max(T->rec_chunks, T->fwd_chunks) * npix;
+    if ((int64_t)blocks * a.np > cap) blocks = (int)(cap / a.np);
+    const size_t smem = (size_t)warps * a.np * sizeof(float);
+    e = cudaFuncSetAttribute(k_fwd_sub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_fwd_sub<<<blocks, warps * 32, smem, s>>>(a, f, T->fwd_part);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_sum_list(T->fwd_part, blocks, a.np, p->sub_pix + p->sub_off[subset], g, s);
+    done = e == cudaSuccess;
+    return e;
+}
+
+cudaError_t sub_adjoint_sparse(const caxsi_plan *p, const TablePath *T, int subset, const float *w, float *f,
+                               cudaStream_t s) {
+    const SubArgs a = sub_args(p, T, subset);
+    k_adj_sub<<<(unsigned)ceil_div64(a.R, 8), 256, 0, s>>>(a, w, f);
+    return cudaGetLastError();
 }

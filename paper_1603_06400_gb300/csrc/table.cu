@@ -766,6 +766,13 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
         if (!T->use_records) return CAXSI_ERR_UNSUPPORTED;
         if ((st = table_set_subsets(p)) != CAXSI_OK) return st;
         if (subset >= T->sub.P) return CAXSI_ERR_UNSUPPORTED;
+        // FP32: W only at the subset's knots, per record, instead of the whole contraction
+        if (path == CAXSI_PATH_TABLE_FP32 && !p->no_sparse_subsets && sub_sparse_ok(p, f, g_out, 160)) {
+            bool done = false;
+            CAXSI_PROF(p, "sub_fwd_sparse", s);
+            CAXSI_CUDA_TRY(sub_forward_sparse(p, T, subset, f, g_out, s, done));
+            if (done) return CAXSI_OK;
+        }
     }
     const DevGeo &d = p->dg;
     const float one = 1.f, zero = 0.f;
@@ -852,6 +859,12 @@ caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path
         if (!T->use_records) return CAXSI_ERR_UNSUPPORTED;
         if ((st = table_set_subsets(p)) != CAXSI_OK) return st;
         if (subset >= T->sub.P) return CAXSI_ERR_UNSUPPORTED;
+        // FP32: V only at the subset's knots, contracted per record
+        if (path == CAXSI_PATH_TABLE_FP32 && !p->no_sparse_subsets && sub_sparse_ok(p, w, f_out, 256)) {
+            CAXSI_PROF(p, "sub_adj_sparse", s);
+            CAXSI_CUDA_TRY(sub_adjoint_sparse(p, T, subset, w, f_out, s));
+            return CAXSI_OK;
+        }
     }
     const DevGeo &d = p->dg;
     const int out_kind = path == CAXSI_PATH_TABLE_FP32 ? 0 : (path == CAXSI_PATH_TABLE_BF16 ? 1 : 2);

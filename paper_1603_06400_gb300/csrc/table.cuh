@@ -167,6 +167,16 @@ cudaError_t sym_forward(const caxsi_plan *p, const TablePath *T, float *part, cu
 // out_kind as for records_adjoint
 cudaError_t sym_adjoint(const caxsi_plan *p, const TablePath *T, const float *w, int out_kind, cudaStream_t s);
 cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, int subset, float *part, cudaStream_t s);
+// Sparse subset operators (FP32, per-record contractions against the rows of S~);
+// sub_sparse_ok says whether they apply to these arrays and pay at this density
+// (average records per voxel and subset up to max_per_voxel); the forward sets
+// done = false (and does nothing) when the subset's image does not fit shared
+// memory.
+bool sub_sparse_ok(const caxsi_plan *p, const void *a, const void *b, int max_per_voxel);
+cudaError_t sub_forward_sparse(const caxsi_plan *p, const TablePath *T, int subset, const float *f, float *g,
+                               cudaStream_t s, bool &done);
+cudaError_t sub_adjoint_sparse(const caxsi_plan *p, const TablePath *T, int subset, const float *w, float *f,
+                               cudaStream_t s);
 // out_kind: 0 = FP32 rows in tab, 1 = bf16 rows in v16, 2 = fp16 rows in v16
 cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, int subset, const float *w,
                             int out_kind, cudaStream_t s);

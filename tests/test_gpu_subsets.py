@@ -226,3 +226,35 @@ def test_paper_scale_subsets_sampled(cx):
         assert rel_l2(fp[vox], oracle.adjoint_voxels(g, phi, mask, wm, vox)) <= REL_L2_TOL
     assert plan.info()["device_error"] == 0
     plan.close()
+
+
+@pytest.mark.parametrize("name", sorted(GEOMS))
+def test_sparse_subset_operators_equal_the_contracted_ones(cx, name):
+    """The FP32 subset operators contracted per record at the subset's knots
+    (default) against the whole-object contractions (CAXSI_OPT_SPARSE_SUBSETS 0),
+    for every subset of each partition, and the sensitivities b1_p.  The
+    16-subset partition is sparse enough for both sparse operators to be used."""
+    caxsi, torch = cx
+    g = GEOMS[name]()
+    phi = synth.tungsten_spectrum(g)
+    mask = synth.random_mask(g, 51)
+    plan = caxsi.Plan(g, phi, mask)
+    P = caxsi.PATHS["table_fp32"]
+    f = _t(torch, synth.phantom(g, 5, n_ellipses=3) + 0.05 * synth.uniform_random((g.X, g.J, g.Q), 52))
+    w = _t(torch, synth.uniform_random((g.M, g.N), 53) + 0.1)
+    ones = torch.ones((g.M, g.N), device="cuda:0")
+    parts = list(_partitions(caxsi, g).values())
+    parts.append(np.minimum((synth.uniform_random((g.M * g.N,), 54) * 16).astype(np.int32), 15))
+    for part in parts:
+        plan.set_subsets(part)
+        for s in range(plan.n_subsets):
+            out = []
+            for sparse in (True, False):
+                plan.set_sparse_subsets(sparse)
+                out.append((plan.forward_subset(s, f, path=P).cpu().numpy(),
+                            plan.adjoint_subset(s, w, path=P).cpu().numpy(),
+                            plan.adjoint_subset(s, ones, path=P).cpu().numpy()))
+            for a, b in zip(*out):
+                assert rel_l2(a, b) <= 1e-6
+    assert plan.info()["device_error"] == 0
+    plan.close()
