@@ -1228,10 +1228,12 @@ __device__ __forceinline__ float warp_sum(float x) {
 }
 
 // Forward: W at a record's two knots as dot products of the voxel's f row with
-// two rows of S~ (computed once per run of equal t, the upper one reused by the
-// next run when adjacent); each warp adds w0 W_t + w1 W_t+1 of its records into
-// its own compact image (np floats, by list position), and the block sums its
-// warps' images in warp order into its partial image part[blockIdx.x][np].
+// two rows of S~, once per run of equal t; the runs of a batch of 32 records are
+// found with a ballot and taken four at a time, their eight rows loaded before
+// any is reduced (the loads, not the arithmetic, set the pace).  Each warp adds
+// w0 W_t + w1 W_t+1 of its records into its own compact image (np floats, by
+// list position), and the block sums its warps' images in warp order into its
+// partial image part[blockIdx.x][np].
 __global__ void k_fwd_sub(SubArgs A, const float *__restrict__ f, float *__restrict__ part) {
     extern __shared__ __align__(16) float img[];   // [warps][np]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -1244,16 +1246,13 @@ __global__ void k_fwd_sub(SubArgs A, const float *__restrict__ f, float *__restr
         if (b == e) continue;   // warp-uniform
         const float4 fq = ql ? *reinterpret_cast<const float4 *>(f + (int64_t)v * A.Q + 4 * lane)
                              : make_float4(0.f, 0.f, 0.f, 0.f);
-        auto dot_s = [&](int t) {
-            float x = 0.f;
-            if (ql) {
-                const float4 s = *reinterpret_cast<const float4 *>(A.S + (int64_t)t * A.Q + 4 * lane);
-                x = fmaf(fq.x, s.x, fmaf(fq.y, s.y, fmaf(fq.z, s.z, fq.w * s.w)));
-            }
-            return warp_sum(x);
+        auto row = [&](int t) {
+            return ql ? *reinterpret_cast<const float4 *>(A.S + (int64_t)t * A.Q + 4 * lane)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
         };
-        int ct = -2;
-        float wt = 0.f, wt1 = 0.f;
+        auto dot = [&](float4 s) { return warp_sum(fmaf(fq.x, s.x, fmaf(fq.y, s.y, fmaf(fq.z, s.z, fq.w * s.w)))); };
+        int ct = -2;                // the run in progress at the end of the previous batch
+        float wt = 0.f, wt1 = 0.f;  // its W at t and t + 1
         for (int64_t r0 = b; r0 < e; r0 += 32) {
             const int n = (int)min((int64_t)32, e - r0);
             uint32_t k = 0u;
@@ -1263,15 +1262,37 @@ __global__ void k_fwd_sub(SubArgs A, const float *__restrict__ f, float *__restr
                 a = A.w0[r0 + lane];
                 c = A.w1[r0 + lane];
             }
-            float val = 0.f;
-            for (int j = 0; j < n; ++j) {
-                const int t = (int)(__shfl_sync(0xffffffffu, k, j) >> 16);
-                if (t != ct) {   // warp-uniform
-                    wt = t == ct + 1 ? wt1 : dot_s(t);
-                    wt1 = dot_s(t + 1);
-                    ct = t;
+            // the batch's runs of equal t: a lane's run starts at the last run start at or
+            // before it (none: the run continued from the previous batch)
+            const int tl = (int)(k >> 16);
+            const int tprev = __shfl_up_sync(0xffffffffu, tl, 1);
+            unsigned starts = __ballot_sync(0xffffffffu, lane < n && (lane == 0 ? tl != ct : tl != tprev));
+            const unsigned upto = starts & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u));
+            const int my_start = upto ? 31 - __clz(upto) : -1;
+            float val = fmaf(a, wt, c * wt1);   // for a run continued from the previous batch
+            // the runs four at a time: their eight rows of S~ are loaded before any is reduced
+            while (starts) {
+                int js[4], ts[4], cnt = 0;
+                for (; cnt < 4 && starts; ++cnt) {
+                    js[cnt] = __ffs(starts) - 1;
+                    starts &= starts - 1u;
+                    ts[cnt] = __shfl_sync(0xffffffffu, tl, js[cnt]);
                 }
-                if (lane == j) val = fmaf(a, wt, c * wt1);
+                float4 s0[4], s1[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q < cnt) {
+                        s0[q] = row(ts[q]);
+                        s1[q] = row(ts[q] + 1);
+                    }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q < cnt) {
+                        wt = dot(s0[q]);
+                        wt1 = dot(s1[q]);
+                        ct = ts[q];
+                        if (my_start == js[q]) val = fmaf(a, wt, c * wt1);
+                    }
             }
             if (lane < n && a != 0.f) mine[A.pos[k & 0xffffu]] += val;   // distinct pixels within a voxel
             __syncwarp();
@@ -1729,10 +1750,10 @@ cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, int subset,
 // The sparse subset operators (k_fwd_sub / k_adj_sub) and when they pay: their
 // runs of equal t each wait for rows of S~ from L2, so they win only while a
 // subset has few records per voxel (measured at paper scale, 64 subsets, 125
-// records per voxel and subset: adjoint 0.24 ms, forward 0.52 ms, a pass 15%
-// faster than with the contractions; 8 subsets, 1 000 records: both several
-// times slower than the contractions).  max_per_voxel: the average records per
-// voxel and subset up to which the sparse form is used.  False also when they do not apply (q rows
+// records per voxel and subset: adjoint 0.24 ms, forward 0.29 ms, against about
+// 0.55 ms each with the contractions; 8 subsets, 1 000 records: several times
+// slower than the contractions).  max_per_voxel: the average records per voxel
+// and subset up to which the sparse form is used.  False also when they do not apply (q rows
 // over 128 or not whole float4s, unaligned arrays), and the caller contracts.
 bool sub_sparse_ok(const caxsi_plan *p, const void *a, const void *b, int max_per_voxel) {
     const int Q = p->dg.Q;
