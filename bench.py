@@ -17,7 +17,7 @@ phantoms and run without any data-path collective (weak scaling).
 Reconstruction experiment (the "recon" key, rank 0): the wall time of the
 plain FP32 iterations to a fixed NMSE, and the time of each alternative to
 reach the same NMSE: bf16 / fp16 table paths, a 2048-sample u table (FP32 and
-bf16), ordered subsets (8 and 64 subsets, with the FP32 table operators and
+bf16), ordered subsets (8, 64 and 128 subsets, with the FP32 table operators and
 with the direct ones, whose subset operators cost ~1/P of a full one), and the
 learned warm start (a U-Net
 trained here for --unet-steps objects, its training time reported apart).  The
@@ -397,7 +397,7 @@ def recon_experiment(caxsi, plan, g, dev, phantom, iters=100, max_iters=300, une
     # operator evaluates only its pixels' pairs (cost ~ 1/P of a full one); on
     # the FP32 table path it still pays the whole-object q contractions.
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for rho_z, sigma_y, max_passes in ((8, 2, 30), (8, 16, 12)):
+    for rho_z, sigma_y, max_passes in ((8, 2, 30), (8, 16, 12), (16, 16, 12)):
         plan.set_subsets(caxsi.os_partition(g.M, g.N, g.rho_y, rho_z, sigma_y))
         n_sub = plan.n_subsets
         for path, tag in (("table_fp32", ""), ("direct", "_direct")):
