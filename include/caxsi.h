@@ -174,9 +174,9 @@ caxsi_status caxsi_recon_step(caxsi_plan *plan, const float *y_dev, const float 
  * records grouped by subset if the plan's tables exist already; otherwise the
  * first table-path subset call builds them (that call then synchronises).
  * Errors: INVALID (sizes, an index out of range, n_subsets outside
- * [1, min(CAXSI_MAX_SUBSETS, M*N)]), UNSUPPORTED (the table paths' subset
- * calls, when the geometry has no pair records: more than 65536 pixels or
- * knots), CUDA, OOM. */
+ * [1, min(CAXSI_MAX_SUBSETS, M*N)]), CUDA, OOM.  Where the geometry has no pair
+ * records (more than 65536 pixels or knots) the partition still serves the
+ * direct path, and the table paths' subset calls return UNSUPPORTED. */
 caxsi_status caxsi_plan_set_subsets(caxsi_plan *plan, int n_subsets, const int32_t *subset_of_pixel);
 
 /* g = A_p f: g_dev (M*N, device) holds the subset's pixels of A f and 0 at every

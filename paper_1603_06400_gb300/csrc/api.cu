@@ -284,8 +284,11 @@ caxsi_status caxsi_plan_set_subsets(caxsi_plan *p, int n_subsets, const int32_t 
     CAXSI_CUDA_TRY(cudaMemcpy(p->sub_pos, pos.data(), npix * sizeof(int), cudaMemcpyHostToDevice));
     ++p->sub_gen;
     p->n_subsets = n_subsets;
-    // the table paths' grouped records now if the table exists, else on first use
+    // the table paths' grouped records now if the table exists, else on first use;
+    // a geometry without pair records keeps the partition for the direct path (its
+    // table-path subset calls then return UNSUPPORTED)
     caxsi_status st = p->table ? table_set_subsets(p) : CAXSI_OK;
+    if (st == CAXSI_ERR_UNSUPPORTED) st = CAXSI_OK;
     if (st != CAXSI_OK) p->n_subsets = 0;
     return st;
 }

@@ -299,6 +299,18 @@ def test_large_detector_uses_on_the_fly_table_kernels(cx):
     with pytest.raises(caxsi.CaxsiError) as e:     # the 16-bit paths need the records
         plan.forward(_t(torch, f), path=caxsi.PATHS["table_bf16"])
     assert e.value.status == 6
+    # a partition still serves the direct path; the table paths' subset calls refuse
+    sub = caxsi.os_partition(g.M, g.N, g.rho_y, 2, 4)
+    plan.set_subsets(sub)
+    inside = (sub == 3).reshape(g.M, g.N)
+    gs = plan.forward_subset(3, _t(torch, f), path=caxsi.PATHS["direct"]).cpu().numpy()
+    assert np.all(gs[~inside] == 0.0)
+    assert rel_l2(gs[inside], oracle.forward(g, phi, mask, _f32(f))[inside]) <= REL_L2_TOL
+    fs = plan.adjoint_subset(3, _t(torch, w), path=caxsi.PATHS["direct"]).cpu().numpy()
+    assert rel_l2(fs, oracle.adjoint(g, phi, mask, np.where(inside, _f32(w), 0.0))) <= REL_L2_TOL
+    with pytest.raises(caxsi.CaxsiError) as e:
+        plan.forward_subset(3, _t(torch, f), path=p)
+    assert e.value.status == 6
     assert plan.info()["device_error"] == 0
     plan.close()
 
