@@ -162,17 +162,21 @@ caxsi_status caxsi_recon_step(caxsi_plan *plan, const float *y_dev, const float 
  * here (the Python binding builds the paper's one).  CAXSI_PATH_DIRECT
  * evaluates only the pairs of the subset's pixels, so a subset operator costs
  * about 1/P of the full one (the point of the algorithm).  The table paths
- * stream only the subset's pair records (records grouped by subset), but their
- * q contractions stay whole-object, so a subset operator there costs most of a
- * full one.
+ * stream only the subset's pair records (records grouped by subset).  In FP32,
+ * when the subsets average at most a few hundred records per voxel and Q is a
+ * multiple of 4 up to 128, each record is contracted with its two rows of the
+ * spectral matrix directly, so a subset operator costs about 1/P of a full one
+ * there too; otherwise (the 16-bit paths, denser subsets) the q contractions
+ * stay whole-object and a subset operator costs most of a full one.
  */
 #define CAXSI_MAX_SUBSETS 1024
 
 /* Set (or replace) the partition.  subset_of_pixel: host, M*N int32 in
- * [0, n_subsets), row-major (m, n).  Uploads the subsets' pixel lists, drops
- * the cached subset sensitivities and (synchronously) builds the table paths'
- * records grouped by subset if the plan's tables exist already; otherwise the
- * first table-path subset call builds them (that call then synchronises).
+ * [0, n_subsets), row-major (m, n).  Synchronises the device first (work in
+ * flight may still read the old partition), uploads the subsets' pixel lists,
+ * drops the cached subset sensitivities and builds the table paths' records
+ * grouped by subset if the plan's tables exist already; otherwise the first
+ * table-path subset call builds them (that call then synchronises).
  * Errors: INVALID (sizes, an index out of range, n_subsets outside
  * [1, min(CAXSI_MAX_SUBSETS, M*N)]), CUDA, OOM.  Where the geometry has no pair
  * records (more than 65536 pixels or knots) the partition still serves the

@@ -229,10 +229,16 @@ caxsi_status caxsi_recon_step(caxsi_plan *p, const float *y_dev, const float *r_
     const int64_t nf = (int64_t)p->dg.R * p->dg.Q;
     caxsi_status st;
     if (!p->b1[path]) {
-        CAXSI_CUDA_TRY(cudaMalloc(&p->b1[path], nf * sizeof(float)));
+        // b1 = A^T 1, cached only once it has been computed
+        float *b1 = nullptr;
+        CAXSI_CUDA_TRY(cudaMalloc(&b1, nf * sizeof(float)));
+        if ((st = run_adjoint(p, p->ones, b1, path, s)) != CAXSI_OK) {
+            cudaStreamSynchronize(s);
+            cudaFree(b1);
+            return st;
+        }
+        p->b1[path] = b1;
         p->table_bytes += nf * 4;
-        st = run_adjoint(p, p->ones, p->b1[path], path, s);
-        if (st != CAXSI_OK) return st;
     }
     // z = A f + r, ratio = y / z, L(f) in FP64
     if ((st = run_forward(p, f_dev, p->gtmp, path, s)) != CAXSI_OK) return st;
@@ -258,6 +264,8 @@ caxsi_status caxsi_plan_set_subsets(caxsi_plan *p, int n_subsets, const int32_t 
         if (subset_of_pixel[k] < 0 || subset_of_pixel[k] >= n_subsets) return CAXSI_ERR_INVALID;
     DeviceGuard dg(p->device);
     if (!dg.ok) return CAXSI_ERR_CUDA;
+    // subset calls in flight on any stream may still read the lists and records
+    CAXSI_CUDA_TRY(cudaDeviceSynchronize());
     p->n_subsets = 0;
     drop_subset_sensitivities(p);
     // the partition and its pixel lists (counting sort of the pixels by subset)
