@@ -282,11 +282,9 @@ caxsi_status caxsi_plan_set_subsets(caxsi_plan *p, int n_subsets, const int32_t 
             pix[fill[s]++] = (int)k;
         }
     }
-    if (!p->sub_pix) {
-        CAXSI_CUDA_TRY(cudaMalloc(&p->sub_pix, npix * sizeof(int)));
-        CAXSI_CUDA_TRY(cudaMalloc(&p->sub_of_pix, npix * sizeof(int)));
-        CAXSI_CUDA_TRY(cudaMalloc(&p->sub_pos, npix * sizeof(int)));
-    }
+    if (!p->sub_pix) CAXSI_CUDA_TRY(cudaMalloc(&p->sub_pix, npix * sizeof(int)));
+    if (!p->sub_of_pix) CAXSI_CUDA_TRY(cudaMalloc(&p->sub_of_pix, npix * sizeof(int)));
+    if (!p->sub_pos) CAXSI_CUDA_TRY(cudaMalloc(&p->sub_pos, npix * sizeof(int)));
     CAXSI_CUDA_TRY(cudaMemcpy(p->sub_pix, pix.data(), npix * sizeof(int), cudaMemcpyHostToDevice));
     CAXSI_CUDA_TRY(cudaMemcpy(p->sub_of_pix, subset_of_pixel, npix * sizeof(int), cudaMemcpyHostToDevice));
     CAXSI_CUDA_TRY(cudaMemcpy(p->sub_pos, pos.data(), npix * sizeof(int), cudaMemcpyHostToDevice));
@@ -432,8 +430,11 @@ static caxsi_status host_call(caxsi_plan *p, const float *in_host, int64_t in_le
     const int64_t big = nf > ng ? nf : ng;
     if (!p->stage_in) {
         CAXSI_CUDA_TRY(cudaMalloc(&p->stage_in, big * sizeof(float)));
+        p->table_bytes += big * 4;
+    }
+    if (!p->stage_out) {
         CAXSI_CUDA_TRY(cudaMalloc(&p->stage_out, big * sizeof(float)));
-        p->table_bytes += 2 * big * 4;
+        p->table_bytes += big * 4;
     }
     p->launches = 0;
     cudaStream_t s = 0;

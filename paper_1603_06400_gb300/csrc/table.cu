@@ -545,7 +545,6 @@ __global__ void k_transpose_S(const float *__restrict__ S, int B, int Q, int Bp,
 
 // cuBLAS handle, workspace and 16-bit operand copies (first table call).
 caxsi_status blas_setup(caxsi_plan *p, TablePath *T) {
-    if (T->blas) return CAXSI_OK;
     const DevGeo &d = p->dg;
     if (cublasCreate(&T->blas) != CUBLAS_STATUS_SUCCESS) {
         T->blas = nullptr;
@@ -675,6 +674,9 @@ caxsi_status batch_layout(caxsi_plan *p, TablePath *T, int nb, const int32_t *ra
     if (bs.nb == nb && bs.ranges.size() == (size_t)(2 * nb) &&
         std::equal(bs.ranges.begin(), bs.ranges.end(), ranges))
         return CAXSI_OK;
+    // forget the old layout first: a failure below leaves no layout to reuse
+    bs.nb = 0;
+    bs.ranges.clear();
     std::vector<int4> items;
     std::vector<int2> oi(nb);
     std::vector<int64_t> rowmap;
@@ -737,12 +739,18 @@ caxsi_status batch_layout(caxsi_plan *p, TablePath *T, int nb, const int32_t *ra
 caxsi_status ensure_table(caxsi_plan *p, int path) {
     if (path < CAXSI_PATH_TABLE_FP32 || path > CAXSI_PATH_TABLE_FP16) return CAXSI_ERR_UNSUPPORTED;
     if (!p->table) {
+        // all or nothing: a table that failed half way is dropped, and the next call
+        // builds it again
+        const int64_t bytes0 = p->table_bytes;
         caxsi_status st = build_table(p);
-        if (st != CAXSI_OK) return st;
-    }
-    if (!p->table->blas) {
-        caxsi_status st = blas_setup(p, p->table);
-        if (st != CAXSI_OK) return st;
+        if (st == CAXSI_OK) st = blas_setup(p, p->table);
+        if (st != CAXSI_OK) {
+            cudaDeviceSynchronize();
+            free_table(p->table);
+            p->table = nullptr;
+            p->table_bytes = bytes0;
+            return st;
+        }
     }
     // the 16-bit paths take their adjoint rows from the record kernel
     if (path != CAXSI_PATH_TABLE_FP32 && !p->table->use_records) return CAXSI_ERR_UNSUPPORTED;
