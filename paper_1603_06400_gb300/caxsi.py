@@ -152,13 +152,6 @@ def _check(status: int, where: str):
         raise CaxsiError(status, where)
 
 
-def _stream_handle(stream):
-    import torch
-    if stream is None:
-        stream = torch.cuda.current_stream()
-    return ctypes.c_void_p(stream.cuda_stream)
-
-
 def _dev(t, n, name):
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
@@ -215,34 +208,48 @@ class Plan:
             mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.byref(h)),
             "caxsi_plan_create")
         self.handle = h
+        import torch
+        self.device = torch.cuda.current_device()   # the library builds the plan there
+
+    def _dev(self, t, n, name):
+        ptr = _dev(t, n, name)
+        if t.device.index != self.device:
+            raise ValueError(f"{name} is on {t.device}, the plan on cuda:{self.device}")
+        return ptr
+
+    def _stream(self, stream):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        return ctypes.c_void_p(stream.cuda_stream)
 
     # -- device-pointer calls -------------------------------------------------
     def forward(self, f, out=None, path=PATH_DIRECT, stream=None):
         import torch
         if out is None:
             out = torch.empty((self.M, self.N), device=f.device, dtype=torch.float32)
-        _check(self.lib.caxsi_forward(self.handle, _dev(f, self.f_len, "f"), self.f_len,
-                                      _dev(out, self.g_len, "g"), self.g_len, int(path),
-                                      _stream_handle(stream)), "caxsi_forward")
+        _check(self.lib.caxsi_forward(self.handle, self._dev(f, self.f_len, "f"), self.f_len,
+                                      self._dev(out, self.g_len, "g"), self.g_len, int(path),
+                                      self._stream(stream)), "caxsi_forward")
         return out
 
     def adjoint(self, w, out=None, path=PATH_DIRECT, stream=None):
         import torch
         if out is None:
             out = torch.empty((self.X, self.J, self.Q), device=w.device, dtype=torch.float32)
-        _check(self.lib.caxsi_adjoint(self.handle, _dev(w, self.g_len, "w"), self.g_len,
-                                      _dev(out, self.f_len, "f"), self.f_len, int(path),
-                                      _stream_handle(stream)), "caxsi_adjoint")
+        _check(self.lib.caxsi_adjoint(self.handle, self._dev(w, self.g_len, "w"), self.g_len,
+                                      self._dev(out, self.f_len, "f"), self.f_len, int(path),
+                                      self._stream(stream)), "caxsi_adjoint")
         return out
 
     def recon_step(self, y, f, r=None, beta=0.0, delta=0.0, path=PATH_DIRECT,
                    want_nll=False, stream=None):
         nll = ctypes.c_double(0.0)
-        rp = _dev(r, self.g_len, "r") if r is not None else ctypes.c_void_p(None)
+        rp = self._dev(r, self.g_len, "r") if r is not None else ctypes.c_void_p(None)
         _check(self.lib.caxsi_recon_step(
-            self.handle, _dev(y, self.g_len, "y"), rp, _dev(f, self.f_len, "f"), self.f_len,
+            self.handle, self._dev(y, self.g_len, "y"), rp, self._dev(f, self.f_len, "f"), self.f_len,
             float(beta), float(delta), int(path),
-            ctypes.byref(nll) if want_nll else None, _stream_handle(stream)), "caxsi_recon_step")
+            ctypes.byref(nll) if want_nll else None, self._stream(stream)), "caxsi_recon_step")
         return nll.value if want_nll else None
 
     # -- ordered subsets (Sec. VI, Algorithm 5) --------------------------------
@@ -260,28 +267,28 @@ class Plan:
         import torch
         if out is None:
             out = torch.empty((self.M, self.N), device=f.device, dtype=torch.float32)
-        _check(self.lib.caxsi_forward_subset(self.handle, int(subset), _dev(f, self.f_len, "f"), self.f_len,
-                                             _dev(out, self.g_len, "g"), self.g_len, int(path),
-                                             _stream_handle(stream)), "caxsi_forward_subset")
+        _check(self.lib.caxsi_forward_subset(self.handle, int(subset), self._dev(f, self.f_len, "f"), self.f_len,
+                                             self._dev(out, self.g_len, "g"), self.g_len, int(path),
+                                             self._stream(stream)), "caxsi_forward_subset")
         return out
 
     def adjoint_subset(self, subset, w, out=None, path=PATH_TABLE_FP32, stream=None):
         import torch
         if out is None:
             out = torch.empty((self.X, self.J, self.Q), device=w.device, dtype=torch.float32)
-        _check(self.lib.caxsi_adjoint_subset(self.handle, int(subset), _dev(w, self.g_len, "w"), self.g_len,
-                                             _dev(out, self.f_len, "f"), self.f_len, int(path),
-                                             _stream_handle(stream)), "caxsi_adjoint_subset")
+        _check(self.lib.caxsi_adjoint_subset(self.handle, int(subset), self._dev(w, self.g_len, "w"), self.g_len,
+                                             self._dev(out, self.f_len, "f"), self.f_len, int(path),
+                                             self._stream(stream)), "caxsi_adjoint_subset")
         return out
 
     def recon_step_subset(self, subset, y, f, r=None, beta=0.0, delta=0.0, path=PATH_TABLE_FP32,
                           want_nll=False, stream=None):
         nll = ctypes.c_double(0.0)
-        rp = _dev(r, self.g_len, "r") if r is not None else ctypes.c_void_p(None)
+        rp = self._dev(r, self.g_len, "r") if r is not None else ctypes.c_void_p(None)
         _check(self.lib.caxsi_recon_step_subset(
-            self.handle, int(subset), _dev(y, self.g_len, "y"), rp, _dev(f, self.f_len, "f"), self.f_len,
+            self.handle, int(subset), self._dev(y, self.g_len, "y"), rp, self._dev(f, self.f_len, "f"), self.f_len,
             float(beta), float(delta), int(path), ctypes.byref(nll) if want_nll else None,
-            _stream_handle(stream)), "caxsi_recon_step_subset")
+            self._stream(stream)), "caxsi_recon_step_subset")
         return nll.value if want_nll else None
 
     def os_pass(self, y, f, r=None, beta=0.0, delta=0.0, path=PATH_TABLE_FP32, stream=None):
@@ -311,9 +318,9 @@ class Plan:
         if out is None:
             out = torch.empty((nb, self.M, self.N), device=f.device, dtype=torch.float32)
         _check(self.lib.caxsi_forward_batch(self.handle, nb, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                            _dev(f, nb * self.f_len, "f"), nb * self.f_len,
-                                            _dev(out, nb * self.g_len, "g"), nb * self.g_len, int(path),
-                                            _stream_handle(stream)), "caxsi_forward_batch")
+                                            self._dev(f, nb * self.f_len, "f"), nb * self.f_len,
+                                            self._dev(out, nb * self.g_len, "g"), nb * self.g_len, int(path),
+                                            self._stream(stream)), "caxsi_forward_batch")
         return out
 
     def adjoint_batch(self, w, ranges=None, out=None, path=PATH_TABLE_FP32, stream=None):
@@ -324,9 +331,9 @@ class Plan:
         if out is None:
             out = torch.empty((nb, self.X, self.J, self.Q), device=w.device, dtype=torch.float32)
         _check(self.lib.caxsi_adjoint_batch(self.handle, nb, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                            _dev(w, nb * self.g_len, "w"), nb * self.g_len,
-                                            _dev(out, nb * self.f_len, "f"), nb * self.f_len, int(path),
-                                            _stream_handle(stream)), "caxsi_adjoint_batch")
+                                            self._dev(w, nb * self.g_len, "w"), nb * self.g_len,
+                                            self._dev(out, nb * self.f_len, "f"), nb * self.f_len, int(path),
+                                            self._stream(stream)), "caxsi_adjoint_batch")
         return out
 
     # -- the update step and its reverse mode -------------------------------------
@@ -335,19 +342,19 @@ class Plan:
         n = f.numel()
         if out is None:
             out = torch.empty_like(f)
-        _check(self.lib.caxsi_em_update(self.handle, _dev(f, n, "f"), _dev(b1, n, "b1"), _dev(b2, n, "b2"),
-                                        float(beta), float(delta), _dev(out, n, "out"), n,
-                                        _stream_handle(stream)), "caxsi_em_update")
+        _check(self.lib.caxsi_em_update(self.handle, self._dev(f, n, "f"), self._dev(b1, n, "b1"), self._dev(b2, n, "b2"),
+                                        float(beta), float(delta), self._dev(out, n, "out"), n,
+                                        self._stream(stream)), "caxsi_em_update")
         return out
 
     def em_update_vjp(self, f, b1, b2, grad_out, beta=0.0, delta=0.0, stream=None):
         import torch
         n = f.numel()
         gf, gb2 = torch.empty_like(f), torch.empty_like(f)
-        _check(self.lib.caxsi_em_update_vjp(self.handle, _dev(f, n, "f"), _dev(b1, n, "b1"), _dev(b2, n, "b2"),
-                                            float(beta), float(delta), _dev(grad_out, n, "grad_out"),
-                                            _dev(gf, n, "grad_f"), _dev(gb2, n, "grad_b2"), n,
-                                            _stream_handle(stream)), "caxsi_em_update_vjp")
+        _check(self.lib.caxsi_em_update_vjp(self.handle, self._dev(f, n, "f"), self._dev(b1, n, "b1"), self._dev(b2, n, "b2"),
+                                            float(beta), float(delta), self._dev(grad_out, n, "grad_out"),
+                                            self._dev(gf, n, "grad_f"), self._dev(gb2, n, "grad_b2"), n,
+                                            self._stream(stream)), "caxsi_em_update_vjp")
         return gf, gb2
 
     # -- host-buffer calls ----------------------------------------------------
