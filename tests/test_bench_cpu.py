@@ -1,0 +1,102 @@
+"""Roofline bookkeeping of bench.py on CPU: the algorithmic work per launch that
+the bench divides by each kernel's measured time, checked against the counts it
+is made of at the paper-scale workload (object 128 x 256 voxels x 128 q bins,
+detector 64 x 256 pixels, 8258 knots, 152 SMs), and the rule that a DRAM
+traffic figure is dropped once the kernel's source has changed."""
+import os
+import shutil
+
+import pytest
+
+import bench
+import synth
+
+NSM = 152
+B = 8258            # knots of the paper-scale workload
+BP = 8264           # rows padded to a multiple of 8, one spare knot included
+N_REC = 263_508_210     # plain pair records (12 B each)
+N_SYM = 124_970_898     # mirror-symmetric adjoint records (12 B each)
+
+
+@pytest.fixture(scope="module")
+def paper():
+    g = synth.paper_geometry()
+    info = {"n_open_pairs": 0, "n_breakpoints": B, "n_records": N_REC, "n_sym_records": N_SYM}
+    return g, info
+
+
+def test_record_kernels_bytes(paper):
+    g, info = paper
+    R, npix = g.X * g.J, g.M * g.N
+    assert (R, npix) == (32768, 16384)
+    pairs = g.X * (g.J // 2)                       # voxel pairs (j, J-1-j)
+    quad = (g.M // 2) * (g.N // 2)                 # pixels of one detector quadrant
+    unit, fwd, bound = bench.kernel_work("sym_pairs_fwd", g, info, "table_fp32", NSM)
+    assert (unit, bound) == ("GB/s", "hbm")
+    # 21-byte record per (voxel pair, quadrant pixel), W rows, one partial image per SM
+    assert fwd == 21 * pairs * quad + 4 * R * BP + 4 * NSM * npix
+    assert fwd == pytest.approx(2.502e9, rel=1e-3)
+    _, adj, _ = bench.kernel_work("sym_pairs_adj", g, info, "table_fp32", NSM)
+    assert adj == 12 * N_SYM + 4 * R * B + 4 * NSM * npix
+    assert adj == pytest.approx(2.592e9, rel=1e-3)
+    # the 16-bit paths write 2-byte V rows
+    _, adj16, _ = bench.kernel_work("sym_pairs_adj", g, info, "table_bf16", NSM)
+    assert adj - adj16 == 2 * R * B
+    # plain records: 12 B each, one block per two SMs' worth of voxel chunks
+    _, rf, _ = bench.kernel_work("rec_pairs_fwd", g, info, "table_fp32", NSM)
+    _, ra, _ = bench.kernel_work("rec_pairs_adj", g, info, "table_fp32", NSM)
+    assert rf == 12 * N_REC + 4 * R * BP + 4 * 2 * NSM * npix
+    assert ra == 12 * N_REC + 4 * R * B + 4 * 2 * NSM * npix
+
+
+def test_contraction_work(paper):
+    g, info = paper
+    R = g.X * g.J
+    unit, flops, bound = bench.kernel_work("tc_gemm_adj_3xtf32", g, info, "table_fp32", NSM)
+    assert (unit, bound) == ("TFLOP/s", "tensor")
+    assert flops == 3 * 2 * R * B * g.Q                   # three TF32 product passes
+    assert flops == pytest.approx(2.078e11, rel=1e-3)
+    _, f16, _ = bench.kernel_work("tc_gemm_adj_bf16", g, info, "table_bf16", NSM)
+    assert f16 == flops / 3
+    unit, wbytes, bound = bench.kernel_work("tc_gemm_fwd_3xtf32", g, info, "table_fp32", NSM)
+    assert (unit, bound) == ("GB/s", "hbm")
+    # writes the FP32 knot table, reads f's TF32 high and low parts
+    assert wbytes == 4 * R * B + 8 * R * g.Q
+
+
+def test_direct_kernels_are_alu_bound(paper):
+    g, info = paper
+    info = dict(info, n_open_pairs=1000)
+    unit, flops, bound = bench.kernel_work("fwd_direct", g, info, "direct", NSM)
+    assert (unit, bound) == ("TFLOP/s", "alu")
+    assert flops == 1000 * (8.0 * g.K + 30.0)
+    assert bench.kernel_work("no_such_kernel", g, info, "direct", NSM) == (None, None, None)
+
+
+def test_traffic_dropped_when_the_source_changes(tmp_path, monkeypatch):
+    src_dir = tmp_path / "paper_1603_06400_gb300" / "csrc"
+    src_dir.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    root = bench.ROOT
+    for f in ("records.cu", "tc_gemm.cu"):
+        shutil.copy(os.path.join(root, "paper_1603_06400_gb300", "csrc", f), src_dir / f)
+    shutil.copy(os.path.join(root, "profiles", "ncu_traffic.txt"), tmp_path / "profiles" / "ncu_traffic.txt")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    names = ("sym_pairs_adj", "sym_pairs_fwd", "tc_gemm_adj_3xtf32", "tc_gemm_fwd_3xtf32")
+    now = {n: bench.traffic_for(n, "table_fp32") for n in names}
+    for n, v in now.items():
+        # the committed figures are valid for the committed sources
+        assert v is not None and v > 1e9, n
+    assert bench.traffic_for("_note", "table_fp32") is None
+    with open(src_dir / "records.cu", "a") as fh:
+        fh.write("\n// changed\n")
+    assert bench.traffic_for("sym_pairs_adj", "table_fp32") is None
+    assert bench.traffic_for("sym_pairs_fwd", "table_fp32") is None
+    assert bench.traffic_for("tc_gemm_adj_3xtf32", "table_fp32") == now["tc_gemm_adj_3xtf32"]
+
+
+def test_peaks_fall_back_without_the_measured_file(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    peaks, kind = bench.measured_peaks()
+    assert kind == "fallback"
+    assert peaks["hbm_gbs"] == 6800.0 and peaks["bf16_tflops"] == 1900.0
