@@ -3,8 +3,8 @@ the bench divides by each kernel's measured time, checked against the counts it
 is made of at the paper-scale workload (object 128 x 256 voxels x 128 q bins,
 detector 64 x 256 pixels, 8258 knots, 152 SMs), and the rule that a DRAM
 traffic figure is dropped once the kernel's source has changed."""
-import os
-import shutil
+import hashlib
+import json
 
 import pytest
 
@@ -77,22 +77,25 @@ def test_traffic_dropped_when_the_source_changes(tmp_path, monkeypatch):
     src_dir = tmp_path / "paper_1603_06400_gb300" / "csrc"
     src_dir.mkdir(parents=True)
     (tmp_path / "profiles").mkdir()
-    root = bench.ROOT
+    shas = {}
     for f in ("records.cu", "tc_gemm.cu"):
-        shutil.copy(os.path.join(root, "paper_1603_06400_gb300", "csrc", f), src_dir / f)
-    shutil.copy(os.path.join(root, "profiles", "ncu_traffic.txt"), tmp_path / "profiles" / "ncu_traffic.txt")
+        data = f"// stand-in source of {f}\n".encode()
+        (src_dir / f).write_bytes(data)
+        shas[f] = hashlib.sha256(data).hexdigest()[:16]
+    table = {"sym_pairs_adj": {"dram_bytes_per_launch": 2.5e9, "source": "records.cu", "source_sha": shas["records.cu"]},
+             "tc_gemm_adj_3xtf32": {"dram_bytes_per_launch": 1.1e9, "source": "tc_gemm.cu",
+                                    "source_sha": shas["tc_gemm.cu"]},
+             "_note": "per launch"}
+    (tmp_path / "profiles" / "ncu_traffic.txt").write_text(json.dumps(table))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    names = ("sym_pairs_adj", "sym_pairs_fwd", "tc_gemm_adj_3xtf32", "tc_gemm_fwd_3xtf32")
-    now = {n: bench.traffic_for(n, "table_fp32") for n in names}
-    for n, v in now.items():
-        # the committed figures are valid for the committed sources
-        assert v is not None and v > 1e9, n
+    assert bench.traffic_for("sym_pairs_adj", "table_fp32") == 2.5e9
+    assert bench.traffic_for("tc_gemm_adj_3xtf32", "table_fp32") == 1.1e9
+    assert bench.traffic_for("sym_pairs_fwd", "table_fp32") is None      # not captured
     assert bench.traffic_for("_note", "table_fp32") is None
     with open(src_dir / "records.cu", "a") as fh:
-        fh.write("\n// changed\n")
-    assert bench.traffic_for("sym_pairs_adj", "table_fp32") is None
-    assert bench.traffic_for("sym_pairs_fwd", "table_fp32") is None
-    assert bench.traffic_for("tc_gemm_adj_3xtf32", "table_fp32") == now["tc_gemm_adj_3xtf32"]
+        fh.write("// changed\n")
+    assert bench.traffic_for("sym_pairs_adj", "table_fp32") is None      # stale
+    assert bench.traffic_for("tc_gemm_adj_3xtf32", "table_fp32") == 1.1e9
 
 
 def test_peaks_fall_back_without_the_measured_file(tmp_path, monkeypatch):
