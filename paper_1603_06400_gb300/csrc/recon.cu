@@ -2,6 +2,7 @@
 // Appendices B-C): the likelihood ratio y / (A f + r) with the negative
 // log-likelihood accumulated in FP64, and the closed-form update of Eq. 10
 // with the Huber edge-preserving penalty on the 4 spatial neighbours.
+#include <float.h>
 #include <math.h>
 
 #include "internal.cuh"
@@ -73,6 +74,17 @@ k_ratio_nll(const float *__restrict__ g, const float *__restrict__ y, const floa
 // the positive root of chi1 x^2 + chi2 x - chi3 = 0 (the Lemma), written without
 // cancellation for chi2 > 0.  n = nobj * R * Q: objects of the same geometry
 // back to back, each with its own neighbourhoods.
+// omega(d) = psi_dot(d) / d of the Huber penalty, from |d| and delta: 1 within
+// delta, delta / |d| beyond.  Beyond delta with delta normal, |d| is normal too
+// and the hardware quotient (within 2 ulp) serves; a zero or subnormal delta
+// keeps the IEEE quotient.  The IEEE form, evaluated for every neighbour as the
+// select compiles it, divides by |d| = 0 wherever the image is flat, and that
+// case runs its slow path: the update took twice as long on a flat image.
+__device__ __forceinline__ float huber_omega(float ad, float delta) {
+    if (ad <= delta) return 1.f;
+    return delta >= FLT_MIN ? __fdividef(delta, ad) : delta / ad;
+}
+
 struct UpdTerms {
     float fh, b3, b5, chi1, chi2, chi3, x;
     int kind;   // 0: root with chi1 > 0, 1: chi3 / chi2, 2: value kept
@@ -104,7 +116,7 @@ __device__ __forceinline__ UpdTerms upd_terms(const DevGeo &g, const float *__re
             if (!ok) continue;
             const float d = u.fh - f[k];
             const float ad = fabsf(d);
-            u.b3 += 2.f * (ad <= delta ? 1.f : delta / ad);
+            u.b3 += 2.f * huber_omega(ad, delta);
             u.b5 += fminf(fmaxf(d, -delta), delta);
         }
     }
@@ -136,7 +148,7 @@ __device__ __forceinline__ float update_value(float fh, const float (&nb)[4], co
             if (!ok[q]) continue;
             const float d = fh - nb[q];
             const float ad = fabsf(d);
-            b3 += 2.f * (ad <= delta ? 1.f : delta / ad);
+            b3 += 2.f * huber_omega(ad, delta);
             b5 += fminf(fmaxf(d, -delta), delta);
         }
     }
