@@ -240,9 +240,9 @@ caxsi_status caxsi_recon_step(caxsi_plan *p, const float *y_dev, const float *r_
         p->b1[path] = b1;
         p->table_bytes += nf * 4;
     }
-    // z = A f + r, ratio = y / z, L(f) in FP64
+    // z = A f + r, ratio = y / z, and L(f) in FP64 when asked for
     if ((st = run_forward(p, f_dev, p->gtmp, path, s)) != CAXSI_OK) return st;
-    if ((st = recon_ratio(p, y_dev, r_dev, nullptr, -1, s)) != CAXSI_OK) return st;
+    if ((st = recon_ratio(p, y_dev, r_dev, nullptr, -1, nll_out != nullptr, s)) != CAXSI_OK) return st;
     if (nll_out) {
         int64_t keep = p->launches;
         st = recon_nll_fetch(p, nll_out, s);
@@ -344,9 +344,9 @@ caxsi_status caxsi_recon_step_subset(caxsi_plan *p, int subset, const float *y_d
         if ((st = run_adjoint(p, p->ones, b1p, path, s, subset)) != CAXSI_OK) return st;
         p->b1_sub_ok[path][subset] = 1;
     }
-    // z_p = A_p f + r_p, ratio on the subset's pixels, L_p(f) in FP64
+    // z_p = A_p f + r_p, ratio on the subset's pixels, and L_p(f) in FP64 when asked for
     if ((st = run_forward(p, f_dev, p->gtmp, path, s, subset)) != CAXSI_OK) return st;
-    if ((st = recon_ratio(p, y_dev, r_dev, p->sub_of_pix, subset, s)) != CAXSI_OK) return st;
+    if ((st = recon_ratio(p, y_dev, r_dev, p->sub_of_pix, subset, nll_out != nullptr, s)) != CAXSI_OK) return st;
     if (nll_out) {
         int64_t keep = p->launches;
         st = recon_nll_fetch(p, nll_out, s);

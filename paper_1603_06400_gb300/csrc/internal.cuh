@@ -139,7 +139,8 @@ int64_t table_sym_records(const caxsi_plan *p);
 // ---- recon.cu ----------------------------------------------------------------
 // sub != null: only pixels with sub[i] == subset enter (ratio 0 and no
 // likelihood term elsewhere).
-caxsi_status recon_ratio(caxsi_plan *p, const float *y, const float *r, const int *sub, int subset,
+// ratio = y / (g + r); with nll, the FP64 negative log-likelihood too (in nll_dev)
+caxsi_status recon_ratio(caxsi_plan *p, const float *y, const float *r, const int *sub, int subset, bool nll,
                          cudaStream_t s);
 caxsi_status recon_update(caxsi_plan *p, const float *f_old, float beta, float delta,
                           const float *b1, cudaStream_t s);

@@ -68,6 +68,27 @@ k_ratio_nll(const float *__restrict__ g, const float *__restrict__ y, const floa
     }
 }
 
+// The ratio alone, for calls that do not ask for the likelihood: the same
+// quotient as k_ratio_nll and the same error word, without the FP64 log and
+// lgamma terms (slow on this part's FP64 units).
+__global__ void k_ratio(const float *__restrict__ g, const float *__restrict__ y, const float *__restrict__ r,
+                        const int *__restrict__ sub, int subset, float *__restrict__ ratio, int *err, int64_t n) {
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const float z = r ? g[idx] + r[idx] : g[idx];
+        const float yy = y[idx];
+        float rt = 0.f;
+        if (sub && sub[idx] != subset) {
+            // outside the subset: no ratio
+        } else if (z > 0.f) {
+            rt = yy / z;
+        } else if (yy > 0.f) {
+            *err = 1;
+        }
+        ratio[idx] = rt;
+    }
+}
+
 // chi1 = beta (b3 + b4), chi2 = b1 + beta (-f (b3 + b4) + b5 + b6), chi3 = f b2,
 // b3 = b4 = 2 sum_k omega(f_j - f_k), b5 = b6 = sum_k psi_dot(f_j - f_k) over the
 // 4 spatial neighbours (symmetric neighbourhood, unit weights); the update is
@@ -321,9 +342,19 @@ __global__ void k_update_vjp2(DevGeo g, const float *__restrict__ f, float delta
 
 }  // namespace
 
-caxsi_status recon_ratio(caxsi_plan *p, const float *y, const float *r, const int *sub, int subset,
+caxsi_status recon_ratio(caxsi_plan *p, const float *y, const float *r, const int *sub, int subset, bool nll,
                          cudaStream_t s) {
     const int64_t n = (int64_t)p->dg.M * p->dg.N;
+    if (!nll) {
+        {
+            CAXSI_PROF(p, "ratio", s);
+            const int64_t nb = ceil_div64(n, 256);
+            k_ratio<<<(unsigned)(nb < 4 * p->num_sms ? nb : 4 * p->num_sms), 256, 0, s>>>(
+                p->gtmp, y, r, sub, subset, p->ratio, p->err_flag, n);
+        }
+        CAXSI_LAUNCH_CHECK(p);
+        return CAXSI_OK;
+    }
     {
         CAXSI_PROF(p, "ratio_nll", s);
         k_ratio_nll<<<p->nll_blocks, NLL_THREADS, 0, s>>>(p->gtmp, y, r, sub, subset, p->ratio, p->nll_part,

@@ -210,6 +210,33 @@ def test_recon_reports_nonpositive_mean(cx):
     # y = 0 where z = 0 is allowed: ratio 0, likelihood 0
     nll = plan.recon_step(torch.zeros(g.g_len, device="cuda:0"), f, want_nll=True)
     assert nll == 0.0
+    # without the likelihood the call returns, and the next call that asks for it
+    # reports the error; the one after that is clean again
+    plan.recon_step(y, f)
+    assert torch.equal(f, before)
+    with pytest.raises(caxsi.CaxsiError) as e:
+        plan.recon_step(torch.zeros(g.g_len, device="cuda:0"), f, want_nll=True)
+    assert e.value.status == 4
+    assert plan.recon_step(torch.zeros(g.g_len, device="cuda:0"), f, want_nll=True) == 0.0
+    plan.close()
+
+
+@pytest.mark.parametrize("path", FP32_PATHS)
+def test_recon_step_same_with_and_without_the_likelihood(cx, path):
+    caxsi, torch = cx
+    g = GEOMS["ragged"]()
+    phi = synth.tungsten_spectrum(g)
+    mask = synth.random_mask(g, 5)
+    f_true = synth.phantom(g, 2, n_ellipses=2)
+    y = synth.poisson_counts(oracle.forward(g, phi, mask, f_true) * 200.0, 6)
+    plan, P = _plan(caxsi, g, phi, mask, path)
+    f0 = _t(torch, np.full((g.X, g.J, g.Q), 0.3))
+    f1, f2 = f0.clone(), f0.clone()
+    yt = _t(torch, y)
+    for _ in range(3):
+        plan.recon_step(yt, f1, beta=0.05, delta=0.01, path=P, want_nll=True)
+        plan.recon_step(yt, f2, beta=0.05, delta=0.01, path=P)
+    assert torch.equal(f1, f2)
     plan.close()
 
 
