@@ -21,6 +21,7 @@ from __future__ import annotations
 import ctypes
 import math
 import os
+import platform
 import subprocess
 import threading
 
@@ -29,7 +30,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "caxsi_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
-_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+# one library per machine type: a build made on another architecture is never loaded
+_LIB_PATH = os.path.join(_BUILD, f"liboracle_{platform.machine()}.so")
 _lock = threading.Lock()
 _lib = None
 

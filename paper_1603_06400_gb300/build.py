@@ -4,6 +4,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import glob
 import os
+import platform
 import shutil
 import subprocess
 
@@ -13,6 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libcaxsi.so")
+STAMP = os.path.join(LIBDIR, "build_stamp.txt")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -35,17 +37,26 @@ def _deps():
         glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__]
 
 
-def is_stale() -> bool:
-    if not os.path.exists(LIB):
+def _stamp(extra_flags=()) -> str:
+    # a library built on another machine type or with other flags is rebuilt
+    return " ".join([platform.machine()] + ARCH + NVCC_FLAGS + list(extra_flags))
+
+
+def is_stale(extra_flags=()) -> bool:
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return True
+    with open(STAMP) as fh:
+        if fh.read().strip() != _stamp(extra_flags):
+            return True
     t = os.path.getmtime(LIB)
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and not is_stale():
+    if not force and not is_stale(extra_flags):
         return LIB
-    objdir = os.path.join(LIBDIR, "obj")
+    # objects per process: concurrent builds do not share them
+    objdir = os.path.join(LIBDIR, f"obj{os.getpid()}")
     os.makedirs(objdir, exist_ok=True)
     cc = nvcc()
     base = [cc] + ARCH + NVCC_FLAGS + list(extra_flags) + ["-I", INCLUDE, "-I", CSRC]
@@ -66,9 +77,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + ["-lcublas"]
     r = subprocess.run(cmd, capture_output=True, text=True)
+    shutil.rmtree(objdir, ignore_errors=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP + f".tmp{os.getpid()}", "w") as fh:
+        fh.write(_stamp(extra_flags) + "\n")
+    os.replace(STAMP + f".tmp{os.getpid()}", STAMP)
     return LIB
 
 
