@@ -1,7 +1,8 @@
 """The oracle's pins catch plausible mistakes.
 
 Each case plants one mistake (a dropped factor, a wrong exponent, a swapped
-weight or index, a wrong plane, a subset step that leaks outside its subset)
+weight or index, a wrong plane, a wrong sign or root in the update, a subset
+step that leaks outside its subset)
 in a temporary copy of the oracle, on the CPU, and checks that the pin suites
 fail on it.
 """
@@ -33,6 +34,19 @@ MUTATIONS = {
     "object y pitch": (C_SRC, "* g->rho_y * g->p_y; }", "* g->p_y; }"),
     "adjoint weight": (C_SRC, "frow[l + 1] += base * ck * a;", "frow[l + 1] += base * ck * (1.0 - a);"),
     "energy bin centre": (C_SRC, "(k + 0.5) * dE", "(k + 1.0) * dE"),
+    # the update of Eq. 10 and its penalty terms (Appendices B-C)
+    "Huber weight beyond delta": (PY_SRC, "1.0, delta / np.where(a > 0, a, 1.0))",
+                                  "1.0, 1.0 / np.where(a > 0, a, 1.0))"),
+    "psi_dot sign": (PY_SRC, "b5 += np.where(ok, huber_grad(d, delta), 0.0)",
+                     "b5 += np.where(ok, huber_grad(-d, delta), 0.0)"),
+    "b3 factor 2": (PY_SRC, "b3 += np.where(ok, 2.0 * huber_curv(d, delta), 0.0)",
+                    "b3 += np.where(ok, huber_curv(d, delta), 0.0)"),
+    "chi2 penalty sign": (PY_SRC, "chi2 = b1 + beta * (-f_hat * (b3 + b4) + b5 + b6)",
+                          "chi2 = b1 + beta * (f_hat * (b3 + b4) + b5 + b6)"),
+    "Lemma minus root": (PY_SRC, "root = (-b + np.sqrt(b * b + 4.0 * a * c)) / (2.0 * a)",
+                         "root = (-b - np.sqrt(b * b + 4.0 * a * c)) / (2.0 * a)"),
+    "Lemma linear case": (PY_SRC, "lin = np.where(b > 0, c / b, np.inf)", "lin = np.where(b > 0, b / c, np.inf)"),
+    "Huber quadratic half": (PY_SRC, "np.where(a <= delta, 0.5 * t * t,", "np.where(a <= delta, t * t,"),
     # ordered subsets (Algorithm 5)
     "OS ratio outside the subset": (PY_SRC, "ok = in_subset & (z > 0)", "ok = z > 0"),
     "OS sensitivity of all pixels": (PY_SRC, "return At(np.asarray(in_subset, dtype=np.float64))",

@@ -80,6 +80,48 @@ def test_penalty_gradient_is_b5_plus_b6():
         assert fd == pytest.approx(b5[idx] + b6[idx], abs=1e-6)
 
 
+def test_separable_surrogate_majorises_the_penalty():
+    # Appendix B: with b3..b6 taken at f_hat, the separable surrogate
+    #   P(f) = R(f_hat) + sum_j (b5 + b6)_j (f_j - f_hat_j) + 1/2 sum_j (b3 + b4)_j (f_j - f_hat_j)^2
+    # lies above R everywhere and touches it at f_hat (Huber's quadratic majoriser
+    # of each psi, then (a - b)^2 <= 2 a^2 + 2 b^2 to separate the voxels).  The
+    # curvature is tight: along a checkerboard perturbation in the quadratic zone
+    # R curves as 16 per voxel (the largest eigenvalue of twice the 4-neighbour
+    # Laplacian) and so does P.
+    rng = np.random.default_rng(3)
+    f_hat = rng.uniform(0.5, 1.0, size=(6, 7, 3))
+    d = 0.15
+    b3, b4, b5, b6 = oracle.b_terms(f_hat, d)
+    R0 = oracle.penalty(f_hat, d)
+
+    def sur(f):
+        e = f - f_hat
+        return R0 + float(np.sum((b5 + b6) * e)) + 0.5 * float(np.sum((b3 + b4) * e * e))
+
+    assert sur(f_hat) == pytest.approx(R0, rel=1e-15)
+    ii, jj = np.meshgrid(np.arange(6), np.arange(7), indexing="ij")
+    checker = ((-1.0) ** (ii + jj))[:, :, None] * np.ones((1, 1, 3))
+    for scale in (1e-3, 1e-2, 0.1, 1.0):
+        for trial in range(20):
+            e = scale * rng.standard_normal(f_hat.shape)
+            f = f_hat + e
+            assert sur(f) >= oracle.penalty(f, d) - 1e-12 * (1.0 + abs(R0)), (scale, trial)
+        f = f_hat + scale * checker
+        assert sur(f) >= oracle.penalty(f, d) - 1e-12 * (1.0 + abs(R0)), scale
+    # flat image, checkerboard of amplitude well inside delta: both sides gain
+    # 4 eps^2 per neighbour edge (R: (2 eps)^2 per edge; P: 2 eps^2 times the
+    # voxel's degree, summed over voxels), so the bound is attained
+    flat = np.full((6, 7, 3), 0.7)
+    c3, c4, c5, c6 = oracle.b_terms(flat, d)
+    eps = 0.01
+    e = eps * checker
+    R_pert = oracle.penalty(flat + e, d) - oracle.penalty(flat, d)
+    P_pert = 0.5 * float(np.sum((c3 + c4) * e * e)) + float(np.sum((c5 + c6) * e))
+    edges = 3 * ((6 - 1) * 7 + 6 * (7 - 1))
+    assert R_pert == pytest.approx(4 * eps ** 2 * edges, rel=1e-9)
+    assert P_pert == pytest.approx(R_pert, rel=1e-12)
+
+
 def test_beta_zero_is_mlem():
     rng = np.random.default_rng(2)
     f = rng.uniform(0.1, 1, size=(3, 4, 5))
