@@ -34,6 +34,17 @@ MUTATIONS = {
     "object y pitch": (C_SRC, "* g->rho_y * g->p_y; }", "* g->p_y; }"),
     "adjoint weight": (C_SRC, "frow[l + 1] += base * ck * a;", "frow[l + 1] += base * ck * (1.0 - a);"),
     "energy bin centre": (C_SRC, "(k + 0.5) * dE", "(k + 1.0) * dE"),
+    "angular factor": (C_SRC, "(1.0 + cos(o->theta) * cos(o->theta))", "(1.0 + cos(o->theta))"),
+    "G_od from s_y": (C_SRC, "o->God = fabs(s[0]) /", "o->God = fabs(s[1]) /"),
+    "mask ray from y = 0": (C_SRC, "double ym = y + t * (yp - y);", "double ym = t * yp;"),
+    # the same mistake in the forward and the adjoint (the adjoint identity cannot see it)
+    "q step range / Q": (C_SRC, [("double dq = (g->q_max - g->q_min) / (g->Q - 1);",
+                                  "double dq = (g->q_max - g->q_min) / g->Q;")] * 2),
+    "no zero sample past the q grid": (C_SRC, [
+        ("if (!(tau > -1.0 && tau < (double)Q)) return 0.0;",
+         "if (!(tau >= 0.0 && tau <= (double)(Q - 1))) return 0.0;"),
+        ("if (!(tau > -1.0 && tau < (double)g->Q)) continue;",
+         "if (!(tau >= 0.0 && tau <= (double)(g->Q - 1))) continue;")]),
     # the update of Eq. 10 and its penalty terms (Appendices B-C)
     "Huber weight beyond delta": (PY_SRC, "1.0, delta / np.where(a > 0, a, 1.0))",
                                   "1.0, 1.0 / np.where(a > 0, a, 1.0))"),
@@ -56,14 +67,17 @@ MUTATIONS = {
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_pins_catch_planted_mistake(name, tmp_path):
-    rel, before, after = MUTATIONS[name]
+    rel, *edit = MUTATIONS[name]
+    edits = edit[0] if len(edit) == 1 else [tuple(edit)]
     src = open(os.path.join(ROOT, rel)).read()
-    assert before in src
+    for before, after in edits:        # each pair replaces one occurrence, in order
+        assert before in src, before
+        src = src.replace(before, after, 1)
     for d in ("oracle", "synth", "tests"):
         shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
                         ignore=shutil.ignore_patterns("_build", "__pycache__"))
     shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path / "pytest.ini")
-    (tmp_path / rel).write_text(src.replace(before, after, 1))
+    (tmp_path / rel).write_text(src)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         "tests/test_oracle_pins.py", "tests/test_oracle_recon.py"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=600)

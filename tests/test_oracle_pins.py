@@ -135,19 +135,53 @@ def test_single_open_cell_ray_trace():
     assert np.count_nonzero(oracle.forward(g, synth.tungsten_spectrum(g), mask, f)) > 0
 
 
+def test_open_cell_seen_from_off_axis_voxels():
+    # Voxels up to 16 mm off the central plane: the mask crossing of a ray moves by
+    # (1 - t) y with the voxel's y (t = (X_mask - x)/(X_det - x)), several cells here.
+    # From each voxel, the ray through the open cell's centre, extended to the
+    # detector, lands on a pixel that sees the cell; pixels 4 steps away in y or z
+    # (3.2 mm at the mask plane, past the 1 mm half-cell) do not.
+    g = small_geometry(X=3, J=5, M=24, N=40, p_y=1.0, p_z=1.0, rho_y=8)
+    rows, cols = g.mask_rows, g.mask_cols
+    mask = np.zeros((rows, cols), np.uint8)
+    rc, cc = rows // 2, cols // 2 - 1
+    mask[rc, cc] = 1
+    yc = g.mask_y0 + (cc + 0.5) * g.mask_cell
+    zc = g.mask_z0 + (rc + 0.5) * g.mask_cell
+    seen = 0
+    for i in range(g.X):
+        x = g.x_center + (i - (g.X - 1) / 2) * g.dx
+        for j in range(g.J):
+            y = (j - (g.J - 1) / 2) * g.rho_y * g.p_y
+            s = (g.X_det - x) / (g.X_mask - x)
+            yd, zd = y + (yc - y) * s, zc * s
+            n = int(round(yd / g.p_y + (g.N - 1) / 2))
+            m = int(round(zd / g.p_z + (g.M - 1) / 2))
+            assert 0 <= n < g.N and 0 <= m < g.M
+            assert oracle.pair(g, mask, i, j, m, n)["T"] == 1.0, (i, j)
+            seen += 1
+            for dm, dn in ((4, 0), (-4, 0), (0, 4), (0, -4)):
+                if 0 <= m + dm < g.M and 0 <= n + dn < g.N:
+                    assert oracle.pair(g, mask, i, j, m + dm, n + dn)["T"] == 0.0, (i, j, dm, dn)
+    assert seen == g.X * g.J
+    assert max(abs((j - (g.J - 1) / 2) * g.rho_y * g.p_y) for j in range(g.J)) == 16.0
+
+
 # --------------------------------------------------------------------------
 # Point scatterer: Bragg-law annulus and its values, by polar coordinates
 # --------------------------------------------------------------------------
 
-def test_point_scatterer_footprint():
+@pytest.mark.parametrize("l", [0, 17])
+def test_point_scatterer_footprint(l):
     # One voxel on the central ray, one q bin, one energy bin (a narrow spectrum):
     # the detector sees a ring where E sin(theta/2)/hc is within one q step of q_l.
+    # For the first bin the ring includes the half step below q_0: the q samples
+    # are hat functions, the grid extended by a zero sample at each end.
     g = synth.make_geometry(X=1, J=1, Q=40, M=64, N=128, K=1, rho_y=1, p_y=0.76,
                             p_z=0.76, dx=2.0, E_min=59.0, E_max=61.0, q_min=0.1,
                             q_max=3.5, C=1.0)
     mask = np.ones((g.mask_rows, g.mask_cols), np.uint8)
     phi = np.array([1.0])
-    l = 17
     f = np.zeros((1, 1, g.Q))
     f[0, 0, l] = 1.0
     out = oracle.forward(g, phi, mask, f)
