@@ -45,6 +45,14 @@ MUTATIONS = {
          "if (!(tau >= 0.0 && tau <= (double)(Q - 1))) return 0.0;"),
         ("if (!(tau > -1.0 && tau < (double)g->Q)) continue;",
          "if (!(tau >= 0.0 && tau <= (double)(g->Q - 1))) continue;")]),
+    "C dropped": (C_SRC, [("out[t] = g->C * acc;", "out[t] = acc;"), ("frow[l] *= g->C;", "frow[l] *= 1.0;"),
+                          ("H[p * cols + v * g->Q + l] = g->C * pr.Gso", "H[p * cols + v * g->Q + l] = pr.Gso")]),
+    "spectrum dropped": (C_SRC, [("double ck = phi[k] * E * dE / (g->hc * g->hc);",
+                                  "double ck = E * dE / (g->hc * g->hc);")] * 2),
+    "pixel z half pitch": (C_SRC, "return (m - 0.5 * (g->M - 1)) * g->p_z;", "return (m - 0.5 * g->M) * g->p_z;"),
+    "dtheta one-sided": (C_SRC, "double sm[3] = {s[0], s[1], s[2] - h};", "double sm[3] = {s[0], s[1], s[2]};"),
+    "EM mean without background": (PY_SRC, "    z = A(f_hat) + r\n    if np.any",
+                                   "    z = A(f_hat)\n    if np.any"),
     # the update of Eq. 10 and its penalty terms (Appendices B-C)
     "Huber weight beyond delta": (PY_SRC, "1.0, delta / np.where(a > 0, a, 1.0))",
                                   "1.0, 1.0 / np.where(a > 0, a, 1.0))"),

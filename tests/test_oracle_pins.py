@@ -179,7 +179,7 @@ def test_point_scatterer_footprint(l):
     # are hat functions, the grid extended by a zero sample at each end.
     g = synth.make_geometry(X=1, J=1, Q=40, M=64, N=128, K=1, rho_y=1, p_y=0.76,
                             p_z=0.76, dx=2.0, E_min=59.0, E_max=61.0, q_min=0.1,
-                            q_max=3.5, C=1.0)
+                            q_max=3.5, C=2.5)
     mask = np.ones((g.mask_rows, g.mask_cols), np.uint8)
     phi = np.array([1.0])
     f = np.zeros((1, 1, g.Q))
@@ -211,7 +211,7 @@ def test_point_scatterer_footprint(l):
             h = g.p_z / 2
             dth = _law_of_cosines_angle([L, yp, zp + h], [L, yp, zp - h])
             ang = (1 + math.cos(theta) ** 2) * math.cos(theta / 2)
-            expect = Gso * God * dth * ang * E * dE / g.hc ** 2 * hat
+            expect = g.C * Gso * God * dth * ang * E * dE / g.hc ** 2 * hat
             assert out[m, n] == pytest.approx(expect, rel=1e-8, abs=1e-300)
             inside = R_lo < R < R_hi
             assert (out[m, n] > 0) == inside
