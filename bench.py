@@ -3,7 +3,8 @@
 coherent-scatter operators on the paper-scale workload.
 
 Workload (one "step" = one penalised EM-type iteration, i.e. one forward
-model, one adjoint and the elementwise update, through caxsi_recon_step):
+model, one adjoint and the elementwise update, through caxsi_recon_step; the
+likelihood, a monitoring value the update does not use, is not requested):
 object 256 (y, across the fan) x 128 (x, along the beam) voxels x 128 q bins
 (0.1-3.5 nm^-1), detector 256 x 64 pixels, 64 energy bins (20-100 keV),
 tungsten-like spectrum, Bernoulli(0.5) mask with a 2-pixel feature, 10 seeded
