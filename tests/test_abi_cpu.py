@@ -83,3 +83,85 @@ def test_null_and_invalid_arguments_rejected_before_any_cuda_call(lib):
     assert lib.caxsi_adjoint_subset(None, 0, None, 0, None, 0, 1, None) == 1
     assert lib.caxsi_recon_step_subset(None, 0, None, None, None, 0, 0.0, 0.0, 1, None, None) == 1
     lib.caxsi_plan_destroy(None)
+
+
+# --------------------------------------------------------------------------
+# The binding agrees with the headers: struct layouts (compiled by gcc from the
+# header itself) and the parameter list of every declared function
+# --------------------------------------------------------------------------
+
+def _strip_comments(txt):
+    txt = re.sub(r"/\*.*?\*/", " ", txt, flags=re.S)
+    return re.sub(r"//[^\n]*", " ", txt)
+
+
+def _declarations():
+    """name -> parameter kinds ('ptr', 'i32', 'i64', 'f32', 'f64') of every
+    function declared in include/*.h."""
+    kinds = {"int": "i32", "int32_t": "i32", "caxsi_status": "i32", "int64_t": "i64",
+             "float": "f32", "double": "f64"}
+    out = {}
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        txt = _strip_comments(open(os.path.join(ROOT, "include", h)).read())
+        for name, params in re.findall(r"\b(caxsi_\w+)\s*\(([^;{}()]*)\)\s*;", txt):
+            ps = [p.strip() for p in params.split(",") if p.strip()]
+            if ps == ["void"]:
+                ps = []
+            ks = []
+            for p in ps:
+                if "*" in p:
+                    ks.append("ptr")
+                    continue
+                words = p.replace("const", " ").split()
+                assert len(words) == 2, (name, p)       # type and parameter name
+                ks.append(kinds[words[0]])
+            out[name] = ks
+    return out
+
+
+def _kind(ct):
+    if ct in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(ct, type) and issubclass(ct, ctypes._Pointer)):
+        return "ptr"
+    sizes = {ctypes.c_int: "i32", ctypes.c_int32: "i32", ctypes.c_int64: "i64", ctypes.c_long: "i64",
+             ctypes.c_float: "f32", ctypes.c_double: "f64"}
+    return sizes[ct]
+
+
+def test_binding_parameter_lists_match_the_headers(lib):
+    decls = _declarations()
+    assert len(decls) == len(declared_functions())
+    for name, kinds in decls.items():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, f"{name}: the binding sets no argument types"
+        got = [_kind(t) for t in fn.argtypes]
+        assert got == kinds, f"{name}: header {kinds}, binding {got}"
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"caxsi_geometry": caxsi.CGeometry, "caxsi_plan_info_t": caxsi.CPlanInfo,
+               "caxsi_kernel_stat": caxsi.CKernelStat}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "caxsi.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, value = ln.split()
+        got[(cname, field)] = int(value)
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for field, _ in cls._fields_:
+            assert got[(cname, field)] == getattr(cls, field).offset, (cname, field)
