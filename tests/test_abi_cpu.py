@@ -165,3 +165,17 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for field, _ in cls._fields_:
             assert got[(cname, field)] == getattr(cls, field).offset, (cname, field)
+
+
+def test_binding_return_types_match_the_headers(lib):
+    want = {"caxsi_status": ctypes.c_int, "void": None, "const char *": ctypes.c_char_p}
+    seen = 0
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        txt = _strip_comments(open(os.path.join(ROOT, "include", h)).read())
+        for ret, name in re.findall(r"(caxsi_status|void|const\s+char\s*\*)\s*(caxsi_\w+)\s*\([^;{}()]*\)\s*;", txt):
+            ret = "const char *" if "char" in ret else ret
+            assert getattr(lib, name).restype is want[ret], (name, ret)
+            seen += 1
+    assert seen == len(declared_functions())
