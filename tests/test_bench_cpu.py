@@ -103,3 +103,30 @@ def test_peaks_fall_back_without_the_measured_file(tmp_path, monkeypatch):
     peaks, kind = bench.measured_peaks()
     assert kind == "fallback"
     assert peaks["hbm_gbs"] == 6800.0 and peaks["bf16_tflops"] == 1900.0
+
+
+def _sampler(rows):
+    s = bench.ClockSampler.__new__(bench.ClockSampler)    # no nvidia-smi process
+    s.samples = rows
+    s.proc = None
+    return s
+
+
+def test_clock_summary_of_the_timed_window():
+    active, idle = "Active", "Not Active"
+    rows = [(0.5, f"2070, 2070, 300.0, 0x0, {idle}, {idle}, {idle}, {idle}"),      # before the window
+            (1.1, f"1980, 2070, 1350.5, 0x4, {idle}, {idle}, {idle}, {active}"),
+            (1.2, f"2010, 2070, 1380.0, 0x0, {idle}, {idle}, {idle}, {idle}"),
+            (1.3, "garbled line"),
+            (1.4, f"[N/A], 2070, 1380.0, 0x0, {idle}, {idle}, {idle}, {idle}"),
+            (1.5, f"2040, 2070, 1390.0, 0x0, {idle}, {idle}, {idle}, {idle}"),
+            (3.0, f"1200, 2070, 200.0, 0x40, {idle}, {active}, {idle}, {idle}")]      # after it
+    s = _sampler(rows).summary(1.0, 2.0)
+    assert s == {"sm_mhz": 2010.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_clock_summary_falls_back_to_all_samples():
+    rows = [(0.1, "2070, 2070, 300.0, 0x0, Not Active, Not Active, Active, Not Active")]
+    s = _sampler(rows).summary(5.0, 6.0)       # nothing inside the window: every sample counts
+    assert s["samples"] == 1 and s["reasons"] == ["sw_thermal_slowdown"]
+    assert _sampler([]).summary(0.0, 1.0) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
