@@ -10,6 +10,7 @@ import os
 import shutil
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -73,20 +74,42 @@ MUTATIONS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
-def test_pins_catch_planted_mistake(name, tmp_path):
+def _run_mutant(name, work, env):
+    """Plant one mutation in a copy of the oracle under `work` and run the pin
+    suites on it: (pytest return code, end of its output), or (None, why) when
+    the mutation's text is not in the source any more."""
     rel, *edit = MUTATIONS[name]
     edits = edit[0] if len(edit) == 1 else [tuple(edit)]
     src = open(os.path.join(ROOT, rel)).read()
     for before, after in edits:        # each pair replaces one occurrence, in order
-        assert before in src, before
+        if before not in src:
+            return None, f"text not found: {before!r}"
         src = src.replace(before, after, 1)
     for d in ("oracle", "synth", "tests"):
-        shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
+        shutil.copytree(os.path.join(ROOT, d), work / d,
                         ignore=shutil.ignore_patterns("_build", "__pycache__"))
-    shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path / "pytest.ini")
-    (tmp_path / rel).write_text(src)
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), work / "pytest.ini")
+    (work / rel).write_text(src)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         "tests/test_oracle_pins.py", "tests/test_oracle_recon.py"],
-                       cwd=tmp_path, capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, f"mutation '{name}' survived the pins:\n{r.stdout[-2000:]}"
+                       cwd=work, capture_output=True, text=True, timeout=600, env=env)
+    return r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    # the mutants are independent: run them side by side, each oracle on 2 threads
+    base = tmp_path_factory.mktemp("mutants")
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    names = sorted(MUTATIONS)
+    workers = max(1, min(len(names), (os.cpu_count() or 2) // 2))
+    with ThreadPoolExecutor(workers) as ex:
+        futs = {n: ex.submit(_run_mutant, n, base / f"m{i}", env) for i, n in enumerate(names)}
+        return {n: f.result() for n, f in futs.items()}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, outcomes):
+    rc, out = outcomes[name]
+    assert rc is not None, f"mutation '{name}': {out}"
+    assert rc != 0, f"mutation '{name}' survived the pins:\n{out}"
