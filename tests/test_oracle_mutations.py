@@ -38,6 +38,11 @@ MUTATIONS = {
     "angular factor": (C_SRC, "(1.0 + cos(o->theta) * cos(o->theta))", "(1.0 + cos(o->theta))"),
     "G_od from s_y": (C_SRC, "o->God = fabs(s[0]) /", "o->God = fabs(s[1]) /"),
     "mask ray from y = 0": (C_SRC, "double ym = y + t * (yp - y);", "double ym = t * yp;"),
+    "G_so without the voxel's y": (C_SRC, "pow(x * x + y * y, 1.5)", "pow(x * x, 1.5)"),
+    "dtheta across y": (C_SRC, [("double sp[3] = {s[0], s[1], s[2] + h};", "double sp[3] = {s[0], s[1] + h, s[2]};"),
+                                ("double sm[3] = {s[0], s[1], s[2] - h};", "double sm[3] = {s[0], s[1] - h, s[2]};")]),
+    "pixel y half pitch": (C_SRC, "return (n - 0.5 * (g->N - 1)) * g->p_y;", "return (n - 0.5 * g->N) * g->p_y;"),
+    "mask z unscaled": (C_SRC, "double zm = t * zp;", "double zm = zp;"),
     # the same mistake in the forward and the adjoint (the adjoint identity cannot see it)
     "q step range / Q": (C_SRC, [("double dq = (g->q_max - g->q_min) / (g->Q - 1);",
                                   "double dq = (g->q_max - g->q_min) / g->Q;")] * 2),
@@ -65,6 +70,7 @@ MUTATIONS = {
                           "chi2 = b1 + beta * (f_hat * (b3 + b4) + b5 + b6)"),
     "Lemma minus root": (PY_SRC, "root = (-b + np.sqrt(b * b + 4.0 * a * c)) / (2.0 * a)",
                          "root = (-b - np.sqrt(b * b + 4.0 * a * c)) / (2.0 * a)"),
+    "chi3 without f_hat": (PY_SRC, "chi3 = f_hat * b2\n", "chi3 = b2\n"),
     "Lemma linear case": (PY_SRC, "lin = np.where(b > 0, c / b, np.inf)", "lin = np.where(b > 0, b / c, np.inf)"),
     "Huber quadratic half": (PY_SRC, "np.where(a <= delta, 0.5 * t * t,", "np.where(a <= delta, t * t,"),
     # ordered subsets (Algorithm 5)
