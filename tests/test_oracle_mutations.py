@@ -70,6 +70,10 @@ MUTATIONS = {
                           "chi2 = b1 + beta * (f_hat * (b3 + b4) + b5 + b6)"),
     "Lemma minus root": (PY_SRC, "root = (-b + np.sqrt(b * b + 4.0 * a * c)) / (2.0 * a)",
                          "root = (-b - np.sqrt(b * b + 4.0 * a * c)) / (2.0 * a)"),
+    "q form: sin instead of sin^2": (PY_SRC, "np.cos(0.5 * theta) / s2 ** 2 * phi_fn", "np.cos(0.5 * theta) / s2 * phi_fn"),
+    "q form: angular factor": (PY_SRC, "return q * (1.0 + np.cos(theta) ** 2)", "return q * (1.0 + np.cos(theta))"),
+    "likelihood: ln y! off by one": (PY_SRC, "math.lgamma(v + 1.0)", "math.lgamma(v + 2.0)"),
+    "likelihood: sign of y ln z": (PY_SRC, "np.sum(z - ylogz + _lgamma1(y))", "np.sum(z + ylogz + _lgamma1(y))"),
     "chi3 without f_hat": (PY_SRC, "chi3 = f_hat * b2\n", "chi3 = b2\n"),
     "Lemma linear case": (PY_SRC, "lin = np.where(b > 0, c / b, np.inf)", "lin = np.where(b > 0, b / c, np.inf)"),
     "Huber quadratic half": (PY_SRC, "np.where(a <= delta, 0.5 * t * t,", "np.where(a <= delta, t * t,"),
