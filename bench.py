@@ -57,7 +57,8 @@ N_PHANTOMS = 10
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    # 500 steps of ~1.8 ms: the clock sampler (every 100 ms) sees the timed region ~9 times
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--path", default="table_fp32",
@@ -277,9 +278,11 @@ def run_reference(args):
     import oracle
     g = geometry(args.workload)
     phi, mask, f, w = cpu_inputs(g)
-    # per step a bounded sample (~1 s of CPU work) of one forward + adjoint
+    # per step a bounded sample of one forward + adjoint: ~1 s of CPU work, less when
+    # there are many steps, so that the whole run takes about two minutes at most
+    per_step = min(1.0, 120.0 / max(1, args.warmup + args.steps))
     probe, took, _, _ = oracle_eval_seconds(g, phi, mask, f, w, 16, 16, 1)
-    scale = max(1.0, 1.0 / max(took, 1e-3))
+    scale = max(1.0, per_step / max(took, 1e-3))
     n = int(min(g.M * g.N, 16 * scale))
     times = []
     for s in range(args.warmup + args.steps):
