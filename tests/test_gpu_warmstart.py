@@ -5,7 +5,6 @@ upsampling, autograd) with the same bf16 rounding of the convolution inputs as
 the tensor-core GEMMs; tolerances cover bf16 rounding of the backward operands
 (relative L2 <= 3e-2 for gradients) and FP32 accumulation elsewhere.
 """
-import math
 
 import numpy as np
 import pytest
