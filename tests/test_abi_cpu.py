@@ -147,7 +147,9 @@ def test_struct_layouts_match_the_header(tmp_path):
         pytest.skip("no C compiler")
     structs = {"caxsi_geometry": caxsi.CGeometry, "caxsi_plan_info_t": caxsi.CPlanInfo,
                "caxsi_kernel_stat": caxsi.CKernelStat}
-    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "caxsi.h"', "int main(void) {"]
+    # both public headers compile as plain C11, without CUDA headers
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "caxsi.h"', '#include "caxsi_nn.h"',
+             "int main(void) {"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for field, _ in cls._fields_:
@@ -156,7 +158,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines) + "\n")
     exe = tmp_path / "layout"
-    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    subprocess.run([cc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
     got = {}
     for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
         cname, field, value = ln.split()
