@@ -169,11 +169,32 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def kernel_work(name, g, info, path, nsm):
-    """Algorithmic work of one launch of the named kernel: (unit, amount, bound).
+def operator_alg_bytes(g):
+    """Algorithmic HBM bytes of one application of A (or of A^T): the object f (4 R Q B), the detector image (4 M N B) and the
+    per-offset geometry table streamed once (one 16-byte entry per scatter vector
+    (i, d, m), X M (N + rho_y (J - 1)) entries).  The design's own records and
+    knot rows are not counted: they are this implementation's choice of what to
+    precompute (the paper's online/offline trade-off), not the operator's need."""
+    nd = g.N + g.rho_y * (g.J - 1)
+    return 4.0 * g.X * g.J * g.Q + 4.0 * g.M * g.N + 16.0 * g.X * g.M * nd
 
-    The amounts are the minimum bytes or flops the kernel's job needs: 12-byte records, one table row
-    per voxel, partial images; 2 R B Q flop per product pass of a contraction."""
+
+def operator_alg_flops(g, open_pairs):
+    """The per-energy flop count of one application of A (or A^T) done by direct
+    summation (Algorithm 1 / 3): per open (voxel, pixel) pair, K energy terms of
+    8 flop plus 30 flop of scatter geometry."""
+    return open_pairs * (8.0 * g.K + 30.0)
+
+
+def kernel_work(name, g, info, path, nsm):
+    """Work of one launch of the named kernel on this design's basis: (unit,
+    amount, bound)  (the operator's own algorithmic bytes are operator_alg_bytes).
+
+    The amounts are the bytes or flops this design streams or issues: 12-byte
+    records, one knot-table row per voxel, partial images; 2 R B Q flop per
+    product pass of a contraction.  They are not the operator's algorithmic
+    bytes (operator_alg_bytes), which are far fewer: the records and knot rows
+    are precomputed state this design chose to stream."""
     open_pairs = info["n_open_pairs"]
     B = info["n_breakpoints"]
     Bp = (B + 1 + 7) // 8 * 8
@@ -209,6 +230,54 @@ def kernel_work(name, g, info, path, nsm):
         passes = 3 if name.endswith("3xtf32") else 1
         return "TFLOP/s", passes * 2.0 * R * B * g.Q, "tensor"
     return None, None, None
+
+
+def roofline_line(dom, avg_s, design, g, info, path, kernels, steps, peaks, peak_kind, nsm):
+    """The bench line's roofline object.  `frac` is on the operator's algorithmic
+    basis: for the table paths the operator's algorithmic HBM bytes (operator_alg_bytes)
+    over the dominant kernel's average launch time; for the direct path its FP32
+    flops over the FP32 SIMT peak (the two coincide with `design` there).  The
+    design's own basis is kept under `design`.  Per step (one A and one A^T) the
+    DRAM traffic of the step's kernels that have a current ncu figure is set
+    against the two operators' algorithmic bytes."""
+    hbm = float(peaks["hbm_gbs"])
+    if design["bound"] == "alu":
+        line = {"bound": "alu", "kernel": dom, "achieved": design["achieved"], "peak": design["peak"],
+                "unit": "TFLOP/s", "frac": design["frac"], "traffic": traffic_for(dom, path),
+                "peak_source": design["peak_source"],
+                "alg_work_per_launch": design["work_per_launch"],
+                "basis": "operator: K energy terms x 8 flop + 30 flop per open pair"}
+    else:
+        alg = operator_alg_bytes(g)
+        achieved = alg / avg_s / 1e9
+        line = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic_for(dom, path),
+                "peak_source": f"HBM copy bandwidth, {peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "alg_bytes": alg, "alg_frac": achieved / hbm,
+                "basis": "operator: f + detector image + per-offset geometry table of one application "
+                         "of A or A^T, over the dominant kernel's time"}
+    line["design"] = design
+    # per step: DRAM traffic of the step's kernels (ncu, current sources only) against 2 operators
+    step_traffic, covered = 0.0, []
+    for k, st in kernels.items():
+        t = traffic_for(k, path)
+        if t is not None:
+            step_traffic += t * st["launches"] / max(steps, 1)
+            covered.append(k)
+    if covered:
+        alg_step = 2.0 * operator_alg_bytes(g)
+        line["step"] = {"traffic_bytes": step_traffic, "alg_bytes": alg_step,
+                        "traffic_over_alg": step_traffic / alg_step, "kernels_with_traffic": sorted(covered)}
+    # the per-energy flops of A + A^T by direct summation over the step's kernel time: above the FP32
+    # SIMT peak when the path does not do the per-energy work (the table paths)
+    step_s = sum(st["total_ms"] for st in kernels.values()) / 1e3 / max(steps, 1)
+    if step_s > 0 and info.get("n_open_pairs"):
+        fp32 = nsm * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        eq = 2.0 * operator_alg_flops(g, info["n_open_pairs"]) / step_s / 1e12
+        line["alu_equivalent"] = {"tflops": eq, "fp32_simt_peak": fp32, "frac": eq / fp32,
+                                  "note": "per-energy flops of one A + one A^T by direct summation over the "
+                                          "step's kernel time; not work this path performs"}
+    return line
 
 
 def traffic_for(name, path):
@@ -735,10 +804,12 @@ def run_ours(args):
                 peak_note = (f"dense {'TF32 = bf16 / 2 (nominal ratio)' if tf32 else 'bf16/fp16'} from "
                              f"the {peak_kind} sustained bf16 GEMM rate")
                 achieved = work / avg_s / 1e12
-            roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
-                        "unit": unit, "frac": achieved / peak,
-                        "traffic": traffic_for(dom, args.path), "peak_source": peak_note,
-                        "work_per_launch": work}
+            design = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                      "frac": achieved / peak, "peak_source": peak_note, "work_per_launch": work,
+                      "basis": "the bytes / flops this design streams or issues per launch "
+                               "(records, knot-table rows, partial images; contraction passes)"}
+            roofline = roofline_line(dom, avg_s, design, g, info, args.path, kernels, args.steps, peaks,
+                                     peak_kind, nsm)
     launches = sum(n for n, _ in kstats.values())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

@@ -171,6 +171,22 @@ caxsi_status caxsi_recon_step(caxsi_plan *plan, const float *y_dev, const float 
  */
 #define CAXSI_MAX_SUBSETS 1024
 
+/* The symmetry-preserving partition of Sec. VI, as a map pixel -> subset for
+ * caxsi_plan_set_subsets.  Rows: the upper half of the detector (m < M/2) is
+ * split into rho_z classes of row step rho_z, and every row's mirror image about
+ * the centre line z = 0 (row M-1-m) joins its class.  Columns: classes of step
+ * sigma_y, every column's mirror image about y = 0 (column c -> sigma_y-1-c
+ * within the step) joining its class, so sigma_y / 2 column classes.  Subset of
+ * pixel (m, n) = row class * (sigma_y / 2) + column class; n_subsets =
+ * rho_z * sigma_y / 2.  sigma_y keeps the translation symmetry when it is a
+ * multiple of the translation step rho_y; sigma_y <= 0 picks rho_y when rho_y is
+ * even and 16 rho_y otherwise (the paper's example uses a column step of 16).
+ *   subset_of_pixel  host, M*N int32, written row-major in (m, n).
+ * Host only (no device work).  Errors: INVALID when the output is NULL, M is
+ * odd, rho_z does not divide M/2, or sigma_y is odd, does not divide N or is
+ * not a multiple of rho_y. */
+caxsi_status caxsi_os_partition(int M, int N, int rho_y, int rho_z, int sigma_y, int32_t *subset_of_pixel);
+
 /* Set (or replace) the partition.  subset_of_pixel: host, M*N int32 in
  * [0, n_subsets), row-major (m, n).  Synchronises the device first (work in
  * flight may still read the old partition), uploads the subsets' pixel lists,
@@ -236,19 +252,37 @@ caxsi_status caxsi_adjoint_batch(caxsi_plan *plan, int n_objects, const int32_t 
  * root with the Huber penalty of caxsi_recon_step) from f, b1 = A^T 1 and
  * b2 = A^T (y / z), elementwise with the 4-neighbour stencil; f_len is a multiple
  * of X*J*Q (objects of this geometry back to back, each with its own
- * neighbourhoods).  All pointers device, f_out must not alias f.
+ * neighbourhoods).  All pointers device; f_out must not overlap f (INVALID).
  * caxsi_em_update_vjp: the reverse mode of caxsi_em_update: given grad_out =
  * dL/df_out, writes grad_f = dL/df and grad_b2 = dL/db2 (b1 is treated as a
  * constant), by implicit differentiation of the root
  * ((2 chi1 x + chi2) dx = dchi3 - x dchi2 - x^2 dchi1) through the Huber terms
  * (derivatives taken one-sided at |f_j - f_k| = delta).  Used with A and A^T to
  * unroll the reconstruction under automatic differentiation; the paper has no
- * such step.  Errors: INVALID, CUDA, OOM. */
+ * such step.  grad_f and grad_b2 must not overlap each other or any input
+ * (INVALID).  Errors: INVALID, CUDA, OOM. */
 caxsi_status caxsi_em_update(caxsi_plan *plan, const float *f_dev, const float *b1_dev, const float *b2_dev,
                              float beta, float delta, float *f_out_dev, int64_t f_len, void *stream);
 caxsi_status caxsi_em_update_vjp(caxsi_plan *plan, const float *f_dev, const float *b1_dev,
                                  const float *b2_dev, float beta, float delta, const float *grad_out_dev,
                                  float *grad_f_dev, float *grad_b2_dev, int64_t f_len, void *stream);
+
+/* ---- The likelihood ratio as a differentiable function ------------------------
+ * caxsi_ratio: ratio = y / z with z = g + r (the ratio of Algorithm 4, whose
+ * adjoint gives b2), elementwise over n elements (any number of detector images
+ * back to back).  z > 0: y / z in FP32.  z <= 0: 0; if y > 0 there as well the
+ * plan's error word is set, and the next call of this plan that returns the
+ * likelihood (caxsi_recon_step with nll_out) reports CAXSI_ERR_NONPOS_MEAN.
+ * caxsi_ratio_vjp: its reverse mode with respect to g: grad_g = -grad_ratio y / z^2
+ * where z > 0, 0 elsewhere.  The paper has no reverse mode; it serves unrolled
+ * reconstructions under automatic differentiation.
+ *   g_dev, y_dev, grad_ratio_dev  device, n floats;  r_dev  device, n floats, or
+ *   NULL for r = 0;  ratio_dev / grad_g_dev  device, n floats, overwritten.
+ * Asynchronous on stream.  Errors: INVALID (NULL pointers, n < 1), CUDA. */
+caxsi_status caxsi_ratio(caxsi_plan *plan, const float *g_dev, const float *y_dev, const float *r_dev,
+                         float *ratio_dev, int64_t n, void *stream);
+caxsi_status caxsi_ratio_vjp(caxsi_plan *plan, const float *g_dev, const float *y_dev, const float *r_dev,
+                             const float *grad_ratio_dev, float *grad_g_dev, int64_t n, void *stream);
 
 /* Host-buffer forms: copy the input from host memory to plan-owned device
  * staging buffers, evaluate, copy the result back to host memory, and

@@ -7,7 +7,8 @@ reconstruction unrolled over a fixed number of iterations, optionally
 checkpointed per iteration (activations are recomputed in the backward pass
 instead of being kept), and differentiable with respect to its start and to
 per-iteration step scalings.  Operators and updates run in the library's
-kernels through the C ABI; the ratio y / z and the losses are elementwise glue.
+kernels through the C ABI, the likelihood ratio y / (A f + r) and its reverse
+mode included (caxsi_ratio, caxsi_ratio_vjp); only the losses are torch glue.
 A single object is f [X, J, Q]; a batch is f [nb, X, J, Q] with y [nb, M, N],
 each object a voxel range of the shared geometry.
 """
@@ -47,6 +48,10 @@ class Operator:
     def update(self, f, b1, b2, beta=0.0, delta=0.0):
         return _Update.apply(f.contiguous(), b1.contiguous(), b2.contiguous(), self, float(beta), float(delta))
 
+    def ratio(self, g, y, r=None):
+        """y / (g + r) (0 where g + r <= 0), differentiable with respect to g."""
+        return _Ratio.apply(g.contiguous(), y.contiguous(), None if r is None else r.contiguous(), self)
+
 
 class _Forward(torch.autograd.Function):
     @staticmethod
@@ -84,14 +89,22 @@ class _Update(torch.autograd.Function):
         return gf, None, gb2, None, None, None
 
 
+class _Ratio(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, g, y, r, op):
+        ctx.save_for_backward(g, y, r)
+        ctx.op = op
+        return op.plan.ratio(g, y, r)
+
+    @staticmethod
+    def backward(ctx, grad):
+        g, y, r = ctx.saved_tensors
+        return ctx.op.plan.ratio_vjp(g, y, grad.contiguous(), r), None, None, None
+
+
 def em_step(op: Operator, y, f, b1, r=None, beta=0.0, delta=0.0):
     """One EM-type iteration (Algorithm 4): z = A f + r, b2 = A^T (y / z), Eq. 10."""
-    z = op(f)
-    if r is not None:
-        z = z + r
-    pos = z > 0
-    ratio = torch.where(pos, y / torch.where(pos, z, torch.ones_like(z)), torch.zeros_like(z))
-    return op.update(f, b1, op.T(ratio), beta, delta)
+    return op.update(f, b1, op.T(op.ratio(op(f), y, r)), beta, delta)
 
 
 def unrolled_em(op: Operator, y, f0, n_iter: int = 10, r=None, beta=0.0, delta=0.0,

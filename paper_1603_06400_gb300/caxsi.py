@@ -129,6 +129,10 @@ def load():
             for name, at in nn.items():
                 getattr(lib, name).argtypes = at
                 getattr(lib, name).restype = ctypes.c_int
+            lib.caxsi_os_partition.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, I32P]
+            lib.caxsi_ratio.argtypes = [P, P, P, P, P, I64, P]
+            lib.caxsi_ratio_vjp.argtypes = [P, P, P, P, P, P, I64, P]
             lib.caxsi_status_string.argtypes = [ctypes.c_int]
             lib.caxsi_status_string.restype = ctypes.c_char_p
             for name in ("caxsi_plan_create", "caxsi_forward", "caxsi_adjoint",
@@ -136,7 +140,8 @@ def load():
                          "caxsi_plan_info", "caxsi_profile_enable", "caxsi_profile_read",
                          "caxsi_plan_set_subsets", "caxsi_forward_subset", "caxsi_adjoint_subset",
                          "caxsi_recon_step_subset", "caxsi_forward_batch", "caxsi_adjoint_batch",
-                         "caxsi_em_update", "caxsi_em_update_vjp"):
+                         "caxsi_em_update", "caxsi_em_update_vjp", "caxsi_os_partition", "caxsi_ratio",
+                         "caxsi_ratio_vjp"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -163,28 +168,20 @@ def _dev(t, n, name):
 
 def os_partition(M: int, N: int, rho_y: int, rho_z: int, sigma_y: int | None = None) -> np.ndarray:
     """Subset index of every detector pixel (int32 [M*N], row-major in (m, n)) for
-    the symmetry-preserving ordered-subset partition of Sec. VI.
-
-    Rows: the top half is split into rho_z classes of step rho_z, and each row's
-    mirror image about the centre line z = 0 joins its class.  Columns: classes of
-    step sigma_y, each joined by its mirror image about y = 0, so sigma_y / 2 column
-    classes.  sigma_y must be even, divide N, and be a multiple of the translation
-    step rho_y (so that translation symmetry is kept); it defaults to rho_y when
-    rho_y is even and to 16 * rho_y otherwise (the paper's example uses 16).
-    Subset index = row class * (sigma_y / 2) + column class.
-    """
-    if sigma_y is None:
-        sigma_y = rho_y if rho_y % 2 == 0 else 16 * rho_y
-    if M % 2 or (M // 2) % rho_z or rho_z < 1:
-        raise ValueError("rho_z must divide M / 2 (M even)")
-    if sigma_y < 2 or sigma_y % 2 or N % sigma_y or sigma_y % rho_y:
-        raise ValueError("sigma_y must be even, divide N and be a multiple of rho_y")
-    m = np.arange(M)
-    row_class = np.where(m < M // 2, m, M - 1 - m) % rho_z
-    n = np.arange(N) % sigma_y
-    col_class = np.minimum(n, sigma_y - 1 - n)
-    sub = row_class[:, None] * (sigma_y // 2) + col_class[None, :]
-    return np.ascontiguousarray(sub.reshape(-1), dtype=np.int32)
+    the symmetry-preserving ordered-subset partition of Sec. VI, computed by the
+    library (caxsi_os_partition: rows in rho_z classes joined with their up-down
+    mirrors, columns in sigma_y / 2 classes of step sigma_y joined with their
+    left-right mirrors).  sigma_y defaults to rho_y when rho_y is even and to
+    16 * rho_y otherwise.  Raises ValueError for steps the library rejects."""
+    out = np.empty(M * N, dtype=np.int32)
+    st = load().caxsi_os_partition(int(M), int(N), int(rho_y), int(rho_z),
+                                   0 if sigma_y is None else int(sigma_y),
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if st != 0:
+        raise ValueError(f"os_partition: M={M}, N={N}, rho_y={rho_y}, rho_z={rho_z}, sigma_y={sigma_y} "
+                         f"rejected ({STATUS.get(st, st)}): rho_z must divide M / 2 (M even), sigma_y must be "
+                         "even, divide N and be a multiple of rho_y")
+    return out
 
 
 class Plan:
@@ -356,6 +353,29 @@ class Plan:
                                             self._dev(gf, n, "grad_f"), self._dev(gb2, n, "grad_b2"), n,
                                             self._stream(stream)), "caxsi_em_update_vjp")
         return gf, gb2
+
+    # -- the likelihood ratio and its reverse mode ---------------------------------
+    def ratio(self, g, y, r=None, out=None, stream=None):
+        """y / (g + r) elementwise (0 where g + r <= 0); g, y, r of any equal size."""
+        import torch
+        n = g.numel()
+        if out is None:
+            out = torch.empty_like(g)
+        rp = self._dev(r, n, "r") if r is not None else ctypes.c_void_p(None)
+        _check(self.lib.caxsi_ratio(self.handle, self._dev(g, n, "g"), self._dev(y, n, "y"), rp,
+                                    self._dev(out, n, "ratio"), n, self._stream(stream)), "caxsi_ratio")
+        return out
+
+    def ratio_vjp(self, g, y, grad_ratio, r=None, stream=None):
+        """d(sum grad_ratio * ratio) / dg = -grad_ratio y / (g + r)^2 where g + r > 0."""
+        import torch
+        n = g.numel()
+        out = torch.empty_like(g)
+        rp = self._dev(r, n, "r") if r is not None else ctypes.c_void_p(None)
+        _check(self.lib.caxsi_ratio_vjp(self.handle, self._dev(g, n, "g"), self._dev(y, n, "y"), rp,
+                                        self._dev(grad_ratio, n, "grad_ratio"), self._dev(out, n, "grad_g"), n,
+                                        self._stream(stream)), "caxsi_ratio_vjp")
+        return out
 
     # -- host-buffer calls ----------------------------------------------------
     def forward_host(self, f, out=None, path=PATH_DIRECT):

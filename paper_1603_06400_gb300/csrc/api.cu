@@ -134,6 +134,13 @@ void drop_subset_sensitivities(caxsi_plan *p) {
 
 bool subset_ok(const caxsi_plan *p, int subset) { return subset >= 0 && subset < p->n_subsets; }
 
+// [a, a + n) and [b, b + n) (floats) share an element
+bool overlaps(const void *a, const void *b, int64_t n) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    const uintptr_t len = (uintptr_t)n * sizeof(float);
+    return x < y + len && y < x + len;
+}
+
 }  // namespace
 
 extern "C" {
@@ -398,6 +405,8 @@ caxsi_status caxsi_em_update(caxsi_plan *p, const float *f_dev, const float *b1_
     if (!p || !f_dev || !b1_dev || !b2_dev || !f_out_dev) return CAXSI_ERR_INVALID;
     const int64_t nf = (int64_t)p->dg.R * p->dg.Q;
     if (f_len < nf || f_len % nf) return CAXSI_ERR_INVALID;
+    // the update reads the neighbours of every element of f while writing f_out
+    if (overlaps(f_out_dev, f_dev, f_len)) return CAXSI_ERR_INVALID;
     if (!isfinite(beta) || beta < 0.f || !isfinite(delta) || delta < 0.f) return CAXSI_ERR_INVALID;
     DeviceGuard dg(p->device);
     if (!dg.ok) return CAXSI_ERR_CUDA;
@@ -412,12 +421,36 @@ caxsi_status caxsi_em_update_vjp(caxsi_plan *p, const float *f_dev, const float 
         return CAXSI_ERR_INVALID;
     const int64_t nf = (int64_t)p->dg.R * p->dg.Q;
     if (f_len < nf || f_len % nf) return CAXSI_ERR_INVALID;
+    // both passes read f, b1, b2 and grad_out (the second pass at the neighbours too)
+    // while writing grad_f and grad_b2
+    for (const float *out : {(const float *)grad_f_dev, (const float *)grad_b2_dev})
+        for (const float *in : {f_dev, b1_dev, b2_dev, grad_out_dev})
+            if (overlaps(out, in, f_len)) return CAXSI_ERR_INVALID;
+    if (overlaps(grad_f_dev, grad_b2_dev, f_len)) return CAXSI_ERR_INVALID;
     if (!isfinite(beta) || beta < 0.f || !isfinite(delta) || delta < 0.f) return CAXSI_ERR_INVALID;
     DeviceGuard dg(p->device);
     if (!dg.ok) return CAXSI_ERR_CUDA;
     p->launches = 0;
     return recon_update_vjp(p, f_dev, b1_dev, b2_dev, beta, delta, grad_out_dev, grad_f_dev, grad_b2_dev, f_len,
                             (cudaStream_t)stream);
+}
+
+caxsi_status caxsi_ratio(caxsi_plan *p, const float *g_dev, const float *y_dev, const float *r_dev,
+                         float *ratio_dev, int64_t n, void *stream) {
+    if (!p || !g_dev || !y_dev || !ratio_dev || n < 1) return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return CAXSI_ERR_CUDA;
+    p->launches = 0;
+    return recon_ratio_ext(p, g_dev, y_dev, r_dev, ratio_dev, n, (cudaStream_t)stream);
+}
+
+caxsi_status caxsi_ratio_vjp(caxsi_plan *p, const float *g_dev, const float *y_dev, const float *r_dev,
+                             const float *grad_ratio_dev, float *grad_g_dev, int64_t n, void *stream) {
+    if (!p || !g_dev || !y_dev || !grad_ratio_dev || !grad_g_dev || n < 1) return CAXSI_ERR_INVALID;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return CAXSI_ERR_CUDA;
+    p->launches = 0;
+    return recon_ratio_vjp(p, g_dev, y_dev, r_dev, grad_ratio_dev, grad_g_dev, n, (cudaStream_t)stream);
 }
 
 static caxsi_status host_call(caxsi_plan *p, const float *in_host, int64_t in_len, float *out_host,
@@ -553,6 +586,26 @@ caxsi_status caxsi_profile_read(caxsi_plan *p, caxsi_kernel_stat *out, int capac
     prof_clear(p);
     *count = n;
     return st;
+}
+
+caxsi_status caxsi_os_partition(int M, int N, int rho_y, int rho_z, int sigma_y, int32_t *subset_of_pixel) {
+    if (!subset_of_pixel || M < 2 || N < 1 || rho_y < 1 || rho_z < 1) return CAXSI_ERR_INVALID;
+    if (sigma_y <= 0) sigma_y = rho_y % 2 == 0 ? rho_y : 16 * rho_y;
+    // rows: the upper half in rho_z classes of step rho_z, each row's mirror image
+    // about z = 0 in its class; columns: classes of step sigma_y, each column's
+    // mirror image about y = 0 in its class (sigma_y / 2 column classes)
+    if (M % 2 || (M / 2) % rho_z) return CAXSI_ERR_INVALID;
+    if (sigma_y < 2 || sigma_y % 2 || N % sigma_y || sigma_y % rho_y) return CAXSI_ERR_INVALID;
+    const int cols = sigma_y / 2;
+    for (int m = 0; m < M; ++m) {
+        const int row_class = (m < M / 2 ? m : M - 1 - m) % rho_z;
+        for (int n = 0; n < N; ++n) {
+            const int c = n % sigma_y;
+            const int col_class = c < sigma_y - 1 - c ? c : sigma_y - 1 - c;
+            subset_of_pixel[(int64_t)m * N + n] = row_class * cols + col_class;
+        }
+    }
+    return CAXSI_OK;
 }
 
 const char *caxsi_status_string(caxsi_status s) {

@@ -148,6 +148,11 @@ caxsi_status recon_nll_fetch(caxsi_plan *p, double *out, cudaStream_t s);
 // n = nobj * R * Q elements (objects back to back)
 caxsi_status recon_update_ext(caxsi_plan *p, const float *f, const float *b1, const float *b2, float beta,
                               float delta, float *out, int64_t n, cudaStream_t s);
+// ratio = y / (g + r) over n elements of caller buffers, and its reverse mode
+caxsi_status recon_ratio_ext(caxsi_plan *p, const float *g, const float *y, const float *r, float *ratio, int64_t n,
+                             cudaStream_t s);
+caxsi_status recon_ratio_vjp(caxsi_plan *p, const float *g, const float *y, const float *r, const float *gr,
+                             float *gg, int64_t n, cudaStream_t s);
 caxsi_status recon_update_vjp(caxsi_plan *p, const float *f, const float *b1, const float *b2, float beta,
                               float delta, const float *gx, float *gf, float *gb2, int64_t n, cudaStream_t s);
 

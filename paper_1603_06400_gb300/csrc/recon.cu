@@ -89,6 +89,32 @@ __global__ void k_ratio(const float *__restrict__ g, const float *__restrict__ y
     }
 }
 
+// The ratio y / (g + r) over n elements of caller buffers (any number of
+// detector images back to back), with the edge rules of k_ratio, and its
+// reverse mode: d ratio / d g = -y / z^2 = -(y / z) / z where z > 0, 0 elsewhere
+// (the ratio is 0 there whatever g is).
+__global__ void k_ratio_ext(const float *__restrict__ g, const float *__restrict__ y, const float *__restrict__ r,
+                            float *__restrict__ ratio, int *err, int64_t n) {
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const float z = r ? g[idx] + r[idx] : g[idx];
+        const float yy = y[idx];
+        float rt = 0.f;
+        if (z > 0.f) rt = yy / z;
+        else if (yy > 0.f) *err = 1;
+        ratio[idx] = rt;
+    }
+}
+
+__global__ void k_ratio_vjp(const float *__restrict__ g, const float *__restrict__ y, const float *__restrict__ r,
+                            const float *__restrict__ gr, float *__restrict__ gg, int64_t n) {
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const float z = r ? g[idx] + r[idx] : g[idx];
+        gg[idx] = z > 0.f ? -(gr[idx] * (y[idx] / z)) / z : 0.f;
+    }
+}
+
 // chi1 = beta (b3 + b4), chi2 = b1 + beta (-f (b3 + b4) + b5 + b6), chi3 = f b2,
 // b3 = b4 = 2 sum_k omega(f_j - f_k), b5 = b6 = sum_k psi_dot(f_j - f_k) over the
 // 4 spatial neighbours (symmetric neighbourhood, unit weights); the update is
@@ -418,6 +444,29 @@ caxsi_status recon_update_vjp(caxsi_plan *p, const float *f, const float *b1, co
     {
         CAXSI_PROF(p, "em_update_vjp2", s);
         k_update_vjp2<<<nb, 256, 0, s>>>(p->dg, f, delta, gb3, gb5, gf, n);
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    return CAXSI_OK;
+}
+
+caxsi_status recon_ratio_ext(caxsi_plan *p, const float *g, const float *y, const float *r, float *ratio, int64_t n,
+                             cudaStream_t s) {
+    const int64_t nb = ceil_div64(n, 256);
+    {
+        CAXSI_PROF(p, "ratio", s);
+        k_ratio_ext<<<(unsigned)(nb < 4 * p->num_sms ? nb : 4 * p->num_sms), 256, 0, s>>>(g, y, r, ratio,
+                                                                                        p->err_flag, n);
+    }
+    CAXSI_LAUNCH_CHECK(p);
+    return CAXSI_OK;
+}
+
+caxsi_status recon_ratio_vjp(caxsi_plan *p, const float *g, const float *y, const float *r, const float *gr,
+                             float *gg, int64_t n, cudaStream_t s) {
+    const int64_t nb = ceil_div64(n, 256);
+    {
+        CAXSI_PROF(p, "ratio_vjp", s);
+        k_ratio_vjp<<<(unsigned)(nb < 4 * p->num_sms ? nb : 4 * p->num_sms), 256, 0, s>>>(g, y, r, gr, gg, n);
     }
     CAXSI_LAUNCH_CHECK(p);
     return CAXSI_OK;

@@ -73,6 +73,61 @@ def test_direct_kernels_are_alu_bound(paper):
     assert bench.kernel_work("no_such_kernel", g, info, "direct", NSM) == (None, None, None)
 
 
+def test_operator_algorithmic_bytes_and_flops(paper):
+    g, _ = paper
+    # f (128 x 256 voxels x 128 q) + detector image (64 x 256) + one 16-byte entry per
+    # scatter vector (i, d, m): 128 x 64 x (256 + 255) entries
+    alg = bench.operator_alg_bytes(g)
+    assert alg == 4 * 128 * 256 * 128 + 4 * 64 * 256 + 16 * 128 * 64 * 511
+    assert alg == pytest.approx(83.86e6, rel=1e-3)
+    # K = 64 energy terms of 8 flop + 30 flop of geometry per open pair
+    assert bench.operator_alg_flops(g, 10) == 10 * (8 * 64 + 30)
+
+
+def test_roofline_line_uses_the_operator_basis(paper, monkeypatch):
+    g, info = paper
+    info = dict(info, n_open_pairs=268_435_456)
+    peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
+    monkeypatch.setattr(bench, "traffic_for", lambda name, path: {"sym_pairs_adj": 2.5e9, "sym_pairs_fwd": 2.5e9}.get(name))
+    _, work, bound = bench.kernel_work("sym_pairs_adj", g, info, "table_fp32", NSM)
+    avg_s = 0.73e-3
+    design = {"bound": bound, "achieved": work / avg_s / 1e9, "peak": 6800.0, "unit": "GB/s",
+              "frac": work / avg_s / 1e9 / 6800.0, "peak_source": "x", "work_per_launch": work}
+    kernels = {"sym_pairs_adj": {"launches": 10, "total_ms": 7.3, "avg_ms": 0.73},
+               "sym_pairs_fwd": {"launches": 10, "total_ms": 4.0, "avg_ms": 0.40},
+               "tc_gemm_adj_3xtf32": {"launches": 10, "total_ms": 3.3, "avg_ms": 0.33}}
+    line = bench.roofline_line("sym_pairs_adj", avg_s, design, g, info, "table_fp32", kernels, 10, peaks,
+                               "measured", NSM)
+    alg = bench.operator_alg_bytes(g)
+    assert line["bound"] == "hbm" and line["unit"] == "GB/s"
+    assert line["alg_bytes"] == alg
+    assert line["achieved"] == pytest.approx(alg / avg_s / 1e9)
+    assert line["frac"] == pytest.approx(alg / avg_s / 1e9 / 6800.0)
+    assert line["frac"] == pytest.approx(0.0169, rel=1e-2)       # 84 MB in 0.73 ms of 6.8 TB/s
+    assert line["design"]["frac"] == pytest.approx(0.522, rel=1e-2)
+    # per step: the traffic of the two kernels with a figure against two operator applications
+    assert line["step"]["traffic_bytes"] == pytest.approx(5.0e9)
+    assert line["step"]["traffic_over_alg"] == pytest.approx(5.0e9 / (2 * alg))
+    assert line["step"]["kernels_with_traffic"] == ["sym_pairs_adj", "sym_pairs_fwd"]
+    # the per-energy flops of A + A^T over the 1.46 ms step of kernels
+    eq = 2 * bench.operator_alg_flops(g, info["n_open_pairs"]) / 1.46e-3 / 1e12
+    assert line["alu_equivalent"]["tflops"] == pytest.approx(eq)
+    assert line["alu_equivalent"]["fp32_simt_peak"] == pytest.approx(NSM * 128 * 2 * 2070e6 / 1e12)
+
+
+def test_direct_path_roofline_is_its_flops(paper, monkeypatch):
+    g, info = paper
+    info = dict(info, n_open_pairs=1000)
+    monkeypatch.setattr(bench, "traffic_for", lambda name, path: None)
+    design = {"bound": "alu", "achieved": 8.0, "peak": 80.5, "unit": "TFLOP/s", "frac": 8.0 / 80.5,
+              "peak_source": "x", "work_per_launch": 5.42e5}
+    kernels = {"adj_direct": {"launches": 1, "total_ms": 38.0, "avg_ms": 38.0}}
+    line = bench.roofline_line("adj_direct", 0.038, design, g, info, "direct", kernels, 1,
+                               {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "measured", NSM)
+    assert line["bound"] == "alu" and line["frac"] == design["frac"]
+    assert "step" not in line
+
+
 def test_traffic_dropped_when_the_source_changes(tmp_path, monkeypatch):
     src_dir = tmp_path / "paper_1603_06400_gb300" / "csrc"
     src_dir.mkdir(parents=True)

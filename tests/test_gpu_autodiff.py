@@ -8,6 +8,8 @@
   finite differences of the same functions evaluated by the oracle, on a
   16 x 16 x 16 object.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -259,4 +261,72 @@ def test_checkpointing_lowers_peak_memory(cx, tiny):
     # without checkpointing each iteration keeps its input and A^T(ratio) (two
     # object-sized tensors); with it, only its input
     assert peaks[True] < 0.75 * peaks[False], peaks
+    plan.close()
+
+
+def test_ratio_and_its_reverse_mode(cx, tiny):
+    """caxsi_ratio / caxsi_ratio_vjp against the definitions in FP64, with the edge
+    rules: z <= 0 gives ratio 0 and derivative 0; a positive count there sets the
+    error word that the next likelihood call reports."""
+    caxsi, _, torch = cx
+    g, phi, mask = tiny
+    plan = caxsi.Plan(g, phi, mask)
+    n = 3 * g.M * g.N + 5      # any length: images back to back and a ragged tail
+    rng = np.random.default_rng(3)
+    gg = rng.uniform(0.1, 4.0, n).astype(np.float32)
+    y = rng.poisson(3.0, n).astype(np.float32)
+    r = rng.uniform(0.0, 0.5, n).astype(np.float32)
+    gg[:7] = [0.0, -1.0, 0.0, -0.5, 2.0, 0.0, -0.25]
+    r[:7] = [0.0, 0.5, 0.0, 0.0, 0.0, 0.0, 0.0]
+    y[:7] = [0.0, 0.0, 0.0, 0.0, 5.0, 0.0, 0.0]
+    gr = rng.normal(size=n).astype(np.float32)
+    for rr in (None, r):
+        z = gg.astype(np.float64) + (0.0 if rr is None else rr.astype(np.float64))
+        want = np.where(z > 0, y / np.where(z > 0, z, 1.0), 0.0)
+        dwant = np.where(z > 0, -gr * y / np.where(z > 0, z, 1.0) ** 2, 0.0)
+        rt = None if rr is None else _t(torch, rr)
+        got = plan.ratio(_t(torch, gg), _t(torch, y), rt).double().cpu().numpy()
+        dgot = plan.ratio_vjp(_t(torch, gg), _t(torch, y), _t(torch, gr), rt).double().cpu().numpy()
+        np.testing.assert_allclose(got, want, rtol=2e-7, atol=0)
+        np.testing.assert_allclose(dgot, dwant, rtol=1e-6, atol=0)
+        assert np.all(got[z <= 0] == 0) and np.all(dgot[z <= 0] == 0)
+    # no positive count met z <= 0 so far: a likelihood call succeeds
+    zero_counts = torch.zeros((g.M, g.N), device="cuda:0")    # no count can meet z <= 0
+    f = torch.full((g.X, g.J, g.Q), 0.1, device="cuda:0")
+    plan.recon_step(zero_counts, f.clone(), want_nll=True)
+    bad_y = y.copy()
+    bad_y[1] = 2.0          # z = -1 + 0.5 < 0 with a positive count
+    plan.ratio(_t(torch, gg), _t(torch, bad_y), _t(torch, r))
+    with pytest.raises(caxsi.CaxsiError) as e:
+        plan.recon_step(zero_counts, f.clone(), want_nll=True)
+    assert e.value.status == 4
+    plan.recon_step(zero_counts, f.clone(), want_nll=True)     # the word is cleared once reported
+    plan.close()
+
+
+def test_update_rejects_overlapping_outputs(cx):
+    caxsi, _, torch = cx
+    g = geom16()
+    plan = caxsi.Plan(g, synth.tungsten_spectrum(g), synth.random_mask(g, 5))
+    shape = (g.X, g.J, g.Q)
+    f, b1, b2, c = (torch.rand(shape, device="cuda:0") + 0.5 for _ in range(4))
+    with pytest.raises(caxsi.CaxsiError) as e:
+        plan.em_update(f, b1, b2, 0.1, 0.1, out=f)          # in place
+    assert e.value.status == 1
+    # a buffer that overlaps f by one element
+    big = torch.rand(2 * f.numel(), device="cuda:0") + 0.5
+    fa, fb = big[: f.numel()].view(shape), big[f.numel() - 1: 2 * f.numel() - 1].view(shape)
+    with pytest.raises(caxsi.CaxsiError):
+        plan.em_update(fa, b1, b2, 0.1, 0.1, out=fb)
+    lib, P = plan.lib, ctypes.c_void_p
+    n = f.numel()
+    # reverse mode: grad_f on top of an input or of grad_b2
+    for gf_t, gb_t in ((f, c.clone()), (c.clone(), b2), (b1.clone(), None)):
+        gb_t = gf_t if gb_t is None else gb_t
+        st = lib.caxsi_em_update_vjp(plan.handle, P(f.data_ptr()), P(b1.data_ptr()), P(b2.data_ptr()), 0.1, 0.1,
+                                     P(c.data_ptr()), P(gf_t.data_ptr()), P(gb_t.data_ptr()), n, None)
+        assert st == 1
+    # disjoint buffers are accepted and give the same result as before
+    out = plan.em_update(f, b1, b2, 0.1, 0.1)
+    assert torch.isfinite(out).all()
     plan.close()
