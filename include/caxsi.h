@@ -247,6 +247,55 @@ caxsi_status caxsi_adjoint_batch(caxsi_plan *plan, int n_objects, const int32_t 
                                  const float *w_dev, int64_t w_len, float *f_dev, int64_t f_len, int path,
                                  void *stream);
 
+/* ---- Objects of different geometries in one launch -----------------------------
+ * A multi-object set groups n_objects plans, each with its own geometry (object
+ * extents X, J, Q, detector, spectrum, mask), so that the forward model or the
+ * adjoint of every object runs in ONE persistent kernel launch: the launch's
+ * blocks (forward) or warps (adjoint) take work items -- an object's voxel chunk
+ * and 8 x 32 detector tile for A, an object's voxel and detector row range for
+ * A^T, the units of the single-plan direct kernels -- from an atomic counter
+ * until none is left (no waits: a pop never polls), and the item that completes
+ * an output region sums its partial results in ascending order.  Each object's
+ * result is bit-identical to caxsi_forward / caxsi_adjoint on its own plan with
+ * CAXSI_PATH_DIRECT, whatever the order the items ran in.  The paper evaluates
+ * one object at a time; the set serves batched and differentiable
+ * reconstruction of objects of uneven sizes (training data, unrolled
+ * iterations).
+ *
+ * Packed layouts: object b's f is the X_b*J_b*Q_b floats ([X_b][J_b][Q_b]) at
+ * offset F_b = sum_{c<b} X_c J_c Q_c of f_dev, its detector image the M_b*N_b
+ * floats at offset G_b = sum_{c<b} M_c N_c of g_dev / w_dev (caxsi_multi_layout
+ * returns F_0..F_n and G_0..G_n).
+ *
+ * The set refers to the plans (it does not own them) and uses their scratch:
+ * destroy it before them, and order its calls with the plans' own calls.  All
+ * plans must be on one device.  Errors: INVALID (NULL, lengths, plans on
+ * different devices, n_objects outside [1, CAXSI_MAX_MULTI]), UNSUPPORTED (a
+ * path other than CAXSI_PATH_DIRECT; shared memory too small for the largest
+ * K and Q), CUDA, OOM. */
+#define CAXSI_MAX_MULTI 4096
+typedef struct caxsi_multi caxsi_multi;
+caxsi_status caxsi_multi_create(caxsi_plan *const *plans, int n_objects, caxsi_multi **out);
+void caxsi_multi_destroy(caxsi_multi *multi);
+/* f_offsets, g_offsets: host arrays of n_objects + 1 entries, filled with F_b, G_b. */
+caxsi_status caxsi_multi_layout(const caxsi_multi *multi, int64_t *f_offsets, int64_t *g_offsets);
+/* g = A f for every object (f_len = F_n, g_len = G_n); one launch.  Asynchronous. */
+caxsi_status caxsi_multi_forward(caxsi_multi *multi, const float *f_dev, int64_t f_len, float *g_dev,
+                                 int64_t g_len, int path, void *stream);
+/* f = A^T w for every object (w_len = G_n, f_len = F_n); one launch.  Asynchronous. */
+caxsi_status caxsi_multi_adjoint(caxsi_multi *multi, const float *w_dev, int64_t w_len, float *f_dev,
+                                 int64_t f_len, int path, void *stream);
+/* The update of Eq. 10 (as caxsi_em_update) for every object with its own
+ * geometry and neighbourhoods, f_len = F_n, one launch; and its reverse mode (as
+ * caxsi_em_update_vjp), two launches.  Outputs must not overlap inputs (INVALID). */
+caxsi_status caxsi_multi_em_update(caxsi_multi *multi, const float *f_dev, const float *b1_dev,
+                                   const float *b2_dev, float beta, float delta, float *f_out_dev,
+                                   int64_t f_len, void *stream);
+caxsi_status caxsi_multi_em_update_vjp(caxsi_multi *multi, const float *f_dev, const float *b1_dev,
+                                       const float *b2_dev, float beta, float delta,
+                                       const float *grad_out_dev, float *grad_f_dev, float *grad_b2_dev,
+                                       int64_t f_len, void *stream);
+
 /* ---- The update step as a differentiable function ------------------------------
  * caxsi_em_update: f_out = the closed-form update of Eq. 10 (the Lemma's positive
  * root with the Huber penalty of caxsi_recon_step) from f, b1 = A^T 1 and

@@ -10,7 +10,8 @@ per-iteration step scalings.  Operators and updates run in the library's
 kernels through the C ABI, the likelihood ratio y / (A f + r) and its reverse
 mode included (caxsi_ratio, caxsi_ratio_vjp); only the losses are torch glue.
 A single object is f [X, J, Q]; a batch is f [nb, X, J, Q] with y [nb, M, N],
-each object a voxel range of the shared geometry.
+each object a voxel range of the shared geometry; objects of different
+geometries (MultiOperator over a caxsi.Multi set) are packed flat arrays.
 """
 from __future__ import annotations
 
@@ -48,9 +49,45 @@ class Operator:
     def update(self, f, b1, b2, beta=0.0, delta=0.0):
         return _Update.apply(f.contiguous(), b1.contiguous(), b2.contiguous(), self, float(beta), float(delta))
 
+    def _em_update(self, f, b1, b2, beta, delta):
+        return self.plan.em_update(f, b1, b2, beta, delta)
+
+    def _em_update_vjp(self, f, b1, b2, g, beta, delta):
+        return self.plan.em_update_vjp(f, b1, b2, g, beta, delta)
+
     def ratio(self, g, y, r=None):
         """y / (g + r) (0 where g + r <= 0), differentiable with respect to g."""
         return _Ratio.apply(g.contiguous(), y.contiguous(), None if r is None else r.contiguous(), self)
+
+
+class MultiOperator:
+    """The operator of a caxsi.Multi set (objects of different geometries, packed
+    flat arrays) with the interface of Operator, so that em_step and unrolled_em
+    run on it: A, A^T and the update each one launch for all objects."""
+
+    def __init__(self, multi: "caxsi.Multi"):
+        self.multi = multi
+        self.plan = multi.plans[0]      # the ratio kernel's device and error word
+        self.path = caxsi.PATH_DIRECT
+
+    def _fwd(self, f):
+        return self.multi.forward(f, path=self.path)
+
+    def _adj(self, w):
+        return self.multi.adjoint(w, path=self.path)
+
+    __call__ = Operator.__call__
+    T = Operator.T
+    ratio = Operator.ratio
+
+    def update(self, f, b1, b2, beta=0.0, delta=0.0):
+        return _Update.apply(f.contiguous(), b1.contiguous(), b2.contiguous(), self, float(beta), float(delta))
+
+    def _em_update(self, f, b1, b2, beta, delta):
+        return self.multi.em_update(f, b1, b2, beta, delta)
+
+    def _em_update_vjp(self, f, b1, b2, g, beta, delta):
+        return self.multi.em_update_vjp(f, b1, b2, g, beta, delta)
 
 
 class _Forward(torch.autograd.Function):
@@ -80,12 +117,12 @@ class _Update(torch.autograd.Function):
     def forward(ctx, f, b1, b2, op, beta, delta):
         ctx.save_for_backward(f, b1, b2)
         ctx.op, ctx.beta, ctx.delta = op, beta, delta
-        return op.plan.em_update(f, b1, b2, beta, delta)
+        return op._em_update(f, b1, b2, beta, delta)
 
     @staticmethod
     def backward(ctx, g):
         f, b1, b2 = ctx.saved_tensors
-        gf, gb2 = ctx.op.plan.em_update_vjp(f, b1, b2, g.contiguous(), ctx.beta, ctx.delta)
+        gf, gb2 = ctx.op._em_update_vjp(f, b1, b2, g.contiguous(), ctx.beta, ctx.delta)
         return gf, None, gb2, None, None, None
 
 

@@ -133,6 +133,15 @@ def load():
                                                ctypes.c_int, I32P]
             lib.caxsi_ratio.argtypes = [P, P, P, P, P, I64, P]
             lib.caxsi_ratio_vjp.argtypes = [P, P, P, P, P, P, I64, P]
+            I64P = ctypes.POINTER(ctypes.c_int64)
+            lib.caxsi_multi_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P)]
+            lib.caxsi_multi_destroy.argtypes = [P]
+            lib.caxsi_multi_destroy.restype = None
+            lib.caxsi_multi_layout.argtypes = [P, I64P, I64P]
+            lib.caxsi_multi_forward.argtypes = [P, P, I64, P, I64, ctypes.c_int, P]
+            lib.caxsi_multi_adjoint.argtypes = [P, P, I64, P, I64, ctypes.c_int, P]
+            lib.caxsi_multi_em_update.argtypes = [P, P, P, P, ctypes.c_float, ctypes.c_float, P, I64, P]
+            lib.caxsi_multi_em_update_vjp.argtypes = [P, P, P, P, ctypes.c_float, ctypes.c_float, P, P, P, I64, P]
             lib.caxsi_status_string.argtypes = [ctypes.c_int]
             lib.caxsi_status_string.restype = ctypes.c_char_p
             for name in ("caxsi_plan_create", "caxsi_forward", "caxsi_adjoint",
@@ -141,7 +150,8 @@ def load():
                          "caxsi_plan_set_subsets", "caxsi_forward_subset", "caxsi_adjoint_subset",
                          "caxsi_recon_step_subset", "caxsi_forward_batch", "caxsi_adjoint_batch",
                          "caxsi_em_update", "caxsi_em_update_vjp", "caxsi_os_partition", "caxsi_ratio",
-                         "caxsi_ratio_vjp"):
+                         "caxsi_ratio_vjp", "caxsi_multi_create", "caxsi_multi_layout", "caxsi_multi_forward",
+                         "caxsi_multi_adjoint", "caxsi_multi_em_update", "caxsi_multi_em_update_vjp"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -442,6 +452,107 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             self.lib.caxsi_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Multi:
+    """Objects of different geometries, one Plan each, whose forward models and
+    adjoints run as one persistent kernel launch per call (caxsi_multi_*, direct
+    FP32 path).  Arrays are packed: object b's f occupies f_offsets[b] ..
+    f_offsets[b+1] of a flat float32 tensor, its detector image g_offsets[b] ..
+    g_offsets[b+1].  Each object's result is bit-identical to its own plan's call."""
+
+    def __init__(self, plans):
+        self.lib = load()
+        self.plans = list(plans)
+        n = len(self.plans)
+        arr = (ctypes.c_void_p * n)(*[p.handle.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(self.lib.caxsi_multi_create(arr, n, ctypes.byref(h)), "caxsi_multi_create")
+        self.handle = h
+        fo = np.zeros(n + 1, np.int64)
+        go = np.zeros(n + 1, np.int64)
+        I64P = ctypes.POINTER(ctypes.c_int64)
+        _check(self.lib.caxsi_multi_layout(self.handle, fo.ctypes.data_as(I64P), go.ctypes.data_as(I64P)),
+               "caxsi_multi_layout")
+        self.f_offsets, self.g_offsets = fo, go
+        self.f_len, self.g_len = int(fo[-1]), int(go[-1])
+        self.device = self.plans[0].device
+
+    def _dev(self, t, n, name):
+        ptr = _dev(t, n, name)
+        if t.device.index != self.device:
+            raise ValueError(f"{name} is on {t.device}, the plans on cuda:{self.device}")
+        return ptr
+
+    def _stream(self, stream):
+        return self.plans[0]._stream(stream)
+
+    # packing helpers (views, no arithmetic)
+    def pack_f(self, objs):
+        import torch
+        return torch.cat([o.reshape(-1) for o in objs]).contiguous()
+
+    def pack_g(self, imgs):
+        import torch
+        return torch.cat([o.reshape(-1) for o in imgs]).contiguous()
+
+    def unpack_f(self, flat):
+        return [flat[self.f_offsets[b]:self.f_offsets[b + 1]].view(p.X, p.J, p.Q)
+                for b, p in enumerate(self.plans)]
+
+    def unpack_g(self, flat):
+        return [flat[self.g_offsets[b]:self.g_offsets[b + 1]].view(p.M, p.N) for b, p in enumerate(self.plans)]
+
+    def forward(self, f, out=None, path=PATH_DIRECT, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.g_len, device=f.device, dtype=torch.float32)
+        _check(self.lib.caxsi_multi_forward(self.handle, self._dev(f, self.f_len, "f"), self.f_len,
+                                            self._dev(out, self.g_len, "g"), self.g_len, int(path),
+                                            self._stream(stream)), "caxsi_multi_forward")
+        return out
+
+    def adjoint(self, w, out=None, path=PATH_DIRECT, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.f_len, device=w.device, dtype=torch.float32)
+        _check(self.lib.caxsi_multi_adjoint(self.handle, self._dev(w, self.g_len, "w"), self.g_len,
+                                            self._dev(out, self.f_len, "f"), self.f_len, int(path),
+                                            self._stream(stream)), "caxsi_multi_adjoint")
+        return out
+
+    def em_update(self, f, b1, b2, beta=0.0, delta=0.0, out=None, stream=None):
+        import torch
+        n = self.f_len
+        if out is None:
+            out = torch.empty_like(f)
+        _check(self.lib.caxsi_multi_em_update(self.handle, self._dev(f, n, "f"), self._dev(b1, n, "b1"),
+                                              self._dev(b2, n, "b2"), float(beta), float(delta),
+                                              self._dev(out, n, "out"), n, self._stream(stream)),
+               "caxsi_multi_em_update")
+        return out
+
+    def em_update_vjp(self, f, b1, b2, grad_out, beta=0.0, delta=0.0, stream=None):
+        import torch
+        n = self.f_len
+        gf, gb2 = torch.empty_like(f), torch.empty_like(f)
+        _check(self.lib.caxsi_multi_em_update_vjp(self.handle, self._dev(f, n, "f"), self._dev(b1, n, "b1"),
+                                                  self._dev(b2, n, "b2"), float(beta), float(delta),
+                                                  self._dev(grad_out, n, "grad_out"), self._dev(gf, n, "grad_f"),
+                                                  self._dev(gb2, n, "grad_b2"), n, self._stream(stream)),
+               "caxsi_multi_em_update_vjp")
+        return gf, gb2
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.caxsi_multi_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

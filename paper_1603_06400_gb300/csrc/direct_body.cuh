@@ -1,0 +1,188 @@
+// Per-pair work of the direct (matrix-free, FP32) forward and adjoint, shared
+// by the single-plan kernels (direct.cu) and the persistent multi-object kernels
+// (multi.cu), so that both evaluate every object with the same arithmetic in
+// the same order.  See direct.cu for the structure of the two operators.
+#pragma once
+
+#include "internal.cuh"
+#include "pairgeo.cuh"
+
+namespace direct_impl {
+
+constexpr int FWD_WARPS = 8;
+constexpr int FWD_THREADS = FWD_WARPS * 32;
+constexpr int FWD_VS = 32;  // voxels staged per shared-memory round
+constexpr int ADJ_WARPS = 4;
+
+struct Tables {
+    DevGeo g;
+    const float4 *vox;
+    const float *zrow;
+    const float *god;
+    const uint32_t *tbits;
+    const float2 *energy;
+};
+
+
+// One block's work of the forward: detector tile bx (or listed pixels bx * 256 ..)
+// and voxel chunk by, written to partial image by.  Shared by the single-plan
+// kernel (bx, by = the block index) and the persistent multi-object kernel.
+template <bool LIST>
+__device__ __forceinline__ void fwd_direct_body(const Tables &T, const float *__restrict__ f,
+                                                float *__restrict__ part, int vc, int tiles_n,
+                                                const int *__restrict__ list, int np, int bx, int by,
+                                                unsigned char *smem_raw) {
+    const DevGeo &g = T.g;
+    const int QP = g.Q + 2;
+    float2 *s_en = reinterpret_cast<float2 *>(smem_raw);
+    float4 *s_vox = reinterpret_cast<float4 *>(s_en + ((g.K + 1) & ~1));
+    float2 *s_f = reinterpret_cast<float2 *>(s_vox + FWD_VS);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int m, n, e = 0;
+    bool valid;
+    if (LIST) {   // listed pixel e
+        e = bx * FWD_THREADS + tid;
+        valid = e < np;
+        const int p = valid ? list[e] : 0;
+        m = p / g.N;
+        n = p - m * g.N;
+    } else {      // 8 x 32 tile of the detector
+        const int tm = bx / tiles_n, tn = bx % tiles_n;
+        m = tm * FWD_WARPS + warp;
+        n = tn * 32 + lane;
+        valid = (m < g.M) && (n < g.N);
+    }
+    const int v0 = by * vc;
+    const int v1 = min(v0 + vc, g.R);
+
+    for (int k = tid; k < g.K; k += FWD_THREADS) s_en[k] = T.energy[k];
+    const float Npix = (float)n - g.cN;
+    const float sz = valid ? T.zrow[m] : 0.f;
+    const int wsel = n >> 5, bsel = n & 31;
+    float acc = 0.f;
+
+    for (int vb = v0; vb < v1; vb += FWD_VS) {
+        const int nv = min(FWD_VS, v1 - vb);
+        __syncthreads();
+        for (int idx = tid; idx < nv * QP; idx += FWD_THREADS) {
+            const int vv = idx / QP, lp = idx - vv * QP;
+            const float *row = f + (int64_t)(vb + vv) * g.Q;
+            const float F0 = (lp >= 1 && lp <= g.Q) ? row[lp - 1] : 0.f;
+            const float F1 = (lp + 1 <= g.Q) ? row[lp] : 0.f;
+            s_f[idx] = make_float2(F0, F1 - F0);
+        }
+        if (tid < nv) s_vox[tid] = T.vox[vb + tid];
+        __syncthreads();
+        if (!valid) continue;
+        for (int vv = 0; vv < nv; ++vv) {
+            const int v = vb + vv;
+            const uint32_t word = T.tbits[((int64_t)v * g.M + m) * g.Nw + wsel];
+            if (!((word >> bsel) & 1u)) continue;
+            const int i = v / g.J, j = v - i * g.J;
+            const float4 vx = s_vox[vv];
+            float u, ang;
+            pair_u_angular(vx.x, vx.y, vx.w, Npix, sz, g.p_y, g.Xd, u, ang);
+            const float gd = T.god[((int64_t)i * g.M + m) * g.ND + (n - g.rho_y * j - g.d_min)];
+            const float2 *fr = s_f + vv * QP;
+            float e_acc = 0.f;
+#pragma unroll 8
+            for (int k = 0; k < g.K; ++k) {
+                const float2 ak = s_en[k];
+                float tau = fmaf(ak.x, u, -g.b);
+                tau = fminf(fmaxf(tau, -1.f), g.Qf);
+                const float fl = floorf(tau);
+                const float al = tau - fl;
+                const float2 F = fr[(int)fl + 1];
+                e_acc = fmaf(ak.y, fmaf(al, F.y, F.x), e_acc);
+            }
+            acc = fmaf(vx.z * gd * ang, e_acc, acc);
+        }
+    }
+    if (valid) {
+        if (LIST) part[(int64_t)by * np + e] = acc;
+        else part[(int64_t)by * g.M * g.N + (int64_t)m * g.N + n] = acc;
+    }
+}
+
+// One warp's work of the adjoint: voxel v, detector rows of split part sp (or the
+// listed pixels), into the warp's lane-private rows acc ([Q+3][32], zeroed by the
+// caller), written to out + (sp R + v) Q.  Shared by the single-plan kernel and
+// the persistent multi-object kernel.
+template <bool LIST>
+__device__ __forceinline__ void adj_direct_body(const Tables &T, const float *__restrict__ w,
+                                                float *__restrict__ out, int rows_per_split,
+                                                const int *__restrict__ list, int np, int v, int sp,
+                                                const float2 *s_en, float *acc, int lane) {
+    const DevGeo &g = T.g;
+    const int i = v / g.J, j = v - i * g.J;
+    const float4 vx = T.vox[v];
+    float *my = acc + lane;
+    // one pair (pixel (m, n)) scattered into the lane's q row
+    auto pair = [&](int m, int n) {
+        const uint32_t word = T.tbits[((int64_t)v * g.M + m) * g.Nw + (n >> 5)];
+        if (!((word >> (n & 31)) & 1u)) return;
+        const float wv = w[(int64_t)m * g.N + n];
+        if (wv == 0.f) return;
+        float u, ang;
+        pair_u_angular(vx.x, vx.y, vx.w, (float)n - g.cN, T.zrow[m], g.p_y, g.Xd, u, ang);
+        const float base = vx.z * T.god[((int64_t)i * g.M + m) * g.ND + (n - g.rho_y * j - g.d_min)] * ang * wv;
+#pragma unroll 4
+        for (int k = 0; k < g.K; ++k) {
+            const float2 ak = s_en[k];
+            float tau = fmaf(ak.x, u, -g.b);
+            tau = fminf(fmaxf(tau, -1.f), g.Qf);
+            const float fl = floorf(tau);
+            const float al = tau - fl;
+            const int lp = (int)fl + 1;
+            const float cb = ak.y * base;
+            const float hi = cb * al;
+            my[lp * 32] += cb - hi;
+            my[(lp + 1) * 32] += hi;
+        }
+    };
+    if (LIST) {
+        for (int e = lane; e < np; e += 32) {
+            const int p = list[e];
+            const int m = p / g.N;
+            pair(m, p - m * g.N);
+        }
+    } else {
+        const int m0 = sp * rows_per_split, m1 = min(g.M, m0 + rows_per_split);
+        for (int m = m0; m < m1; ++m)
+            for (int nb = 0; nb < g.N; nb += 32) {
+                const int n = nb + lane;
+                if (n >= g.N) break;
+                pair(m, n);
+            }
+    }
+    __syncwarp();
+    float *dst = out + ((int64_t)sp * g.R + v) * g.Q;
+    for (int lp = 1 + lane; lp <= g.Q; lp += 32) {
+        const float *rowp = acc + lp * 32;
+        float s = 0.f;
+        for (int c = 0; c < 32; ++c) s += rowp[(lane + c) & 31];
+        dst[lp - 1] = s;
+    }
+}
+
+inline Tables tables_of(const caxsi_plan *p) {
+    Tables T;
+    T.g = p->dg;
+    T.vox = p->vox;
+    T.zrow = p->zrow;
+    T.god = p->god;
+    T.tbits = p->tbits;
+    T.energy = p->energy;
+    return T;
+}
+
+inline size_t fwd_smem(const DevGeo &g) {
+    return ((g.K + 1) & ~1) * sizeof(float2) + FWD_VS * sizeof(float4) +
+           (size_t)FWD_VS * (g.Q + 2) * sizeof(float2);
+}
+inline size_t adj_smem(const DevGeo &g) {
+    return ((g.K + 1) & ~1) * sizeof(float2) + (size_t)ADJ_WARPS * (g.Q + 3) * 32 * sizeof(float);
+}
+
+}  // namespace direct_impl

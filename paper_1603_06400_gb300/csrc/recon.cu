@@ -301,12 +301,13 @@ cudaError_t launch_update(const DevGeo &g, const float *f, const float *b1, cons
 // gradients of chi1..3, hence of b2_j, of f_j through chi2 and chi3, and of b3_j
 // and b5_j (kept in gb3, gb5) with their derivatives with respect to f_j itself
 // (omega'(d) = -delta sign(d) / d^2 beyond delta, psi_dot'(d) = 1 within it).
-__global__ void k_update_vjp1(DevGeo g, const float *__restrict__ f, const float *__restrict__ b1,
-                              const float *__restrict__ b2, float beta, float delta,
-                              const float *__restrict__ gx, float *__restrict__ gf, float *__restrict__ gb2,
-                              float *__restrict__ gb3, float *__restrict__ gb5, int64_t n) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n) return;
+// Element idx of arrays that start at an object's first element (objects of g's
+// geometry back to back).
+__device__ __forceinline__ void update_vjp1_elem(const DevGeo &g, const float *__restrict__ f,
+                                                 const float *__restrict__ b1, const float *__restrict__ b2,
+                                                 float beta, float delta, const float *__restrict__ gx,
+                                                 float *__restrict__ gf, float *__restrict__ gb2,
+                                                 float *__restrict__ gb3, float *__restrict__ gb5, int64_t idx) {
     const UpdTerms u = upd_terms(g, f, b1, b2, beta, delta, idx);
     const float gxi = gx[idx];
     if (u.kind == 2) {
@@ -347,10 +348,9 @@ __global__ void k_update_vjp1(DevGeo g, const float *__restrict__ f, const float
 }
 
 // Pass 2: each neighbour k of j adds -(gb3_k 2 omega'(f_k - f_j) + gb5_k psi_dot'(f_k - f_j)).
-__global__ void k_update_vjp2(DevGeo g, const float *__restrict__ f, float delta, const float *__restrict__ gb3,
-                              const float *__restrict__ gb5, float *__restrict__ gf, int64_t n) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n) return;
+__device__ __forceinline__ void update_vjp2_elem(const DevGeo &g, const float *__restrict__ f, float delta,
+                                                 const float *__restrict__ gb3, const float *__restrict__ gb5,
+                                                 float *__restrict__ gf, int64_t idx) {
     const float fj = f[idx];
     float acc = gf[idx];
 #pragma unroll
@@ -364,6 +364,84 @@ __global__ void k_update_vjp2(DevGeo g, const float *__restrict__ f, float delta
         acc -= gb3[k] * 2.f * domega + gb5[k] * (ad < delta ? 1.f : 0.f);
     }
     gf[idx] = acc;
+}
+
+__global__ void k_update_vjp1(DevGeo g, const float *__restrict__ f, const float *__restrict__ b1,
+                              const float *__restrict__ b2, float beta, float delta,
+                              const float *__restrict__ gx, float *__restrict__ gf, float *__restrict__ gb2,
+                              float *__restrict__ gb3, float *__restrict__ gb5, int64_t n) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    update_vjp1_elem(g, f, b1, b2, beta, delta, gx, gf, gb2, gb3, gb5, idx);
+}
+
+__global__ void k_update_vjp2(DevGeo g, const float *__restrict__ f, float delta, const float *__restrict__ gb3,
+                              const float *__restrict__ gb5, float *__restrict__ gf, int64_t n) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    update_vjp2_elem(g, f, delta, gb3, gb5, gf, idx);
+}
+
+// ---- objects of different geometries packed back to back ------------------------
+// Object b's elements are [foff[b], foff[b+1]) with the geometry geos[b]; its
+// voxels are [vox0[b], vox0[b+1]) in the packed voxel order.
+
+__device__ __forceinline__ int multi_object(const int64_t *__restrict__ first, int n, int64_t it) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One block per packed voxel, the q channels across the threads (as k_update).
+__global__ void k_update_multi(const DevGeo *__restrict__ geos, const int64_t *__restrict__ vox0,
+                               const int64_t *__restrict__ foff, int nobj, const float *__restrict__ f,
+                               const float *__restrict__ b1, const float *__restrict__ b2, float beta, float delta,
+                               float *__restrict__ fnew) {
+    const int b = multi_object(vox0, nobj, blockIdx.x);
+    const DevGeo g = geos[b];
+    const int v = (int)(blockIdx.x - vox0[b]);
+    const int i = v / g.J, j = v - i * g.J;
+    const int64_t JQ = (int64_t)g.J * g.Q;
+    const bool ok[4] = {i > 0, i + 1 < g.X, j > 0, j + 1 < g.J};
+    const int64_t o = foff[b];
+    for (int l = threadIdx.x; l < g.Q; l += blockDim.x) {
+        const int64_t idx = o + (int64_t)v * g.Q + l;
+        float nb[4] = {0.f, 0.f, 0.f, 0.f};
+        if (beta != 0.f) {
+            nb[0] = ok[0] ? f[idx - JQ] : 0.f;
+            nb[1] = ok[1] ? f[idx + JQ] : 0.f;
+            nb[2] = ok[2] ? f[idx - g.Q] : 0.f;
+            nb[3] = ok[3] ? f[idx + g.Q] : 0.f;
+        }
+        fnew[idx] = update_value(f[idx], nb, ok, b1[idx], b2[idx], beta, delta);
+    }
+}
+
+__global__ void k_update_vjp1_multi(const DevGeo *__restrict__ geos, const int64_t *__restrict__ foff, int nobj,
+                                    const float *__restrict__ f, const float *__restrict__ b1,
+                                    const float *__restrict__ b2, float beta, float delta,
+                                    const float *__restrict__ gx, float *__restrict__ gf, float *__restrict__ gb2,
+                                    float *__restrict__ gb3, float *__restrict__ gb5, int64_t n) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const int b = multi_object(foff, nobj, idx);
+    const int64_t o = foff[b];
+    update_vjp1_elem(geos[b], f + o, b1 + o, b2 + o, beta, delta, gx + o, gf + o, gb2 + o, gb3 + o, gb5 + o,
+                     idx - o);
+}
+
+__global__ void k_update_vjp2_multi(const DevGeo *__restrict__ geos, const int64_t *__restrict__ foff, int nobj,
+                                    const float *__restrict__ f, float delta, const float *__restrict__ gb3,
+                                    const float *__restrict__ gb5, float *__restrict__ gf, int64_t n) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const int b = multi_object(foff, nobj, idx);
+    const int64_t o = foff[b];
+    update_vjp2_elem(geos[b], f + o, delta, gb3 + o, gb5 + o, gf + o, idx - o);
 }
 
 }  // namespace
@@ -469,5 +547,26 @@ caxsi_status recon_ratio_vjp(caxsi_plan *p, const float *g, const float *y, cons
         k_ratio_vjp<<<(unsigned)(nb < 4 * p->num_sms ? nb : 4 * p->num_sms), 256, 0, s>>>(g, y, r, gr, gg, n);
     }
     CAXSI_LAUNCH_CHECK(p);
+    return CAXSI_OK;
+}
+
+caxsi_status multi_update(const DevGeo *geos, const int64_t *vox0, const int64_t *foff, int nobj, int64_t n_vox,
+                          int qmax, const float *f, const float *b1, const float *b2, float beta, float delta,
+                          float *out, cudaStream_t s) {
+    const unsigned thr = (unsigned)(qmax >= 128 ? 128 : (qmax + 31) / 32 * 32);
+    k_update_multi<<<(unsigned)n_vox, thr, 0, s>>>(geos, vox0, foff, nobj, f, b1, b2, beta, delta, out);
+    CAXSI_CUDA_TRY(cudaGetLastError());
+    return CAXSI_OK;
+}
+
+caxsi_status multi_update_vjp(const DevGeo *geos, const int64_t *foff, int nobj, const float *f, const float *b1,
+                              const float *b2, float beta, float delta, const float *gx, float *gf, float *gb2,
+                              float *scratch, int64_t n, cudaStream_t s) {
+    float *gb3 = scratch, *gb5 = scratch + n;
+    const unsigned nb = (unsigned)ceil_div64(n, 256);
+    k_update_vjp1_multi<<<nb, 256, 0, s>>>(geos, foff, nobj, f, b1, b2, beta, delta, gx, gf, gb2, gb3, gb5, n);
+    CAXSI_CUDA_TRY(cudaGetLastError());
+    k_update_vjp2_multi<<<nb, 256, 0, s>>>(geos, foff, nobj, f, delta, gb3, gb5, gf, n);
+    CAXSI_CUDA_TRY(cudaGetLastError());
     return CAXSI_OK;
 }

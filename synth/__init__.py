@@ -249,3 +249,36 @@ def log_uniform_peak(seed: int, lo=1e2, hi=1e4) -> float:
 
 TINY_MASK_SEED = 1001
 PAPER_MASK_SEED = 1002
+
+
+# Objects of uneven size sharing the paper-scale detector, spectrum model and
+# mask: extents uniform in x across the fan J in [64, 256], z along the beam
+# X in [32, 128] and q bins Q in [64, 128] (same q range), at the paper-scale
+# voxel pitches, centred where the paper-scale object is.
+UNEVEN_J = (64, 256)
+UNEVEN_X = (32, 128)
+UNEVEN_Q = (64, 128)
+
+
+def uneven_sizes(n: int, seed: int, X=UNEVEN_X, J=UNEVEN_J, Q=UNEVEN_Q) -> list:
+    """n seeded (X, J, Q) extents, each uniform in its closed range; the first two
+    objects take the range ends (smallest and largest) so that both occur."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(n):
+        if b == 0:
+            out.append((X[0], J[0], Q[0]))
+        elif b == 1:
+            out.append((X[1], J[1], Q[1]))
+        else:
+            out.append((int(rng.integers(X[0], X[1] + 1)), int(rng.integers(J[0], J[1] + 1)),
+                        int(rng.integers(Q[0], Q[1] + 1))))
+    return out
+
+
+def uneven_object_geometry(X: int, J: int, Q: int, base: Geometry | None = None) -> Geometry:
+    """The geometry of one uneven object: `base` (default the paper-scale
+    geometry) with X, J and Q replaced, and C rescaled as make_geometry sets it."""
+    b = base if base is not None else paper_geometry()
+    L = b.X_det - b.x_center
+    return replace(b, X=int(X), J=int(J), Q=int(Q), C=b.x_center ** 2 * L ** 3 / (b.p_z * X * J))
