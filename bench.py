@@ -25,7 +25,9 @@ trained here for --unet-steps objects, its training time reported apart).  The
 "precision" key gives the throughput and the error (against the exact FP32
 path) of the 16-bit contractions and of u tables of 1024-4096 samples.  The
 "batch" key times the batched operators on 32 objects of uneven size against
-one call per object.
+one call per object: objects of uneven extent in x, z and q (one plan each, one
+persistent launch per stage, direct FP32 path), and depth slabs of the
+paper-scale object (table path).
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload per step.
@@ -68,7 +70,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-recon", action="store_true")
     ap.add_argument("--unet-steps", type=int, default=1000,
-                    help="training objects of the learned warm start in the recon experiment (0: skip)")
+                    help="training steps (4 objects each) of the learned warm start in the recon experiments "
+                         "(0: skip)")
     return ap.parse_args()
 
 
@@ -410,7 +413,7 @@ def max_over_ranks(value, dist, device=None):
 # reconstruction: time to the plain FP32 method's final NMSE
 # ---------------------------------------------------------------------------
 
-def recon_experiment(caxsi, plan, g, dev, phantom, iters=100, max_iters=300, unet_steps=1000,
+def recon_experiment(caxsi, plan, g, dev, phantom, iters=100, max_iters=300, warm=None,
                      make_plan=None):
     """Penalised EM (Huber on the spatial neighbours) on one phantom: the plain
     FP32 table path for `iters` iterations gives the target NMSE; each
@@ -500,26 +503,133 @@ def recon_experiment(caxsi, plan, g, dev, phantom, iters=100, max_iters=300, une
                     break
             r["speedup_vs_plain"] = plain["seconds"] / r["seconds"] if r["reached"] else None
             res[f"os_em_{n_sub}{tag}"] = r
-    res["learned"] = learned_experiment(plan, g, y, f_ref, plain, unet_steps) if unet_steps > 0 else None
+    res["learned"] = learned_experiment(plan, g, y, f_ref, plain, warm) if warm is not None else None
     return res
 
 
-def learned_experiment(plan, g, y, f_ref, plain, steps):
-    """The learned warm start: a U-Net (hand-written kernels, bf16 tensor-core
-    convolutions) trained for `steps` objects of the input recipe (seeds 100000+,
-    disjoint from the benchmark phantoms); then, timed: the first EM-type iterate
-    from the flat start, the network's f^0, and EM-type iterations from f^0 until
-    the plain FP32 target NMSE.  Training time is reported apart (done once)."""
+def recon_seeds(caxsi, plan, g, dev, warm, seeds=range(N_PHANTOMS), iters=100, max_iters=300):
+    """Penalised EM on each benchmark phantom (seeds 0-9, peaks log-uniform in
+    [1e2, 1e4]): `iters` plain FP32 iterations give the target NMSE; then the
+    time each alternative needs to reach it: the learned warm start (first
+    iterate + network + EM-type iterations), bf16 contractions, and ordered
+    subsets (128 subsets, FP32 table path).  Device time of the iterations only;
+    per-seed entries and the median and worst speedups."""
+    import torch
+    from paper_1603_06400_gb300 import warmstart  # noqa: F401
+    P = caxsi.PATHS
+    b1 = plan.adjoint(torch.ones((g.M, g.N), device=dev), path=P["table_fp32"])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the partition, its grouped records and the subset sensitivities are set up once,
+    # outside the timing (as b1 is for the plain iterations)
+    plan.set_subsets(caxsi.os_partition(g.M, g.N, g.rho_y, 16, 16))
+    plan.os_pass(torch.zeros((g.M, g.N), device=dev), torch.ones((g.X, g.J, g.Q), device=dev),
+                 path=P["table_fp32"])
+    per = []
+    for p in seeds:
+        f_true = torch.tensor(synth.phantom(g, p), dtype=torch.float32, device=dev)
+        mean = plan.forward(f_true, path=P["table_fp32"])
+        peak = synth.log_uniform_peak(p)
+        y = torch.tensor(synth.poisson_counts((mean * (peak / mean.max())).cpu().numpy().astype(np.float64),
+                                              100 + p), dtype=torch.float32, device=dev)
+        f_ref = f_true * (peak / float(mean.max()))
+        f_init = float(y.sum() / b1.sum())
+        beta = 1e-3 * float(y.sum()) / (g.X * g.J * g.Q)
+        delta = 0.01 * f_init
+        nref = float(torch.sum(f_ref.double() ** 2))
+        nmse = lambda f: float(torch.sum((f.double() - f_ref.double()) ** 2)) / nref
+
+        def timed(fn):
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / 1e3
+
+        def until(f, step, target, cap):
+            total, n = 0.0, 0
+            cur = nmse(f)
+            while (target is None or cur > target) and n < cap:
+                total += timed(lambda: step(f))
+                n += 1
+                cur = nmse(f)
+            return {"iterations": n, "seconds": total, "nmse": cur,
+                    "reached": target is None or cur <= target}
+        f = torch.full((g.X, g.J, g.Q), f_init, device=dev)
+        plain = until(f, lambda x: plan.recon_step(y, x, beta=beta, delta=delta, path=P["table_fp32"]), None,
+                      iters)
+        target = plain["nmse"]
+        ent = {"phantom": p, "peak_counts": peak, "plain_fp32": plain}
+        f = torch.full((g.X, g.J, g.Q), f_init, device=dev)
+        ent["table_bf16"] = until(f, lambda x: plan.recon_step(y, x, beta=beta, delta=delta,
+                                                               path=P["table_bf16"]), target, max_iters)
+        f = torch.full((g.X, g.J, g.Q), f_init, device=dev)
+        r = until(f, lambda x: plan.os_pass(y, x, beta=beta, delta=delta, path=P["table_fp32"]), target, 12)
+        r["passes"] = r.pop("iterations")
+        r["subsets"] = plan.n_subsets
+        ent["os_em_128"] = r
+        if warm is not None:
+            net, maker, _ = warm
+            box = {}
+
+            def start():
+                f1, *_ = maker.make(0, y=y, f_ref=f_ref)
+                sc = float(f1.mean())
+                box["f"] = net.predict(f1, sc, 1e-3 * sc)
+            t0 = timed(start)
+            r = until(box["f"], lambda x: plan.recon_step(y, x, beta=beta, delta=delta, path=P["table_fp32"]),
+                      target, max_iters)
+            r["seconds"] += t0
+            r["first_iterate_and_inference_seconds"] = t0
+            ent["learned"] = r
+        for k in ("table_bf16", "os_em_128", "learned"):
+            if k in ent:
+                ent[k]["speedup_vs_plain"] = plain["seconds"] / ent[k]["seconds"] if ent[k]["reached"] else None
+        per.append(ent)
+    summary = {}
+    for k in ("table_bf16", "os_em_128", "learned"):
+        sp = [e[k]["speedup_vs_plain"] for e in per if k in e]
+        if sp:
+            ok = [v for v in sp if v is not None]
+            summary[k] = {"reached": f"{len(ok)}/{len(sp)}",
+                          "median_speedup": float(np.median(ok)) if ok else None,
+                          "worst_speedup": float(min(ok)) if len(ok) == len(sp) else None,
+                          "median_time_fraction_of_plain": float(np.median([1.0 / v for v in ok])) if ok else None}
+    summary["plain_fp32_final_nmse"] = {"median": float(np.median([e["plain_fp32"]["nmse"] for e in per])),
+                                        "worst": float(max(e["plain_fp32"]["nmse"] for e in per))}
+    return {"iterations": iters, "per_phantom": per, "summary": summary}
+
+
+def train_warm_start(plan, g, steps, batch=4):
+    """Train the warm-start U-Net (hand-written kernels, bf16 tensor-core
+    convolutions) on steps x batch objects of the input recipe (seeds 100000+,
+    disjoint from the benchmark phantoms 0-9), counts drawn on the device; the
+    loss curve is the mean over 8 held-out objects (seeds 150000+).  Returns
+    (net, maker, record); the training time is reported apart (done once)."""
     import torch
     from paper_1603_06400_gb300 import warmstart
-    P = caxsi_paths()
     maker = warmstart.PairMaker(plan, g)
     net = warmstart.UNet(channels=g.Q, base=32, seed=0)
     torch.cuda.synchronize()
     t0 = time.time()
-    losses = warmstart.train(net, maker, steps, lr=1e-3, log=max(1, steps // 10))
+    losses = warmstart.train(net, maker, steps, lr=1e-3, batch=batch, log=max(1, steps // 10),
+                             heldout_seeds=range(150000, 150008))
     torch.cuda.synchronize()
-    train_s = time.time() - t0
+    rec = {"train_steps": steps, "objects_per_step": batch, "train_objects": steps * batch,
+           "train_seconds": time.time() - t0, "heldout_objects": 8,
+           "loss_curve": [{"step": k, "train_batch": a, "heldout_mean": b} for k, a, b in losses]}
+    return net, maker, rec
+
+
+def learned_experiment(plan, g, y, f_ref, plain, warm):
+    """The learned warm start on one phantom, timed: the first EM-type iterate
+    from the flat start, the network's f^0, and EM-type iterations from f^0 until
+    the plain FP32 target NMSE; then the step scalings learned through 10
+    unrolled iterations."""
+    import torch
+    from paper_1603_06400_gb300 import warmstart
+    P = caxsi_paths()
+    net, maker, rec = warm
+    train_s = rec["train_seconds"]
     nref = float(torch.sum(f_ref.double() ** 2))
     nmse = lambda f: float(torch.sum((f.double() - f_ref.double()) ** 2)) / nref
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -557,7 +667,7 @@ def learned_experiment(plan, g, y, f_ref, plain, steps):
     scalings = {"values": [round(float(v), 4) for v in relax], "train_objects": 40, "train_seconds": relax_s,
                 "nmse_after_10_plain_from_f0": after_plain, "nmse_after_10_scaled_from_f0": after_learned}
     return {"step_scalings": scalings, "network": "U-Net, 4 levels, base width 32, 3x3 convs (bf16 tensor-core GEMMs, FP32 accumulation)",
-            "train_steps": steps, "train_seconds": train_s, "train_loss": losses,
+            "training": rec, "train_seconds": train_s,
             "first_iterate_and_inference_seconds": start_s, "f0_nmse": f0_nmse, "em_iterations": n_em,
             "seconds": total, "nmse": cur, "reached": reached,
             "speedup_vs_plain": plain["seconds"] / total if reached else None}
@@ -609,6 +719,64 @@ def batch_experiment(plan, g, n_objects=32, reps=5):
         sec = e0.elapsed_time(e1) / 1e3 / reps
         out[name] = {"seconds": sec, "objects_per_s": n_objects / sec}
     out["speedup"] = out["single_calls"]["seconds"] / out["batched"]["seconds"]
+    return out
+
+
+def uneven_batch_experiment(dev, n_objects=32, reps=3):
+    """Objects of uneven size (x across the fan 64-256, z along the beam 32-128,
+    q bins 64-128; seeded, synth.uneven_sizes) on the paper-scale detector,
+    spectrum and mask, one plan each, as one caxsi_multi set: one forward + one
+    adjoint of all objects (one persistent launch each, direct FP32 path), timed
+    with CUDA events after a warm-up, against the same objects one
+    caxsi_forward / caxsi_adjoint call each (the same arithmetic; results equal
+    bit for bit)."""
+    import torch
+    from paper_1603_06400_gb300 import caxsi
+    base = synth.paper_geometry()
+    phi = synth.tungsten_spectrum(base)
+    mask = synth.random_mask(base, synth.PAPER_MASK_SEED)
+    sizes = synth.uneven_sizes(n_objects, 2024)
+    geos = [synth.uneven_object_geometry(X, J, Q) for X, J, Q in sizes]
+    plans = [caxsi.Plan(g, phi, mask) for g in geos]
+    multi = caxsi.Multi(plans)
+    fs = [synth.phantom_torch(g, 300 + k, dev) for k, g in enumerate(geos)]
+    gen = torch.Generator(device=dev).manual_seed(5)
+    ws = [torch.rand((g.M, g.N), device=dev, generator=gen) + 0.5 for g in geos]
+    f, w = multi.pack_f(fs), multi.pack_g(ws)
+    gm = torch.empty(multi.g_len, device=dev)
+    fm = torch.empty(multi.f_len, device=dev)
+    D = caxsi.PATH_DIRECT
+
+    def batched():
+        multi.forward(f, out=gm)
+        multi.adjoint(w, out=fm)
+
+    def single():
+        for b, pl in enumerate(plans):
+            pl.forward(fs[b], path=D)
+            pl.adjoint(ws[b], path=D)
+    out = {"objects": n_objects, "path": "direct",
+           "sizes": "X in [32, 128], J in [64, 256], Q in [64, 128] (seed 2024); detector 256 x 64, 64 energies",
+           "voxels": int(sum(g.X * g.J for g in geos)), "f_floats": multi.f_len,
+           "launches_per_stage": 1}
+    for name, fn in (("batched", batched), ("single_calls", single)):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        out[name] = {"seconds": sec, "objects_per_s": n_objects / sec}
+    out["speedup"] = out["single_calls"]["seconds"] / out["batched"]["seconds"]
+    same = all(torch.equal(multi.unpack_g(gm)[b], plans[b].forward(fs[b], path=D)) and
+               torch.equal(multi.unpack_f(fm)[b], plans[b].adjoint(ws[b], path=D)) for b in range(n_objects))
+    out["bit_identical_to_single_calls"] = bool(same)
+    multi.close()
+    for pl in plans:
+        pl.close()
     return out
 
 
@@ -839,10 +1007,12 @@ def run_ours(args):
 
     if world == 1 and args.workload != "small" and not args.no_recon:
         line["precision"] = precision_experiment(caxsi, plan, g, dev, make_plan)
-        line["recon"] = recon_experiment(caxsi, plan, g, dev, phantom=0, unet_steps=args.unet_steps,
-                                         make_plan=make_plan)
+        warm = train_warm_start(plan, g, args.unet_steps) if args.unet_steps > 0 else None
+        line["recon"] = recon_experiment(caxsi, plan, g, dev, phantom=0, warm=warm, make_plan=make_plan)
+        line["recon_seeds"] = recon_seeds(caxsi, plan, g, dev, warm)
     if world == 1 and args.workload == "paper" and not args.no_recon:
-        line["batch"] = batch_experiment(plan, g)
+        line["batch"] = {"uneven_objects": uneven_batch_experiment(dev),
+                         "depth_slabs": batch_experiment(plan, g)}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g)
     print(json.dumps(line), flush=True)

@@ -89,6 +89,14 @@ caxsi_status caxsi_nn_axpy(float a, const float *x, float *y, int64_t n, void *s
 #define CAXSI_NN_MSE_PARTS 512
 caxsi_status caxsi_nn_mse(const float *y, const float *t, int64_t n, float *grad, double *loss_dev, void *stream);
 
+/* out[i] ~ Poisson(scale * mean[i]) as an integer-valued float (0 where the mean
+ * is not positive): training counts drawn on the device.  Uniforms come from the
+ * counter-based generator Philox4x32-10 with key `seed` and counter (i, block),
+ * so each element's draw depends only on (seed, i), not on the launch; means
+ * below 10 are drawn by inversion of the cumulative distribution, larger ones
+ * by Hormann's transformed rejection with squeeze (1993).  scale >= 0. */
+caxsi_status caxsi_nn_poisson(const float *mean, float scale, int64_t n, uint64_t seed, float *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

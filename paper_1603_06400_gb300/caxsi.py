@@ -125,6 +125,7 @@ def load():
                 "caxsi_nn_adam": [V, V, V, V, I64_, F32, F32, F32, F32, I, V],
                 "caxsi_nn_axpy": [F32, V, V, I64_, V],
                 "caxsi_nn_mse": [V, V, I64_, V, V, V],
+                "caxsi_nn_poisson": [V, F32, I64_, ctypes.c_uint64, V, V],
             }
             for name, at in nn.items():
                 getattr(lib, name).argtypes = at

@@ -218,6 +218,90 @@ int device_sms() {
 
 caxsi_status launched() { return cudaGetLastError() == cudaSuccess ? CAXSI_OK : CAXSI_ERR_CUDA; }
 
+// ---- Poisson draws from a counter-based generator ---------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as easy
+// as 1, 2, 3", SC 2011): ten rounds of two 32 x 32 -> 64-bit multiplications
+// whose halves are xored with the other counter words and the key, the key
+// advanced by the Weyl constants between rounds.  Counter (element, block of
+// four uniforms, 0, 0), key = the seed: every element's stream is independent of
+// the launch shape.
+struct Philox {
+    uint32_t k0, k1, i0, i1, blk;
+    uint32_t buf[4];
+    int used;
+    __device__ Philox(uint64_t seed, uint64_t idx)
+        : k0((uint32_t)seed), k1((uint32_t)(seed >> 32)), i0((uint32_t)idx), i1((uint32_t)(idx >> 32)), blk(0),
+          used(4) {}
+    __device__ void refill() {
+        uint32_t c0 = i0, c1 = i1, c2 = blk++, c3 = 0u, a = k0, b = k1;
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+            if (r > 0) {
+                a += 0x9E3779B9u;
+                b += 0xBB67AE85u;
+            }
+            const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+            const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+            const uint32_t n0 = hi1 ^ c1 ^ a, n2 = hi0 ^ c3 ^ b;
+            c0 = n0;
+            c1 = lo1;
+            c2 = n2;
+            c3 = lo0;
+        }
+        buf[0] = c0;
+        buf[1] = c1;
+        buf[2] = c2;
+        buf[3] = c3;
+        used = 0;
+    }
+    // uniform in the open interval (0, 1) with 24 random bits
+    __device__ float uniform() {
+        if (used == 4) refill();
+        return ((float)(buf[used++] >> 8) + 0.5f) * 5.9604645e-8f;
+    }
+};
+
+// k ~ Poisson(lam).  lam < 10: inversion by sequential search over the
+// cumulative distribution (one uniform).  lam >= 10: the transformed rejection
+// method with squeeze of Hormann ("The transformed rejection method for
+// generating Poisson random variables", Insurance: Mathematics and Economics 12,
+// 1993), whose acceptance test is taken in FP64.  Both loops are bounded; the
+// bounds are far beyond any draw with a probability above 1e-30.
+__device__ float poisson_draw(Philox &rng, float lam) {
+    if (!(lam > 0.f)) return 0.f;
+    if (lam < 10.f) {
+        const float u = rng.uniform();
+        float p = expf(-lam), F = p;
+        int k = 0;
+        while (u > F && k < 128) {
+            ++k;
+            p *= lam / (float)k;
+            F += p;
+        }
+        return (float)k;
+    }
+    const double L = (double)lam, sl = sqrt(L), logl = log(L);
+    const double b = 0.931 + 2.53 * sl, a = -0.059 + 0.02483 * b;
+    const double inv_alpha = 1.1239 + 1.1328 / (b - 3.4), vr = 0.9277 - 3.6224 / (b - 2.0);
+    for (int it = 0; it < 256; ++it) {
+        const double U = (double)rng.uniform() - 0.5, V = (double)rng.uniform();
+        const double us = 0.5 - fabs(U);
+        const double k = floor((2.0 * a / us + b) * U + L + 0.43);
+        if (us >= 0.07 && V <= vr) return (float)k;
+        if (k < 0.0 || (us < 0.013 && V > us)) continue;
+        if (log(V) + log(inv_alpha) - log(a / (us * us) + b) <= -L + k * logl - lgamma(k + 1.0)) return (float)k;
+    }
+    return rintf(lam);
+}
+
+__global__ void k_poisson(const float *__restrict__ mean, float scale, int64_t n, uint64_t seed,
+                          float *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        Philox rng(seed, (uint64_t)i);
+        out[i] = poisson_draw(rng, scale * mean[i]);
+    }
+}
+
 constexpr int MSE_BLOCKS = CAXSI_NN_MSE_PARTS;
 
 __global__ void k_axpy(float a, const float *__restrict__ x, float *__restrict__ y, int64_t n) {
@@ -343,6 +427,13 @@ caxsi_status caxsi_nn_adam(float *w, const float *g, float *m, float *v, int64_t
 caxsi_status caxsi_nn_axpy(float a, const float *x, float *y, int64_t n, void *stream) {
     if (!x || !y || n < 1 || !isfinite(a)) return CAXSI_ERR_INVALID;
     k_axpy<<<nblocks(n), NT, 0, (cudaStream_t)stream>>>(a, x, y, n);
+    return launched();
+}
+
+caxsi_status caxsi_nn_poisson(const float *mean, float scale, int64_t n, uint64_t seed, float *out, void *stream) {
+    if (!mean || !out || n < 1 || !isfinite(scale) || scale < 0.f) return CAXSI_ERR_INVALID;
+    const int64_t nb = (n + NT - 1) / NT;
+    k_poisson<<<(unsigned)(nb < 4096 ? nb : 4096), NT, 0, (cudaStream_t)stream>>>(mean, scale, n, seed, out);
     return launched();
 }
 

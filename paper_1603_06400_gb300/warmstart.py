@@ -18,7 +18,6 @@ from __future__ import annotations
 import ctypes
 import math
 
-import numpy as np
 import torch
 
 from . import caxsi
@@ -222,14 +221,24 @@ class UNet:
 # ---------------------------------------------------------------------------
 
 class PairMaker:
-    """Phantom -> counts y ~ Poisson(kappa A f) (peak log-uniform in [1e2, 1e4]) ->
-    the first EM-type iterate from the flat start (penalty beta = 1e-3 sum(y)/(XJQ),
-    delta = 0.01 f_init), with the object in count units as the target."""
+    """Phantom -> counts y ~ Poisson(kappa A f) (peak log-uniform in [1e2, 1e4]),
+    drawn on the device (caxsi_nn_poisson, key 100 + seed) -> the first EM-type
+    iterate from the flat start (penalty beta = 1e-3 sum(y)/(XJQ), delta =
+    0.01 f_init), with the object in count units as the target."""
 
     def __init__(self, plan, g, path="table_fp32"):
         self.plan, self.g = plan, g
         self.path = caxsi.PATHS[path]
         self.b1_sum = float(plan.adjoint(torch.ones((g.M, g.N), device="cuda"), path=self.path).double().sum())
+        self.lib = caxsi.load()
+
+    def counts(self, mean, kappa, key):
+        """y ~ Poisson(kappa * mean) on the device (float32, integer values)."""
+        y = torch.empty_like(mean)
+        s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        caxsi._check(self.lib.caxsi_nn_poisson(_p(mean), ctypes.c_float(kappa), mean.numel(),
+                                               ctypes.c_uint64(key), _p(y), s), "caxsi_nn_poisson")
+        return y
 
     def make(self, seed, y=None, f_ref=None):
         import synth
@@ -239,8 +248,7 @@ class PairMaker:
             mean = self.plan.forward(f_true, path=self.path)
             peak = synth.log_uniform_peak(seed)
             kappa = peak / float(mean.max())
-            y = torch.tensor(synth.poisson_counts((mean * kappa).cpu().numpy().astype(np.float64), 100 + seed),
-                             dtype=torch.float32, device="cuda")
+            y = self.counts(mean, kappa, 100 + seed)
             f_ref = f_true * kappa
         ysum = float(y.sum())
         f_init = ysum / self.b1_sum
@@ -251,23 +259,50 @@ class PairMaker:
         return f1, f_ref, y, beta, delta, f_init
 
 
-def train(net: UNet, maker: PairMaker, steps: int, lr: float = 1e-3, first_seed: int = 100000, log=None):
-    """Adam on the normalised MSE ||U(f1/s) - f_ref/s||^2 / n with s = mean(f1),
-    cosine-decayed learning rate, one object per step (seed first_seed + k)."""
+def _inputs(maker: PairMaker, seeds):
+    """Normalised network inputs and targets of the objects `seeds`: f1 / s and
+    f_ref / s with s = mean(f1), stacked as [n*X*J][Q]."""
     g = maker.g
-    R, Q = g.X * g.J, g.Q
+    xs, ts = [], []
+    for sd in seeds:
+        f1, f_ref, *_ = maker.make(sd)
+        s = float(f1.mean())
+        xs.append((f1 / s).view(g.X * g.J, g.Q))
+        ts.append((f_ref / s).view(g.X * g.J, g.Q))
+    return torch.cat(xs).contiguous(), torch.cat(ts).contiguous()
+
+
+def heldout_loss(net: UNet, maker: PairMaker, held) -> float:
+    """Mean normalised MSE of the network on held-out inputs (x, t, n) from _inputs."""
+    x, t, n = held
+    g = maker.g
+    out = net.forward(x, n, g.X, g.J)
+    loss, _ = net.mse(out, t)
+    return float(loss)
+
+
+def train(net: UNet, maker: PairMaker, steps: int, lr: float = 1e-3, batch: int = 4, first_seed: int = 100000,
+          log=None, heldout_seeds=None):
+    """Adam on the normalised MSE ||U(f1/s) - f_ref/s||^2 / n with s = mean(f1) per
+    object, `batch` objects per step (seeds first_seed, first_seed + 1, ...),
+    cosine-decayed learning rate.  With log = L, every L steps (and at the last)
+    records (step, training loss of the step's batch, mean loss on the held-out
+    objects heldout_seeds, which no step trains on)."""
+    g = maker.g
+    held = None
+    if heldout_seeds:
+        hx, ht = _inputs(maker, heldout_seeds)
+        held = (hx, ht, len(heldout_seeds))
     losses = []
     for k in range(steps):
-        f1, f_ref, *_ = maker.make(first_seed + k)
-        s = float(f1.mean())
-        x = (f1 / s).view(R, Q).contiguous()
-        tgt = (f_ref / s).view(R, Q).contiguous()
-        out = net.forward(x, 1, g.X, g.J)
+        x, tgt = _inputs(maker, range(first_seed + k * batch, first_seed + (k + 1) * batch))
+        out = net.forward(x, batch, g.X, g.J)
         loss, grad = net.mse(out, tgt)
+        train_loss = float(loss) if log is not None else None
         net.backward(grad)
         net.step(lr * 0.5 * (1.0 + math.cos(math.pi * k / max(1, steps))))
         if log is not None and (k % log == 0 or k == steps - 1):
-            losses.append((k, float(loss)))
+            losses.append((k, train_loss, heldout_loss(net, maker, held) if held else None))
     return losses
 
 

@@ -98,7 +98,7 @@ def _strip_comments(txt):
 def _declarations():
     """name -> parameter kinds ('ptr', 'i32', 'i64', 'f32', 'f64') of every
     function declared in include/*.h."""
-    kinds = {"int": "i32", "int32_t": "i32", "caxsi_status": "i32", "int64_t": "i64",
+    kinds = {"int": "i32", "int32_t": "i32", "caxsi_status": "i32", "int64_t": "i64", "uint64_t": "i64",
              "float": "f32", "double": "f64"}
     out = {}
     for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
@@ -125,6 +125,7 @@ def _kind(ct):
     if ct in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(ct, type) and issubclass(ct, ctypes._Pointer)):
         return "ptr"
     sizes = {ctypes.c_int: "i32", ctypes.c_int32: "i32", ctypes.c_int64: "i64", ctypes.c_long: "i64",
+             ctypes.c_uint64: "i64", ctypes.c_ulong: "i64",
              ctypes.c_float: "f32", ctypes.c_double: "f64"}
     return sizes[ct]
 

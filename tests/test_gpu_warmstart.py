@@ -198,3 +198,79 @@ def test_step_scalings_train_and_unit_scalings_are_plain_iterations(ws, tiny):
         plan.recon_step(y, f_b, beta=beta, delta=delta, path=caxsi.PATHS["table_fp32"])
     assert torch.allclose(f_a, f_b, rtol=1e-5, atol=1e-6 * float(f_b.abs().max()))
     plan.close()
+
+
+def test_trained_warm_start_beats_the_flat_start_on_held_out_objects(ws, tiny):
+    """Train briefly (200 steps of 4 objects, seeds 100000+), then on 6 held-out
+    objects (seeds 900000+, never trained on): after the same number T = 20 of
+    EM-type iterations, the warm-started reconstruction has a lower NMSE than the
+    flat-started one for every object, by 10 % on average, and reaches the flat
+    start's final NMSE in fewer iterations.  The held-out loss falls during training."""
+    torch, caxsi, warmstart = ws
+    g, phi, mask = tiny
+    plan = caxsi.Plan(g, phi, mask)
+    maker = warmstart.PairMaker(plan, g)
+    net = warmstart.UNet(channels=g.Q, base=16, seed=0)
+    losses = warmstart.train(net, maker, 200, lr=1e-3, batch=4, log=50, heldout_seeds=range(150000, 150004))
+    assert losses[-1][2] < losses[0][2], losses
+    P = caxsi.PATHS["table_fp32"]
+    T = 20
+    ratios = []
+    for k in range(6):
+        f1, f_ref, y, beta, delta, _ = maker.make(900000 + k)
+        nref = float((f_ref.double() ** 2).sum())
+        nmse = lambda f: float(((f.double() - f_ref.double()) ** 2).sum()) / nref
+        flat = f1.clone()              # the first iterate from the flat start is iteration 1
+        for _ in range(T - 1):
+            plan.recon_step(y, flat, beta=beta, delta=delta, path=P)
+        target = nmse(flat)
+        s = float(f1.mean())
+        warm = net.predict(f1, s, 1e-3 * s)
+        hist = [nmse(warm)]
+        for _ in range(T - 1):
+            plan.recon_step(y, warm, beta=beta, delta=delta, path=P)
+            hist.append(nmse(warm))
+        assert hist[-1] < target, (k, hist[-1], target)
+        reach = next(i for i, v in enumerate(hist) if v <= target)
+        assert reach < T - 1, (k, reach)
+        ratios.append(hist[-1] / target)
+    assert float(np.mean(ratios)) < 0.9, ratios
+    plan.close()
+
+
+def test_device_poisson_draws(ws):
+    """caxsi_nn_poisson: integer draws whose mean and variance match the Poisson
+    law over both samplers (inversion below 10, transformed rejection above),
+    a chi-square fit of the frequencies, and reproducibility by seed."""
+    import ctypes
+    torch, caxsi, warmstart = ws
+    lib = caxsi.load()
+    P = warmstart._p
+
+    def draw(lam, n, seed, scale=1.0):
+        mean = torch.full((n,), lam, device="cuda")
+        y = torch.empty_like(mean)
+        assert lib.caxsi_nn_poisson(P(mean), ctypes.c_float(scale), n, ctypes.c_uint64(seed), P(y), None) == 0
+        return y
+    n = 200000
+    for lam in (0.0, 0.3, 3.0, 9.5, 10.0, 57.0, 1000.0, 1e4):
+        y = draw(lam, n, 7).double().cpu().numpy()
+        assert np.all(y == np.round(y)) and y.min() >= 0
+        if lam == 0.0:
+            assert y.max() == 0
+            continue
+        assert abs(y.mean() - lam) <= 5 * np.sqrt(lam / n), lam
+        assert abs(y.var() / lam - 1) <= 5 * np.sqrt(2.0 / n) + 2e-3, lam
+    from scipy import stats
+    for lam in (3.0, 57.0):
+        y = draw(lam, n, 11).cpu().numpy().astype(np.int64)
+        lo, hi = int(stats.poisson.ppf(1e-4, lam)), int(stats.poisson.ppf(1 - 1e-4, lam))
+        obs = np.array([np.sum(y <= lo)] + [np.sum(y == k) for k in range(lo + 1, hi)] + [np.sum(y >= hi)])
+        pk = np.array([stats.poisson.cdf(lo, lam)] + [stats.poisson.pmf(k, lam) for k in range(lo + 1, hi)] +
+                      [stats.poisson.sf(hi - 1, lam)])
+        chi2 = float(np.sum((obs - n * pk) ** 2 / (n * pk)))
+        assert stats.chi2.sf(chi2, len(obs) - 1) > 1e-4, (lam, chi2)
+    a, b, c = draw(5.0, 4096, 1), draw(5.0, 4096, 1), draw(5.0, 4096, 2)
+    assert torch.equal(a, b) and not torch.equal(a, c)
+    # the scale multiplies the mean
+    assert torch.equal(draw(2.5, 4096, 3, scale=2.0), draw(5.0, 4096, 3))
