@@ -85,7 +85,10 @@ k_fwd_direct_multi(const MultiObj *__restrict__ objs, const int64_t *__restrict_
         const MultiObj &o = s_o;
         const int local = (int)(it - first[s_obj]);
         const int chunk = local / o.tiles, tile = local - chunk * o.tiles;
-        fwd_direct_body<false>(o.T, f + o.f_off, o.fpart, o.vc, o.tiles_n, nullptr, 0, tile, chunk, smem_raw);
+        // a register copy of the tables: the body's loops then keep the geometry in
+        // registers instead of re-reading it around its shared-memory stores
+        const Tables T = o.T;
+        fwd_direct_body<false>(T, f + o.f_off, o.fpart, o.vc, o.tiles_n, nullptr, 0, tile, chunk, smem_raw);
         // publish this chunk's partial tile; the last chunk of the tile sums them all
         __threadfence();
         __syncthreads();
@@ -146,7 +149,8 @@ k_adj_direct_multi(const MultiObj *__restrict__ objs, const int64_t *__restrict_
         const int local = (int)(it - first[b]);
         const int v = local / o.split, sp = local - v * o.split;
         float *out = o.split > 1 ? o.apart : f + o.f_off;
-        adj_direct_body<false>(o.T, w + o.g_off, out, o.rps, nullptr, 0, v, sp, s_en, acc, lane);
+        const Tables T = o.T;   // in registers (see the forward)
+        adj_direct_body<false>(T, w + o.g_off, out, o.rps, nullptr, 0, v, sp, s_en, acc, lane);
         if (o.split > 1) {
             // publish this row range's partial row; the last range of the voxel sums them
             __threadfence();
