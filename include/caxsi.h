@@ -402,6 +402,18 @@ caxsi_status caxsi_plan_info(caxsi_plan *plan, caxsi_plan_info_t *info);
  *     1/P of a full one); 0 runs the whole-object contractions as the full
  *     operators do.  Equal up to FP32 rounding. */
 #define CAXSI_OPT_SPARSE_SUBSETS 5
+/*   CAXSI_OPT_TEST_WAIT_LIMIT, CAXSI_OPT_TEST_WITHHOLD_COPY: test hooks of the
+ *     failure path, 0 in normal use.  Every wait of the record kernels for a
+ *     bulk copy is bounded; WAIT_LIMIT sets the record forward's bound in polls
+ *     (0 = the default, about a second), and WITHHOLD_COPY = 1 makes the record
+ *     forward (CAXSI_PATH_TABLE_FP32 with CAXSI_OPT_SYMMETRY 0) skip each block's
+ *     first row copy, so that the wait for it runs out: the kernel then records
+ *     the error (device_error of caxsi_plan_info; CAXSI_ERR_INTERNAL from the
+ *     next call that reports the likelihood), waits for the copies it did issue
+ *     and returns, leaving the context usable; the call's output is then
+ *     undefined.  Nothing is withheld by any other kernel. */
+#define CAXSI_OPT_TEST_WAIT_LIMIT 6
+#define CAXSI_OPT_TEST_WITHHOLD_COPY 7
 caxsi_status caxsi_plan_set_option(caxsi_plan *plan, int key, int value);
 
 /* Kernel timing (tracing).  When enabled, every kernel the plan launches is

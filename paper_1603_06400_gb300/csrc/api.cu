@@ -538,6 +538,14 @@ caxsi_status caxsi_plan_set_option(caxsi_plan *p, int key, int value) {
         p->no_bands = !value;
         return CAXSI_OK;
     }
+    if (key == CAXSI_OPT_TEST_WAIT_LIMIT && value >= 0) {
+        p->test_wait_limit = (uint32_t)value;
+        return CAXSI_OK;
+    }
+    if (key == CAXSI_OPT_TEST_WITHHOLD_COPY && (value == 0 || value == 1)) {
+        p->test_withhold = value;
+        return CAXSI_OK;
+    }
     if (key == CAXSI_OPT_U_SAMPLES && (value == 0 || (value >= 2 && value <= CAXSI_MAX_U_SAMPLES))) {
         if (p->table && value != p->u_samples) return CAXSI_ERR_INVALID;   // fixed once the table is built
         p->u_samples = value;

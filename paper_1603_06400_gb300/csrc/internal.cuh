@@ -101,6 +101,8 @@ struct caxsi_plan {
     int u_samples;            // table paths: 0 = the exact knots; N >= 2: N uniform samples of u (approximate)
     int no_bands;             // 1: the tcgen05 contractions multiply the zeros outside the band of S~ too
     int no_sparse_subsets;    // 1: the FP32 subset operators use the whole-object contractions too
+    uint32_t test_wait_limit; // test hook: polls of the record forward's copy waits (0 = default)
+    int test_withhold;        // test hook: the record forward withholds each block's first row copy
     KernelProfiler prof;
 };
 

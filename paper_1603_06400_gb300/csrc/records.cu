@@ -60,6 +60,11 @@ struct RecArgs {
     const int4 *items;    // null: item k is voxel chunk k, {0, k vc, min(R, (k+1) vc), k vc}
     int n_items, vc;
     int64_t w_stride;     // adjoint input image of object obj: w + obj * w_stride
+    // Test hooks of the forward record kernel (plan options; 0 in normal use):
+    // the polls of its copy waits (0 = WAIT_LIMIT), and whether it withholds the
+    // first row copy of each block so that the wait for it runs out.
+    uint32_t wait_limit;
+    int withhold;
 };
 
 // subset < 0: every record of each voxel; else the records of that subset.
@@ -80,6 +85,8 @@ RecArgs rec_args(const caxsi_plan *p, const TablePath *T, int subset) {
     a.n_items = T->rec_chunks;
     a.vc = T->rec_vc;
     a.w_stride = 0;
+    a.wait_limit = p->test_wait_limit ? p->test_wait_limit : WAIT_LIMIT;
+    a.withhold = p->test_withhold;
     return a;
 }
 
@@ -298,9 +305,9 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void *src, size_t bytes) 
     if (e > b)
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b), "r"((uint32_t)(e - b)) : "memory");
 }
-// Bounded wait: false if the phase did not complete within WAIT_LIMIT polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t k = 0; k < WAIT_LIMIT; ++k)
+// Bounded wait: false if the phase did not complete within `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = WAIT_LIMIT) {
+    for (uint32_t k = 0; k < limit; ++k)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -330,16 +337,18 @@ k_fwd_rec(RecArgs A, const float *__restrict__ Wtab, float *__restrict__ part, i
     }
     bool ok = true;
     uint32_t ph0 = 0u, ph1 = 0u;   // mbarrier phase parity of each buffer
+    bool pend0 = false, pend1 = false;   // thread 0: a copy it issued on that buffer has not been awaited
     for (int k = blockIdx.x; k < A.n_items && ok; k += gridDim.x) {
         const int4 it = item_at<ITEMS>(A, k);
         const int v0 = it.y, v1 = it.z;
         const int64_t r0 = (int64_t)it.w - v0;   // table row of voxel v: r0 + v
         for (int p = tid; p < A.npix; p += RT) g_s[p] = 0.f;
-        if (tid == 0) {
+        if (tid == 0 && !A.withhold) {
             // buffer 0 was last read before the barrier that ended the previous item
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_expect_tx(&bar[0], row_bytes);
             bulk_g2s(wbuf0, Wtab + (r0 + v0) * A.Bp, row_bytes, &bar[0]);
+            pend0 = true;
         }
         __syncthreads();
         for (int v = v0; v < v1; ++v) {
@@ -350,6 +359,7 @@ k_fwd_rec(RecArgs A, const float *__restrict__ Wtab, float *__restrict__ part, i
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_expect_tx(&bar[buf ^ 1], row_bytes);
                 bulk_g2s(buf ? wbuf0 : wbuf1, Wtab + (r0 + v + 1) * A.Bp, row_bytes, &bar[buf ^ 1]);
+                if (buf) pend0 = true; else pend1 = true;
             }
             if (tid == 32 && v + 1 < v1) {
                 const int64_t nb = rec_begin(A, v + 1), nbytes = 4 * (rec_end(A, v + 1) - nb);
@@ -357,12 +367,12 @@ k_fwd_rec(RecArgs A, const float *__restrict__ Wtab, float *__restrict__ part, i
                 bulk_prefetch_l2(A.w0 + nb, (size_t)nbytes);
                 bulk_prefetch_l2(A.w1 + nb, (size_t)nbytes);
             }
-            const int late = mbar_wait(&bar[buf], buf ? ph1 : ph0) ? 0 : 1;
+            const int late = mbar_wait(&bar[buf], buf ? ph1 : ph0, A.wait_limit) ? 0 : 1;
             if (__syncthreads_or(late)) {   // block-uniform decision
                 ok = false;
                 break;
             }
-            if (buf) ph1 ^= 1u; else ph0 ^= 1u;
+            if (buf) { ph1 ^= 1u; pend1 = false; } else { ph0 ^= 1u; pend0 = false; }
             // Whole 16-byte quads per thread: a pixel occurs once per voxel, except the
             // zero-weight pad records, which share the last record's pixel and sit in
             // its quad, so they are accumulated by the same thread, in order.
@@ -406,8 +416,8 @@ k_fwd_rec(RecArgs A, const float *__restrict__ Wtab, float *__restrict__ part, i
     if (!ok && tid == 0) {
         // a copy did not land in time: report, drain the copies this block issued, stop
         atomicExch(err, 1);
-        mbar_wait(&bar[0], ph0);
-        mbar_wait(&bar[1], ph1);
+        if (pend0) mbar_wait(&bar[0], ph0);
+        if (pend1) mbar_wait(&bar[1], ph1);
     }
 }
 
