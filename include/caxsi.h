@@ -358,6 +358,8 @@ typedef struct {
     int64_t n_sym_records;    /* records of the mirror-symmetric adjoint, each serving up to
                                  four pairs (0 until built, or when the geometry has no
                                  mirror symmetry) */
+    int64_t mask_symmetric;   /* 1 if the mask is mirror-symmetric about the central ray in
+                                 y and z and J, M, N are even (CAXSI_OPT_ONLINE_MASK applies) */
 } caxsi_plan_info_t;
 
 caxsi_status caxsi_plan_info(caxsi_plan *plan, caxsi_plan_info_t *info);
@@ -402,6 +404,20 @@ caxsi_status caxsi_plan_info(caxsi_plan *plan, caxsi_plan_info_t *info);
  *     1/P of a full one); 0 runs the whole-object contractions as the full
  *     operators do.  Equal up to FP32 rounding. */
 #define CAXSI_OPT_SPARSE_SUBSETS 5
+/*   CAXSI_OPT_ONLINE_MASK: 0 (default) or 1.  For a secondary mask that is
+ *     mirror-symmetric about the central ray in y and in z (cells centred on the
+ *     ray, pattern equal to its left-right and up-down images; caxsi_plan_info
+ *     reports it, and J, M, N must be even), 1 makes CAXSI_PATH_DIRECT exploit
+ *     the symmetric system design of Sec. III-A / III-C: the four pairs related
+ *     by the left-right and up-down mirrors share geometry AND mask factor, so the
+ *     forward computes each group's geometry and mask factor once and the energy
+ *     sums of the two mirrored voxel columns (Algorithm 2's W_L, W_R and four
+ *     detector quadrants), the adjoint one energy scatter per up-down pixel pair;
+ *     the mask factor is computed online from the mask array (FP64 cell decision,
+ *     as the plan builder takes it) instead of read from the per-pair bits.
+ *     UNSUPPORTED for a mask without that symmetry.  The multi-object set, the
+ *     subset operators and the static-scratch forward keep the per-pair bits. */
+#define CAXSI_OPT_ONLINE_MASK 8
 /*   CAXSI_OPT_TEST_WAIT_LIMIT, CAXSI_OPT_TEST_WITHHOLD_COPY: test hooks of the
  *     failure path, 0 in normal use.  Every wait of the record kernels for a
  *     bulk copy is bounded; WAIT_LIMIT sets the record forward's bound in polls

@@ -45,7 +45,8 @@ class CPlanInfo(ctypes.Structure):
     _fields_ = [("n_offsets", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
                 ("n_breakpoints", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("n_open_pairs", ctypes.c_int64), ("n_records", ctypes.c_int64),
-                ("device_error", ctypes.c_int64), ("n_sym_records", ctypes.c_int64)]
+                ("device_error", ctypes.c_int64), ("n_sym_records", ctypes.c_int64),
+                ("mask_symmetric", ctypes.c_int64)]
 
 
 class CKernelStat(ctypes.Structure):
@@ -432,6 +433,11 @@ class Plan:
         """Mirror-symmetric records for the table paths' full forward and adjoint
         (default on when the geometry allows)."""
         _check(self.lib.caxsi_plan_set_option(self.handle, 2, int(bool(on))), "caxsi_plan_set_option")
+
+    def set_online_mask(self, on: bool = True):
+        """Direct path: exploit a mirror-symmetric mask (shared mask factor of the
+        four mirror pairs, computed online); raises for a mask without the symmetry."""
+        _check(self.lib.caxsi_plan_set_option(self.handle, 8, int(bool(on))), "caxsi_plan_set_option")
 
     def set_gemm_engine(self, engine: str):
         """'tcgen05' (default) or 'cublas' for the table paths' contractions."""

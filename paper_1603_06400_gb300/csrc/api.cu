@@ -58,6 +58,7 @@ void free_plan(caxsi_plan *p) {
     cudaFree(p->zrow);
     cudaFree(p->god);
     cudaFree(p->tbits);
+    cudaFree(p->mask01);
     cudaFree(p->energy);
     cudaFree(p->fwd_part);
     cudaFree(p->adj_part);
@@ -180,7 +181,8 @@ caxsi_status caxsi_plan_create(const caxsi_geometry *geom, const double *phi_hos
     direct_configure(p);
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if ((size_t)smem_max < direct_adj_smem(p) || (size_t)smem_max < direct_fwd_smem(p)) {
+    if ((size_t)smem_max < direct_adj_smem(p) || (size_t)smem_max < direct_fwd_smem(p) ||
+        (size_t)smem_max < symmask_fwd_smem(p->dg) || (size_t)smem_max < symmask_adj_smem(p->dg)) {
         delete p;
         return CAXSI_ERR_UNSUPPORTED;
     }
@@ -506,6 +508,7 @@ caxsi_status caxsi_plan_info(caxsi_plan *p, caxsi_plan_info_t *info) {
     info->n_open_pairs = p->open_pairs;
     info->n_records = table_records(p);
     info->n_sym_records = table_sym_records(p);
+    info->mask_symmetric = p->mask_symmetric;
     return CAXSI_OK;
 }
 
@@ -536,6 +539,11 @@ caxsi_status caxsi_plan_set_option(caxsi_plan *p, int key, int value) {
     }
     if (key == CAXSI_OPT_GEMM_BANDS && (value == 0 || value == 1)) {
         p->no_bands = !value;
+        return CAXSI_OK;
+    }
+    if (key == CAXSI_OPT_ONLINE_MASK && (value == 0 || value == 1)) {
+        if (value && !p->mask_symmetric) return CAXSI_ERR_UNSUPPORTED;
+        p->online_mask = value;
         return CAXSI_OK;
     }
     if (key == CAXSI_OPT_TEST_WAIT_LIMIT && value >= 0) {

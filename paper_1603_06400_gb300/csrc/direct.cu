@@ -123,6 +123,7 @@ size_t direct_fwd_smem(const caxsi_plan *p) { return fwd_smem(p->dg); }
 size_t direct_adj_smem(const caxsi_plan *p) { return adj_smem(p->dg); }
 
 caxsi_status direct_forward(caxsi_plan *p, const float *f, float *g_out, cudaStream_t s) {
+    if (p->online_mask) return symmask_forward(p, f, g_out, s);
     const DevGeo &g = p->dg;
     const int tiles_n = (int)ceil_div64(g.N, 32);
     const int tiles = (int)ceil_div64(g.M, FWD_WARPS) * tiles_n;
@@ -144,6 +145,7 @@ caxsi_status direct_forward(caxsi_plan *p, const float *f, float *g_out, cudaStr
 }
 
 caxsi_status direct_adjoint(caxsi_plan *p, const float *w, float *f_out, cudaStream_t s) {
+    if (p->online_mask) return symmask_adjoint(p, w, f_out, s);
     const DevGeo &g = p->dg;
     const size_t sm = adj_smem(g);
     CAXSI_CUDA_TRY(cudaFuncSetAttribute(k_adj_direct<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));

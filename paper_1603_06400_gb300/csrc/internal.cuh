@@ -101,6 +101,9 @@ struct caxsi_plan {
     int u_samples;            // table paths: 0 = the exact knots; N >= 2: N uniform samples of u (approximate)
     int no_bands;             // 1: the tcgen05 contractions multiply the zeros outside the band of S~ too
     int no_sparse_subsets;    // 1: the FP32 subset operators use the whole-object contractions too
+    uint8_t *mask01;          // [mask_rows][mask_cols] the mask as 0 / 1 (device)
+    int mask_symmetric;       // 1: the mask is mirror-symmetric about the central ray in y and z, J, M, N even
+    int online_mask;          // 1: the direct path uses the symmetric-mask kernels (mask factor online)
     uint32_t test_wait_limit; // test hook: polls of the record forward's copy waits (0 = default)
     int test_withhold;        // test hook: the record forward withholds each block's first row copy
     KernelProfiler prof;
@@ -112,6 +115,11 @@ caxsi_status plan_build_tables(caxsi_plan *p, const double *phi_host, const uint
 // ---- direct.cu ---------------------------------------------------------------
 caxsi_status direct_forward(caxsi_plan *p, const float *f, float *g, cudaStream_t s);
 caxsi_status direct_adjoint(caxsi_plan *p, const float *w, float *f, cudaStream_t s);
+// symmask.cu: the direct operators for a mirror-symmetric mask, mask factor online
+caxsi_status symmask_forward(caxsi_plan *p, const float *f, float *g, cudaStream_t s);
+caxsi_status symmask_adjoint(caxsi_plan *p, const float *w, float *f, cudaStream_t s);
+size_t symmask_fwd_smem(const DevGeo &g);
+size_t symmask_adj_smem(const DevGeo &g);
 void direct_configure(caxsi_plan *p);
 caxsi_status direct_forward_static_scratch(caxsi_plan *p, const float *f, float *g, cudaStream_t s);
 // g[list[e]] = sum over the nparts compact partial images part[c * np + e], c ascending

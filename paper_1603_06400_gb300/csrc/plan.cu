@@ -16,26 +16,9 @@
 #include <stdio.h>
 
 #include "internal.cuh"
+#include "maskgeo.cuh"
 
 namespace {
-
-struct PlanGeo64 {
-    int X, J, M, N, rho_y, rows, cols, ND, d_min;
-    double xc, dx, py, pz, Xd, Xm, C, cell, y0, z0;
-};
-
-__device__ __forceinline__ double vox_x(const PlanGeo64 &g, int i) {
-    return __dadd_rn(g.xc, __dmul_rn((double)i - 0.5 * (g.X - 1), g.dx));
-}
-__device__ __forceinline__ double vox_y(const PlanGeo64 &g, int j) {
-    return __dmul_rn(__dmul_rn((double)j - 0.5 * (g.J - 1), (double)g.rho_y), g.py);
-}
-__device__ __forceinline__ double pix_y(const PlanGeo64 &g, int n) {
-    return __dmul_rn((double)n - 0.5 * (g.N - 1), g.py);
-}
-__device__ __forceinline__ double pix_z(const PlanGeo64 &g, int m) {
-    return __dmul_rn((double)m - 0.5 * (g.M - 1), g.pz);
-}
 
 __global__ void k_plan_voxels(PlanGeo64 g, float4 *vox) {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -76,19 +59,11 @@ __global__ void k_plan_offsets(PlanGeo64 g, float *god) {
     god[t] = (float)(g_od * dth);
 }
 
-// Mask cell indices in FP64, rounded step by step as written.
-__device__ __forceinline__ double plane_t(const PlanGeo64 &g, double x) {
-    return __ddiv_rn(__dsub_rn(g.Xm, x), __dsub_rn(g.Xd, x));
-}
-
 __global__ void k_plan_mask_rows(PlanGeo64 g, int *rowidx) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.X * g.M) return;
     int i = t / g.M, m = t % g.M;
-    double tt = plane_t(g, vox_x(g, i));
-    double zm = __dmul_rn(tt, pix_z(g, m));
-    double rf = floor(__ddiv_rn(__dsub_rn(zm, g.z0), g.cell));
-    rowidx[t] = (rf < 0 || rf >= g.rows) ? -1 : (int)rf;
+    rowidx[t] = mask_row(g, i, m);
 }
 
 __global__ void k_plan_mask_cols(PlanGeo64 g, int *colidx) {
@@ -97,11 +72,7 @@ __global__ void k_plan_mask_cols(PlanGeo64 g, int *colidx) {
     int n = (int)(t % g.N);
     int j = (int)((t / g.N) % g.J);
     int i = (int)(t / ((int64_t)g.N * g.J));
-    double x = vox_x(g, i), y = vox_y(g, j);
-    double tt = plane_t(g, x);
-    double ym = __dadd_rn(y, __dmul_rn(tt, __dsub_rn(pix_y(g, n), y)));
-    double cf = floor(__ddiv_rn(__dsub_rn(ym, g.y0), g.cell));
-    colidx[t] = (cf < 0 || cf >= g.cols) ? -1 : (int)cf;
+    colidx[t] = mask_col(g, i, j, n);
 }
 
 // One 32-bit word of mask factor bits per thread: voxel v, row m, word w.
@@ -144,11 +115,7 @@ __global__ void k_popcount(const uint32_t *bits, int64_t n, unsigned long long *
 caxsi_status plan_build_tables(caxsi_plan *p, const double *phi_host, const uint8_t *mask_host) {
     const caxsi_geometry &G = p->g;
     DevGeo &d = p->dg;
-    PlanGeo64 g;
-    g.X = G.X; g.J = G.J; g.M = G.M; g.N = G.N; g.rho_y = G.rho_y;
-    g.rows = G.mask_rows; g.cols = G.mask_cols; g.ND = d.ND; g.d_min = d.d_min;
-    g.xc = G.x_center; g.dx = G.dx; g.py = G.p_y; g.pz = G.p_z; g.Xd = G.X_det;
-    g.Xm = G.X_mask; g.C = G.C; g.cell = G.mask_cell; g.y0 = G.mask_y0; g.z0 = G.mask_z0;
+    const PlanGeo64 g = plan_geo64(p);
 
     const int64_t R = (int64_t)G.X * G.J;
     const int64_t n_off = (int64_t)G.X * G.M * d.ND;
@@ -199,6 +166,18 @@ caxsi_status plan_build_tables(caxsi_plan *p, const double *phi_host, const uint
         uint8_t *m01 = (uint8_t *)malloc((size_t)n_mask);
         if (!m01) { st = CAXSI_ERR_OOM; break; }
         for (int64_t q = 0; q < n_mask; ++q) m01[q] = mask_host[q] ? 1 : 0;
+        // mirror symmetry about the central ray: cells centred on y = 0 and z = 0 and
+        // the pattern equal to its left-right and up-down images; with J, M, N even
+        // the pairs related by the mirrors then share their mask factor
+        bool sym = G.J % 2 == 0 && G.M % 2 == 0 && G.N % 2 == 0 &&
+                   G.mask_y0 == -0.5 * G.mask_cols * G.mask_cell && G.mask_z0 == -0.5 * G.mask_rows * G.mask_cell;
+        for (int r = 0; r < G.mask_rows && sym; ++r)
+            for (int c = 0; c < G.mask_cols && sym; ++c) {
+                const uint8_t a = m01[(int64_t)r * G.mask_cols + c];
+                sym = a == m01[(int64_t)r * G.mask_cols + (G.mask_cols - 1 - c)] &&
+                      a == m01[(int64_t)(G.mask_rows - 1 - r) * G.mask_cols + c];
+            }
+        p->mask_symmetric = sym ? 1 : 0;
         e = cudaMemcpy(mask_dev, m01, (size_t)n_mask, cudaMemcpyHostToDevice);
         free(m01);
         if (e != cudaSuccess) { st = CAXSI_ERR_CUDA; break; }
@@ -221,7 +200,13 @@ caxsi_status plan_build_tables(caxsi_plan *p, const double *phi_host, const uint
         }
         p->open_pairs = (int64_t)h;
     } while (0);
-    cudaFree(mask_dev);
+    // the 0 / 1 mask stays with the plan (the online mask factor reads it)
+    if (st == CAXSI_OK) {
+        p->mask01 = mask_dev;
+        p->table_bytes += n_mask;
+    } else {
+        cudaFree(mask_dev);
+    }
     cudaFree(rowidx);
     cudaFree(colidx);
     return st;

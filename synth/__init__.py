@@ -159,6 +159,18 @@ def random_mask(g: Geometry, seed: int, open_fraction: float = 0.5) -> np.ndarra
     return (rng.random((g.mask_rows, g.mask_cols)) < open_fraction).astype(np.uint8)
 
 
+def symmetric_mask(g: Geometry, seed: int, open_fraction: float = 0.5) -> np.ndarray:
+    """A mask designed for the mirror symmetries: Bernoulli cells drawn for the
+    upper-left quarter of the (centred, even-sized) cell grid and mirrored left-right
+    and up-down, so the pattern is symmetric about the central ray in y and z."""
+    rows, cols = g.mask_rows, g.mask_cols
+    assert rows % 2 == 0 and cols % 2 == 0
+    rng = np.random.default_rng(seed)
+    q = (rng.random((rows // 2, cols // 2)) < open_fraction).astype(np.uint8)
+    top = np.concatenate([q, q[:, ::-1]], axis=1)
+    return np.ascontiguousarray(np.concatenate([top, top[::-1, :]], axis=0))
+
+
 def _profile(rng, q, n_peaks_max=4):
     prof = np.zeros_like(q)
     lo, hi = q[0] + 0.2, q[-1] - 0.2
