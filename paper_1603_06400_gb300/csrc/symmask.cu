@@ -7,11 +7,11 @@
 // (v', m, N-1-n) with v' = (i, J-1-j), and the image under both share the scatter
 // angle, G_so, G_od, dtheta AND the mask factor T; only the left-right images read
 // another object column (f at v' instead of v).  So:
-//   forward: per voxel pair (v, v') and upper-left quadrant pixel (m, n): the
-//     geometry and T once, the energy sum W for f[v] and for f[v'] (the paper's
-//     W_L, W_R), and four outputs: c W_v to (m, n) and (M-1-m, n), c W_v' to
-//     (m, N-1-n) and (M-1-m, N-1-n) -- a quarter of the geometry and half of the
-//     energy sums of the plain kernel;
+//   forward: per voxel pair (v, v') (v in the left half, j < J/2) and upper-half
+//     pixel (m < M/2, any n): the geometry and T once, the energy sum W for f[v]
+//     and for f[v'] (the paper's W_L, W_R); c W_v goes to (m, n) and (M-1-m, n),
+//     c W_v' to (m, N-1-n) and (M-1-m, N-1-n) -- a quarter of the geometry and
+//     half of the energy sums of the plain kernel;
 //   adjoint: per voxel and upper-half pixel (m, n): the geometry and T once, one
 //     energy scatter of c (w[m][n] + w[M-1-m][n]) -- half of the plain kernel's.
 // T is not read from the precomputed per-pair bits: each block (warp) computes the
@@ -36,10 +36,12 @@ struct SymTables {
     const uint8_t *mask;   // [rows][cols], 0 / 1
 };
 
-// Block: 8 warps over an 8 x 32 tile of the upper-left quadrant (m < M/2,
-// n < N/2); voxel pairs [by pc, (by + 1) pc) of the X * J/2 pairs
-// p = i (J/2) + j, v = i J + j, v' = i J + J-1-j.  Writes the four mirror pixels
-// of each quadrant pixel in partial image by.
+// Block: 8 warps over 8 upper-half rows (m < M/2) and 16 mirrored column pairs:
+// lane l < 16 takes column n = 16 tn + l, lane l + 16 its mirror N-1-n; voxel
+// pairs [by pc, (by + 1) pc) of the X * J/2 pairs p = i (J/2) + j, v = i J + j,
+// v' = i J + J-1-j.  Lane l accumulates c W_v (its own column, from v) and c W_v'
+// (the mirror column, from v'); a pixel's sum is its lane's first plus its mirror
+// lane's second.  Writes each pixel and its up-down image in partial image by.
 __global__ void __launch_bounds__(FWD_THREADS)
 k_fwd_direct_symmask(SymTables S, const float *__restrict__ f, float *__restrict__ part, int pc, int tiles_n) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -55,8 +57,9 @@ k_fwd_direct_symmask(SymTables S, const float *__restrict__ f, float *__restrict
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
-    const int m = tm * FWD_WARPS + warp, n = tn * 32 + lane;
-    const bool valid = m < Mh && n < Nh;
+    const int c16 = tn * 16 + (lane & 15);          // left-half column of the lane's pair
+    const int m = tm * FWD_WARPS + warp, n = lane < 16 ? c16 : g.N - 1 - c16;
+    const bool valid = m < Mh && c16 < Nh;
     const int R2 = g.X * Jh;
     const int p0 = blockIdx.y * pc, p1 = min(p0 + pc, R2);
 
@@ -84,8 +87,8 @@ k_fwd_direct_symmask(SymTables S, const float *__restrict__ f, float *__restrict
                 const int mm = tm * FWD_WARPS + k;
                 s_row[vv * FWD_WARPS + k] = mm < Mh ? mask_row(S.g64, i, mm) : -1;
             } else {
-                const int nn = tn * 32 + (k - FWD_WARPS);
-                s_col[vv * 32 + (k - FWD_WARPS)] = nn < Nh ? mask_col(S.g64, i, j, nn) : -1;
+                const int l = k - FWD_WARPS, cc = tn * 16 + (l & 15);
+                s_col[vv * 32 + l] = cc < Nh ? mask_col(S.g64, i, j, l < 16 ? cc : g.N - 1 - cc) : -1;
             }
         }
         if (tid < nv) {
@@ -121,13 +124,12 @@ k_fwd_direct_symmask(SymTables S, const float *__restrict__ f, float *__restrict
             accR = fmaf(c, wr, accR);
         }
     }
+    // the mirror column's contributions from the right-half voxels are the mirror lane's
+    const float sum = accL + __shfl_xor_sync(0xffffffffu, accR, 16);
     if (valid) {
         float *dst = part + (int64_t)blockIdx.y * g.M * g.N;
-        const int mb = g.M - 1 - m, nb = g.N - 1 - n;
-        dst[(int64_t)m * g.N + n] = accL;
-        dst[(int64_t)mb * g.N + n] = accL;
-        dst[(int64_t)m * g.N + nb] = accR;
-        dst[(int64_t)mb * g.N + nb] = accR;
+        dst[(int64_t)m * g.N + n] = sum;
+        dst[(int64_t)(g.M - 1 - m) * g.N + n] = sum;
     }
 }
 
@@ -224,7 +226,7 @@ size_t symmask_adj_smem(const DevGeo &g) {
 caxsi_status symmask_forward(caxsi_plan *p, const float *f, float *g_out, cudaStream_t s) {
     const DevGeo &g = p->dg;
     const int Mh = g.M / 2, Nh = g.N / 2, R2 = g.X * (g.J / 2);
-    const int tiles_n = (int)ceil_div64(Nh, 32);
+    const int tiles_n = (int)ceil_div64(Nh, 16);
     const int tiles = (int)ceil_div64(Mh, FWD_WARPS) * tiles_n;
     // chunks of voxel pairs: about 16 blocks per SM, at most the plan's partial images
     int chunks = (int)std::min<int64_t>(ceil_div64(16 * p->num_sms, tiles), p->fwd_chunks);
