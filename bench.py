@@ -27,7 +27,9 @@ path) of the 16-bit contractions and of u tables of 1024-4096 samples.  The
 "batch" key times the batched operators on 32 objects of uneven size against
 one call per object: objects of uneven extent in x, z and q (one plan each, one
 persistent launch per stage, direct FP32 path), and depth slabs of the
-paper-scale object (table path).
+paper-scale object (table path).  The "symmetric_mask" key times the direct
+operators for a mirror-symmetric mask with the mask factor computed online
+against the same operators reading per-pair mask bits.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload per step.
@@ -780,6 +782,48 @@ def uneven_batch_experiment(dev, n_objects=32, reps=3):
     return out
 
 
+def symmetric_mask_experiment(dev, reps=3):
+    """The joint system design of Sec. III-A / III-C: with a secondary mask that is
+    mirror-symmetric about the central ray (synth.symmetric_mask), the direct FP32
+    operators share geometry and mask factor among the four mirror pairs and
+    compute the mask factor online (CAXSI_OPT_ONLINE_MASK) instead of reading the
+    precomputed per-pair bits.  Paper-scale workload, phantom 0; one forward + one
+    adjoint timed with CUDA events (after a warm-up), with and without the option,
+    and the relative L2 difference between the two (same operator)."""
+    import torch
+    from paper_1603_06400_gb300 import caxsi
+    g = synth.paper_geometry()
+    phi = synth.tungsten_spectrum(g)
+    mask = synth.symmetric_mask(g, 1003)
+    plan = caxsi.Plan(g, phi, mask)
+    f = torch.tensor(synth.phantom(g, 0), dtype=torch.float32, device=dev)
+    w = torch.rand((g.M, g.N), device=dev, generator=torch.Generator(device=dev).manual_seed(7)) + 0.5
+    D = caxsi.PATH_DIRECT
+    out = {"mask": "mirror-symmetric Bernoulli(0.5) cells (seed 1003)", "path": "direct"}
+    res = {}
+    for on in (False, True):
+        plan.set_online_mask(on)
+        gg, ff = plan.forward(f, path=D), plan.adjoint(w, path=D)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            plan.forward(f, path=D)
+            plan.adjoint(w, path=D)
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        key = "online_symmetric" if on else "per_pair_bits"
+        out[key] = {"evals_per_s": 1.0 / sec, "seconds": sec}
+        res[key] = (gg.double(), ff.double())
+    out["speedup"] = out["per_pair_bits"]["seconds"] / out["online_symmetric"]["seconds"]
+    a, b = res["per_pair_bits"], res["online_symmetric"]
+    out["fwd_rel_l2_vs_bits"] = float(torch.linalg.norm(b[0] - a[0]) / torch.linalg.norm(a[0]))
+    out["adj_rel_l2_vs_bits"] = float(torch.linalg.norm(b[1] - a[1]) / torch.linalg.norm(a[1]))
+    plan.close()
+    return out
+
+
 def precision_experiment(caxsi, plan, g, dev, make_plan, reps=20):
     """Throughput and error of the reduced-cost operators at full size: 16-bit
     contractions (bf16, fp16) on the exact knots, and u tables of 1024, 2048 and
@@ -1011,6 +1055,7 @@ def run_ours(args):
         line["recon"] = recon_experiment(caxsi, plan, g, dev, phantom=0, warm=warm, make_plan=make_plan)
         line["recon_seeds"] = recon_seeds(caxsi, plan, g, dev, warm)
     if world == 1 and args.workload == "paper" and not args.no_recon:
+        line["symmetric_mask"] = symmetric_mask_experiment(dev)
         line["batch"] = {"uneven_objects": uneven_batch_experiment(dev),
                          "depth_slabs": batch_experiment(plan, g)}
     if world == 1 and not args.no_cpu_baseline:
