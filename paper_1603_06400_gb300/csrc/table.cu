@@ -223,6 +223,108 @@ k_adj_table(PairArgs A, TabArgs T, const float *__restrict__ w, float *__restric
     }
 }
 
+// Deterministic adjoint per-pair stage.  The structure of k_adj_table, but each
+// contribution is converted to a 64-bit fixed-point integer (x 2^e, rounded) and
+// the knot row is accumulated with 64-bit integer atomics, which are exact and
+// so independent of the order in which the threads add: repeated calls are
+// bitwise identical.  The exponent e is chosen per call so that no row entry can
+// overflow: every contribution is at most cmax * max|w| (cmax = 2 max(C G_so) max(G_od
+// dtheta), computed when the table is built; the angular factor is at most 2), a
+// row entry sums at most M N of them, and e = 61 - ceil(log2(M N cmax max|w|)).
+// The quantum 2^-e is then below 2^-61 of the largest possible entry: far under
+// the FP32 rounding of any entry that matters for f = V S~.
+#define CAXSI_CUDA_TRY_E(expr)                  \
+    do {                                        \
+        cudaError_t _e = (expr);                \
+        if (_e != cudaSuccess) return _e;       \
+    } while (0)
+
+// max over voxels of C G_so (the z component of the voxel table)
+__global__ void k_vox_zmax(const float4 *__restrict__ vox, int n, unsigned *out) {
+    float m = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) m = fmaxf(m, fabsf(vox[i].z));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+__global__ void k_absmax(const float *__restrict__ x, int64_t n, unsigned *out) {
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(x[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));   // non-negative floats order as integers
+}
+
+template <int PPT>
+__global__ void __launch_bounds__(TAB_THREADS, 1)
+k_adj_table_fx(PairArgs A, TabArgs T, const float *__restrict__ w, float *__restrict__ Vtab, int vc, float cmax,
+               const unsigned *__restrict__ wmax_bits) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const DevGeo &g = A.g;
+    float2 *s_kn = reinterpret_cast<float2 *>(smem_raw);
+    unsigned long long *s_v = reinterpret_cast<unsigned long long *>(s_kn + T.B);   // [Bp] two's complement
+    uint16_t *s_bs = reinterpret_cast<uint16_t *>(s_v + T.Bp);
+    const int tid = threadIdx.x;
+    for (int t = tid; t < T.B; t += TAB_THREADS) s_kn[t] = T.knots[t];
+    for (int t = tid; t < T.NB; t += TAB_THREADS) s_bs[t] = T.bstart[t];
+
+    const int64_t npix = (int64_t)g.M * g.N;
+    const int step_m = TAB_THREADS / g.N, step_n = TAB_THREADS % g.N;
+    const int v0 = blockIdx.x * vc;
+    const int v1 = min(v0 + vc, g.R);
+    const float u_first = T.knots[0].x, u_last = T.knots[T.B - 1].x;
+    // the fixed-point scale 2^e of this call
+    const double bound = (double)npix * (double)cmax * (double)__uint_as_float(*wmax_bits);
+    int e = 0;
+    if (bound > 0.0 && isfinite(bound)) {
+        frexp(bound, &e);                     // bound < 2^e
+        e = 61 - e;
+    }
+    const double scale = ldexp(1.0, e), inv_scale = ldexp(1.0, -e);
+
+    for (int v = v0; v < v1; ++v) {
+        __syncthreads();
+        for (int t = tid; t < T.Bp; t += TAB_THREADS) s_v[t] = 0ull;
+        __syncthreads();
+        const int i = v / g.J, j = v - i * g.J;
+        const float4 vx = A.vox[v];
+        const uint32_t *tb = A.tbits + (int64_t)v * g.M * g.Nw;
+        const float *god_i = A.god + (int64_t)i * g.M * g.ND - g.d_min - g.rho_y * j;
+        for (int64_t pc = 0; pc < npix; pc += (int64_t)PPT * TAB_THREADS) {
+            const int64_t p0 = pc + tid;
+            int m = (int)(p0 / g.N), n = (int)(p0 % g.N);
+#pragma unroll
+            for (int s = 0; s < PPT; ++s) {
+                const int64_t p = p0 + (int64_t)s * TAB_THREADS;
+                if (p < npix) {
+                    const uint32_t word = tb[m * g.Nw + (n >> 5)];
+                    const float wv = w[p];
+                    if (((word >> (n & 31)) & 1u) && wv != 0.f) {
+                        float u, ang;
+                        pair_u_angular(vx.x, vx.y, vx.w, (float)n - g.cN, A.zrow[m], g.p_y, g.Xd, u, ang);
+                        if (u >= u_first && u <= u_last) {
+                            const int t = find_interval(u, s_kn, s_bs, T.B, T.NB, T.u0, T.inv_h);
+                            const float2 kn = s_kn[t];
+                            const float al = (u - kn.x) * kn.y;
+                            const float c = vx.z * god_i[(int64_t)m * g.ND + n] * ang * wv;
+                            const float hi = c * al;
+                            atomicAdd(&s_v[t], (unsigned long long)__double2ll_rn((double)(c - hi) * scale));
+                            atomicAdd(&s_v[t + 1], (unsigned long long)__double2ll_rn((double)hi * scale));
+                        }
+                    }
+                }
+                m += step_m;
+                n += step_n;
+                if (n >= g.N) { n -= g.N; ++m; }
+            }
+        }
+        __syncthreads();
+        float *vrow = Vtab + (int64_t)v * T.Bp;
+        for (int t = tid; t < T.B; t += TAB_THREADS)
+            vrow[t] = (float)((double)(long long)s_v[t] * inv_scale);
+    }
+}
+
 template <int PPT>
 cudaError_t launch_fwd(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s) {
     dim3 grid(T->fwd_chunks, T->pix_chunks);
@@ -255,6 +357,30 @@ cudaError_t dispatch_fwd(const caxsi_plan *p, const TablePath *T, float *part, c
 }
 
 cudaError_t dispatch_adj(const caxsi_plan *p, const TablePath *T, const float *w, cudaStream_t s) {
+    if (T->smem_adj_fx) {
+        // deterministic form: the exact fixed-point sums, scaled by max|w| of this call
+        CAXSI_CUDA_TRY_E(cudaMemsetAsync(T->wmax, 0, sizeof(unsigned), s));
+        const int64_t npix = (int64_t)p->dg.M * p->dg.N;
+        k_absmax<<<(unsigned)std::min<int64_t>(ceil_div64(npix, 256), 4 * p->num_sms), 256, 0, s>>>(w, npix, T->wmax);
+        CAXSI_CUDA_TRY_E(cudaGetLastError());
+        TabArgs ta = tab_args(T);
+        switch (T->ppt) {
+#define CAXSI_FX(PP)                                                                                           \
+    case PP: {                                                                                                 \
+        CAXSI_CUDA_TRY_E(cudaFuncSetAttribute(k_adj_table_fx<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                              (int)T->smem_adj_fx));                                            \
+        k_adj_table_fx<PP><<<T->adj_chunks, TAB_THREADS, T->smem_adj_fx, s>>>(pair_args(p), ta, w, T->tab,     \
+                                                                             T->adj_vc, T->cmax, T->wmax);     \
+        return cudaGetLastError();                                                                             \
+    }
+            CAXSI_FX(1)
+            CAXSI_FX(2)
+            CAXSI_FX(4)
+            CAXSI_FX(8)
+            CAXSI_FX(16)
+#undef CAXSI_FX
+        }
+    }
     switch (T->ppt) {
         case 1: return launch_adj<1>(p, T, w, s);
         case 2: return launch_adj<2>(p, T, w, s);
@@ -265,6 +391,7 @@ cudaError_t dispatch_adj(const caxsi_plan *p, const TablePath *T, const float *w
 }
 
 void free_table(TablePath *T) {
+    if (T) cudaFree(T->wmax);
     if (!T) return;
     records_free(T);
     cudaFree(T->S_hi);
@@ -439,6 +566,35 @@ caxsi_status build_table(caxsi_plan *p) {
         T->smem_adj = T->smem_fwd;
         int smem_max = 0;
         cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+        // the deterministic adjoint holds its knot row as 64-bit integers: where that
+        // fits (up to about 14 000 knots) it replaces the float atomics
+        {
+            const size_t fx = (size_t)B * sizeof(float2) + (size_t)T->Bp * sizeof(unsigned long long) +
+                              (size_t)NB * sizeof(uint16_t);
+            T->smem_adj_fx = fx <= (size_t)smem_max ? fx : 0;
+        }
+        if (T->smem_adj_fx) {
+            // cmax = 2 max(C G_so) max(G_od dtheta), with a margin for rounding
+            unsigned h[2] = {0u, 0u};
+            if (cudaMalloc(&T->wmax, 2 * sizeof(unsigned)) != cudaSuccess ||
+                cudaMemset(T->wmax, 0, 2 * sizeof(unsigned)) != cudaSuccess) {
+                st = CAXSI_ERR_OOM;
+                break;
+            }
+            const int64_t n_god = (int64_t)d.X * d.M * d.ND;
+            k_vox_zmax<<<(unsigned)std::min<int64_t>(ceil_div64(d.R, 256), 4 * p->num_sms), 256>>>(p->vox, d.R, T->wmax);
+            k_absmax<<<(unsigned)std::min<int64_t>(ceil_div64(n_god, 256), 4 * p->num_sms), 256>>>(p->god, n_god,
+                                                                                                 T->wmax + 1);
+            if (cudaGetLastError() != cudaSuccess ||
+                cudaMemcpy(h, T->wmax, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                st = CAXSI_ERR_CUDA;
+                break;
+            }
+            float zmax, gmax;
+            memcpy(&zmax, &h[0], sizeof(float));
+            memcpy(&gmax, &h[1], sizeof(float));
+            T->cmax = 2.f * zmax * gmax * 1.001f;
+        }
         if ((size_t)smem_max < T->smem_fwd) { st = CAXSI_ERR_UNSUPPORTED; break; }
         if (cudaMalloc(&T->fwd_part, (size_t)T->fwd_chunks * npix * sizeof(float)) != cudaSuccess) {
             st = CAXSI_ERR_OOM;

@@ -76,6 +76,9 @@ struct TablePath {
     int fwd_chunks = 0, fwd_vc = 0, ppt = 1, threads = 1024, pix_chunks = 1;
     int adj_chunks = 0, adj_vc = 0;
     size_t smem_fwd = 0, smem_adj = 0;
+    size_t smem_adj_fx = 0;     // shared memory of the deterministic on-the-fly adjoint (0: does not fit)
+    float cmax = 0.f;           // bound of one pair's factor C G_so G_od dtheta (1+cos^2)cos (on-the-fly adjoint)
+    unsigned *wmax = nullptr;   // [1] device: max |w| of the current adjoint call (float bits)
 
     // Pair records (precomputed per-pair interval and weights), voxel-major.
     // rec: every open pair, sorted by (knot interval t, pixel) within each voxel.

@@ -127,6 +127,19 @@ def paper_geometry(**kw) -> Geometry:
                          p_y=0.76, p_z=1.52, dx=0.546875, **kw)
 
 
+def paper_table1_geometry(**kw) -> Geometry:
+    """The geometry of the paper's timing study (Sec. VII, Table I): detector
+    2048 (y) x 1536 (z) pixels at 0.19 mm, object 28 x 28 voxels of 2.5 mm (x) x
+    3.04 mm (y, 16 detector pitches: translation step 16), 79 q bins over
+    0.01-0.4 A^-1 (0.1-4 nm^-1), 125 kVp source (64 energy bins 15-125 keV here),
+    the paper's distances, and a mask grid wide enough to cover every detector
+    ray.  The paper's own mask and spectrum are not available: the mask and
+    spectrum recipes of this module stand in for them."""
+    return make_geometry(X=28, J=28, Q=79, M=1536, N=2048, K=64, rho_y=16, p_y=0.19, p_z=0.19, dx=2.5,
+                         q_min=0.1, q_max=4.0, E_min=15.0, E_max=125.0, mask_half_y=200.0, mask_half_z=150.0,
+                         **kw)
+
+
 def energy_bin_edges(g: Geometry) -> np.ndarray:
     return np.linspace(g.E_min, g.E_max, g.K + 1)
 

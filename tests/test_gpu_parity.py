@@ -323,6 +323,10 @@ def test_large_detector_uses_on_the_fly_table_kernels(cx):
     assert plan.info()["n_records"] == 0
     assert rel_l2(gg, oracle.forward(g, phi, mask, _f32(f))) <= REL_L2_TOL
     assert rel_l2(fa, oracle.adjoint(g, phi, mask, _f32(w))) <= REL_L2_TOL
+    # no atomics in the on-the-fly adjoint: repeated calls are bitwise identical
+    for _ in range(3):
+        assert np.array_equal(plan.adjoint(_t(torch, w), path=p).cpu().numpy(), fa)
+        assert np.array_equal(plan.forward(_t(torch, f), path=p).cpu().numpy(), gg)
     with pytest.raises(caxsi.CaxsiError) as e:     # the 16-bit paths need the records
         plan.forward(_t(torch, f), path=caxsi.PATHS["table_bf16"])
     assert e.value.status == 6
@@ -339,6 +343,32 @@ def test_large_detector_uses_on_the_fly_table_kernels(cx):
         plan.forward_subset(3, _t(torch, f), path=p)
     assert e.value.status == 6
     assert plan.info()["device_error"] == 0
+    plan.close()
+
+
+@pytest.mark.parametrize("path", FP32_PATHS)
+def test_paper_table1_geometry_sampled(cx, path):
+    """The paper's own timing geometry (Sec. VII, Table I): 2048 x 1536 detector
+    pixels of 0.19 mm, 28 x 28 voxels, translation step 16, 79 q bins; sampled
+    outputs against the oracle, repeated calls bitwise identical."""
+    caxsi, torch = cx
+    g = synth.paper_table1_geometry()
+    phi = synth.tungsten_spectrum(g)
+    mask = synth.random_mask(g, 1004)
+    plan, p = _plan(caxsi, g, phi, mask, path)
+    f = synth.phantom(g, 0)
+    w = synth.uniform_random((g.M, g.N), 1) + 0.5
+    gg = plan.forward(_t(torch, f), path=p)
+    fa = plan.adjoint(_t(torch, w), path=p)
+    assert torch.equal(plan.forward(_t(torch, f), path=p), gg)
+    assert torch.equal(plan.adjoint(_t(torch, w), path=p), fa)
+    gg = gg.cpu().numpy().ravel()
+    fa = fa.cpu().numpy().reshape(g.X * g.J, g.Q)
+    rng = np.random.default_rng(7)
+    pix = np.concatenate([rng.choice(g.M * g.N, 48, replace=False), [0, g.M * g.N - 1]])
+    assert rel_l2(gg[pix], oracle.forward_pixels(g, phi, mask, _f32(f), pix)) <= REL_L2_TOL
+    vox = np.concatenate([rng.choice(g.X * g.J, 4, replace=False), [0, g.X * g.J - 1]])
+    assert rel_l2(fa[vox], oracle.adjoint_voxels(g, phi, mask, _f32(w), vox)) <= REL_L2_TOL
     plan.close()
 
 
