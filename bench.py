@@ -29,7 +29,9 @@ one call per object: objects of uneven extent in x, z and q (one plan each, one
 persistent launch per stage, direct FP32 path), and depth slabs of the
 paper-scale object (table path).  The "symmetric_mask" key times the direct
 operators for a mirror-symmetric mask with the mask factor computed online
-against the same operators reading per-pair mask bits.
+against the same operators reading per-pair mask bits.  The "paper_table1" key
+times one forward and one adjoint on the paper's own timing geometry (2048 x 1536
+detector, 28 x 28 voxels), its MATLAB times beside them as context.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload per step.
@@ -782,6 +784,48 @@ def uneven_batch_experiment(dev, n_objects=32, reps=3):
     return out
 
 
+def paper_table1_experiment(dev, reps=3):
+    """The paper's own timing geometry (Sec. VII, Table I: 2048 x 1536 detector
+    pixels of 0.19 mm, 28 x 28 voxels, translation step 16, 79 q bins; 64 energy
+    bins and the synthetic spectrum and mask stand in for the paper's 125 kVp
+    source and its mask): one forward and one adjoint, timed separately with CUDA
+    events after a warm-up, on the direct FP32 path and on the FP32 table path
+    (on-the-fly knot interpolation: the detector is too large for 16-bit pair
+    records).  The paper's MATLAB times are printed beside them as context; they
+    are another machine's and another implementation's (with its own 6.2 %
+    forward approximation error), not a target."""
+    import torch
+    from paper_1603_06400_gb300 import caxsi
+    g = synth.paper_table1_geometry()
+    phi = synth.tungsten_spectrum(g)
+    mask = synth.random_mask(g, 1004)
+    plan = caxsi.Plan(g, phi, mask)
+    f = torch.tensor(synth.phantom(g, 0), dtype=torch.float32, device=dev)
+    w = torch.rand((g.M, g.N), device=dev, generator=torch.Generator(device=dev).manual_seed(7)) + 0.5
+    out = {"geometry": "detector 2048 x 1536 pixels (0.19 mm), object 28 x 28 voxels (2.5 x 3.04 mm), "
+                       "79 q bins 0.1-4 nm^-1, 64 energy bins 15-125 keV",
+           "pairs": g.X * g.J * g.M * g.N, "open_pairs": plan.info()["n_open_pairs"],
+           "paper_matlab_seconds": {"forward_all_optimisations": 61.04, "backward_all_optimisations": 287.40,
+                                    "forward_no_optimisation": 10516.88, "backward_no_optimisation": 10512.32}}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+    for path in ("direct", "table_fp32"):
+        P = caxsi.PATHS[path]
+        out[path] = {"forward_seconds": timed(lambda: plan.forward(f, path=P)),
+                     "adjoint_seconds": timed(lambda: plan.adjoint(w, path=P))}
+    plan.close()
+    return out
+
+
 def symmetric_mask_experiment(dev, reps=3):
     """The joint system design of Sec. III-A / III-C: with a secondary mask that is
     mirror-symmetric about the central ray (synth.symmetric_mask), the direct FP32
@@ -1056,6 +1100,7 @@ def run_ours(args):
         line["recon_seeds"] = recon_seeds(caxsi, plan, g, dev, warm)
     if world == 1 and args.workload == "paper" and not args.no_recon:
         line["symmetric_mask"] = symmetric_mask_experiment(dev)
+        line["paper_table1"] = paper_table1_experiment(dev)
         line["batch"] = {"uneven_objects": uneven_batch_experiment(dev),
                          "depth_slabs": batch_experiment(plan, g)}
     if world == 1 and not args.no_cpu_baseline:
