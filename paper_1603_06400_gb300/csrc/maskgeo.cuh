@@ -58,3 +58,47 @@ static __device__ __forceinline__ int mask_col(const PlanGeo64 &g, int i, int j,
     const double cf = floor(__ddiv_rn(__dsub_rn(ym, g.y0), g.cell));
     return (cf < 0 || cf >= g.cols) ? -1 : (int)cf;
 }
+
+// The same cell decisions from an FP32 estimate, falling back to the FP64 formula
+// when the estimate is within MASK_EDGE cell widths of a cell edge.  The FP32
+// estimate's error is far below MASK_EDGE (a few ulps of coordinates below 10^3
+// cell widths), so away from the edges the floor of the estimate is the floor of
+// the exact value, and next to them the FP64 formula decides: the result equals
+// mask_row / mask_col.
+#define MASK_EDGE 4e-3f
+
+struct MaskGeo32 {
+    float xc, dx, ymul, py, pz, Xd, Xm, inv_cell, y0, z0;
+    float hx, hj, hn, hm;   // (X-1)/2, (J-1)/2, (N-1)/2, (M-1)/2
+};
+
+inline MaskGeo32 mask_geo32(const PlanGeo64 &g) {
+    MaskGeo32 m;
+    m.xc = (float)g.xc; m.dx = (float)g.dx; m.ymul = (float)(g.rho_y * g.py); m.py = (float)g.py;
+    m.pz = (float)g.pz; m.Xd = (float)g.Xd; m.Xm = (float)g.Xm; m.inv_cell = (float)(1.0 / g.cell);
+    m.y0 = (float)g.y0; m.z0 = (float)g.z0;
+    m.hx = 0.5f * (float)(g.X - 1); m.hj = 0.5f * (float)(g.J - 1); m.hn = 0.5f * (float)(g.N - 1);
+    m.hm = 0.5f * (float)(g.M - 1);
+    return m;
+}
+
+static __device__ __forceinline__ bool near_edge(float u) { return fabsf(u - rintf(u)) < MASK_EDGE; }
+
+static __device__ __forceinline__ int mask_row_fast(const PlanGeo64 &g, const MaskGeo32 &h, int i, int m) {
+    const float x = fmaf((float)i - h.hx, h.dx, h.xc);
+    const float t = (h.Xm - x) / (h.Xd - x);
+    const float u = (t * (((float)m - h.hm) * h.pz) - h.z0) * h.inv_cell;
+    if (near_edge(u)) return mask_row(g, i, m);
+    const float r = floorf(u);
+    return (r < 0.f || r >= (float)g.rows) ? -1 : (int)r;
+}
+
+static __device__ __forceinline__ int mask_col_fast(const PlanGeo64 &g, const MaskGeo32 &h, int i, int j, int n) {
+    const float x = fmaf((float)i - h.hx, h.dx, h.xc);
+    const float t = (h.Xm - x) / (h.Xd - x);
+    const float y = ((float)j - h.hj) * h.ymul, yn = ((float)n - h.hn) * h.py;
+    const float u = (fmaf(t, yn - y, y) - h.y0) * h.inv_cell;
+    if (near_edge(u)) return mask_col(g, i, j, n);
+    const float c = floorf(u);
+    return (c < 0.f || c >= (float)g.cols) ? -1 : (int)c;
+}

@@ -15,9 +15,10 @@
 //   adjoint: per voxel and upper-half pixel (m, n): the geometry and T once, one
 //     energy scatter of c (w[m][n] + w[M-1-m][n]) -- half of the plain kernel's.
 // T is not read from the precomputed per-pair bits: each block (warp) computes the
-// mask cells its rays cross, in FP64 with the plan builder's formula
-// (maskgeo.cuh), for its staged voxels and its detector rows and columns, and
-// looks the cell up in the mask array (rows x cols bytes, L1-resident).  The
+// mask cells its rays cross for its staged voxels and its detector rows and
+// columns -- in FP32, and with the plan builder's FP64 formula where the FP32
+// estimate lies next to a cell edge (maskgeo.cuh), so the decision is the plan's
+// -- and looks the cell up in the mask array (rows x cols bytes, L1-resident).  The
 // per-pair bit table is then not needed by these kernels.
 #include <algorithm>
 
@@ -33,6 +34,7 @@ constexpr int SVS = 16;   // voxel pairs staged per shared-memory round (forward
 struct SymTables {
     Tables T;
     PlanGeo64 g64;
+    MaskGeo32 g32;
     const uint8_t *mask;   // [rows][cols], 0 / 1
 };
 
@@ -85,10 +87,10 @@ k_fwd_direct_symmask(SymTables S, const float *__restrict__ f, float *__restrict
             const int pp = pb + vv, i = pp / Jh, j = pp - i * Jh;
             if (k < FWD_WARPS) {
                 const int mm = tm * FWD_WARPS + k;
-                s_row[vv * FWD_WARPS + k] = mm < Mh ? mask_row(S.g64, i, mm) : -1;
+                s_row[vv * FWD_WARPS + k] = mm < Mh ? mask_row_fast(S.g64, S.g32, i, mm) : -1;
             } else {
                 const int l = k - FWD_WARPS, cc = tn * 16 + (l & 15);
-                s_col[vv * 32 + l] = cc < Nh ? mask_col(S.g64, i, j, l < 16 ? cc : g.N - 1 - cc) : -1;
+                s_col[vv * 32 + l] = cc < Nh ? mask_col_fast(S.g64, S.g32, i, j, l < 16 ? cc : g.N - 1 - cc) : -1;
             }
         }
         if (tid < nv) {
@@ -157,13 +159,13 @@ k_adj_direct_symmask(SymTables S, const float *__restrict__ w, float *__restrict
     __syncthreads();
     if (v >= g.R) return;
     const int i = v / g.J, j = v - i * g.J;
-    for (int nn = lane; nn < g.N; nn += 32) colc[nn] = mask_col(S.g64, i, j, nn);
+    for (int nn = lane; nn < g.N; nn += 32) colc[nn] = mask_col_fast(S.g64, S.g32, i, j, nn);
     __syncwarp();
     const float4 vx = T.vox[v];
     float *my = acc + lane;
     const int m0 = sp * rows_per_split, m1 = min(Mh, m0 + rows_per_split);
     for (int m = m0; m < m1; ++m) {
-        const int row = mask_row(S.g64, i, m);
+        const int row = mask_row_fast(S.g64, S.g32, i, m);
         if (row < 0) continue;
         const uint8_t *mrow = S.mask + row * S.g64.cols;
         const float sz = T.zrow[m];
@@ -207,6 +209,7 @@ SymTables sym_tables(const caxsi_plan *p) {
     SymTables S;
     S.T = tables_of(p);
     S.g64 = plan_geo64(p);
+    S.g32 = mask_geo32(S.g64);
     S.mask = p->mask01;
     return S;
 }
