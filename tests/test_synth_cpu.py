@@ -105,3 +105,46 @@ def test_count_draws():
     assert min(peaks) >= 1e2 and max(peaks) <= 1e4
     # log-uniform: the median is near the geometric mean 1e3
     assert 3e2 < float(np.median(peaks)) < 3e3
+
+
+def test_symmetric_mask_is_mirror_symmetric_and_seeded():
+    for g in (synth.tiny_geometry(), synth.paper_geometry()):
+        m = synth.symmetric_mask(g, 5)
+        assert m.shape == (g.mask_rows, g.mask_cols) and m.dtype == np.uint8
+        np.testing.assert_array_equal(m, m[:, ::-1])      # left-right about y = 0
+        np.testing.assert_array_equal(m, m[::-1, :])      # up-down about z = 0
+        assert 0.4 < m.mean() < 0.6
+        # the grid is centred on the central ray, as the symmetry needs
+        assert g.mask_y0 == -0.5 * g.mask_cols * g.mask_cell and g.mask_z0 == -0.5 * g.mask_rows * g.mask_cell
+        np.testing.assert_array_equal(m, synth.symmetric_mask(g, 5))
+        assert not np.array_equal(m, synth.symmetric_mask(g, 6))
+
+
+def test_uneven_sizes_cover_their_ranges():
+    sizes = synth.uneven_sizes(32, 2024)
+    assert len(sizes) == 32 and sizes[0] == (32, 64, 64) and sizes[1] == (128, 256, 128)
+    X, J, Q = map(np.array, zip(*sizes))
+    assert X.min() == 32 and X.max() == 128 and J.min() == 64 and J.max() == 256
+    assert Q.min() == 64 and Q.max() == 128
+    assert len(set(sizes)) == 32                         # sizes differ in every dimension
+    g = synth.uneven_object_geometry(77, 162, 113)
+    base = synth.paper_geometry()
+    assert (g.X, g.J, g.Q) == (77, 162, 113)
+    assert (g.M, g.N, g.K, g.p_y, g.dx, g.q_min, g.q_max) == (base.M, base.N, base.K, base.p_y, base.dx,
+                                                              base.q_min, base.q_max)
+    # C scales like the recipe's dimensional constant (inversely with X J)
+    assert g.C * 77 * 162 == pytest.approx(base.C * base.X * base.J)
+
+
+def test_paper_table1_geometry_matches_the_timing_study():
+    g = synth.paper_table1_geometry()
+    assert (g.N, g.M) == (2048, 1536) and g.p_y == g.p_z == 0.19          # 0.19 mm pixels
+    assert (g.X, g.J) == (28, 28) and g.dx == 2.5
+    assert g.rho_y == 16 and g.rho_y * g.p_y == pytest.approx(3.04)          # 3.04 mm object pitch
+    assert g.Q == 79 and (g.q_min, g.q_max) == (0.1, 4.0)                   # 0.01-0.4 per Angstrom
+    assert g.E_max == 125.0
+    # the mask grid covers every ray from the object to the detector edges
+    t = (g.X_mask - (g.x_center - 0.5 * (g.X - 1) * g.dx)) / (g.X_det - (g.x_center - 0.5 * (g.X - 1) * g.dx))
+    y_obj, y_det = 0.5 * g.J * g.rho_y * g.p_y, 0.5 * g.N * g.p_y
+    assert (1 - t) * y_obj + t * y_det < -g.mask_y0        # the widest crossing, object and detector edges
+    assert t * 0.5 * g.M * g.p_z < -g.mask_z0
