@@ -558,9 +558,9 @@ def recon_seeds(caxsi, plan, g, dev, warm, seeds=range(N_PHANTOMS), iters=100, m
                 cur = nmse(f)
             return {"iterations": n, "seconds": total, "nmse": cur,
                     "reached": target is None or cur <= target}
-        f = torch.full((g.X, g.J, g.Q), f_init, device=dev)
-        plain = until(f, lambda x: plan.recon_step(y, x, beta=beta, delta=delta, path=P["table_fp32"]), None,
-                      iters)
+        f_plain = torch.full((g.X, g.J, g.Q), f_init, device=dev)
+        step_plain = lambda x: plan.recon_step(y, x, beta=beta, delta=delta, path=P["table_fp32"])
+        plain = until(f_plain, step_plain, None, iters)
         target = plain["nmse"]
         ent = {"phantom": p, "peak_counts": peak, "plain_fp32": plain}
         f = torch.full((g.X, g.J, g.Q), f_init, device=dev)
@@ -580,11 +580,18 @@ def recon_seeds(caxsi, plan, g, dev, warm, seeds=range(N_PHANTOMS), iters=100, m
                 sc = float(f1.mean())
                 box["f"] = net.predict(f1, sc, 1e-3 * sc)
             t0 = timed(start)
-            r = until(box["f"], lambda x: plan.recon_step(y, x, beta=beta, delta=delta, path=P["table_fp32"]),
-                      target, max_iters)
+            f0_nmse = nmse(box["f"])
+            r = until(box["f"], step_plain, target, max_iters)
             r["seconds"] += t0
             r["first_iterate_and_inference_seconds"] = t0
+            r["f0_nmse"] = f0_nmse
             ent["learned"] = r
+            # a stronger comparison: the plain iterations (continued past the target)
+            # needed to reach the network's starting image f^0
+            extra = until(f_plain, step_plain, f0_nmse, 300)
+            ent["plain_to_learned_f0"] = {"iterations": iters + extra["iterations"],
+                                          "seconds": plain["seconds"] + extra["seconds"],
+                                          "reached": extra["reached"], "nmse": extra["nmse"]}
         for k in ("table_bf16", "os_em_128", "learned"):
             if k in ent:
                 ent[k]["speedup_vs_plain"] = plain["seconds"] / ent[k]["seconds"] if ent[k]["reached"] else None
@@ -598,6 +605,13 @@ def recon_seeds(caxsi, plan, g, dev, warm, seeds=range(N_PHANTOMS), iters=100, m
                           "median_speedup": float(np.median(ok)) if ok else None,
                           "worst_speedup": float(min(ok)) if len(ok) == len(sp) else None,
                           "median_time_fraction_of_plain": float(np.median([1.0 / v for v in ok])) if ok else None}
+    p2 = [e["plain_to_learned_f0"] for e in per if "plain_to_learned_f0" in e]
+    if p2:
+        summary["plain_iterations_to_learned_f0"] = {
+            "reached": f"{sum(1 for e in p2 if e['reached'])}/{len(p2)}",
+            "median_iterations": float(np.median([e["iterations"] for e in p2])),
+            "note": "plain FP32 iterations from the flat start needed to reach the NMSE of the network's f^0 "
+                    "(capped at the plain run plus 300)"}
     summary["plain_fp32_final_nmse"] = {"median": float(np.median([e["plain_fp32"]["nmse"] for e in per])),
                                         "worst": float(max(e["plain_fp32"]["nmse"] for e in per))}
     return {"iterations": iters, "per_phantom": per, "summary": summary}
