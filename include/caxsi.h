@@ -76,7 +76,12 @@ typedef enum {
  *   into its transposed table (adjoint).  FP32 arithmetic throughout.
  * TABLE_BF16 / TABLE_FP16: as TABLE_FP32 with the contraction over q on
  *   tensor cores with bf16 / fp16 operands and FP32 accumulation (reduced
- *   precision; the error against FP64 is measured, not bounded to 1e-5). */
+ *   precision; the error against FP64 is measured, not bounded to 1e-5).  The
+ *   tables the contractions produce and consume (W and V, one row per voxel) are
+ *   kept in 16 bits where the mirror-symmetric records are used (bf16 for
+ *   TABLE_BF16's W and V, fp16 for TABLE_FP16's V; TABLE_FP16's W stays FP32,
+ *   as fp16's range would not hold every value); the pair weights, the
+ *   interpolation position and all accumulations stay FP32. */
 typedef enum {
     CAXSI_PATH_DIRECT = 0,
     CAXSI_PATH_TABLE_FP32 = 1,

@@ -748,18 +748,23 @@ __global__ void k_sym_build(PairArgs A, TabArgs T, int R2, int nrec, uint32_t *_
 // record adds its 8 pairs' contributions to its 4 pixels (owned by the record
 // within the pair: no conflicts, no atomics).  A thread loads SYM_U records
 // before it uses the first, so that their loads overlap.
+// WT: the element type of the knot rows (float, or bf16 for the bf16 path).
 constexpr int SYM_U = 4;
+__device__ __forceinline__ float wval(const float *w, int t) { return w[t]; }
+__device__ __forceinline__ float wval(const __nv_bfloat16 *w, int t) { return __bfloat162float(w[t]); }
+
+template <typename WT>
 __global__ void __launch_bounds__(RT, 1)
-k_fwd_sym(SymArgs S, const float *__restrict__ Wtab, float *__restrict__ part, int *err) {
+k_fwd_sym(SymArgs S, const WT *__restrict__ Wtab, float *__restrict__ part, int *err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int npix_al = (S.npix + 3) & ~3;
     float *g_s = reinterpret_cast<float *>(smem_raw);
-    float *wb = g_s + npix_al;                                  // [2 buffers][2 rows][Bp]
+    WT *wb = reinterpret_cast<WT *>(g_s + npix_al);             // [2 buffers][2 rows][Bp]
     uint64_t *bar = reinterpret_cast<uint64_t *>(wb + 4 * S.Bp);
     const int tid = threadIdx.x;
     const int s0 = blockIdx.x * S.vc, s1 = min(s0 + S.vc, S.R2);
     if (s0 >= s1) return;   // block-uniform
-    const uint32_t row_bytes = (uint32_t)S.Bp * 4u;
+    const uint32_t row_bytes = (uint32_t)S.Bp * (uint32_t)sizeof(WT);
     auto issue = [&](int s, int buf) {
         const int i = s / S.J2, jq = s - i * S.J2;
         const int64_t v = (int64_t)i * S.J + jq, vp = (int64_t)i * S.J + (S.J - 1 - jq);
@@ -794,7 +799,7 @@ k_fwd_sym(SymArgs S, const float *__restrict__ Wtab, float *__restrict__ part, i
             break;
         }
         if (buf) ph1 ^= 1u; else ph0 ^= 1u;
-        const float *Wv = wb + (2 * buf) * S.Bp, *Wp = Wv + S.Bp;
+        const WT *Wv = wb + (2 * buf) * S.Bp, *Wp = Wv + S.Bp;
         const int64_t base = (int64_t)s * S.nrec;
         for (int r0 = tid; r0 < S.nrec; r0 += SYM_U * RT) {
             uint32_t t2[SYM_U], bits[SYM_U];
@@ -816,10 +821,10 @@ k_fwd_sym(SymArgs S, const float *__restrict__ Wtab, float *__restrict__ part, i
                 const int r = r0 + u * RT;
                 if (r >= S.nrec) break;
                 const int ta = (int)(t2[u] & 0xffffu), tbb = (int)(t2[u] >> 16);
-                const float xav = fmaf(ww[u].x, Wv[ta], ww[u].y * Wv[ta + 1]);
-                const float xap = fmaf(ww[u].x, Wp[ta], ww[u].y * Wp[ta + 1]);
-                const float xbv = fmaf(ww[u].z, Wv[tbb], ww[u].w * Wv[tbb + 1]);
-                const float xbp = fmaf(ww[u].z, Wp[tbb], ww[u].w * Wp[tbb + 1]);
+                const float xav = fmaf(ww[u].x, wval(Wv, ta), ww[u].y * wval(Wv, ta + 1));
+                const float xap = fmaf(ww[u].x, wval(Wp, ta), ww[u].y * wval(Wp, ta + 1));
+                const float xbv = fmaf(ww[u].z, wval(Wv, tbb), ww[u].w * wval(Wv, tbb + 1));
+                const float xbp = fmaf(ww[u].z, wval(Wp, tbb), ww[u].w * wval(Wp, tbb + 1));
                 const uint32_t bt = bits[u];
                 const int m = r / S.NH, n = r - m * S.NH;
                 const int mm = S.M - 1 - m, nn = S.N - 1 - n;
@@ -1658,12 +1663,20 @@ caxsi_status sym_build(caxsi_plan *p, TablePath *T) {
     return sym_adj_build(p, T);
 }
 
-cudaError_t sym_forward(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s) {
+cudaError_t sym_forward(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s, bool w16) {
     const int npix = p->dg.M * p->dg.N;
     const size_t smem = fwd_sym_smem(npix, T->Bp);
-    cudaError_t e = cudaFuncSetAttribute(k_fwd_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (w16) {
+        cudaError_t e = cudaFuncSetAttribute(k_fwd_sym<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        k_fwd_sym<__nv_bfloat16><<<T->sym.chunks, RT, smem, s>>>(
+            sym_args(p, T), reinterpret_cast<const __nv_bfloat16 *>(T->v16), part, p->err_flag + 1);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_fwd_sym<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_fwd_sym<<<T->sym.chunks, RT, smem, s>>>(sym_args(p, T), T->tab, part, p->err_flag + 1);
+    k_fwd_sym<float><<<T->sym.chunks, RT, smem, s>>>(sym_args(p, T), T->tab, part, p->err_flag + 1);
     return cudaGetLastError();
 }
 

@@ -940,6 +940,8 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
     }
     const DevGeo &d = p->dg;
     const float one = 1.f, zero = 0.f;
+    // the full forward over the mirror-symmetric records
+    const bool sym_fwd = T->use_records && subset < 0 && T->sym.ok && !p->no_symmetry;
     if (cublasSetStream(T->blas, s) != CUBLAS_STATUS_SUCCESS) return CAXSI_ERR_CUDA;
     if (p->gemm_engine == 0 && path == CAXSI_PATH_TABLE_FP32) {
         // Wtab[r][t] = sum_l f[r][l] S~[t][l] by the tcgen05 GEMM, 3xTF32.  With
@@ -967,9 +969,13 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
         }
         CAXSI_LAUNCH_CHECK(p);
         {
+            // the bf16 path keeps its knot rows in bf16 for the mirror-symmetric forward
+            // (half the bytes written here and streamed there); the fp16 path keeps
+            // FP32 rows (fp16's range would not hold every table value)
             CAXSI_PROF(p, k == 0 ? "tc_gemm_fwd_bf16" : "tc_gemm_fwd_fp16", s);
+            uint16_t *w16 = (k == 0 && sym_fwd) ? reinterpret_cast<uint16_t *>(T->v16) : nullptr;
             CAXSI_CUDA_TRY(tc_gemm(1 + k, 256, d.R, T->B, d.Q, T->f16, nullptr, T->Qp, T->S16[k], nullptr, T->Qp,
-                                   T->tab, T->Bp, p->err_flag + 1, p->num_sms, s, kband_of(p, 1)));
+                                   T->tab, T->Bp, p->err_flag + 1, p->num_sms, s, kband_of(p, 1), nullptr, w16));
         }
         CAXSI_LAUNCH_CHECK(p);
     } else if (path == CAXSI_PATH_TABLE_FP32) {
@@ -993,9 +999,9 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
             return CAXSI_ERR_CUDA;
     }
     int nparts = T->fwd_chunks;
-    if (T->use_records && subset < 0 && T->sym.ok && !p->no_symmetry) {
+    if (sym_fwd) {
         CAXSI_PROF(p, "sym_pairs_fwd", s);
-        CAXSI_CUDA_TRY(sym_forward(p, T, T->fwd_part, s));
+        CAXSI_CUDA_TRY(sym_forward(p, T, T->fwd_part, s, path == CAXSI_PATH_TABLE_BF16 && p->gemm_engine == 0));
         nparts = T->sym.chunks;
     } else if (T->use_records) {
         CAXSI_PROF(p, "rec_pairs_fwd", s);

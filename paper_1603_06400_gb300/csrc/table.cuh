@@ -166,7 +166,8 @@ inline TabArgs tab_args(const TablePath *T) {
 caxsi_status records_build(caxsi_plan *p, TablePath *T);
 caxsi_status records_build_subsets(caxsi_plan *p, TablePath *T, int P, const int32_t *sub_host);
 caxsi_status sym_build(caxsi_plan *p, TablePath *T);
-cudaError_t sym_forward(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s);
+// w16: the knot rows are bf16 (in T->v16) instead of FP32 (in T->tab)
+cudaError_t sym_forward(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s, bool w16 = false);
 // out_kind as for records_adjoint
 cudaError_t sym_adjoint(const caxsi_plan *p, const TablePath *T, const float *w, int out_kind, cudaStream_t s);
 cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, int subset, float *part, cudaStream_t s);
@@ -188,7 +189,8 @@ cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, int subset,
 // kband / nband (device, or null): B is zero outside bands; see tc_gemm.cu.
 cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const void *A2, int64_t lda,
                     const void *B, const void *B2, int64_t ldb, float *C, int64_t ldc, int *err,
-                    int num_sms, cudaStream_t s, const int2 *kband = nullptr, const int2 *nband = nullptr);
+                    int num_sms, cudaStream_t s, const int2 *kband = nullptr, const int2 *nband = nullptr,
+                    uint16_t *C16 = nullptr);
 // Band tables from the nonzero range of each row of B[N][K] along K (kband: per
 // n-tile of bn rows, the k-blocks to keep) or of each column along N (nband: per
 // K-chunk, the 32-column quarters to keep); eb = operand element bytes.

@@ -167,6 +167,7 @@ struct TcArgs {
     const int2 *nband;   // [chunks] column-quarter range of each K-chunk, or null (all)
     int vec_ok;     // rows of C start on 16-byte boundaries (vector stores allowed)
     int tma_store;  // C is written by TMA tensor stores through shared memory
+    uint16_t *C16;  // non-null: C is written as bf16 (round to nearest) here instead of FP32 to C
 };
 
 constexpr uint32_t TCG_STG = 4096;   // per epilogue warp: one 32 x 32 FP32 chunk, 128-byte swizzled
@@ -379,7 +380,63 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                 mb_arrive(&acce[b]);
             }
             if (!ok) break;
-            if (a.tma_store) {
+            if (a.C16 && a.tma_store) {
+                // bf16 tiles by TMA tensor stores: chunk c0 of 64 columns, lane = row, its
+                // 64 columns as 8 words of 8 bf16 at 16-byte slot j ^ (row & 7)
+                uint4 *stg = reinterpret_cast<uint4 *>(stg_base + (warp - 2) * TCG_STG);
+#pragma unroll
+                for (int c0 = 0; c0 < CW; c0 += 64) {
+                    const int col = n0 + c0;
+                    if (col >= a.N) break;   // warp-uniform
+                    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                    __syncwarp();
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        uint32_t wd[4];
+#pragma unroll
+                        for (int h2 = 0; h2 < 4; ++h2) {
+                            const __nv_bfloat162 b2 = __floats2bfloat162_rn(run[c0 + 8 * j + 2 * h2],
+                                                                           run[c0 + 8 * j + 2 * h2 + 1]);
+                            wd[h2] = *reinterpret_cast<const uint32_t *>(&b2);
+                        }
+                        stg[lane * 8 + (j ^ (lane & 7))] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) tma_store_2d(&tC, s_addr(stg), col, m0 + q * 32);
+                }
+            } else if (a.C16) {
+                // bf16 rows: each lane stores its row's 32 columns as four 16-byte words
+                if (row < a.M) {
+                    uint16_t *crow16 = a.C16 + (int64_t)row * a.ldc;
+#pragma unroll
+                    for (int c0 = 0; c0 < CW; c0 += 32) {
+                        const int col = n0 + c0;
+                        if (col >= a.N) break;
+                        if (a.vec_ok && col + 32 <= a.N) {
+                            uint4 *dst = reinterpret_cast<uint4 *>(crow16 + col);
+#pragma unroll
+                            for (int v4 = 0; v4 < 4; ++v4) {
+                                uint32_t wd[4];
+#pragma unroll
+                                for (int h2 = 0; h2 < 4; ++h2) {
+                                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(run[c0 + 8 * v4 + 2 * h2],
+                                                                                   run[c0 + 8 * v4 + 2 * h2 + 1]);
+                                    wd[h2] = *reinterpret_cast<const uint32_t *>(&b2);
+                                }
+                                dst[v4] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                if (col + i < a.N) {
+                                    const __nv_bfloat16 b = __float2bfloat16_rn(run[c0 + i]);
+                                    crow16[col + i] = *reinterpret_cast<const uint16_t *>(&b);
+                                }
+                        }
+                    }
+                }
+            } else if (a.tma_store) {
                 // chunk c0: lane = row, its 32 columns as 8 float4 at 16-byte slot j ^ (row & 7)
                 float4 *stg = reinterpret_cast<float4 *>(stg_base + (warp - 2) * TCG_STG);
 #pragma unroll
@@ -483,10 +540,12 @@ cudaError_t launch_tc(const CUtensorMap &tA, const CUtensorMap &tA2, const CUten
 // kind 0: A = (A_hi, A_lo), B = (B_hi, B_lo) FP32 arrays (3xTF32); kind 3: A in
 // FP32 (split on chip, A2 ignored), B = (B_hi, B_lo); kind 1 / 2: A, B bf16 / fp16
 // (A2, B2 ignored).  bn = 256 or 128.  Row strides in
-// elements must make 16-byte multiples; base pointers 16-byte aligned.
+// elements must make 16-byte multiples; base pointers 16-byte aligned.  With C16
+// non-null the result is written there as bf16 (round to nearest), row stride
+// ldc elements, and C is not used.
 cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const void *A2, int64_t lda,
                     const void *B, const void *B2, int64_t ldb, float *C, int64_t ldc, int *err,
-                    int num_sms, cudaStream_t s, const int2 *kband, const int2 *nband) {
+                    int num_sms, cudaStream_t s, const int2 *kband, const int2 *nband, uint16_t *C16) {
     const int eb = (kind == 0 || kind == 3) ? 4 : 2;
     if (kband && nband) return cudaErrorInvalidValue;              // one kind of band at a time
     if (nband && (N + bn - 1) / bn != 1) return cudaErrorInvalidValue;   // quarters of the only n-tile
@@ -510,11 +569,20 @@ cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const 
     a.C = C;
     a.ldc = ldc;
     a.err = err;
-    a.vec_ok = ((ldc & 3) == 0) && (((uintptr_t)C & 15) == 0);
-    // C by TMA tensor stores: 32 x 32 boxes with the 128-byte swizzle of the staging buffer
+    a.C16 = C16;
     CUtensorMap tC;
-    a.tma_store = a.vec_ok && make_map(&tC, C, 4, M, N, ldc, 32) ? 1 : 0;
-    if (!a.tma_store) tC = tA;
+    if (C16) {
+        // bf16 output: TMA tensor stores of 32 rows x 64 columns (128-byte rows), else
+        // 16-byte vector stores of 8 columns
+        a.vec_ok = ((ldc & 7) == 0) && (((uintptr_t)C16 & 15) == 0);
+        a.tma_store = a.vec_ok && make_map(&tC, C16, 2, M, N, ldc, 32) ? 1 : 0;
+        if (!a.tma_store) tC = tA;
+    } else {
+        a.vec_ok = ((ldc & 3) == 0) && (((uintptr_t)C & 15) == 0);
+        // C by TMA tensor stores: 32 x 32 boxes with the 128-byte swizzle of the staging buffer
+        a.tma_store = a.vec_ok && make_map(&tC, C, 4, M, N, ldc, 32) ? 1 : 0;
+        if (!a.tma_store) tC = tA;
+    }
     a.ntn = (N + bn - 1) / bn;
     a.ntiles = ((M + 127) / 128) * a.ntn;
     a.nk = (K * eb + 127) / 128;
