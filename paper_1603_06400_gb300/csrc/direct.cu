@@ -81,7 +81,7 @@ k_adj_direct(Tables T, const float *__restrict__ w, float *__restrict__ out, int
     const int item = blockIdx.x * ADJ_WARPS + warp;
     const int v = item / split, sp = item - (item / split) * split;
     for (int k = tid; k < g.K; k += blockDim.x) s_en[k] = T.energy[k];
-    float *acc = s_acc + (int64_t)warp * QB * 32;
+    float *acc = s_acc + (int64_t)warp * adj_warp_floats(g.Q);
     for (int b = lane; b < QB * 32; b += 32) acc[b] = 0.f;
     __syncthreads();
     if (v >= g.R) return;

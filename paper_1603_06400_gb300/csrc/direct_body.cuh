@@ -75,10 +75,18 @@ __device__ __forceinline__ void fwd_direct_body(const Tables &T, const float *__
         if (tid < nv) s_vox[tid] = T.vox[vb + tid];
         __syncthreads();
         if (!valid) continue;
+        // the staged voxels this pixel's pairs are open for, taken in ascending order:
+        // a lane's loop runs over its own open pairs only (a warp over the largest
+        // count among its lanes, not over every staged voxel)
+        uint32_t open = 0u;
         for (int vv = 0; vv < nv; ++vv) {
+            const uint32_t word = T.tbits[((int64_t)(vb + vv) * g.M + m) * g.Nw + wsel];
+            open |= ((word >> bsel) & 1u) << vv;
+        }
+        while (open) {
+            const int vv = __ffs(open) - 1;
+            open &= open - 1u;
             const int v = vb + vv;
-            const uint32_t word = T.tbits[((int64_t)v * g.M + m) * g.Nw + wsel];
-            if (!((word >> bsel) & 1u)) continue;
             const int i = v / g.J, j = v - i * g.J;
             const float4 vx = s_vox[vv];
             float u, ang;
@@ -118,12 +126,8 @@ __device__ __forceinline__ void adj_direct_body(const Tables &T, const float *__
     const int i = v / g.J, j = v - i * g.J;
     const float4 vx = T.vox[v];
     float *my = acc + lane;
-    // one pair (pixel (m, n)) scattered into the lane's q row
-    auto pair = [&](int m, int n) {
-        const uint32_t word = T.tbits[((int64_t)v * g.M + m) * g.Nw + (n >> 5)];
-        if (!((word >> (n & 31)) & 1u)) return;
-        const float wv = w[(int64_t)m * g.N + n];
-        if (wv == 0.f) return;
+    // one open pair (pixel (m, n), weight wv != 0) scattered into the lane's q row
+    auto pair_open = [&](int m, int n, float wv) {
         float u, ang;
         pair_u_angular(vx.x, vx.y, vx.w, (float)n - g.cN, T.zrow[m], g.p_y, g.Xd, u, ang);
         const float base = vx.z * T.god[((int64_t)i * g.M + m) * g.ND + (n - g.rho_y * j - g.d_min)] * ang * wv;
@@ -141,20 +145,51 @@ __device__ __forceinline__ void adj_direct_body(const Tables &T, const float *__
             my[(lp + 1) * 32] += hi;
         }
     };
+    auto is_open = [&](int m, int n) {
+        const uint32_t word = T.tbits[((int64_t)v * g.M + m) * g.Nw + (n >> 5)];
+        return ((word >> (n & 31)) & 1u) != 0u;
+    };
     if (LIST) {
         for (int e = lane; e < np; e += 32) {
             const int p = list[e];
-            const int m = p / g.N;
-            pair(m, p - m * g.N);
+            const int m = p / g.N, n = p - m * g.N;
+            const float wv = w[p];
+            if (is_open(m, n) && wv != 0.f) pair_open(m, n, wv);
         }
     } else {
+        // The open pairs with a nonzero weight are queued in pixel order in a ring of
+        // 64 slots after the warp's q rows and taken 32 at a time, one per lane, so
+        // the lanes of a batch all do work (about half the pairs are closed by the
+        // mask).  The assignment of pairs to lanes is fixed by the pixel order.
+        int *q = reinterpret_cast<int *>(acc + (g.Q + 3) * 32);
+        const unsigned lt = (1u << lane) - 1u;
+        int head = 0, cnt = 0;
+        auto take = [&](int p) {
+            const int m = p / g.N;
+            pair_open(m, p - m * g.N, w[p]);
+        };
         const int m0 = sp * rows_per_split, m1 = min(g.M, m0 + rows_per_split);
         for (int m = m0; m < m1; ++m)
             for (int nb = 0; nb < g.N; nb += 32) {
                 const int n = nb + lane;
-                if (n >= g.N) break;
-                pair(m, n);
+                const bool ok = n < g.N && is_open(m, n) && w[(int64_t)m * g.N + n] != 0.f;
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                if (ok) q[(head + cnt + __popc(bal & lt)) & 63] = m * g.N + n;
+                cnt += __popc(bal);
+                __syncwarp();
+                if (cnt >= 32) {   // warp-uniform
+                    const int p = q[(head + lane) & 63];
+                    head = (head + 32) & 63;
+                    cnt -= 32;
+                    __syncwarp();   // the batch is read before later groups refill its slots
+                    take(p);
+                }
             }
+        if (cnt > 0) {
+            const int p = lane < cnt ? q[(head + lane) & 63] : -1;
+            __syncwarp();
+            if (p >= 0) take(p);
+        }
     }
     __syncwarp();
     float *dst = out + ((int64_t)sp * g.R + v) * g.Q;
@@ -181,8 +216,10 @@ inline size_t fwd_smem(const DevGeo &g) {
     return ((g.K + 1) & ~1) * sizeof(float2) + FWD_VS * sizeof(float4) +
            (size_t)FWD_VS * (g.Q + 2) * sizeof(float2);
 }
+// per warp: q rows [(Q + 3) x 32] floats and a ring of 64 queued pixels
+__host__ __device__ inline size_t adj_warp_floats(int Q) { return (size_t)(Q + 3) * 32 + 64; }
 inline size_t adj_smem(const DevGeo &g) {
-    return ((g.K + 1) & ~1) * sizeof(float2) + (size_t)ADJ_WARPS * (g.Q + 3) * 32 * sizeof(float);
+    return ((g.K + 1) & ~1) * sizeof(float2) + (size_t)ADJ_WARPS * adj_warp_floats(g.Q) * sizeof(float);
 }
 
 }  // namespace direct_impl

@@ -111,7 +111,7 @@ k_fwd_direct_multi(const MultiObj *__restrict__ objs, const int64_t *__restrict_
 }
 
 // Warp-level items; each warp keeps its object's description and energy table
-// in its own slice of shared memory: [ADJ_WARPS] x ([kmax] float2, [(qmax+3) x 32] float).
+// in its own slice of shared memory: [ADJ_WARPS] x ([kmax] float2, [(qmax+3) x 32 + 64] float).
 __global__ void __launch_bounds__(ADJ_WARPS * 32)
 k_adj_direct_multi(const MultiObj *__restrict__ objs, const int64_t *__restrict__ first, int nobj,
                    const float *__restrict__ w, float *__restrict__ f, unsigned *queue, unsigned *cnt, int kmax,
@@ -120,7 +120,7 @@ k_adj_direct_multi(const MultiObj *__restrict__ objs, const int64_t *__restrict_
     __shared__ MultiObj s_o[ADJ_WARPS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ke = (kmax + 1) & ~1;
-    const size_t per_warp = (size_t)ke * sizeof(float2) + (size_t)(qmax + 3) * 32 * sizeof(float);
+    const size_t per_warp = (size_t)ke * sizeof(float2) + adj_warp_floats(qmax) * sizeof(float);
     float2 *s_en = reinterpret_cast<float2 *>(smem_raw + warp * per_warp);
     float *acc = reinterpret_cast<float *>(s_en + ke);
     const int64_t total = first[nobj];
@@ -295,7 +295,7 @@ caxsi_status caxsi_multi_create(caxsi_plan *const *plans, int n_objects, caxsi_m
         return CAXSI_ERR_INVALID;
     }
     m->n_cnt = n_cnt;
-    m->smem_adj = (size_t)ADJ_WARPS * (((m->kmax + 1) & ~1) * sizeof(float2) + (size_t)(m->qmax + 3) * 32 * sizeof(float));
+    m->smem_adj = (size_t)ADJ_WARPS * (((m->kmax + 1) & ~1) * sizeof(float2) + adj_warp_floats(m->qmax) * sizeof(float));
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device);
     const size_t static_fwd = sizeof(MultiObj) + 64, static_adj = ADJ_WARPS * sizeof(MultiObj);

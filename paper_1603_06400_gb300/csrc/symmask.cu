@@ -137,8 +137,9 @@ k_fwd_direct_symmask(SymTables S, const float *__restrict__ f, float *__restrict
 
 // Warp per (voxel, range of upper-half rows); lane-private q rows as in the plain
 // adjoint, the voxel's mask columns for every detector column cached in the
-// warp's shared-memory slice.  Shared memory per warp: [(Q+3) x 32] floats, then
-// [N] ints.
+// warp's shared-memory slice, the open pairs queued and taken 32 at a time as in
+// the plain adjoint.  Shared memory per warp: [(Q+3) x 32] floats, then [N] ints,
+// then a ring of 64 ints.
 __global__ void __launch_bounds__(ADJ_WARPS * 32)
 k_adj_direct_symmask(SymTables S, const float *__restrict__ w, float *__restrict__ out, int split,
                      int rows_per_split) {
@@ -150,8 +151,9 @@ k_adj_direct_symmask(SymTables S, const float *__restrict__ w, float *__restrict
     float2 *s_en = reinterpret_cast<float2 *>(smem_raw);
     float *s_warp = reinterpret_cast<float *>(s_en + ((g.K + 1) & ~1));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    float *acc = s_warp + (int64_t)warp * (QB * 32 + g.N);
+    float *acc = s_warp + (int64_t)warp * (QB * 32 + g.N + 64);
     int *colc = reinterpret_cast<int *>(acc + QB * 32);
+    int *ring = colc + g.N;   // [64] queued open pairs (m N + n)
     const int item = blockIdx.x * ADJ_WARPS + warp;
     const int v = item / split, sp = item - (item / split) * split;
     for (int k = tid; k < g.K; k += blockDim.x) s_en[k] = T.energy[k];
@@ -164,36 +166,59 @@ k_adj_direct_symmask(SymTables S, const float *__restrict__ w, float *__restrict
     const float4 vx = T.vox[v];
     float *my = acc + lane;
     const int m0 = sp * rows_per_split, m1 = min(Mh, m0 + rows_per_split);
+    // one open pair (upper-half pixel m, n; the up-down pair's weights added)
+    auto take = [&](int p) {
+        const int m = p / g.N, n = p - m * g.N;
+        const float wv = w[p] + w[(int64_t)(g.M - 1 - m) * g.N + n];
+        float u, ang;
+        pair_u_angular(vx.x, vx.y, vx.w, (float)n - g.cN, T.zrow[m], g.p_y, g.Xd, u, ang);
+        const float base = vx.z * T.god[((int64_t)i * g.M + m) * g.ND + (n - g.rho_y * j - g.d_min)] * ang * wv;
+#pragma unroll 4
+        for (int k = 0; k < g.K; ++k) {
+            const float2 ak = s_en[k];
+            float tau = fmaf(ak.x, u, -g.b);
+            tau = fminf(fmaxf(tau, -1.f), g.Qf);
+            const float fl = floorf(tau);
+            const float al = tau - fl;
+            const int lp = (int)fl + 1;
+            const float cb = ak.y * base;
+            const float hi = cb * al;
+            my[lp * 32] += cb - hi;
+            my[(lp + 1) * 32] += hi;
+        }
+    };
+    // the open pairs with a nonzero weight queued in pixel order, taken 32 at a time
+    const unsigned lt = (1u << lane) - 1u;
+    int head = 0, cnt = 0;
     for (int m = m0; m < m1; ++m) {
         const int row = mask_row_fast(S.g64, S.g32, i, m);
-        if (row < 0) continue;
+        if (row < 0) continue;   // warp-uniform
         const uint8_t *mrow = S.mask + row * S.g64.cols;
-        const float sz = T.zrow[m];
         const float *wa = w + (int64_t)m * g.N, *wb = w + (int64_t)(g.M - 1 - m) * g.N;
         for (int nb = 0; nb < g.N; nb += 32) {
             const int n = nb + lane;
-            if (n >= g.N) break;
-            const int col = colc[n];
-            if (col < 0 || !mrow[col]) continue;
-            const float wv = wa[n] + wb[n];
-            if (wv == 0.f) continue;
-            float u, ang;
-            pair_u_angular(vx.x, vx.y, vx.w, (float)n - g.cN, sz, g.p_y, g.Xd, u, ang);
-            const float base = vx.z * T.god[((int64_t)i * g.M + m) * g.ND + (n - g.rho_y * j - g.d_min)] * ang * wv;
-#pragma unroll 4
-            for (int k = 0; k < g.K; ++k) {
-                const float2 ak = s_en[k];
-                float tau = fmaf(ak.x, u, -g.b);
-                tau = fminf(fmaxf(tau, -1.f), g.Qf);
-                const float fl = floorf(tau);
-                const float al = tau - fl;
-                const int lp = (int)fl + 1;
-                const float cb = ak.y * base;
-                const float hi = cb * al;
-                my[lp * 32] += cb - hi;
-                my[(lp + 1) * 32] += hi;
+            bool ok = false;
+            if (n < g.N) {
+                const int col = colc[n];
+                ok = col >= 0 && mrow[col] && wa[n] + wb[n] != 0.f;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            if (ok) ring[(head + cnt + __popc(bal & lt)) & 63] = m * g.N + n;
+            cnt += __popc(bal);
+            __syncwarp();
+            if (cnt >= 32) {
+                const int p = ring[(head + lane) & 63];
+                head = (head + 32) & 63;
+                cnt -= 32;
+                __syncwarp();
+                take(p);
             }
         }
+    }
+    if (cnt > 0) {
+        const int p = lane < cnt ? ring[(head + lane) & 63] : -1;
+        __syncwarp();
+        if (p >= 0) take(p);
     }
     __syncwarp();
     float *dst = out + ((int64_t)sp * g.R + v) * g.Q;
@@ -223,7 +248,7 @@ size_t symmask_fwd_smem(const DevGeo &g) {
            (size_t)SVS * (FWD_WARPS + 32) * sizeof(int);
 }
 size_t symmask_adj_smem(const DevGeo &g) {
-    return ((g.K + 1) & ~1) * sizeof(float2) + (size_t)ADJ_WARPS * ((g.Q + 3) * 32 + g.N) * sizeof(float);
+    return ((g.K + 1) & ~1) * sizeof(float2) + (size_t)ADJ_WARPS * ((g.Q + 3) * 32 + g.N + 64) * sizeof(float);
 }
 
 caxsi_status symmask_forward(caxsi_plan *p, const float *f, float *g_out, cudaStream_t s) {
