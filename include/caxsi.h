@@ -274,8 +274,9 @@ caxsi_status caxsi_adjoint_batch(caxsi_plan *plan, int n_objects, const int32_t 
  *
  * The set refers to the plans (it does not own them) and uses their scratch:
  * destroy it before them, and order its calls with the plans' own calls.  All
- * plans must be on one device.  Errors: INVALID (NULL, lengths, plans on
- * different devices, n_objects outside [1, CAXSI_MAX_MULTI]), UNSUPPORTED (a
+ * plans must be on one device, and a plan may appear only once (its scratch holds
+ * its object's partial results).  Errors: INVALID (NULL, lengths, plans on
+ * different devices, a plan given twice, n_objects outside [1, CAXSI_MAX_MULTI]), UNSUPPORTED (a
  * path other than CAXSI_PATH_DIRECT; shared memory too small for the largest
  * K and Q), CUDA, OOM. */
 #define CAXSI_MAX_MULTI 4096

@@ -240,6 +240,12 @@ caxsi_status caxsi_multi_create(caxsi_plan *const *plans, int n_objects, caxsi_m
     if (!plans || !out || n_objects < 1 || n_objects > CAXSI_MAX_MULTI) return CAXSI_ERR_INVALID;
     for (int b = 0; b < n_objects; ++b)
         if (!plans[b] || plans[b]->device != plans[0]->device) return CAXSI_ERR_INVALID;
+    // each object's partial results go to its plan's scratch: a plan may serve one object only
+    {
+        std::vector<const caxsi_plan *> sorted(plans, plans + n_objects);
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return CAXSI_ERR_INVALID;
+    }
     caxsi_multi *m = new (std::nothrow) caxsi_multi();
     if (!m) return CAXSI_ERR_OOM;
     m->device = plans[0]->device;

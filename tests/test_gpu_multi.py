@@ -142,6 +142,9 @@ def test_multi_errors(cx):
                                    0, None) == 1
     assert lib.caxsi_multi_forward(None, P(f.data_ptr()), multi.f_len, P(g.data_ptr()), multi.g_len, 0, None) == 1
     assert lib.caxsi_multi_create(None, 2, None) == 1
+    with pytest.raises(caxsi.CaxsiError) as e:       # one plan for two objects: shared scratch
+        caxsi.Multi([plans[0], plans[1], plans[0]])
+    assert e.value.status == 1
     multi.close()
     for pl in plans:
         pl.close()
