@@ -36,6 +36,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "internal.cuh"
@@ -980,21 +981,38 @@ __global__ void k_sadj_fill(PairArgs A, TabArgs T, int R2, int wpb, const int64_
     }
 }
 
-// Adjoint over the symmetric lists: the run-ownership reduction of k_adj_rec, with
-// two sums per run (voxels v and v' of the pair) and the two V rows interleaved in
-// shared memory as float2 {row v, row v'}.  A record adds w0 x and w1 x to knots t
-// and t + 1, x = w[m, n] b0 + w[M-1-m, n] b1 for v and w[m, N-1-n] b2 +
-// w[M-1-m, N-1-n] b3 for v' (b the mask bits).  The input image is held per
-// quadrant pixel (m, n0) as float4 {w[m, n0], w[M-1-m, n0], w[m, N-1-n0],
-// w[M-1-m, N-1-n0]}, so a record reads one of them and its class says which half
-// is v's.  Each warp stages up to SADJ_SQ quads of its segment of the next pair's
-// list by TMA; the rest of the segment is read from global memory (an L2 prefetch
-// of it measured slower: the warp waits while its lane issues the prefetches).
-constexpr int SADJ_SQ = 48;
+// Adjoint over the symmetric lists.  A record adds w0 x and w1 x to knots t and
+// t + 1 of two V rows (voxels v and v' of the pair), x = w[m, n] b0 + w[M-1-m, n] b1
+// for v and w[m, N-1-n] b2 + w[M-1-m, N-1-n] b3 for v' (b the mask bits).  The
+// input image is held in shared memory per quadrant pixel (m, n0) as float4
+// {w[m, n0], w[M-1-m, n0], w[m, N-1-n0], w[M-1-m, N-1-n0]}, so a record reads one of
+// them and its class says which half is v's.
+//
+// Work item = (voxel pair s, knot segment [t_lo, t_lo + L)), one warp each; a warp
+// takes the block's next item from a shared-memory counter when it comes free, and
+// nothing else synchronises the warps once the image is loaded.  The warp reads the
+// quads of the pair's t-sorted list that can reach the segment (records with t in
+// [t_lo - 1, t_lo + L), from a per-plan table), 32 quads per row, lane l taking
+// quad l of the row (coalesced).  Within its quad a lane sums each run of equal t;
+// a run that continues across lanes is carried by a segmented scan over the lanes
+// of the lanes' last runs (as many doubling steps as the longest chain of lanes
+// needs), and a run that continues past the row by a warp-uniform carry.  Every run
+// is completed exactly once, by the lane holding its last record, and added into
+// the warp's segment buffer V[t - t_lo] (LO sums) and, after a warp barrier,
+// V[t + 1 - t_lo] (HI sums); each entry gets at most one LO and one HI sum, so the
+// result does not depend on their order.  Runs outside the segment are dropped at
+// that point.  The buffer is then written to the two V rows (consecutive lanes,
+// consecutive 8 bytes) and cleared.  Every sum has a fixed order, set by the plan:
+// repeated calls are bitwise equal.
+constexpr int SEG_T = 1024;
+constexpr int SEG_W = SEG_T / 32;
+constexpr int T_NONE = -2;            // "no carried run"
+constexpr int T_PAST = 1 << 30;       // t of the records past the item's last quad
 
 struct SymAdjArgs {
-    int R2, J, J2, M, N, npix, Bp, vc;
+    int R2, J, J2, M, N, Bp, nseg, L;
     const int64_t *off;
+    const uint32_t *seg;    // [R2 * nseg] first quad | end quad << 16, relative to the pair's list
     const uint32_t *key;
     const float *w0, *w1;
 };
@@ -1002,223 +1020,231 @@ struct SymAdjArgs {
 // Two-lane FP32 arithmetic in one packed instruction (each lane rounded as fmaf / +).
 __device__ __forceinline__ float2 f2fma(float a, float2 x, float2 y) { return __ffma2_rn(make_float2(a, a), x, y); }
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 shfl_up2(float2 v, int o) {
+    return make_float2(__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o));
+}
+__device__ __forceinline__ float2 shfl2(float2 v, int l) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, l), __shfl_sync(0xffffffffu, v.y, l));
+}
+__device__ __forceinline__ uint4 ld_stream_u4(const uint4 *p) {
+    uint4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ float4 ld_stream_f4(const float4 *p) {
+    float4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p));
+    return r;
+}
 
 template <typename OutT>
-__global__ void __launch_bounds__(ADJ_T, 1)
-k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab, int *err) {
+__global__ void __launch_bounds__(SEG_T, 1)
+k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int npix_al = (A.npix + 3) & ~3;
-    float4 *w4 = reinterpret_cast<float4 *>(smem_raw);                // [M/2][N/2] quadrant pixels
-    float2 *V = reinterpret_cast<float2 *>(smem_raw + 4 * (size_t)npix_al);   // [Bp] {row v, row v'}
-    uint4 *stg_k = reinterpret_cast<uint4 *>(V + A.Bp);               // [ADJ_W][SADJ_SQ]
-    float4 *stg_a = reinterpret_cast<float4 *>(stg_k + ADJ_W * SADJ_SQ);
-    float4 *stg_c = stg_a + ADJ_W * SADJ_SQ;
-    uint4 *stg_p = reinterpret_cast<uint4 *>(stg_c + ADJ_W * SADJ_SQ);   // [ADJ_W]
-    uint32_t *slot_t = reinterpret_cast<uint32_t *>(stg_p + ADJ_W);
-    float2 *slot_lo = reinterpret_cast<float2 *>(slot_t + ADJ_T);
-    float2 *slot_hi = slot_lo + ADJ_T;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(slot_hi + ADJ_T);    // [ADJ_W]
-    int *offr = reinterpret_cast<int *>(bar + ADJ_W);                  // [vc + 1] list starts - off[s0]
+    __shared__ int next_item;
+    const int NH = A.N / 2, nq = (A.M / 2) * NH;
+    float4 *w4 = reinterpret_cast<float4 *>(smem_raw);                                  // [nq]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int s0 = blockIdx.x * A.vc, s1 = min(s0 + A.vc, A.R2);
-    if (s0 >= s1) return;   // block-uniform
-    const int64_t base = A.off[s0];   // the block's lists are contiguous from here
-
-    auto segment = [&](int64_t ob, int64_t oe, int &ws, int &we, int &perq) {
-        const int nq = (int)((oe - ob) >> 2);
-        perq = (nq + ADJ_T - 1) / ADJ_T;
-        ws = min(nq, warp * 32 * perq);
-        we = min(nq, ws + 32 * perq);
-    };
-    // The whole warp: stage the warp's segment of the list [ob, oe), one copy per
-    // lane 0-3 after lane 0 has set the expected bytes (the stage was last read
-    // through the generic proxy, hence the proxy fences).
-    auto issue = [&](int64_t ob, int64_t oe) {
-        int ws, we, perq;
-        segment(ob, oe, ws, we, perq);
-        const int ns = min(we, ws + SADJ_SQ) - ws;
-        const bool kp = ws > 0 && ws < we;
-        if (lane == 0) mbar_expect_tx(&bar[warp], 48u * (uint32_t)ns + (kp ? 16u : 0u));
-        __syncwarp();
-        if (lane < 4) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const int64_t r = ob + 4 * (int64_t)ws;
-        if (lane == 0 && ns > 0) bulk_g2s(stg_k + warp * SADJ_SQ, A.key + r, 16u * ns, &bar[warp]);
-        if (lane == 1 && ns > 0) bulk_g2s(stg_a + warp * SADJ_SQ, A.w0 + r, 16u * ns, &bar[warp]);
-        if (lane == 2 && ns > 0) bulk_g2s(stg_c + warp * SADJ_SQ, A.w1 + r, 16u * ns, &bar[warp]);
-        if (lane == 3 && kp) bulk_g2s(stg_p + warp, A.key + ob + 4 * (int64_t)(ws - 1), 16u, &bar[warp]);
-    };
-
-    if (tid == 0) {
-        for (int k = 0; k < ADJ_W; ++k) mbar_init(&bar[k], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    for (int t = tid; t < A.Bp; t += ADJ_T) V[t] = make_float2(0.f, 0.f);
-    for (int k = tid; k <= s1 - s0; k += ADJ_T) offr[k] = (int)(A.off[s0 + k] - base);
-    {
-        const int NH = A.N / 2, nq = (A.M / 2) * NH;
-        for (int e = tid; e < nq; e += ADJ_T) {
-            const int m = e / NH, n0 = e - m * NH;
-            const float *ra = w + (int64_t)m * A.N, *rb = w + (int64_t)(A.M - 1 - m) * A.N;
-            w4[e] = make_float4(ra[n0], rb[n0], ra[A.N - 1 - n0], rb[A.N - 1 - n0]);
-        }
-    }
-    __syncthreads();
-    uint32_t par = 0u;       // parity of the warp's outstanding phase
-    bool pending = false;    // the warp has staged copies in flight
-    bool ok = true;
-    issue(base, base + offr[1]);
-    pending = true;
+    float2 *V = reinterpret_cast<float2 *>(smem_raw + 16 * (size_t)nq) + (size_t)warp * A.L;   // [L]
+    float4 *V4 = reinterpret_cast<float4 *>(V);
     const float2 zero2 = make_float2(0.f, 0.f);
-    for (int s = s0; s < s1; ++s) {
-        const int late = __any_sync(0xffffffffu, !mbar_wait(&bar[warp], par)) ? 1 : 0;
-        const int64_t ob = base + offr[s - s0], oe = base + offr[s - s0 + 1];
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid == 0) next_item = 0;
+    for (int e = tid; e < nq; e += SEG_T) {
+        const int m = e / NH, n0 = e - m * NH;
+        const float *ra = w + (int64_t)m * A.N, *rb = w + (int64_t)(A.M - 1 - m) * A.N;
+        w4[e] = make_float4(ra[n0], rb[n0], ra[A.N - 1 - n0], rb[A.N - 1 - n0]);
+    }
+    for (int e = lane; e < (A.L >> 1); e += 32) V4[e] = zero4;
+    __syncthreads();
 
-        int ws, we, perq;
-        segment(ob, oe, ws, we, perq);
-        const int q0 = min(we, ws + lane * perq), q1 = min(we, q0 + perq);
-        const int i0 = q0 - ws, sb = warp * SADJ_SQ;
+    const int nitems = A.R2 * A.nseg;
+    const unsigned L = (unsigned)A.L;
+    for (;;) {
+        // the block's items are blockIdx.x + j gridDim.x, in segment-major order (all
+        // pairs' segment 0, then segment 1, ...), so that every block gets a like mix
+        // of dense and sparse segments
+        int j = 0;
+        if (lane == 0) j = atomicAdd(&next_item, 1);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        const int64_t k = blockIdx.x + (int64_t)j * gridDim.x;
+        if (k >= nitems) break;
+        const int sg = (int)(k / A.R2), s = (int)(k - (int64_t)sg * A.R2);
+        const int tlo = sg * A.L;
+        const uint32_t qr = A.seg[(int64_t)s * A.nseg + sg];
+        const int qa = (int)(qr & 0xffffu), qe = (int)(qr >> 16);
+        const int64_t ob = A.off[s];
         const uint4 *K4 = reinterpret_cast<const uint4 *>(A.key + ob);
-        const float4 *A4 = reinterpret_cast<const float4 *>(A.w0 + ob);
-        const float4 *C4 = reinterpret_cast<const float4 *>(A.w1 + ob);
-        // The part's first two quads come to registers (from the stage, or from
-        // global memory past it), so that the stage can be refilled at once.
-        uint4 k0 = make_uint4(0u, 0u, 0u, 0u), k1 = k0;
-        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, c0 = a0, c1 = a0;
-        uint32_t kprev = 0u;
-        if (!late) {
-            if (q0 < q1) {
-                if (i0 < SADJ_SQ) { k0 = stg_k[sb + i0]; a0 = stg_a[sb + i0]; c0 = stg_c[sb + i0]; }
-                else { k0 = K4[q0]; a0 = A4[q0]; c0 = C4[q0]; }
-                if (q0 > 0) {
-                    if (lane == 0) kprev = stg_p[warp].w;
-                    else if (i0 - 1 < SADJ_SQ) kprev = stg_k[sb + i0 - 1].w;
-                    else kprev = A.key[ob + 4 * (int64_t)q0 - 1];
+        const float4 *W0 = reinterpret_cast<const float4 *>(A.w0 + ob);
+        const float4 *W1 = reinterpret_cast<const float4 *>(A.w1 + ob);
+        int ct = T_NONE;                 // the run carried from the previous row
+        float2 clo = zero2, chi = zero2;
+        for (int qb = qa; qb < qe; qb += 32) {
+            const int q = qb + lane;
+            int t[4];
+            float2 lo[4], hi[4];
+            if (q < qe) {
+                const uint4 kq = ld_stream_u4(K4 + q);
+                const float4 a = ld_stream_f4(W0 + q), c = ld_stream_f4(W1 + q);
+                const uint32_t kk[4] = {kq.x, kq.y, kq.z, kq.w};
+                const float aa[4] = {a.x, a.y, a.z, a.w}, cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const uint32_t kr = kk[r];
+                    t[r] = (int)(kr >> 18);
+                    const float4 im = w4[(kr >> 5) & 0x1fffu];
+                    // {image pixels 0 + 1, pixels 2 + 3} of the open pairs; the class
+                    // says which of the two is voxel v's
+                    const float2 sp = __fadd2_rn(make_float2((kr & 1u) ? im.x : 0.f, (kr & 4u) ? im.z : 0.f),
+                                                 make_float2((kr & 2u) ? im.y : 0.f, (kr & 8u) ? im.w : 0.f));
+                    const bool cls = (kr & 16u) != 0u;
+                    const float2 x = make_float2(cls ? sp.y : sp.x, cls ? sp.x : sp.y);
+                    lo[r] = f2fma(aa[r], x, zero2);
+                    hi[r] = f2fma(cc[r], x, zero2);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    t[r] = T_PAST;
+                    lo[r] = zero2;
+                    hi[r] = zero2;
                 }
             }
-            if (q0 + 1 < q1) {
-                if (i0 + 1 < SADJ_SQ) { k1 = stg_k[sb + i0 + 1]; a1 = stg_a[sb + i0 + 1]; c1 = stg_c[sb + i0 + 1]; }
-                else { k1 = K4[q0 + 1]; a1 = A4[q0 + 1]; c1 = C4[q0 + 1]; }
+            // runs within the quad, summed from zero; lo[r] / hi[r] become the sums of
+            // the runs that end at record r (r < 3), and the last run's sum goes to
+            // (alo, ahi)
+            float2 alo = lo[0], ahi = hi[0];
+#pragma unroll
+            for (int r = 1; r < 4; ++r) {
+                if (t[r] != t[r - 1]) {
+                    lo[r - 1] = alo;
+                    hi[r - 1] = ahi;
+                    alo = lo[r];
+                    ahi = hi[r];
+                } else {
+                    alo = f2add(alo, lo[r]);
+                    ahi = f2add(ahi, hi[r]);
+                }
             }
-            // `dep` is 0 but depends on every register read from the stage, so the
-            // warp barrier below is passed only once those reads have completed.
-            unsigned dep = k0.x ^ k0.y ^ k0.z ^ k0.w ^ k1.x ^ k1.y ^ k1.z ^ k1.w ^ kprev ^
-                           __float_as_uint(a0.x) ^ __float_as_uint(a0.y) ^ __float_as_uint(a0.z) ^
-                           __float_as_uint(a0.w) ^ __float_as_uint(a1.x) ^ __float_as_uint(a1.y) ^
-                           __float_as_uint(a1.z) ^ __float_as_uint(a1.w) ^ __float_as_uint(c0.x) ^
-                           __float_as_uint(c0.y) ^ __float_as_uint(c0.z) ^ __float_as_uint(c0.w) ^
-                           __float_as_uint(c1.x) ^ __float_as_uint(c1.y) ^ __float_as_uint(c1.z) ^
-                           __float_as_uint(c1.w);
-            asm volatile("and.b32 %0, %0, 0;" : "+r"(dep));
-            kprev += dep;
+            const int t0 = t[0], t3 = t[3];
+            // the last run continued from the lane before (lane 0: from the row before)
+            const int tprev = __shfl_up_sync(0xffffffffu, t3, 1);
+            const bool cont = lane == 0 ? t0 == ct : t0 == tprev;
+            const bool link = cont && t0 == t3;   // the whole quad continues that run
+            // segmented inclusive scan over the lanes of the last runs' sums: a segment
+            // starts at every lane that does not continue its predecessor's run; the
+            // doubling stops once it spans the longest segment
+            float2 Olo = alo, Ohi = ahi;
+            if (lane == 0 && link) {
+                Olo = f2add(Olo, clo);
+                Ohi = f2add(Ohi, chi);
+            }
+            const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || !link);
+            const int sst = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));
+            const unsigned span = __reduce_max_sync(0xffffffffu, (unsigned)(lane - sst));
+            for (int o = 1; (unsigned)o <= span; o <<= 1) {   // warp-uniform
+                const float2 ylo = shfl_up2(Olo, o), yhi = shfl_up2(Ohi, o);
+                if (lane - o >= sst) {
+                    Olo = f2add(Olo, ylo);
+                    Ohi = f2add(Ohi, yhi);
+                }
+            }
+            // the carry into this lane's first run
+            const float2 plo = shfl_up2(Olo, 1), phi = shfl_up2(Ohi, 1);
+            float2 Clo = zero2, Chi = zero2;
+            if (cont) {
+                Clo = lane == 0 ? clo : plo;
+                Chi = lane == 0 ? chi : phi;
+            }
+            // the carried run of the row before ends there if lane 0 does not continue it
+            const bool flush = __shfl_sync(0xffffffffu, !cont, 0) && ct != T_NONE;
+            const int tnext = __shfl_down_sync(0xffffffffu, t0, 1);
+            const bool fin3 = lane < 31 && t3 != tnext;   // the last run ends in this lane
+            lo[3] = alo;
+            hi[3] = ahi;
+            // LO sums of the completed runs, then (after a warp barrier) the HI sums
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const bool end = r < 3 ? t[r] != t[r + 1] : fin3;
+                if (end) {
+                    if (t[r] == t0) {
+                        lo[r] = f2add(Clo, lo[r]);
+                        hi[r] = f2add(Chi, hi[r]);
+                    }
+                    const unsigned d = (unsigned)(t[r] - tlo);
+                    if (d < L) V[d] = f2add(V[d], lo[r]);
+                }
+            }
+            if (flush && lane == 0) {
+                const unsigned d = (unsigned)(ct - tlo);
+                if (d < L) V[d] = f2add(V[d], clo);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const bool end = r < 3 ? t[r] != t[r + 1] : fin3;
+                if (end) {
+                    const unsigned d = (unsigned)(t[r] + 1 - tlo);
+                    if (d < L) V[d] = f2add(V[d], hi[r]);
+                }
+            }
+            if (flush && lane == 0) {
+                const unsigned d = (unsigned)(ct + 1 - tlo);
+                if (d < L) V[d] = f2add(V[d], chi);
+            }
+            __syncwarp();
+            // lane 31's last run goes on into the next row
+            ct = __shfl_sync(0xffffffffu, t3, 31);
+            clo = shfl2(Olo, 31);
+            chi = shfl2(Ohi, 31);
+        }
+        if (ct != T_NONE && lane == 0) {   // the last carried run ends with the item
+            const unsigned d = (unsigned)(ct - tlo);
+            if (d < L) V[d] = f2add(V[d], clo);
+            const unsigned d1 = (unsigned)(ct + 1 - tlo);
+            if (d1 < L) V[d1] = f2add(V[d1], chi);
         }
         __syncwarp();
-        if (!late) {   // warp-uniform
-            par ^= 1u;
-            pending = false;
-            if (s + 1 < s1) {
-                issue(base + offr[s + 1 - s0], base + offr[s + 2 - s0]);
-                pending = true;
-            }
-        }
-
-        uint32_t ct = SENT, pt = SENT, st = SENT;
-        bool cont = false;
-        float2 clo = zero2, chi = zero2, ph = zero2, slo = zero2, shi = zero2;
-        if (!late && q0 < q1) {
-            cont = q0 > 0;
-            ct = (cont ? kprev : k0.x) >> 18;
-            auto take = [&](uint32_t k, float wa, float wb) {
-                const uint32_t t = k >> 18;
-                const float4 c = w4[(k >> 5) & 0x1fffu];
-                // {image pixels 0 + 1, pixels 2 + 3} of the open pairs; the class says
-                // which of the two is voxel v's
-                const float2 sp = __fadd2_rn(make_float2((k & 1u) ? c.x : 0.f, (k & 4u) ? c.z : 0.f),
-                                             make_float2((k & 2u) ? c.y : 0.f, (k & 8u) ? c.w : 0.f));
-                const bool cls = (k & 16u) != 0u;
-                const float2 x = make_float2(cls ? sp.y : sp.x, cls ? sp.x : sp.y);
-                if (t != ct) {
-                    if (cont) {   // the continued run ends inside the part
-                        st = ct;
-                        slo = clo;
-                        shi = chi;
-                        cont = false;
-                    } else {      // a complete head run
-                        const float2 lo = pt + 1 == ct ? f2add(clo, ph) : clo;
-                        if (pt != SENT && pt + 1 != ct) V[pt + 1] = ph;
-                        V[ct] = lo;
-                        pt = ct;
-                        ph = chi;
-                    }
-                    ct = t;
-                    clo = zero2;
-                    chi = zero2;
-                }
-                clo = f2fma(wa, x, clo);
-                chi = f2fma(wb, x, chi);
-            };
-            auto take4 = [&](const uint4 &k, const float4 &a, const float4 &c) {
-                take(k.x, a.x, c.x);
-                take(k.y, a.y, c.y);
-                take(k.z, a.z, c.z);
-                take(k.w, a.w, c.w);
-            };
-            take4(k0, a0, c0);
-            if (q0 + 1 < q1) take4(k1, a1, c1);
-            for (int q = q0 + 2; q < q1; ++q) take4(K4[q], A4[q], C4[q]);
-            if (cont) {      // the whole part continues one run
-                st = ct;
-                slo = clo;
-                shi = chi;
-                ct = SENT;
-            }
-        }
-        slot_t[tid] = st;
-        slot_lo[tid] = slo;
-        slot_hi[tid] = shi;
-        if (__syncthreads_or(late)) {   // block-uniform decision
-            ok = false;
-            break;
-        }
-        if (ct != SENT) {    // the last head run: add its continuations, in order
-            for (int k = tid + 1; k < ADJ_T && slot_t[k] == ct; ++k) {
-                clo = f2add(clo, slot_lo[k]);
-                chi = f2add(chi, slot_hi[k]);
-            }
-            float2 lo = clo;
-            if (pt != SENT) {
-                if (pt + 1 == ct) lo = f2add(lo, ph);
-                else V[pt + 1] = ph;
-            }
-            V[ct] = lo;
-        }
-        __syncthreads();
-        if (ct != SENT) V[ct + 1] = f2add(V[ct + 1], chi);
-        __syncthreads();
-        // write rows v and v' and clear V for the next pair: knots 2e, 2e + 1 per
-        // float4 e of V (consecutive lanes, consecutive 16 bytes: no bank conflicts)
+        // rows v and v' over the segment; clear the buffer for the next item
         const int i = s / A.J2, jq = s - i * A.J2;
-        OutT *rv = Vtab + ((int64_t)i * A.J + jq) * A.Bp;
-        OutT *rp = Vtab + ((int64_t)i * A.J + (A.J - 1 - jq)) * A.Bp;
-        float4 *V4 = reinterpret_cast<float4 *>(V);
-        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int e = tid; e < (A.Bp >> 1); e += ADJ_T) {
+        OutT *rv = Vtab + ((int64_t)i * A.J + jq) * A.Bp + tlo;
+        OutT *rp = Vtab + ((int64_t)i * A.J + (A.J - 1 - jq)) * A.Bp + tlo;
+        const int nL = min(A.L, A.Bp - tlo);
+        for (int e = lane; 2 * e < nL; e += 32) {
             const float4 x = V4[e];
             V4[e] = zero4;
             store_v2(rv + 2 * e, x.x, x.z);
             store_v2(rp + 2 * e, x.y, x.w);
         }
-        __syncthreads();
-    }
-    if (!ok && lane == 0) {
-        // a copy did not land in time: report, drain this warp's copies in flight, stop
-        atomicExch(err, 1);
-        if (pending) mbar_wait(&bar[warp], par);
+        __syncwarp();
     }
 }
 
-size_t adj_sym_smem(int npix, int Bp, int vc) {
-    return (size_t)((npix + 3) & ~3) * 4 + (size_t)Bp * 8 + (size_t)ADJ_W * SADJ_SQ * 48 + ADJ_W * 16 +
-           (size_t)ADJ_T * 20 + ADJ_W * 8 + 4 * (size_t)(vc + 1);
+// Shared memory of k_adj_sym: the quadrant image and one segment buffer per warp.
+size_t adj_sym_smem(int nq, int L) { return 16 * (size_t)nq + (size_t)SEG_W * L * sizeof(float2); }
+
+// The quad range of each (voxel pair, knot segment) item: the quads that hold the
+// records with t in [sg L - 1, (sg + 1) L), by binary search in the t-sorted list.
+__global__ void k_sadj_segs(const int64_t *__restrict__ off, const uint32_t *__restrict__ key, int R2, int nseg,
+                            int L, uint32_t *__restrict__ seg) {
+    const int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (it >= (int64_t)R2 * nseg) return;
+    const int s = (int)(it / nseg), sg = (int)(it - (int64_t)s * nseg);
+    const int64_t b = off[s];
+    const int n = (int)(off[s + 1] - b);
+    auto first_at_least = [&](int tv) {
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((int)(key[b + mid] >> 18) < tv) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+    const int a = first_at_least(sg * L - 1), e = first_at_least((sg + 1) * L);
+    seg[it] = (uint32_t)(a >> 2) | ((uint32_t)((e + 3) >> 2) << 16);
 }
 
 // ---- sparse subset operators (ordered subsets) -----------------------------------
@@ -1490,6 +1516,7 @@ void records_free(TablePath *T) {
     cudaFree(T->sym.tb);
     cudaFree(T->sym.w);
     free_set(T->sym.adj);
+    cudaFree(T->sym.adj_seg);
     T->sym = SymSet();
     T->use_records = false;
 }
@@ -1552,19 +1579,24 @@ caxsi_status records_build_subsets(caxsi_plan *p, TablePath *T, int P, const int
 }
 
 // The adjoint's symmetric lists (SymSet::adj): count, pad to quads, fill sorted by
-// t.  Leaves adj.P = 0 (the adjoint then streams the ordinary records) when the
-// sizes do not fit the key or shared memory, or the device memory is not there.
+// t, and find each (pair, knot segment) item's quad range.  Leaves adj.P = 0 (the
+// adjoint then streams the ordinary records) when the sizes do not fit the key or
+// shared memory, or the device memory is not there.
 caxsi_status sym_adj_build(caxsi_plan *p, TablePath *T) {
     const DevGeo &g = p->dg;
     SymSet &y = T->sym;
-    if ((g.M / 2) * (g.N / 2) > 8192 || T->B > 16383) return CAXSI_OK;
-    // one block per SM (its shared memory allows one)
-    const int chunks = p->num_sms < y.R2 ? p->num_sms : y.R2;
-    const int vc = (int)ceil_div64(y.R2, chunks);
-    if ((int64_t)vc * (g.M / 2) * g.N + 4 * (int64_t)vc > INT32_MAX) return CAXSI_OK;   // 32-bit list offsets
+    const int nq = (g.M / 2) * (g.N / 2);
+    if (nq > 8192 || T->B > 16383) return CAXSI_OK;
+    // knot segments: about 16 per pair (at least 64 knots each), as long as one
+    // segment per warp fits beside the image
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
-    if ((size_t)smem_max < adj_sym_smem(g.M * g.N, T->Bp, vc)) return CAXSI_OK;
+    const int64_t lmax = (((int64_t)smem_max - 512 - 16 * (int64_t)nq) / ((int64_t)SEG_W * 8)) & ~int64_t(7);
+    if (lmax < 8) return CAXSI_OK;
+    int nseg = std::max((int)ceil_div64(T->Bp, lmax), std::min(16, (int)ceil_div64(T->Bp, 64)));
+    const int L = (int)((ceil_div64(T->Bp, nseg) + 7) & ~int64_t(7));
+    nseg = (int)ceil_div64(T->Bp, L);
+    if ((int64_t)y.R2 * nseg > INT32_MAX) return CAXSI_OK;
     const int wpb = fill_warps(p, T);
     if (wpb < 1) return CAXSI_OK;
     const PairArgs pa = pair_args(p);
@@ -1591,34 +1623,40 @@ caxsi_status sym_adj_build(caxsi_plan *p, TablePath *T) {
     }
     const int64_t n = h[ng];
     const int64_t nalloc = n > 0 ? n : 4;
+    const int64_t nitems = ng * nseg;
     RecSet &r = y.adj;
     if (cudaMalloc(&r.off, (size_t)(ng + 1) * sizeof(int64_t)) != cudaSuccess ||
         cudaMalloc(&r.key, (size_t)nalloc * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&r.w0, (size_t)nalloc * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&r.w1, (size_t)nalloc * sizeof(float)) != cudaSuccess) {
+        cudaMalloc(&r.w1, (size_t)nalloc * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&y.adj_seg, (size_t)nitems * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
         free_set(r);
+        cudaFree(y.adj_seg);
+        y.adj_seg = nullptr;
         return CAXSI_OK;
     }
-    if (cudaMemcpy(r.off, h.data(), (size_t)(ng + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+    auto fail = [&]() {
+        cudaGetLastError();
         free_set(r);
+        cudaFree(y.adj_seg);
+        y.adj_seg = nullptr;
         return CAXSI_ERR_CUDA;
-    }
+    };
+    if (cudaMemcpy(r.off, h.data(), (size_t)(ng + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail();
     const size_t smem = (size_t)wpb * (T->B + 1) * sizeof(int);
-    if (cudaFuncSetAttribute(k_sadj_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        free_set(r);
-        return CAXSI_ERR_CUDA;
-    }
+    if (cudaFuncSetAttribute(k_sadj_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return fail();
     k_sadj_fill<<<(unsigned)ceil_div64(ng, wpb), wpb * 32, smem>>>(pa, ta, y.R2, wpb, r.off, r.key, r.w0, r.w1);
-    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
-        free_set(r);
-        return CAXSI_ERR_CUDA;
-    }
+    if (cudaGetLastError() != cudaSuccess) return fail();
+    k_sadj_segs<<<(unsigned)ceil_div64(nitems, 256), 256>>>(r.off, r.key, y.R2, nseg, L, y.adj_seg);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return fail();
     r.P = 1;
     r.n = n_real;
-    p->table_bytes += n * 12 + (ng + 1) * 8;
-    y.adj_vc = vc;
-    y.adj_chunks = (int)ceil_div64(y.R2, vc);
+    p->table_bytes += n * 12 + (ng + 1) * 8 + nitems * 4;
+    y.adj_L = L;
+    y.adj_nseg = nseg;
     return CAXSI_OK;
 }
 
@@ -1683,24 +1721,27 @@ cudaError_t sym_forward(const caxsi_plan *p, const TablePath *T, float *part, cu
 template <typename OutT>
 cudaError_t launch_adj_sym(const caxsi_plan *p, const TablePath *T, const float *w, OutT *out, cudaStream_t s) {
     const DevGeo &g = p->dg;
-    const size_t smem = adj_sym_smem(g.M * g.N, T->Bp, T->sym.adj_vc);
+    const SymSet &y = T->sym;
+    const size_t smem = adj_sym_smem((g.M / 2) * (g.N / 2), y.adj_L);
     cudaError_t e = cudaFuncSetAttribute(k_adj_sym<OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const SymSet &y = T->sym;
     SymAdjArgs a;
     a.R2 = y.R2;
     a.J = g.J;
     a.J2 = g.J / 2;
     a.M = g.M;
     a.N = g.N;
-    a.npix = g.M * g.N;
     a.Bp = T->Bp;
-    a.vc = y.adj_vc;
+    a.nseg = y.adj_nseg;
+    a.L = y.adj_L;
     a.off = y.adj.off;
+    a.seg = y.adj_seg;
     a.key = y.adj.key;
     a.w0 = y.adj.w0;
     a.w1 = y.adj.w1;
-    k_adj_sym<OutT><<<y.adj_chunks, ADJ_T, smem, s>>>(a, w, out, p->err_flag + 1);
+    const int64_t warps = (int64_t)y.R2 * y.adj_nseg;
+    const int grid = (int)std::min<int64_t>(p->num_sms, ceil_div64(warps, SEG_W));
+    k_adj_sym<OutT><<<grid, SEG_T, smem, s>>>(a, w, out);
     return cudaGetLastError();
 }
 

@@ -59,7 +59,10 @@ struct SymSet {
     // pairs are all closed are left out.  adj.P = 0 when the sizes do not fit the
     // key ((M/2)(N/2) > 8192 or B > 16383) or shared memory.
     RecSet adj;
-    int adj_chunks = 0, adj_vc = 0;   // adjoint blocks, voxel pairs per block
+    // the adjoint's work items: (pair s, knot segment [sg L, (sg + 1) L)), with the
+    // quad range of the records that reach the segment (first | end << 16)
+    int adj_L = 0, adj_nseg = 0;
+    uint32_t *adj_seg = nullptr;   // [R2 * adj_nseg]
 };
 
 struct TablePath {

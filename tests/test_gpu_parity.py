@@ -372,14 +372,20 @@ def test_paper_table1_geometry_sampled(cx, path):
     plan.close()
 
 
-@pytest.mark.parametrize("name", ["tiny", "even_small"])
+@pytest.mark.parametrize("name", ["tiny", "even_small", "long_runs"])
 def test_mirror_symmetric_operators_equal_the_plain_records(cx, name):
     """The forward and the adjoint over mirror-symmetric records (a record serves a
     pair and its mirror images) against one record per open pair, and both
-    against the oracle."""
+    against the oracle.  "long_runs" has two energies and four q bins, so that a
+    voxel pair's few knots carry runs of up to hundreds of records: runs that cross
+    many lanes and several 128-record rows of the adjoint's warp."""
     caxsi, torch = cx
-    g = synth.tiny_geometry() if name == "tiny" else synth.make_geometry(
-        X=3, J=6, Q=20, M=10, N=24, K=9, rho_y=2, p_y=3.0, p_z=5.0, dx=9.0)
+    if name == "tiny":
+        g = synth.tiny_geometry()
+    elif name == "even_small":
+        g = synth.make_geometry(X=3, J=6, Q=20, M=10, N=24, K=9, rho_y=2, p_y=3.0, p_z=5.0, dx=9.0)
+    else:
+        g = synth.make_geometry(X=2, J=4, Q=4, M=32, N=64, K=2, rho_y=1, p_y=3.04, p_z=3.04, dx=9.0)
     phi = synth.tungsten_spectrum(g)
     mask = synth.random_mask(g, 55)
     f = synth.phantom(g, 6, n_ellipses=3) + 0.05 * synth.uniform_random((g.X, g.J, g.Q), 7)
