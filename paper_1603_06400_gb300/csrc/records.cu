@@ -29,9 +29,9 @@
 // and its left-right / up-down mirror images, which share the interval and the
 // weights: the full forward streams one 21-byte record per voxel pair and
 // quadrant pixel (8 pairs, k_fwd_sym), the full adjoint t-sorted lists per voxel
-// pair of 12-byte records that stand for 4 pairs each (k_adj_sym, the same
-// run-ownership reduction with two sums per run).  The subset and batched
-// operators stream the one-pair records.
+// pair of 12-byte records that stand for 4 pairs each (k_adj_sym: one warp per
+// voxel pair and knot segment, runs of equal t joined across lanes by a warp
+// scan).  The subset and batched operators stream the one-pair records.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
