@@ -214,15 +214,17 @@ def kernel_work(name, g, info, path, nsm):
         return "TFLOP/s", open_pairs * (8.0 * g.K + 30.0), "alu"
     sym_chunks = min(nsm, g.X * (g.J // 2))   # one block per SM over the voxel pairs
     if name == "sym_pairs_fwd":
-        # one 21-byte record per voxel pair and quadrant pixel (8 pairs), two W rows
-        # per voxel pair, one partial image per block
+        # one 21-byte record per voxel pair and quadrant pixel (8 pairs), two W rows per
+        # voxel pair (FP32; bf16 on the bf16 path), one partial image per block
         recs = (g.X * (g.J // 2)) * ((g.M // 2) * (g.N // 2))
-        return "GB/s", 21.0 * recs + 4.0 * R * Bp + 4.0 * sym_chunks * npix, "hbm"
+        wb = 2.0 if path == "table_bf16" else 4.0
+        return "GB/s", 21.0 * recs + wb * R * Bp + 4.0 * sym_chunks * npix, "hbm"
     if name == "sym_pairs_adj":
-        # 12-byte records (up to 4 pairs each), one V row per voxel, the input
-        # image once per block
+        # records of a 4-byte key and two weights (FP32; bf16 on the bf16 path), up to
+        # 4 pairs each, one V row per voxel, the input image once per block
         vb = {"table_fp32": 4.0, "table_bf16": 2.0, "table_fp16": 2.0}[path]
-        return "GB/s", 12.0 * info["n_sym_records"] + vb * R * B + 4.0 * sym_chunks * npix, "hbm"
+        rb = 8.0 if path == "table_bf16" else 12.0
+        return "GB/s", rb * info["n_sym_records"] + vb * R * B + 4.0 * sym_chunks * npix, "hbm"
     if name == "rec_pairs_fwd":
         # 12-byte records, one W row per voxel, one partial image per block
         return "GB/s", 12.0 * n_rec + 4.0 * R * Bp + 4.0 * chunks * npix, "hbm"

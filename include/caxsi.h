@@ -80,8 +80,11 @@ typedef enum {
  *   tables the contractions produce and consume (W and V, one row per voxel) are
  *   kept in 16 bits where the mirror-symmetric records are used (bf16 for
  *   TABLE_BF16's W and V, fp16 for TABLE_FP16's V; TABLE_FP16's W stays FP32,
- *   as fp16's range would not hold every value); the pair weights, the
- *   interpolation position and all accumulations stay FP32. */
+ *   as fp16's range would not hold every value).  TABLE_BF16's adjoint also
+ *   streams the mirror-symmetric adjoint records' pair weights w0, w1 as bf16 (a
+ *   copy that the plan keeps beside the FP32 one); the knot interval of each
+ *   pair, the mask factors, the forward's pair weights and all accumulations
+ *   stay exact / FP32. */
 typedef enum {
     CAXSI_PATH_DIRECT = 0,
     CAXSI_PATH_TABLE_FP32 = 1,

@@ -751,6 +751,12 @@ __global__ void k_sym_build(PairArgs A, TabArgs T, int R2, int nrec, uint32_t *_
 // before it uses the first, so that their loads overlap.
 // WT: the element type of the knot rows (float, or bf16 for the bf16 path).
 constexpr int SYM_U = 4;
+// Four bf16 record weights, widened exactly to FP32.
+__device__ __forceinline__ float4 bf16x4_to_f4(uint2 u) {
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u), __uint_as_float(u.y << 16),
+                       __uint_as_float(u.y & 0xffff0000u));
+}
+
 __device__ __forceinline__ float wval(const float *w, int t) { return w[t]; }
 __device__ __forceinline__ float wval(const __nv_bfloat16 *w, int t) { return __bfloat162float(w[t]); }
 
@@ -1015,6 +1021,7 @@ struct SymAdjArgs {
     const uint32_t *seg;    // [R2 * nseg] first quad | end quad << 16, relative to the pair's list
     const uint32_t *key;
     const float *w0, *w1;
+    const uint16_t *w0_16, *w1_16;   // the same weights as bf16 (the bf16 path), or null
 };
 
 // Two-lane FP32 arithmetic in one packed instruction (each lane rounded as fmaf / +).
@@ -1038,8 +1045,19 @@ __device__ __forceinline__ float4 ld_stream_f4(const float4 *p) {
                  : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p));
     return r;
 }
+__device__ __forceinline__ uint2 ld_stream_u2(const uint2 *p) {
+    uint2 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
+    return r;
+}
+// A quad's weights (four records) from FP32 or bf16 storage.
+template <bool W16>
+__device__ __forceinline__ float4 quad_w(const float *w, const uint16_t *w16, int64_t ob, int q) {
+    if (W16) return bf16x4_to_f4(ld_stream_u2(reinterpret_cast<const uint2 *>(w16 + ob) + q));
+    return ld_stream_f4(reinterpret_cast<const float4 *>(w + ob) + q);
+}
 
-template <typename OutT>
+template <typename OutT, bool W16>
 __global__ void __launch_bounds__(SEG_T, 1)
 k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1077,8 +1095,6 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab) {
         const int qa = (int)(qr & 0xffffu), qe = (int)(qr >> 16);
         const int64_t ob = A.off[s];
         const uint4 *K4 = reinterpret_cast<const uint4 *>(A.key + ob);
-        const float4 *W0 = reinterpret_cast<const float4 *>(A.w0 + ob);
-        const float4 *W1 = reinterpret_cast<const float4 *>(A.w1 + ob);
         int ct = T_NONE;                 // the run carried from the previous row
         float2 clo = zero2, chi = zero2;
         for (int qb = qa; qb < qe; qb += 32) {
@@ -1087,7 +1103,7 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab) {
             float2 lo[4], hi[4];
             if (q < qe) {
                 const uint4 kq = ld_stream_u4(K4 + q);
-                const float4 a = ld_stream_f4(W0 + q), c = ld_stream_f4(W1 + q);
+                const float4 a = quad_w<W16>(A.w0, A.w0_16, ob, q), c = quad_w<W16>(A.w1, A.w1_16, ob, q);
                 const uint32_t kk[4] = {kq.x, kq.y, kq.z, kq.w};
                 const float aa[4] = {a.x, a.y, a.z, a.w}, cc[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
@@ -1515,6 +1531,8 @@ void records_free(TablePath *T) {
     cudaFree(T->sym.tt);
     cudaFree(T->sym.tb);
     cudaFree(T->sym.w);
+    cudaFree(T->sym.adj_w0_16);
+    cudaFree(T->sym.adj_w1_16);
     free_set(T->sym.adj);
     cudaFree(T->sym.adj_seg);
     T->sym = SymSet();
@@ -1576,6 +1594,32 @@ caxsi_status records_build_subsets(caxsi_plan *p, TablePath *T, int P, const int
     cudaFree(d_sub);
     if (st == CAXSI_OK && T->sub.P == 0) st = CAXSI_ERR_OOM;
     return st;
+}
+
+// bf16 copies of the record weights for the bf16 path (round to nearest even).
+__global__ void k_w_to_bf16(const float *__restrict__ x, int64_t n, uint16_t *__restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = __bfloat16_as_ushort(__float2bfloat16_rn(x[i]));
+}
+
+// Allocate and fill a bf16 copy of n FP32 weights; leaves *out null (the bf16 path
+// then streams the FP32 weights) when the memory is not there.
+caxsi_status bf16_copy(caxsi_plan *p, const float *x, int64_t n, uint16_t **out) {
+    *out = nullptr;
+    if (n <= 0) return CAXSI_OK;
+    if (cudaMalloc(out, (size_t)n * sizeof(uint16_t)) != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return CAXSI_OK;
+    }
+    k_w_to_bf16<<<(unsigned)std::min<int64_t>(ceil_div64(n, 256), 8 * (int64_t)p->num_sms), 256>>>(x, n, *out);
+    if (cudaGetLastError() != cudaSuccess) {
+        cudaFree(*out);
+        *out = nullptr;
+        return CAXSI_ERR_CUDA;
+    }
+    p->table_bytes += n * 2;
+    return CAXSI_OK;
 }
 
 // The adjoint's symmetric lists (SymSet::adj): count, pad to quads, fill sorted by
@@ -1657,7 +1701,14 @@ caxsi_status sym_adj_build(caxsi_plan *p, TablePath *T) {
     p->table_bytes += n * 12 + (ng + 1) * 8 + nitems * 4;
     y.adj_L = L;
     y.adj_nseg = nseg;
-    return CAXSI_OK;
+    caxsi_status st = bf16_copy(p, r.w0, n, &y.adj_w0_16);
+    if (st == CAXSI_OK) st = bf16_copy(p, r.w1, n, &y.adj_w1_16);
+    if (st == CAXSI_OK && (!y.adj_w0_16 || !y.adj_w1_16)) {   // both or neither
+        cudaFree(y.adj_w0_16);
+        cudaFree(y.adj_w1_16);
+        y.adj_w0_16 = y.adj_w1_16 = nullptr;
+    }
+    return st;
 }
 
 // Build the mirror-symmetric records when the geometry allows them (J, M, N
@@ -1704,7 +1755,7 @@ caxsi_status sym_build(caxsi_plan *p, TablePath *T) {
 cudaError_t sym_forward(const caxsi_plan *p, const TablePath *T, float *part, cudaStream_t s, bool w16) {
     const int npix = p->dg.M * p->dg.N;
     const size_t smem = fwd_sym_smem(npix, T->Bp);
-    if (w16) {
+    if (w16) {   // the bf16 path: bf16 knot rows (the records keep FP32 weights: bf16 ones measured slower)
         cudaError_t e = cudaFuncSetAttribute(k_fwd_sym<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
@@ -1718,12 +1769,13 @@ cudaError_t sym_forward(const caxsi_plan *p, const TablePath *T, float *part, cu
     return cudaGetLastError();
 }
 
-template <typename OutT>
+template <typename OutT, bool W16>
 cudaError_t launch_adj_sym(const caxsi_plan *p, const TablePath *T, const float *w, OutT *out, cudaStream_t s) {
     const DevGeo &g = p->dg;
     const SymSet &y = T->sym;
     const size_t smem = adj_sym_smem((g.M / 2) * (g.N / 2), y.adj_L);
-    cudaError_t e = cudaFuncSetAttribute(k_adj_sym<OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_adj_sym<OutT, W16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     SymAdjArgs a;
     a.R2 = y.R2;
@@ -1739,16 +1791,24 @@ cudaError_t launch_adj_sym(const caxsi_plan *p, const TablePath *T, const float 
     a.key = y.adj.key;
     a.w0 = y.adj.w0;
     a.w1 = y.adj.w1;
+    a.w0_16 = y.adj_w0_16;
+    a.w1_16 = y.adj_w1_16;
     const int64_t warps = (int64_t)y.R2 * y.adj_nseg;
     const int grid = (int)std::min<int64_t>(p->num_sms, ceil_div64(warps, SEG_W));
-    k_adj_sym<OutT><<<grid, SEG_T, smem, s>>>(a, w, out);
+    k_adj_sym<OutT, W16><<<grid, SEG_T, smem, s>>>(a, w, out);
     return cudaGetLastError();
 }
 
+// out_kind 1 (the bf16 path): bf16 V rows, and bf16 record weights when the plan
+// has them; 2 (fp16): fp16 V rows; 0: FP32.
 cudaError_t sym_adjoint(const caxsi_plan *p, const TablePath *T, const float *w, int out_kind, cudaStream_t s) {
-    if (out_kind == 1) return launch_adj_sym(p, T, w, reinterpret_cast<__nv_bfloat16 *>(T->v16), s);
-    if (out_kind == 2) return launch_adj_sym(p, T, w, reinterpret_cast<__half *>(T->v16), s);
-    return launch_adj_sym(p, T, w, T->tab, s);
+    if (out_kind == 1) {
+        __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(T->v16);
+        if (T->sym.adj_w0_16) return launch_adj_sym<__nv_bfloat16, true>(p, T, w, out, s);
+        return launch_adj_sym<__nv_bfloat16, false>(p, T, w, out, s);
+    }
+    if (out_kind == 2) return launch_adj_sym<__half, false>(p, T, w, reinterpret_cast<__half *>(T->v16), s);
+    return launch_adj_sym<float, false>(p, T, w, T->tab, s);
 }
 
 cudaError_t records_forward(const caxsi_plan *p, const TablePath *T, int subset, float *part, cudaStream_t s) {

@@ -59,6 +59,7 @@ struct SymSet {
     // pairs are all closed are left out.  adj.P = 0 when the sizes do not fit the
     // key ((M/2)(N/2) > 8192 or B > 16383) or shared memory.
     RecSet adj;
+    uint16_t *adj_w0_16 = nullptr, *adj_w1_16 = nullptr;   // adj.w0 / adj.w1 as bf16 (the bf16 path), or null
     // the adjoint's work items: (pair s, knot segment [sg L, (sg + 1) L)), with the
     // quad range of the records that reach the segment (first | end << 16)
     int adj_L = 0, adj_nseg = 0;

@@ -39,9 +39,13 @@ def test_record_kernels_bytes(paper):
     _, adj, _ = bench.kernel_work("sym_pairs_adj", g, info, "table_fp32", NSM)
     assert adj == 12 * N_SYM + 4 * R * B + 4 * NSM * npix
     assert adj == pytest.approx(2.592e9, rel=1e-3)
-    # the 16-bit paths write 2-byte V rows
-    _, adj16, _ = bench.kernel_work("sym_pairs_adj", g, info, "table_bf16", NSM)
+    # the 16-bit paths write 2-byte V rows; the bf16 path streams bf16 record weights
+    _, adj16, _ = bench.kernel_work("sym_pairs_adj", g, info, "table_fp16", NSM)
     assert adj - adj16 == 2 * R * B
+    _, adjb, _ = bench.kernel_work("sym_pairs_adj", g, info, "table_bf16", NSM)
+    assert adj - adjb == 2 * R * B + 4 * N_SYM
+    _, fwdb, _ = bench.kernel_work("sym_pairs_fwd", g, info, "table_bf16", NSM)
+    assert fwd - fwdb == 2 * R * BP
     # plain records: 12 B each, one block per two SMs' worth of voxel chunks
     _, rf, _ = bench.kernel_work("rec_pairs_fwd", g, info, "table_fp32", NSM)
     _, ra, _ = bench.kernel_work("rec_pairs_adj", g, info, "table_fp32", NSM)
