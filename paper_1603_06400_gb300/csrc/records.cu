@@ -1079,7 +1079,6 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab) {
     __syncthreads();
 
     const int nitems = A.R2 * A.nseg;
-    const unsigned L = (unsigned)A.L;
     for (;;) {
         // the block's items are blockIdx.x + j gridDim.x, in segment-major order (all
         // pairs' segment 0, then segment 1, ...), so that every block gets a like mix
@@ -1090,20 +1089,34 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab) {
         const int64_t k = blockIdx.x + (int64_t)j * gridDim.x;
         if (k >= nitems) break;
         const int sg = (int)(k / A.R2), s = (int)(k - (int64_t)sg * A.R2);
-        const int tlo = sg * A.L;
         const uint32_t qr = A.seg[(int64_t)s * A.nseg + sg];
         const int qa = (int)(qr & 0xffffu), qe = (int)(qr >> 16);
+        const int tlo = sg * A.L;
+        const unsigned L = (unsigned)min(A.L, A.Bp - tlo);   // the segment's knots
         const int64_t ob = A.off[s];
         const uint4 *K4 = reinterpret_cast<const uint4 *>(A.key + ob);
         int ct = T_NONE;                 // the run carried from the previous row
         float2 clo = zero2, chi = zero2;
+        // the next row's quad is loaded while a row is summed
+        uint4 nk = make_uint4(0u, 0u, 0u, 0u);
+        float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nc = na;
+        if (qa + lane < qe) {
+            nk = ld_stream_u4(K4 + qa + lane);
+            na = quad_w<W16>(A.w0, A.w0_16, ob, qa + lane);
+            nc = quad_w<W16>(A.w1, A.w1_16, ob, qa + lane);
+        }
         for (int qb = qa; qb < qe; qb += 32) {
             const int q = qb + lane;
+            const uint4 kq = nk;
+            const float4 a = na, c = nc;
+            if (q + 32 < qe) {
+                nk = ld_stream_u4(K4 + q + 32);
+                na = quad_w<W16>(A.w0, A.w0_16, ob, q + 32);
+                nc = quad_w<W16>(A.w1, A.w1_16, ob, q + 32);
+            }
             int t[4];
             float2 lo[4], hi[4];
             if (q < qe) {
-                const uint4 kq = ld_stream_u4(K4 + q);
-                const float4 a = quad_w<W16>(A.w0, A.w0_16, ob, q), c = quad_w<W16>(A.w1, A.w1_16, ob, q);
                 const uint32_t kk[4] = {kq.x, kq.y, kq.z, kq.w};
                 const float aa[4] = {a.x, a.y, a.z, a.w}, cc[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
@@ -1227,7 +1240,7 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab) {
         const int i = s / A.J2, jq = s - i * A.J2;
         OutT *rv = Vtab + ((int64_t)i * A.J + jq) * A.Bp + tlo;
         OutT *rp = Vtab + ((int64_t)i * A.J + (A.J - 1 - jq)) * A.Bp + tlo;
-        const int nL = min(A.L, A.Bp - tlo);
+        const int nL = (int)L;
         for (int e = lane; 2 * e < nL; e += 32) {
             const float4 x = V4[e];
             V4[e] = zero4;
@@ -1640,7 +1653,7 @@ caxsi_status sym_adj_build(caxsi_plan *p, TablePath *T) {
     int nseg = std::max((int)ceil_div64(T->Bp, lmax), std::min(16, (int)ceil_div64(T->Bp, 64)));
     const int L = (int)((ceil_div64(T->Bp, nseg) + 7) & ~int64_t(7));
     nseg = (int)ceil_div64(T->Bp, L);
-    if ((int64_t)y.R2 * nseg > INT32_MAX) return CAXSI_OK;
+    if (L > lmax || (int64_t)y.R2 * nseg > INT32_MAX) return CAXSI_OK;
     const int wpb = fill_warps(p, T);
     if (wpb < 1) return CAXSI_OK;
     const PairArgs pa = pair_args(p);
