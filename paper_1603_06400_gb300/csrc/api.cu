@@ -78,6 +78,11 @@ void free_plan(caxsi_plan *p) {
     cudaFree(p->err_flag);
     cudaFree(p->stage_in);
     cudaFree(p->stage_out);
+    if (p->copy_stream) {
+        cudaEventDestroy(p->pipe_ev[0]);
+        cudaEventDestroy(p->pipe_ev[1]);
+        cudaStreamDestroy(p->copy_stream);
+    }
     delete p;
 }
 
@@ -473,13 +478,47 @@ static caxsi_status host_call(caxsi_plan *p, const float *in_host, int64_t in_le
     }
     p->launches = 0;
     cudaStream_t s = 0;
-    CAXSI_CUDA_TRY(cudaMemcpyAsync(p->stage_in, in_host, in_len * sizeof(float), cudaMemcpyHostToDevice, s));
+    // the FP32 table path overlaps the copy of f with half of the contraction
+    const int64_t half = (p->dg.R / 2) & ~int64_t(127);
+    const bool piped = path == CAXSI_PATH_TABLE_FP32 && half > 0;
+    if (piped && !p->copy_stream) {
+        CAXSI_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+        if (cudaEventCreateWithFlags(&p->pipe_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->pipe_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+            cudaStreamDestroy(p->copy_stream);
+            p->copy_stream = nullptr;
+            return CAXSI_ERR_CUDA;
+        }
+    }
+    HostPipe pipe{half, p->copy_stream, p->pipe_ev[0], p->pipe_ev[1], out_host, 0};
+    if (piped && fwd) {
+        // the first half of f, then the second on the copy stream (one after the other:
+        // they share the link) while the first half's contraction runs
+        const int64_t n1 = half * p->dg.Q;
+        CAXSI_CUDA_TRY(cudaMemcpyAsync(p->stage_in, in_host, n1 * sizeof(float), cudaMemcpyHostToDevice, s));
+        CAXSI_CUDA_TRY(cudaEventRecord(pipe.out_half, s));
+        CAXSI_CUDA_TRY(cudaStreamWaitEvent(pipe.cs, pipe.out_half, 0));
+        CAXSI_CUDA_TRY(cudaMemcpyAsync(p->stage_in + n1, in_host + n1, (in_len - n1) * sizeof(float),
+                                       cudaMemcpyHostToDevice, pipe.cs));
+        CAXSI_CUDA_TRY(cudaEventRecord(pipe.in_ready, pipe.cs));
+    } else {
+        CAXSI_CUDA_TRY(cudaMemcpyAsync(p->stage_in, in_host, in_len * sizeof(float), cudaMemcpyHostToDevice, s));
+    }
+    p->pipe = piped ? &pipe : nullptr;
     caxsi_status st = fwd ? run_forward(p, p->stage_in, p->stage_out, path, s)
                           : run_adjoint(p, p->stage_in, p->stage_out, path, s);
-    if (st != CAXSI_OK) return st;
-    CAXSI_CUDA_TRY(cudaMemcpyAsync(out_host, p->stage_out, out_len * sizeof(float), cudaMemcpyDeviceToHost, s));
-    CAXSI_CUDA_TRY(cudaStreamSynchronize(s));
-    return CAXSI_OK;
+    p->pipe = nullptr;
+    if (st == CAXSI_OK) {
+        // the part of the result that the adjoint has not sent already
+        const int64_t from = fwd ? 0 : pipe.out_from * p->dg.Q;
+        if (cudaMemcpyAsync(out_host + from, p->stage_out + from, (out_len - from) * sizeof(float),
+                            cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            st = CAXSI_ERR_CUDA;
+    }
+    // both streams are drained before returning, also after an error
+    if (cudaStreamSynchronize(s) != cudaSuccess) st = CAXSI_ERR_CUDA;
+    if (piped && cudaStreamSynchronize(pipe.cs) != cudaSuccess) st = CAXSI_ERR_CUDA;
+    return st;
 }
 
 caxsi_status caxsi_forward_host(caxsi_plan *p, const float *f_host, int64_t f_len, float *g_host,

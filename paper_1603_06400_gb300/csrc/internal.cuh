@@ -47,6 +47,23 @@ constexpr int NLL_THREADS = 64;
 // Table-path data (piecewise-linear structure of W in u); built on first use.
 struct TablePath;
 
+// A host-buffer call on the FP32 table path splits the voxel rows at `rows`
+// (a whole number of 128-row tiles) and runs the contraction of each half as its
+// own launch, so that one half's copy overlaps the other half's contraction:
+// forward -- the second half of f arrives on copy_stream and `in_ready` records
+// its end (the forward waits for it before the second half, or before anything
+// when it does not split); adjoint -- after the first half's contraction the
+// adjoint records `out_half`, copies that half of f to out_host on copy_stream
+// and sets `out_from` = rows, so that the caller copies only the rest.  Each
+// output row is computed exactly as without the split.
+struct HostPipe {
+    int64_t rows;
+    cudaStream_t cs;
+    cudaEvent_t in_ready, out_half;
+    float *out_host;
+    int64_t out_from;
+};
+
 struct caxsi_plan {
     caxsi_geometry g;
     DevGeo dg;
@@ -89,6 +106,11 @@ struct caxsi_plan {
     int *err_flag;      // [3] device words: [0] non-positive mean, [1] copy wait timed out,
                         // [2] completion counter of the likelihood blocks
     float *stage_in, *stage_out;  // host-API staging, lazily
+    // Host-buffer calls on the FP32 table path overlap their large copy with the
+    // contraction: set only during such a call (see HostPipe).
+    struct HostPipe *pipe;
+    cudaStream_t copy_stream;     // lazily, with the two events below
+    cudaEvent_t pipe_ev[2];
 
     TablePath *table;
 

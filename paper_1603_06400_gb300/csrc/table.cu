@@ -943,12 +943,37 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
     // the full forward over the mirror-symmetric records
     const bool sym_fwd = T->use_records && subset < 0 && T->sym.ok && !p->no_symmetry;
     if (cublasSetStream(T->blas, s) != CUBLAS_STATUS_SUCCESS) return CAXSI_ERR_CUDA;
-    if (p->gemm_engine == 0 && path == CAXSI_PATH_TABLE_FP32) {
+    const bool raw_hi = d.Q == T->Qp && (reinterpret_cast<uintptr_t>(f) & 15) == 0;
+    // a host-buffer call: the second half of f may still be on its way
+    HostPipe *pipe = p->pipe;
+    const bool split = pipe && p->gemm_engine == 0 && path == CAXSI_PATH_TABLE_FP32 && raw_hi && subset < 0 &&
+                       pipe->rows > 0 && pipe->rows < d.R;
+    if (pipe && !split) CAXSI_CUDA_TRY(cudaStreamWaitEvent(s, pipe->in_ready, 0));
+    if (split) {
+        // Wtab = f S~^T as below, the rows of each half in their own launch: the
+        // second after the second half of f has arrived
+        const int64_t r1 = pipe->rows;
+        for (int h = 0; h < 2; ++h) {
+            const int64_t r0 = h ? r1 : 0, nr = h ? d.R - r1 : r1;
+            if (h) CAXSI_CUDA_TRY(cudaStreamWaitEvent(s, pipe->in_ready, 0));
+            {
+                CAXSI_PROF(p, "split_tf32", s);
+                CAXSI_CUDA_TRY(trunc_remainder(f + r0 * d.Q, nr * d.Q, T->f_lo + r0 * d.Q, s));
+            }
+            CAXSI_LAUNCH_CHECK(p);
+            {
+                CAXSI_PROF(p, "tc_gemm_fwd_3xtf32", s);
+                CAXSI_CUDA_TRY(tc_gemm(0, 256, (int)nr, T->B, d.Q, f + r0 * d.Q, T->f_lo + r0 * d.Q, T->Qp, T->S_hi,
+                                       T->S_lo, T->Qp, T->tab + r0 * T->Bp, T->Bp, p->err_flag + 1, p->num_sms, s,
+                                       kband_of(p, 0)));
+            }
+            CAXSI_LAUNCH_CHECK(p);
+        }
+    } else if (p->gemm_engine == 0 && path == CAXSI_PATH_TABLE_FP32) {
         // Wtab[r][t] = sum_l f[r][l] S~[t][l] by the tcgen05 GEMM, 3xTF32.  With
         // unpadded aligned rows f itself is the high part (the tensor core reads
         // FP32 as TF32 by dropping the low 13 mantissa bits) and only the
         // remainder is written; otherwise both parts go to padded copies.
-        const bool raw_hi = d.Q == T->Qp && (reinterpret_cast<uintptr_t>(f) & 15) == 0;
         {
             CAXSI_PROF(p, "split_tf32", s);
             if (raw_hi) CAXSI_CUDA_TRY(trunc_remainder(f, (int64_t)d.R * d.Q, T->f_lo, s));
@@ -1051,6 +1076,30 @@ caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path
     }
     CAXSI_LAUNCH_CHECK(p);
     const float one = 1.f, zero = 0.f;
+    HostPipe *pipe = p->pipe;
+    if (tc && out_kind == 0 && subset < 0 && pipe && pipe->rows > 0 && pipe->rows < d.R) {
+        // a host-buffer call: the rows of each half in their own launch, the first
+        // half copied to the host while the second is contracted
+        const int64_t r1 = pipe->rows;
+        for (int h = 0; h < 2; ++h) {
+            const int64_t r0 = h ? r1 : 0, nr = h ? d.R - r1 : r1;
+            {
+                CAXSI_PROF(p, "tc_gemm_adj_3xtf32", s);
+                CAXSI_CUDA_TRY(tc_gemm(3, 128, (int)nr, d.Q, T->B, T->tab + r0 * T->Bp, nullptr, T->Bp, T->St_hi,
+                                       T->St_lo, T->Bp, f_out + r0 * d.Q, d.Q, p->err_flag + 1, p->num_sms, s,
+                                       nullptr, nband_of(p, 0)));
+            }
+            CAXSI_LAUNCH_CHECK(p);
+            if (h == 0) {
+                CAXSI_CUDA_TRY(cudaEventRecord(pipe->out_half, s));
+                CAXSI_CUDA_TRY(cudaStreamWaitEvent(pipe->cs, pipe->out_half, 0));
+                CAXSI_CUDA_TRY(cudaMemcpyAsync(pipe->out_host, f_out, r1 * d.Q * sizeof(float),
+                                               cudaMemcpyDeviceToHost, pipe->cs));
+                pipe->out_from = r1;
+            }
+        }
+        return CAXSI_OK;
+    }
     if (tc) {
         // f[r][l] = sum_t V[r][t] S~^T[l][t] by the tcgen05 GEMM
         const int k = out_kind;

@@ -263,6 +263,12 @@ def test_paper_scale_sampled(cx, path):
     vox = np.concatenate([rng.choice(g.X * g.J, 24, replace=False), [0, g.X * g.J - 1]])
     refv = oracle.adjoint_voxels(g, phi, mask, _f32(w), vox)
     assert rel_l2(fa[vox], refv) <= REL_L2_TOL
+    # the host-buffer forms (on the FP32 table path: each contraction in two row
+    # halves, one half's copy overlapping the other half's contraction) give the
+    # device forms' results bit for bit
+    f32, w32 = np.asarray(f, np.float32), np.asarray(w, np.float32)
+    np.testing.assert_array_equal(plan.forward_host(f32, path=p).ravel(), gg)
+    np.testing.assert_array_equal(plan.adjoint_host(w32, path=p).reshape(g.X * g.J, g.Q), fa)
     plan.close()
 
 
