@@ -27,6 +27,16 @@ struct Tables {
 // One block's work of the forward: detector tile bx (or listed pixels bx * 256 ..)
 // and voxel chunk by, written to partial image by.  Shared by the single-plan
 // kernel (bx, by = the block index) and the persistent multi-object kernel.
+//
+// Lane l of a warp owns one pixel; the block stages FWD_VS voxels (their q rows
+// and positions) at a time.  A warp queues the open pairs of its 32 pixels with
+// the staged voxels, voxel by voxel, in a ring of 64 slots and takes them 32 at a
+// time, one per lane, so that no lane idles on a closed pair (about half are
+// closed by the mask).  A pair's contribution goes to its pixel's accumulator in
+// shared memory; the pairs of one pixel within a batch are applied in rounds by
+// their rank in the queue, so that every pixel adds its open voxels' terms in
+// ascending voxel order, one fma each: the result is that of a plain loop over
+// the voxels.
 template <bool LIST>
 __device__ __forceinline__ void fwd_direct_body(const Tables &T, const float *__restrict__ f,
                                                 float *__restrict__ part, int vc, int tiles_n,
@@ -37,6 +47,8 @@ __device__ __forceinline__ void fwd_direct_body(const Tables &T, const float *__
     float2 *s_en = reinterpret_cast<float2 *>(smem_raw);
     float4 *s_vox = reinterpret_cast<float4 *>(s_en + ((g.K + 1) & ~1));
     float2 *s_f = reinterpret_cast<float2 *>(s_vox + FWD_VS);
+    float *s_acc = reinterpret_cast<float *>(s_f + (size_t)FWD_VS * QP);   // [FWD_WARPS][32] per pixel
+    int *s_q = reinterpret_cast<int *>(s_acc + FWD_THREADS);              // [FWD_WARPS][64] ring
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int m, n, e = 0;
@@ -60,7 +72,10 @@ __device__ __forceinline__ void fwd_direct_body(const Tables &T, const float *__
     const float Npix = (float)n - g.cN;
     const float sz = valid ? T.zrow[m] : 0.f;
     const int wsel = n >> 5, bsel = n & 31;
-    float acc = 0.f;
+    float *acc = s_acc + warp * 32;
+    int *q = s_q + warp * 64;
+    acc[lane] = 0.f;
+    const unsigned lt = (1u << lane) - 1u;
 
     for (int vb = v0; vb < v1; vb += FWD_VS) {
         const int nv = min(FWD_VS, v1 - vb);
@@ -74,42 +89,73 @@ __device__ __forceinline__ void fwd_direct_body(const Tables &T, const float *__
         }
         if (tid < nv) s_vox[tid] = T.vox[vb + tid];
         __syncthreads();
-        if (!valid) continue;
-        // the staged voxels this pixel's pairs are open for, taken in ascending order:
-        // a lane's loop runs over its own open pairs only (a warp over the largest
-        // count among its lanes, not over every staged voxel)
-        uint32_t open = 0u;
-        for (int vv = 0; vv < nv; ++vv) {
-            const uint32_t word = T.tbits[((int64_t)(vb + vv) * g.M + m) * g.Nw + wsel];
-            open |= ((word >> bsel) & 1u) << vv;
-        }
-        while (open) {
-            const int vv = __ffs(open) - 1;
-            open &= open - 1u;
-            const int v = vb + vv;
-            const int i = v / g.J, j = v - i * g.J;
-            const float4 vx = s_vox[vv];
-            float u, ang;
-            pair_u_angular(vx.x, vx.y, vx.w, Npix, sz, g.p_y, g.Xd, u, ang);
-            const float gd = T.god[((int64_t)i * g.M + m) * g.ND + (n - g.rho_y * j - g.d_min)];
-            const float2 *fr = s_f + vv * QP;
-            float e_acc = 0.f;
+        // pair (staged voxel vv, pixel of lane pl), or none (entry < 0): its term,
+        // added to the pixel's accumulator; a pixel's pairs in one batch are applied
+        // in rounds by their order in the queue (ascending voxel)
+        auto take = [&](int entry) {
+            const int pl = entry >= 0 ? (entry & 31) : lane;
+            const int pm = __shfl_sync(0xffffffffu, m, pl), pn = __shfl_sync(0xffffffffu, n, pl);
+            const float pN = __shfl_sync(0xffffffffu, Npix, pl), pz = __shfl_sync(0xffffffffu, sz, pl);
+            float c = 0.f, e_acc = 0.f;
+            if (entry >= 0) {
+                const int vv = entry >> 5, v = vb + vv;
+                const int i = v / g.J, j = v - i * g.J;
+                const float4 vx = s_vox[vv];
+                float u, ang;
+                pair_u_angular(vx.x, vx.y, vx.w, pN, pz, g.p_y, g.Xd, u, ang);
+                const float gd = T.god[((int64_t)i * g.M + pm) * g.ND + (pn - g.rho_y * j - g.d_min)];
+                const float2 *fr = s_f + vv * QP;
 #pragma unroll 8
-            for (int k = 0; k < g.K; ++k) {
-                const float2 ak = s_en[k];
-                float tau = fmaf(ak.x, u, -g.b);
-                tau = fminf(fmaxf(tau, -1.f), g.Qf);
-                const float fl = floorf(tau);
-                const float al = tau - fl;
-                const float2 F = fr[(int)fl + 1];
-                e_acc = fmaf(ak.y, fmaf(al, F.y, F.x), e_acc);
+                for (int k = 0; k < g.K; ++k) {
+                    const float2 ak = s_en[k];
+                    float tau = fmaf(ak.x, u, -g.b);
+                    tau = fminf(fmaxf(tau, -1.f), g.Qf);
+                    const float fl = floorf(tau);
+                    const float al = tau - fl;
+                    const float2 F = fr[(int)fl + 1];
+                    e_acc = fmaf(ak.y, fmaf(al, F.y, F.x), e_acc);
+                }
+                c = vx.z * gd * ang;
             }
-            acc = fmaf(vx.z * gd * ang, e_acc, acc);
+            const unsigned same = __match_any_sync(0xffffffffu, entry >= 0 ? pl : 32 + lane);
+            const int rank = __popc(same & lt);
+            const int rounds = (int)__reduce_max_sync(0xffffffffu, entry >= 0 ? (unsigned)rank + 1u : 0u);
+            for (int r = 0; r < rounds; ++r) {   // warp-uniform
+                if (entry >= 0 && rank == r) acc[pl] = fmaf(c, e_acc, acc[pl]);
+                __syncwarp();
+            }
+        };
+        // the open pairs of the warp's pixels, voxel by voxel (lanes in pixel order)
+        int head = 0, cnt = 0;
+        for (int vv = 0; vv < nv; ++vv) {
+            bool ok = false;
+            if (valid) {
+                const uint32_t word = T.tbits[((int64_t)(vb + vv) * g.M + m) * g.Nw + wsel];
+                ok = ((word >> bsel) & 1u) != 0u;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            if (ok) q[(head + cnt + __popc(bal & lt)) & 63] = (vv << 5) | lane;
+            cnt += __popc(bal);
+            __syncwarp();
+            if (cnt >= 32) {   // warp-uniform
+                const int entry = q[(head + lane) & 63];
+                head = (head + 32) & 63;
+                cnt -= 32;
+                __syncwarp();   // the batch is read before later voxels refill its slots
+                take(entry);
+            }
+        }
+        if (cnt > 0) {   // the rest, before the next stage replaces the staged voxels
+            const int entry = lane < cnt ? q[(head + lane) & 63] : -1;
+            __syncwarp();
+            take(entry);
         }
     }
+    __syncwarp();
     if (valid) {
-        if (LIST) part[(int64_t)by * np + e] = acc;
-        else part[(int64_t)by * g.M * g.N + (int64_t)m * g.N + n] = acc;
+        const float total = acc[lane];
+        if (LIST) part[(int64_t)by * np + e] = total;
+        else part[(int64_t)by * g.M * g.N + (int64_t)m * g.N + n] = total;
     }
 }
 
@@ -212,9 +258,10 @@ inline Tables tables_of(const caxsi_plan *p) {
     return T;
 }
 
+// energies, staged voxels and q rows, per-pixel accumulators, per-warp rings of 64 pairs
 inline size_t fwd_smem(const DevGeo &g) {
     return ((g.K + 1) & ~1) * sizeof(float2) + FWD_VS * sizeof(float4) +
-           (size_t)FWD_VS * (g.Q + 2) * sizeof(float2);
+           (size_t)FWD_VS * (g.Q + 2) * sizeof(float2) + FWD_THREADS * sizeof(float) + FWD_WARPS * 64 * sizeof(int);
 }
 // per warp: q rows [(Q + 3) x 32] floats and a ring of 64 queued pixels
 __host__ __device__ inline size_t adj_warp_floats(int Q) { return (size_t)(Q + 3) * 32 + 64; }
