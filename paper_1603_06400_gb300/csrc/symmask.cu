@@ -56,6 +56,8 @@ k_fwd_direct_symmask(SymTables S, const float *__restrict__ f, float *__restrict
     float2 *s_f = reinterpret_cast<float2 *>(s_vox + SVS);            // [2 SVS][QP]
     int *s_row = reinterpret_cast<int *>(s_f + 2 * SVS * QP);         // [SVS][FWD_WARPS]
     int *s_col = s_row + SVS * FWD_WARPS;                             // [SVS][32]
+    float *s_acc = reinterpret_cast<float *>(s_col + SVS * 32);       // [FWD_WARPS][2][32]
+    int *s_q = reinterpret_cast<int *>(s_acc + FWD_WARPS * 64);       // [FWD_WARPS][64] ring
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
@@ -68,7 +70,12 @@ k_fwd_direct_symmask(SymTables S, const float *__restrict__ f, float *__restrict
     for (int k = tid; k < g.K; k += FWD_THREADS) s_en[k] = T.energy[k];
     const float Npix = (float)n - g.cN;
     const float sz = valid ? T.zrow[m] : 0.f;
-    float accL = 0.f, accR = 0.f;
+    // per lane: the sums for its own column (from v) and for its mirror column (from v')
+    float *accL = s_acc + warp * 64, *accR = accL + 32;
+    int *q = s_q + warp * 64;
+    accL[lane] = 0.f;
+    accR[lane] = 0.f;
+    const unsigned lt = (1u << lane) - 1u;
 
     for (int pb = p0; pb < p1; pb += SVS) {
         const int nv = min(SVS, p1 - pb);
@@ -98,36 +105,78 @@ k_fwd_direct_symmask(SymTables S, const float *__restrict__ f, float *__restrict
             s_vox[tid] = T.vox[i * g.J + j];
         }
         __syncthreads();
-        if (!valid) continue;
-        for (int vv = 0; vv < nv; ++vv) {
-            const int row = s_row[vv * FWD_WARPS + warp], col = s_col[vv * 32 + lane];
-            if (row < 0 || col < 0 || !S.mask[row * S.g64.cols + col]) continue;
-            const int pp = pb + vv, i = pp / Jh, j = pp - i * Jh;
-            const float4 vx = s_vox[vv];
-            float u, ang;
-            pair_u_angular(vx.x, vx.y, vx.w, Npix, sz, g.p_y, g.Xd, u, ang);
-            const float gd = T.god[((int64_t)i * g.M + m) * g.ND + (n - g.rho_y * j - g.d_min)];
-            const float2 *fl = s_f + (2 * vv) * QP, *fr = fl + QP;
-            float wl = 0.f, wr = 0.f;
+        // pair (staged voxel pair vv, pixel of lane pl), or none (entry < 0): the two
+        // energy sums, added to lane pl's accumulators; a lane's pairs within one
+        // batch are applied in rounds by their order in the queue (ascending vv)
+        auto take = [&](int entry) {
+            const int pl = entry >= 0 ? (entry & 31) : lane;
+            const int pn = __shfl_sync(0xffffffffu, n, pl);
+            const float pN = __shfl_sync(0xffffffffu, Npix, pl), pz = __shfl_sync(0xffffffffu, sz, pl);
+            float c = 0.f, wl = 0.f, wr = 0.f;
+            if (entry >= 0) {
+                const int vv = entry >> 5;
+                const int pp = pb + vv, i = pp / Jh, j = pp - i * Jh;
+                const float4 vx = s_vox[vv];
+                float u, ang;
+                pair_u_angular(vx.x, vx.y, vx.w, pN, pz, g.p_y, g.Xd, u, ang);
+                const float gd = T.god[((int64_t)i * g.M + m) * g.ND + (pn - g.rho_y * j - g.d_min)];
+                const float2 *fl = s_f + (2 * vv) * QP, *fr = fl + QP;
 #pragma unroll 4
-            for (int k = 0; k < g.K; ++k) {
-                const float2 ak = s_en[k];
-                float tau = fmaf(ak.x, u, -g.b);
-                tau = fminf(fmaxf(tau, -1.f), g.Qf);
-                const float flo = floorf(tau);
-                const float al = tau - flo;
-                const int b = (int)flo + 1;
-                const float2 A = fl[b], B = fr[b];
-                wl = fmaf(ak.y, fmaf(al, A.y, A.x), wl);
-                wr = fmaf(ak.y, fmaf(al, B.y, B.x), wr);
+                for (int k = 0; k < g.K; ++k) {
+                    const float2 ak = s_en[k];
+                    float tau = fmaf(ak.x, u, -g.b);
+                    tau = fminf(fmaxf(tau, -1.f), g.Qf);
+                    const float flo = floorf(tau);
+                    const float al = tau - flo;
+                    const int b = (int)flo + 1;
+                    const float2 A = fl[b], B = fr[b];
+                    wl = fmaf(ak.y, fmaf(al, A.y, A.x), wl);
+                    wr = fmaf(ak.y, fmaf(al, B.y, B.x), wr);
+                }
+                c = vx.z * gd * ang;
             }
-            const float c = vx.z * gd * ang;
-            accL = fmaf(c, wl, accL);
-            accR = fmaf(c, wr, accR);
+            const unsigned same = __match_any_sync(0xffffffffu, entry >= 0 ? pl : 32 + lane);
+            const int rank = __popc(same & lt);
+            const int rounds = (int)__reduce_max_sync(0xffffffffu, entry >= 0 ? (unsigned)rank + 1u : 0u);
+            for (int r = 0; r < rounds; ++r) {   // warp-uniform
+                if (entry >= 0 && rank == r) {
+                    accL[pl] = fmaf(c, wl, accL[pl]);
+                    accR[pl] = fmaf(c, wr, accR[pl]);
+                }
+                __syncwarp();
+            }
+        };
+        // the open pairs of the warp's lanes, voxel pair by voxel pair (the mask cell
+        // of each from the staged rows and columns)
+        int head = 0, cnt = 0;
+        for (int vv = 0; vv < nv; ++vv) {
+            bool ok = false;
+            if (valid) {
+                const int row = s_row[vv * FWD_WARPS + warp], col = s_col[vv * 32 + lane];
+                ok = row >= 0 && col >= 0 && S.mask[row * S.g64.cols + col];
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            if (ok) q[(head + cnt + __popc(bal & lt)) & 63] = (vv << 5) | lane;
+            cnt += __popc(bal);
+            __syncwarp();
+            if (cnt >= 32) {   // warp-uniform
+                const int entry = q[(head + lane) & 63];
+                head = (head + 32) & 63;
+                cnt -= 32;
+                __syncwarp();   // the batch is read before later pairs refill its slots
+                take(entry);
+            }
+        }
+        if (cnt > 0) {   // the rest, before the next stage replaces the staged pairs
+            const int entry = lane < cnt ? q[(head + lane) & 63] : -1;
+            __syncwarp();
+            take(entry);
         }
     }
+    __syncwarp();
+    const float myL = accL[lane], myR = accR[lane];
     // the mirror column's contributions from the right-half voxels are the mirror lane's
-    const float sum = accL + __shfl_xor_sync(0xffffffffu, accR, 16);
+    const float sum = myL + __shfl_xor_sync(0xffffffffu, myR, 16);
     if (valid) {
         float *dst = part + (int64_t)blockIdx.y * g.M * g.N;
         dst[(int64_t)m * g.N + n] = sum;
@@ -245,7 +294,8 @@ cudaError_t launch_sum_parts(const float *part, int nparts, int64_t stride, floa
 
 size_t symmask_fwd_smem(const DevGeo &g) {
     return ((g.K + 1) & ~1) * sizeof(float2) + SVS * sizeof(float4) + (size_t)2 * SVS * (g.Q + 2) * sizeof(float2) +
-           (size_t)SVS * (FWD_WARPS + 32) * sizeof(int);
+           (size_t)SVS * (FWD_WARPS + 32) * sizeof(int) + (size_t)FWD_WARPS * 64 * sizeof(float) +
+           (size_t)FWD_WARPS * 64 * sizeof(int);
 }
 size_t symmask_adj_smem(const DevGeo &g) {
     return ((g.K + 1) & ~1) * sizeof(float2) + (size_t)ADJ_WARPS * ((g.Q + 3) * 32 + g.N + 64) * sizeof(float);
