@@ -346,12 +346,12 @@ caxsi_status caxsi_ratio_vjp(caxsi_plan *plan, const float *g_dev, const float *
  * staging buffers, evaluate, copy the result back to host memory, and
  * synchronise before returning.  Pinned host memory gives the fastest copies.
  * Same lengths and layouts as the device forms, and the same results bit for
- * bit.  On TABLE_FP32 the contraction over q runs in two launches over the two
- * halves of the voxel rows, so that the copy of one half of f overlaps the
- * other half's contraction (forward: the second half of f is copied in while
- * the first half is contracted; adjoint: the first half of f is copied out while
- * the second half is contracted), on a second stream that the plan creates at
- * the first such call. */
+ * bit.  On TABLE_FP32 the contraction over q runs in two launches over two parts
+ * of the voxel rows, so that the copy of one part of f overlaps the other part's
+ * contraction (forward: the second half of f is copied in while the first half
+ * is contracted; adjoint: the rows of the first wave of output tiles are copied
+ * out while the rest are contracted), on a second stream that the plan creates
+ * at the first such call. */
 caxsi_status caxsi_forward_host(caxsi_plan *plan, const float *f_host, int64_t f_len,
                                 float *g_host, int64_t g_len, int path);
 caxsi_status caxsi_adjoint_host(caxsi_plan *plan, const float *w_host, int64_t w_len,

@@ -182,6 +182,11 @@ caxsi_status caxsi_plan_create(const caxsi_geometry *geom, const double *phi_hos
     const double dq = (geom->q_max - geom->q_min) / (geom->Q - 1);
     d.b = (float)(geom->q_min / dq);
     d.Qf = (float)geom->Q;
+    {
+        const double dE = (geom->E_max - geom->E_min) / geom->K;
+        d.a0 = (float)((geom->E_min + 0.5 * dE) / (geom->hc * dq));
+        d.da = (float)(dE / (geom->hc * dq));
+    }
 
     direct_configure(p);
     int smem_max = 0;

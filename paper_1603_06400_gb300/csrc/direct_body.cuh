@@ -14,6 +14,18 @@ constexpr int FWD_THREADS = FWD_WARPS * 32;
 constexpr int FWD_VS = 32;  // voxels staged per shared-memory round
 constexpr int ADJ_WARPS = 4;
 
+// The energies whose term can be nonzero for a pair with u = sin(theta/2):
+// tau_k = a_k u - b rises with k (a_k = a0 + k da), and a term is an exact zero
+// unless -1 < tau_k < Q (outside, the interpolation reads the zero padding of the
+// staged q row, or the adjoint scatters into its discarded padding rows).  The
+// range [k0, k1) is widened by two energies at each end against rounding; a
+// u of 0 or a non-finite bound gives the whole range or none, as the terms do.
+__device__ __forceinline__ void energy_range(const DevGeo &g, float u, int &k0, int &k1) {
+    const float lo = ((g.b - 1.f) / u - g.a0) / g.da, hi = ((g.Qf + g.b) / u - g.a0) / g.da;
+    k0 = lo > 2.f ? (lo < (float)g.K ? (int)lo - 2 : g.K) : 0;
+    k1 = hi < (float)g.K - 3.f ? max(0, (int)fmaxf(hi, -8.f) + 3) : g.K;
+}
+
 struct Tables {
     DevGeo g;
     const float4 *vox;
@@ -105,8 +117,10 @@ __device__ __forceinline__ void fwd_direct_body(const Tables &T, const float *__
                 pair_u_angular(vx.x, vx.y, vx.w, pN, pz, g.p_y, g.Xd, u, ang);
                 const float gd = T.god[((int64_t)i * g.M + pm) * g.ND + (pn - g.rho_y * j - g.d_min)];
                 const float2 *fr = s_f + vv * QP;
+                int k0, k1;
+                energy_range(g, u, k0, k1);
 #pragma unroll 8
-                for (int k = 0; k < g.K; ++k) {
+                for (int k = k0; k < k1; ++k) {
                     const float2 ak = s_en[k];
                     float tau = fmaf(ak.x, u, -g.b);
                     tau = fminf(fmaxf(tau, -1.f), g.Qf);
@@ -177,8 +191,10 @@ __device__ __forceinline__ void adj_direct_body(const Tables &T, const float *__
         float u, ang;
         pair_u_angular(vx.x, vx.y, vx.w, (float)n - g.cN, T.zrow[m], g.p_y, g.Xd, u, ang);
         const float base = vx.z * T.god[((int64_t)i * g.M + m) * g.ND + (n - g.rho_y * j - g.d_min)] * ang * wv;
+        int k0, k1;
+        energy_range(g, u, k0, k1);
 #pragma unroll 4
-        for (int k = 0; k < g.K; ++k) {
+        for (int k = k0; k < k1; ++k) {
             const float2 ak = s_en[k];
             float tau = fmaf(ak.x, u, -g.b);
             tau = fminf(fmaxf(tau, -1.f), g.Qf);

@@ -23,6 +23,7 @@ struct DevGeo {
     float cN;     // (N - 1) / 2
     float b;      // q_min / dq
     float Qf;     // (float)Q
+    float a0, da; // a_k = E_k / (hc dq) = a0 + k da (uniform energy bins)
 };
 
 // Optional per-kernel timing with CUDA events recorded on the launch stream
@@ -47,14 +48,15 @@ constexpr int NLL_THREADS = 64;
 // Table-path data (piecewise-linear structure of W in u); built on first use.
 struct TablePath;
 
-// A host-buffer call on the FP32 table path splits the voxel rows at `rows`
-// (a whole number of 128-row tiles) and runs the contraction of each half as its
-// own launch, so that one half's copy overlaps the other half's contraction:
-// forward -- the second half of f arrives on copy_stream and `in_ready` records
-// its end (the forward waits for it before the second half, or before anything
-// when it does not split); adjoint -- after the first half's contraction the
-// adjoint records `out_half`, copies that half of f to out_host on copy_stream
-// and sets `out_from` = rows, so that the caller copies only the rest.  Each
+// A host-buffer call on the FP32 table path runs the contraction over q in two
+// launches over two parts of the voxel rows, so that one part's copy overlaps the
+// other part's contraction: forward -- the rows split at `rows` (half of them, a
+// whole number of 128-row tiles); the second part of f arrives on copy_stream and
+// `in_ready` records its end (the forward waits for it before the second part, or
+// before anything when it does not split); adjoint -- the first part is one wave
+// of 128-row tiles (one per SM) when there are more; after its contraction the
+// adjoint records `out_half`, copies that part of f to out_host on copy_stream
+// and sets `out_from` to its rows, so that the caller copies only the rest.  Each
 // output row is computed exactly as without the split.
 struct HostPipe {
     int64_t rows;

@@ -121,8 +121,10 @@ k_fwd_direct_symmask(SymTables S, const float *__restrict__ f, float *__restrict
                 pair_u_angular(vx.x, vx.y, vx.w, pN, pz, g.p_y, g.Xd, u, ang);
                 const float gd = T.god[((int64_t)i * g.M + m) * g.ND + (pn - g.rho_y * j - g.d_min)];
                 const float2 *fl = s_f + (2 * vv) * QP, *fr = fl + QP;
+                int k0, k1;
+                energy_range(g, u, k0, k1);
 #pragma unroll 4
-                for (int k = 0; k < g.K; ++k) {
+                for (int k = k0; k < k1; ++k) {
                     const float2 ak = s_en[k];
                     float tau = fmaf(ak.x, u, -g.b);
                     tau = fminf(fmaxf(tau, -1.f), g.Qf);
@@ -222,8 +224,10 @@ k_adj_direct_symmask(SymTables S, const float *__restrict__ w, float *__restrict
         float u, ang;
         pair_u_angular(vx.x, vx.y, vx.w, (float)n - g.cN, T.zrow[m], g.p_y, g.Xd, u, ang);
         const float base = vx.z * T.god[((int64_t)i * g.M + m) * g.ND + (n - g.rho_y * j - g.d_min)] * ang * wv;
+        int k0, k1;
+        energy_range(g, u, k0, k1);
 #pragma unroll 4
-        for (int k = 0; k < g.K; ++k) {
+        for (int k = k0; k < k1; ++k) {
             const float2 ak = s_en[k];
             float tau = fmaf(ak.x, u, -g.b);
             tau = fminf(fmaxf(tau, -1.f), g.Qf);

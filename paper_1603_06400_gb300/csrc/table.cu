@@ -1077,10 +1077,10 @@ caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path
     CAXSI_LAUNCH_CHECK(p);
     const float one = 1.f, zero = 0.f;
     HostPipe *pipe = p->pipe;
-    if (tc && out_kind == 0 && subset < 0 && pipe && pipe->rows > 0 && pipe->rows < d.R) {
-        // a host-buffer call: the rows of each half in their own launch, the first
-        // half copied to the host while the second is contracted
-        const int64_t r1 = pipe->rows;
+    // a host-buffer call with more than one wave of 128-row tiles: the first wave's
+    // rows in their own launch, copied to the host while the rest are contracted
+    const int64_t r1 = (int64_t)p->num_sms * 128;
+    if (tc && out_kind == 0 && subset < 0 && pipe && r1 < d.R) {
         for (int h = 0; h < 2; ++h) {
             const int64_t r0 = h ? r1 : 0, nr = h ? d.R - r1 : r1;
             {
