@@ -348,8 +348,8 @@ caxsi_status caxsi_ratio_vjp(caxsi_plan *plan, const float *g_dev, const float *
  * Same lengths and layouts as the device forms, and the same results bit for
  * bit.  On TABLE_FP32 the contraction over q runs in two launches over two parts
  * of the voxel rows, so that the copy of one part of f overlaps the other part's
- * contraction (forward: the second half of f is copied in while the first half
- * is contracted; adjoint: the rows of the first wave of output tiles are copied
+ * contraction (forward: the last three quarters of f are copied in while the
+ * first quarter is contracted; adjoint: the rows of the first wave of output tiles are copied
  * out while the rest are contracted), on a second stream that the plan creates
  * at the first such call. */
 caxsi_status caxsi_forward_host(caxsi_plan *plan, const float *f_host, int64_t f_len,

@@ -483,9 +483,10 @@ static caxsi_status host_call(caxsi_plan *p, const float *in_host, int64_t in_le
     }
     p->launches = 0;
     cudaStream_t s = 0;
-    // the FP32 table path overlaps the copy of f with half of the contraction
-    const int64_t half = (p->dg.R / 2) & ~int64_t(127);
-    const bool piped = path == CAXSI_PATH_TABLE_FP32 && half > 0;
+    // the FP32 table path overlaps the copy of f with part of the contraction: the
+    // forward contracts the first quarter of the rows while the rest of f arrives
+    const int64_t part = (p->dg.R / 4) & ~int64_t(127);
+    const bool piped = path == CAXSI_PATH_TABLE_FP32 && part > 0;
     if (piped && !p->copy_stream) {
         CAXSI_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
         if (cudaEventCreateWithFlags(&p->pipe_ev[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -495,11 +496,11 @@ static caxsi_status host_call(caxsi_plan *p, const float *in_host, int64_t in_le
             return CAXSI_ERR_CUDA;
         }
     }
-    HostPipe pipe{half, p->copy_stream, p->pipe_ev[0], p->pipe_ev[1], out_host, 0};
+    HostPipe pipe{part, p->copy_stream, p->pipe_ev[0], p->pipe_ev[1], out_host, 0};
     if (piped && fwd) {
-        // the first half of f, then the second on the copy stream (one after the other:
-        // they share the link) while the first half's contraction runs
-        const int64_t n1 = half * p->dg.Q;
+        // the first part of f, then the rest on the copy stream (one after the other:
+        // they share the link) while the first part's contraction runs
+        const int64_t n1 = part * p->dg.Q;
         CAXSI_CUDA_TRY(cudaMemcpyAsync(p->stage_in, in_host, n1 * sizeof(float), cudaMemcpyHostToDevice, s));
         CAXSI_CUDA_TRY(cudaEventRecord(pipe.out_half, s));
         CAXSI_CUDA_TRY(cudaStreamWaitEvent(pipe.cs, pipe.out_half, 0));

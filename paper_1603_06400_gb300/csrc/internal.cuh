@@ -50,8 +50,8 @@ struct TablePath;
 
 // A host-buffer call on the FP32 table path runs the contraction over q in two
 // launches over two parts of the voxel rows, so that one part's copy overlaps the
-// other part's contraction: forward -- the rows split at `rows` (half of them, a
-// whole number of 128-row tiles); the second part of f arrives on copy_stream and
+// other part's contraction: forward -- the rows split at `rows` (a quarter of them,
+// a whole number of 128-row tiles); the second part of f arrives on copy_stream and
 // `in_ready` records its end (the forward waits for it before the second part, or
 // before anything when it does not split); adjoint -- the first part is one wave
 // of 128-row tiles (one per SM) when there are more; after its contraction the

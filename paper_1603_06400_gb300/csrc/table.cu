@@ -944,14 +944,14 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
     const bool sym_fwd = T->use_records && subset < 0 && T->sym.ok && !p->no_symmetry;
     if (cublasSetStream(T->blas, s) != CUBLAS_STATUS_SUCCESS) return CAXSI_ERR_CUDA;
     const bool raw_hi = d.Q == T->Qp && (reinterpret_cast<uintptr_t>(f) & 15) == 0;
-    // a host-buffer call: the second half of f may still be on its way
+    // a host-buffer call: the rest of f may still be on its way
     HostPipe *pipe = p->pipe;
     const bool split = pipe && p->gemm_engine == 0 && path == CAXSI_PATH_TABLE_FP32 && raw_hi && subset < 0 &&
                        pipe->rows > 0 && pipe->rows < d.R;
     if (pipe && !split) CAXSI_CUDA_TRY(cudaStreamWaitEvent(s, pipe->in_ready, 0));
     if (split) {
-        // Wtab = f S~^T as below, the rows of each half in their own launch: the
-        // second after the second half of f has arrived
+        // Wtab = f S~^T as below, the rows of each part in their own launch: the
+        // second after the rest of f has arrived
         const int64_t r1 = pipe->rows;
         for (int h = 0; h < 2; ++h) {
             const int64_t r0 = h ? r1 : 0, nr = h ? d.R - r1 : r1;
