@@ -183,7 +183,13 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
     constexpr uint32_t B_BYTES = BN * 128;
     constexpr uint32_t STAGE = X3 ? 2 * (A_BYTES + B_BYTES) : (A_BYTES + B_BYTES);
     constexpr int KE = X3 ? 32 : 64;  // K elements per 128-byte row slice
-    constexpr uint32_t TMEM_COLS = 2 * BN;
+    // kind 3 keeps B_hi and B_lo side by side in a stage, so that one N = 2 BN
+    // instruction forms A_hi [B_hi | B_lo]: its accumulator is 2 BN columns wide
+    constexpr bool CAT = SPLIT_A;
+    constexpr uint32_t ACC_COLS = CAT ? 2 * BN : BN;
+    constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
+    constexpr uint32_t B2_OFF = CAT ? A_BYTES + B_BYTES : 2 * A_BYTES + B_BYTES;   // B_lo in a stage
+    constexpr uint32_t A2_OFF = CAT ? A_BYTES + 2 * B_BYTES : A_BYTES + B_BYTES;   // A_lo in a stage
     // idesc: D = F32, A/B = TF32 (2) or BF16 (1) or F16 (0), both K-major, N >> 3, M >> 4
     constexpr uint32_t AB = X3 ? 2u : (KIND == 1 ? 1u : 0u);
     constexpr uint32_t IDESC0 = (1u << 4) | (AB << 7) | (AB << 10) | ((uint32_t)(128 >> 4) << 24);
@@ -252,8 +258,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                     tma_load_2d(st, &tA, x, m0, &full[s]);
                     tma_load_2d(st + A_BYTES, &tB, x, n0, &full[s]);
                     if (X3) {
-                        if (!SPLIT_A) tma_load_2d(st + A_BYTES + B_BYTES, &tA2, x, m0, &full[s]);
-                        tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tB2, x, n0, &full[s]);
+                        if (!SPLIT_A) tma_load_2d(st + A2_OFF, &tA2, x, m0, &full[s]);
+                        tma_load_2d(st + B2_OFF, &tB2, x, n0, &full[s]);
                     }
                 }
             }
@@ -270,9 +276,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                     if (!mb_wait(&acce[b], aph ^ 1u, abort)) { *abort = 1; ok = false; break; }
                     fence_after();
                     // the chunk's column quarters [qr.x, qr.y]: N and the TMEM / B offsets
-                    const int2 qr = a.nband ? a.nband[c] : make_int2(0, NQ - 1);
+                    // (kind 3: always all of them, the two halves in one instruction)
+                    const int2 qr = a.nband && !CAT ? a.nband[c] : make_int2(0, NQ - 1);
                     const uint32_t idesc = IDESC0 | ((uint32_t)(((qr.y - qr.x + 1) * 32) >> 3) << 17);
-                    const uint32_t d = tmem + b * BN + (uint32_t)(qr.x * 32);
+                    const uint32_t idesc_cat = IDESC0 | ((uint32_t)((2 * BN) >> 3) << 17);
+                    const uint32_t d = tmem + b * ACC_COLS + (uint32_t)(qr.x * 32);
                     const uint64_t boff = (uint64_t)(qr.x * 32 * 128 / 16);   // 32 rows of 128 bytes, 16-byte units
                     const int k0 = kr.x + c * KCHUNK, k1 = min(kr.y + 1, k0 + KCHUNK);
                     for (int kt = k0; kt < k1; ++kt, ++it) {
@@ -281,9 +289,17 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                         fence_after();
                         unsigned char *st = base + s * STAGE;
                         const uint64_t da = sw128_desc(st), db = sw128_desc(st + A_BYTES) + boff;
-                        const uint64_t dal = sw128_desc(st + A_BYTES + B_BYTES);
-                        const uint64_t dbl = sw128_desc(st + 2 * A_BYTES + B_BYTES) + boff;
-                        if (qr.x <= qr.y) {
+                        const uint64_t dal = sw128_desc(st + A2_OFF);
+                        const uint64_t dbl = sw128_desc(st + B2_OFF) + boff;
+                        if (CAT) {
+                            // A_hi x [B_hi | B_lo]: columns [0, BN) get A_hi B_hi, [BN, 2 BN) A_hi B_lo
+#pragma unroll
+                            for (int ks = 0; ks < 4; ++ks) {
+                                const uint64_t adv = (uint64_t)(ks * 2);  // 32 bytes per instruction, 16-byte units
+                                const uint32_t acc = (kt > k0 || ks > 0) ? 1u : 0u;
+                                mma<KIND>(d, da + adv, db + adv, idesc_cat, acc);
+                            }
+                        } else if (qr.x <= qr.y) {
 #pragma unroll
                             for (int ks = 0; ks < 4; ++ks) {
                                 const uint64_t adv = (uint64_t)(ks * 2);  // 32 bytes per instruction, 16-byte units
@@ -330,7 +346,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                 if (!mb_wait(&full[s], ph, abort)) { *abort = 1; ok = false; break; }
                 unsigned char *st = base + s * STAGE;
                 const float4 *hi = reinterpret_cast<const float4 *>(st);
-                float4 *lo = reinterpret_cast<float4 *>(st + A_BYTES + B_BYTES);
+                float4 *lo = reinterpret_cast<float4 *>(st + A2_OFF);
 #pragma unroll
                 for (int e = ct; e < (int)(A_BYTES / 16); e += 128) {
                     const float4 x = hi[e];
@@ -366,15 +382,21 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                 const uint32_t b = cc & 1u, aph = (cc >> 1) & 1u;
                 if (!mb_wait(&accf[b], aph, abort)) { *abort = 1; ok = false; break; }
                 fence_after();
-                const int2 qr = a.nband ? a.nband[c] : make_int2(0, NQ - 1);
+                const int2 qr = a.nband && !CAT ? a.nband[c] : make_int2(0, NQ - 1);
 #pragma unroll
                 for (int c0 = 0; c0 < CW; c0 += 32) {
                     const int qq = (h * CW + c0) >> 5;   // warp-uniform
                     if (qq < qr.x || qq > qr.y) continue;   // columns the chunk did not touch: zero
                     float r[32];
-                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * BN + h * CW + c0, r);
+                    const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + b * ACC_COLS + h * CW + c0;
+                    tmem_ld32(ta, r);
 #pragma unroll
                     for (int i = 0; i < 32; ++i) run[c0 + i] += r[i];
+                    if (CAT) {   // the A_hi B_lo half of the accumulator
+                        tmem_ld32(ta + BN, r);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) run[c0 + i] += r[i];
+                    }
                 }
                 fence_before();
                 mb_arrive(&acce[b]);
