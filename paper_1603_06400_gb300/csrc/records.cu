@@ -1004,11 +1004,11 @@ __global__ void k_sadj_fill(PairArgs A, TabArgs T, int R2, int wpb, const int64_
 // of the lanes' last runs (as many doubling steps as the longest chain of lanes
 // needs), and a run that continues past the row by a warp-uniform carry.  Every run
 // is completed exactly once, by the lane holding its last record, and added into
-// the warp's segment buffer V[t - t_lo] (LO sums) and, after a warp barrier,
-// V[t + 1 - t_lo] (HI sums); each entry gets at most one LO and one HI sum, so the
-// result does not depend on their order.  Runs outside the segment are dropped at
-// that point.  The buffer is then written to the two V rows (consecutive lanes,
-// consecutive 8 bytes) and cleared.  Every sum has a fixed order, set by the plan:
+// the warp's segment buffer V[t + 1 - t_lo] (HI sums, stored) and, after a warp
+// barrier, V[t - t_lo] (LO sums, added); each entry gets at most one HI and one LO
+// sum, the HI sum first, so the result does not depend on the order of the runs.
+// Runs outside the segment are dropped at that point.  The buffer is then written
+// to the two V rows (consecutive lanes, consecutive 8 bytes) and cleared.  Every sum has a fixed order, set by the plan:
 // repeated calls are bitwise equal.
 constexpr int SEG_T = 1024;
 constexpr int SEG_W = SEG_T / 32;
@@ -1193,7 +1193,11 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab) {
             const bool fin3 = lane < 31 && t3 != tnext;   // the last run ends in this lane
             lo[3] = alo;
             hi[3] = ahi;
-            // LO sums of the completed runs, then (after a warp barrier) the HI sums
+            // HI sums of the completed runs, then (after a warp barrier) the LO sums.
+            // The HI sum of run t is the first value knot t + 1 receives: run t + 1,
+            // whose LO sum goes there too, completes after run t (in this row's LO
+            // phase or a later row), so the HI sums are plain stores into the
+            // cleared buffer and only the LO sums read back.
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const bool end = r < 3 ? t[r] != t[r + 1] : fin3;
@@ -1202,6 +1206,19 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab) {
                         lo[r] = f2add(Clo, lo[r]);
                         hi[r] = f2add(Chi, hi[r]);
                     }
+                    const unsigned d = (unsigned)(t[r] + 1 - tlo);
+                    if (d < L) V[d] = hi[r];
+                }
+            }
+            if (flush && lane == 0) {
+                const unsigned d = (unsigned)(ct + 1 - tlo);
+                if (d < L) V[d] = chi;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const bool end = r < 3 ? t[r] != t[r + 1] : fin3;
+                if (end) {
                     const unsigned d = (unsigned)(t[r] - tlo);
                     if (d < L) V[d] = f2add(V[d], lo[r]);
                 }
@@ -1209,19 +1226,6 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab) {
             if (flush && lane == 0) {
                 const unsigned d = (unsigned)(ct - tlo);
                 if (d < L) V[d] = f2add(V[d], clo);
-            }
-            __syncwarp();
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const bool end = r < 3 ? t[r] != t[r + 1] : fin3;
-                if (end) {
-                    const unsigned d = (unsigned)(t[r] + 1 - tlo);
-                    if (d < L) V[d] = f2add(V[d], hi[r]);
-                }
-            }
-            if (flush && lane == 0) {
-                const unsigned d = (unsigned)(ct + 1 - tlo);
-                if (d < L) V[d] = f2add(V[d], chi);
             }
             __syncwarp();
             // lane 31's last run goes on into the next row
