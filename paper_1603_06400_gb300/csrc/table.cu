@@ -685,18 +685,26 @@ cudaError_t pad_convert(const float *x, int64_t rows, int Q, int Qp, int kind, v
 }
 
 // S~^T [Q][Bp] from S~ [B][Q]: TF32 split and 16-bit copies (zero padding t >= B).
-__global__ void k_transpose_S(const float *__restrict__ S, int B, int Q, int Bp, float *__restrict__ hi,
+// S~^T [Q][B] for the adjoint contraction, stored as the GEMM's B operand in
+// k-block order: element (l, t) at ((l / 128) nkb + t / KE) 128 KE + (l % 128) KE
+// + t % KE, KE = 32 (FP32 splits) or 64 (16-bit copies), nkb = ceil(B / KE), so
+// that each 128-row k-block tile is one contiguous 16 KB block (the rest of the
+// buffer is zero).
+__global__ void k_transpose_S(const float *__restrict__ S, int B, int Q, float *__restrict__ hi,
                               float *__restrict__ lo, __nv_bfloat16 *__restrict__ bf, __half *__restrict__ hf) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)Q * Bp) return;
-    const int l = (int)(idx / Bp), t = (int)(idx % Bp);
-    const float x = t < B ? S[(int64_t)t * Q + l] : 0.f;
+    if (idx >= (int64_t)Q * B) return;
+    const int l = (int)(idx / B), t = (int)(idx % B);
+    const float x = S[(int64_t)t * Q + l];
     float h, lw;
     tf32_split(x, h, lw);
-    hi[idx] = h;
-    lo[idx] = lw;
-    bf[idx] = __float2bfloat16_rn(x);
-    hf[idx] = __float2half_rn(x);
+    const int64_t nkb32 = (B + 31) / 32, nkb64 = (B + 63) / 64;
+    const int64_t i32 = ((l / 128) * nkb32 + t / 32) * 4096 + (l % 128) * 32 + t % 32;
+    const int64_t i64 = ((l / 128) * nkb64 + t / 64) * 8192 + (l % 128) * 64 + t % 64;
+    hi[i32] = h;
+    lo[i32] = lw;
+    bf[i64] = __float2bfloat16_rn(x);
+    hf[i64] = __float2half_rn(x);
 }
 
 // cuBLAS handle, workspace and 16-bit operand copies (first table call).
@@ -722,17 +730,23 @@ caxsi_status blas_setup(caxsi_plan *p, TablePath *T) {
         return CAXSI_ERR_CUDA;
     p->table_bytes += (int64_t)T->blas_ws_bytes + 2 * nS * 2 + (int64_t)d.R * T->Qp * 2 + (int64_t)d.R * T->Bp * 2;
     // operands of the hand-written tcgen05 GEMM
-    const int64_t nSt = (int64_t)d.Q * T->Bp, nf = (int64_t)d.R * T->Qp;
+    // S~^T in k-block order (k_transpose_S): whole 128-row blocks, zero padding
+    const int64_t nf = (int64_t)d.R * T->Qp;
+    const int64_t nrb = (d.Q + 127) / 128;
+    const int64_t nSt32 = nrb * ((T->B + 31) / 32) * 4096, nSt16 = nrb * ((T->B + 63) / 64) * 8192;
     if (cudaMalloc(&T->S_hi, nS * 4) != cudaSuccess || cudaMalloc(&T->S_lo, nS * 4) != cudaSuccess ||
-        cudaMalloc(&T->St_hi, nSt * 4) != cudaSuccess || cudaMalloc(&T->St_lo, nSt * 4) != cudaSuccess ||
-        cudaMalloc(&T->St16[0], nSt * 2) != cudaSuccess || cudaMalloc(&T->St16[1], nSt * 2) != cudaSuccess ||
+        cudaMalloc(&T->St_hi, nSt32 * 4) != cudaSuccess || cudaMalloc(&T->St_lo, nSt32 * 4) != cudaSuccess ||
+        cudaMalloc(&T->St16[0], nSt16 * 2) != cudaSuccess || cudaMalloc(&T->St16[1], nSt16 * 2) != cudaSuccess ||
         cudaMalloc(&T->f_hi, nf * 4) != cudaSuccess || cudaMalloc(&T->f_lo, nf * 4) != cudaSuccess)
         return CAXSI_ERR_OOM;
+    if (cudaMemset(T->St_hi, 0, nSt32 * 4) != cudaSuccess || cudaMemset(T->St_lo, 0, nSt32 * 4) != cudaSuccess ||
+        cudaMemset(T->St16[0], 0, nSt16 * 2) != cudaSuccess || cudaMemset(T->St16[1], 0, nSt16 * 2) != cudaSuccess)
+        return CAXSI_ERR_CUDA;
     if (pad_convert(T->S, T->B, d.Q, T->Qp, 0, T->S_hi, T->S_lo, 0) != cudaSuccess) return CAXSI_ERR_CUDA;
-    k_transpose_S<<<(unsigned)ceil_div64(nSt, 256), 256>>>(T->S, T->B, d.Q, T->Bp, T->St_hi, T->St_lo,
-                                                          (__nv_bfloat16 *)T->St16[0], (__half *)T->St16[1]);
+    k_transpose_S<<<(unsigned)ceil_div64((int64_t)d.Q * T->B, 256), 256>>>(
+        T->S, T->B, d.Q, T->St_hi, T->St_lo, (__nv_bfloat16 *)T->St16[0], (__half *)T->St16[1]);
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return CAXSI_ERR_CUDA;
-    p->table_bytes += 2 * nS * 4 + nSt * 12 + 2 * nf * 4;
+    p->table_bytes += 2 * nS * 4 + nSt32 * 8 + nSt16 * 4 + 2 * nf * 4;
     // the q band of each knot's row of S~ (first and last nonzero), and the GEMMs'
     // band tables from it
     std::vector<float> hS((size_t)T->B * d.Q);
@@ -1087,7 +1101,7 @@ caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path
                 CAXSI_PROF(p, "tc_gemm_adj_3xtf32", s);
                 CAXSI_CUDA_TRY(tc_gemm(3, 128, (int)nr, d.Q, T->B, T->tab + r0 * T->Bp, nullptr, T->Bp, T->St_hi,
                                        T->St_lo, T->Bp, f_out + r0 * d.Q, d.Q, p->err_flag + 1, p->num_sms, s,
-                                       nullptr, nband_of(p, 0)));
+                                       nullptr, nband_of(p, 0), nullptr, 1));
             }
             CAXSI_LAUNCH_CHECK(p);
             if (h == 0) {
@@ -1106,10 +1120,12 @@ caxsi_status table_adjoint(caxsi_plan *p, const float *w, float *f_out, int path
         CAXSI_PROF(p, k == 0 ? "tc_gemm_adj_3xtf32" : (k == 1 ? "tc_gemm_adj_bf16" : "tc_gemm_adj_fp16"), s);
         if (k == 0)
             CAXSI_CUDA_TRY(tc_gemm(3, 128, d.R, d.Q, T->B, T->tab, nullptr, T->Bp, T->St_hi, T->St_lo, T->Bp,
-                                   f_out, d.Q, p->err_flag + 1, p->num_sms, s, nullptr, nband_of(p, 0)));
+                                   f_out, d.Q, p->err_flag + 1, p->num_sms, s, nullptr, nband_of(p, 0), nullptr,
+                                   1));
         else
             CAXSI_CUDA_TRY(tc_gemm(k, 128, d.R, d.Q, T->B, T->v16, nullptr, T->Bp, T->St16[k - 1], nullptr,
-                                   T->Bp, f_out, d.Q, p->err_flag + 1, p->num_sms, s, nullptr, nband_of(p, 1)));
+                                   T->Bp, f_out, d.Q, p->err_flag + 1, p->num_sms, s, nullptr, nband_of(p, 1),
+                                   nullptr, 1));
         return CAXSI_OK;
     }
     if (cublasSetStream(T->blas, s) != CUBLAS_STATUS_SUCCESS) return CAXSI_ERR_CUDA;
@@ -1191,7 +1207,7 @@ caxsi_status table_adjoint_batch(caxsi_plan *p, int nb, const int32_t *ranges, c
     {
         CAXSI_PROF(p, "tc_gemm_adj_3xtf32", s);
         CAXSI_CUDA_TRY(tc_gemm(3, 128, bs.rows, d.Q, T->B, bs.tab, nullptr, T->Bp, T->St_hi, T->St_lo, T->Bp,
-                               bs.fpk, d.Q, p->err_flag + 1, p->num_sms, s, nullptr, nband_of(p, 0)));
+                               bs.fpk, d.Q, p->err_flag + 1, p->num_sms, s, nullptr, nband_of(p, 0), nullptr, 1));
     }
     CAXSI_LAUNCH_CHECK(p);
     {

@@ -194,7 +194,7 @@ cudaError_t records_adjoint(const caxsi_plan *p, const TablePath *T, int subset,
 cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const void *A2, int64_t lda,
                     const void *B, const void *B2, int64_t ldb, float *C, int64_t ldc, int *err,
                     int num_sms, cudaStream_t s, const int2 *kband = nullptr, const int2 *nband = nullptr,
-                    uint16_t *C16 = nullptr);
+                    uint16_t *C16 = nullptr, int b_blocked = 0);
 // Band tables from the nonzero range of each row of B[N][K] along K (kband: per
 // n-tile of bn rows, the k-blocks to keep) or of each column along N (nband: per
 // K-chunk, the 32-column quarters to keep); eb = operand element bytes.

@@ -168,6 +168,7 @@ struct TcArgs {
     int vec_ok;     // rows of C start on 16-byte boundaries (vector stores allowed)
     int tma_store;  // C is written by TMA tensor stores through shared memory
     uint16_t *C16;  // non-null: C is written as bf16 (round to nearest) here instead of FP32 to C
+    int b_blocked;  // B (and B2) in k-block order: tile (n-tile j, k-block k) at rows (j nk + k) BN of a [.][KE] map
 };
 
 constexpr uint32_t TCG_STG = 4096;   // per epilogue warp: one 32 x 32 FP32 chunk, 128-byte swizzled
@@ -255,11 +256,13 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                     unsigned char *st = base + s * STAGE;
                     mb_expect_tx(&full[s], SPLIT_A ? STAGE - A_BYTES : STAGE);
                     const int x = kt * KE;
+                    const int xb = a.b_blocked ? 0 : x;
+                    const int yb = a.b_blocked ? ((n0 / BN) * a.nk + kt) * BN : n0;
                     tma_load_2d(st, &tA, x, m0, &full[s]);
-                    tma_load_2d(st + A_BYTES, &tB, x, n0, &full[s]);
+                    tma_load_2d(st + A_BYTES, &tB, xb, yb, &full[s]);
                     if (X3) {
                         if (!SPLIT_A) tma_load_2d(st + A2_OFF, &tA2, x, m0, &full[s]);
-                        tma_load_2d(st + B2_OFF, &tB2, x, n0, &full[s]);
+                        tma_load_2d(st + B2_OFF, &tB2, xb, yb, &full[s]);
                     }
                 }
             }
@@ -567,19 +570,24 @@ cudaError_t launch_tc(const CUtensorMap &tA, const CUtensorMap &tA2, const CUten
 // ldc elements, and C is not used.
 cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const void *A2, int64_t lda,
                     const void *B, const void *B2, int64_t ldb, float *C, int64_t ldc, int *err,
-                    int num_sms, cudaStream_t s, const int2 *kband, const int2 *nband, uint16_t *C16) {
+                    int num_sms, cudaStream_t s, const int2 *kband, const int2 *nband, uint16_t *C16,
+                    int b_blocked) {
     const int eb = (kind == 0 || kind == 3) ? 4 : 2;
     if (kband && nband) return cudaErrorInvalidValue;              // one kind of band at a time
     if (nband && (N + bn - 1) / bn != 1) return cudaErrorInvalidValue;   // quarters of the only n-tile
+    const int ke = 128 / eb, nk = (K * eb + 127) / 128;
+    // B in k-block order: a [ntn * nk * bn][ke] map whose (bn x ke) boxes are the tiles
+    const int64_t brows = b_blocked ? (int64_t)((N + bn - 1) / bn) * nk * bn : N;
+    const int64_t bcols = b_blocked ? ke : K, bld = b_blocked ? ke : ldb;
     CUtensorMap tA, tA2, tB, tB2;
-    if (!make_map(&tA, A, eb, M, K, lda, 128) || !make_map(&tB, B, eb, N, K, ldb, bn))
+    if (!make_map(&tA, A, eb, M, K, lda, 128) || !make_map(&tB, B, eb, brows, bcols, bld, bn))
         return cudaErrorInvalidValue;
     if (kind == 0) {
-        if (!make_map(&tA2, A2, eb, M, K, lda, 128) || !make_map(&tB2, B2, eb, N, K, ldb, bn))
+        if (!make_map(&tA2, A2, eb, M, K, lda, 128) || !make_map(&tB2, B2, eb, brows, bcols, bld, bn))
             return cudaErrorInvalidValue;
     } else if (kind == 3) {
         tA2 = tA;
-        if (!make_map(&tB2, B2, eb, N, K, ldb, bn)) return cudaErrorInvalidValue;
+        if (!make_map(&tB2, B2, eb, brows, bcols, bld, bn)) return cudaErrorInvalidValue;
     } else {
         tA2 = tA;
         tB2 = tB;
@@ -592,6 +600,7 @@ cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const 
     a.ldc = ldc;
     a.err = err;
     a.C16 = C16;
+    a.b_blocked = b_blocked;
     CUtensorMap tC;
     if (C16) {
         // bf16 output: TMA tensor stores of 32 rows x 64 columns (128-byte rows), else
