@@ -685,6 +685,23 @@ cudaError_t pad_convert(const float *x, int64_t rows, int Q, int Qp, int kind, v
 }
 
 // S~^T [Q][Bp] from S~ [B][Q]: TF32 split and 16-bit copies (zero padding t >= B).
+// S~ [B][Q] TF32-split for the forward contraction (B operand, 256-row n-tiles),
+// stored in k-block order: element (t, l) at ((t / 256) nkq + l / 32) 256 * 32 +
+// (t % 256) 32 + l % 32, nkq = ceil(Q / 32): each 256-row k-block tile is one
+// contiguous 32 KB block (the rest of the buffer is zero).
+__global__ void k_block_S(const float *__restrict__ S, int B, int Q, float *__restrict__ hi,
+                          float *__restrict__ lo) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)B * Q) return;
+    const int t = (int)(idx / Q), l = (int)(idx % Q);
+    float h, lw;
+    tf32_split(S[idx], h, lw);
+    const int64_t nkq = (Q + 31) / 32;
+    const int64_t i = ((t / 256) * nkq + l / 32) * 8192 + (t % 256) * 32 + l % 32;
+    hi[i] = h;
+    lo[i] = lw;
+}
+
 // S~^T [Q][B] for the adjoint contraction, stored as the GEMM's B operand in
 // k-block order: element (l, t) at ((l / 128) nkb + t / KE) 128 KE + (l % 128) KE
 // + t % KE, KE = 32 (FP32 splits) or 64 (16-bit copies), nkb = ceil(B / KE), so
@@ -734,7 +751,8 @@ caxsi_status blas_setup(caxsi_plan *p, TablePath *T) {
     const int64_t nf = (int64_t)d.R * T->Qp;
     const int64_t nrb = (d.Q + 127) / 128;
     const int64_t nSt32 = nrb * ((T->B + 31) / 32) * 4096, nSt16 = nrb * ((T->B + 63) / 64) * 8192;
-    if (cudaMalloc(&T->S_hi, nS * 4) != cudaSuccess || cudaMalloc(&T->S_lo, nS * 4) != cudaSuccess ||
+    const int64_t nSb = std::max<int64_t>(nS, (int64_t)(T->B + 255) / 256 * ((d.Q + 31) / 32) * 8192);
+    if (cudaMalloc(&T->S_hi, nSb * 4) != cudaSuccess || cudaMalloc(&T->S_lo, nSb * 4) != cudaSuccess ||
         cudaMalloc(&T->St_hi, nSt32 * 4) != cudaSuccess || cudaMalloc(&T->St_lo, nSt32 * 4) != cudaSuccess ||
         cudaMalloc(&T->St16[0], nSt16 * 2) != cudaSuccess || cudaMalloc(&T->St16[1], nSt16 * 2) != cudaSuccess ||
         cudaMalloc(&T->f_hi, nf * 4) != cudaSuccess || cudaMalloc(&T->f_lo, nf * 4) != cudaSuccess)
@@ -742,7 +760,9 @@ caxsi_status blas_setup(caxsi_plan *p, TablePath *T) {
     if (cudaMemset(T->St_hi, 0, nSt32 * 4) != cudaSuccess || cudaMemset(T->St_lo, 0, nSt32 * 4) != cudaSuccess ||
         cudaMemset(T->St16[0], 0, nSt16 * 2) != cudaSuccess || cudaMemset(T->St16[1], 0, nSt16 * 2) != cudaSuccess)
         return CAXSI_ERR_CUDA;
-    if (pad_convert(T->S, T->B, d.Q, T->Qp, 0, T->S_hi, T->S_lo, 0) != cudaSuccess) return CAXSI_ERR_CUDA;
+    if (cudaMemset(T->S_hi, 0, nSb * 4) != cudaSuccess || cudaMemset(T->S_lo, 0, nSb * 4) != cudaSuccess)
+        return CAXSI_ERR_CUDA;
+    k_block_S<<<(unsigned)ceil_div64((int64_t)T->B * d.Q, 256), 256>>>(T->S, T->B, d.Q, T->S_hi, T->S_lo);
     k_transpose_S<<<(unsigned)ceil_div64((int64_t)d.Q * T->B, 256), 256>>>(
         T->S, T->B, d.Q, T->St_hi, T->St_lo, (__nv_bfloat16 *)T->St16[0], (__half *)T->St16[1]);
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return CAXSI_ERR_CUDA;
@@ -979,7 +999,7 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
                 CAXSI_PROF(p, "tc_gemm_fwd_3xtf32", s);
                 CAXSI_CUDA_TRY(tc_gemm(0, 256, (int)nr, T->B, d.Q, f + r0 * d.Q, T->f_lo + r0 * d.Q, T->Qp, T->S_hi,
                                        T->S_lo, T->Qp, T->tab + r0 * T->Bp, T->Bp, p->err_flag + 1, p->num_sms, s,
-                                       kband_of(p, 0)));
+                                       kband_of(p, 0), nullptr, nullptr, 1));
             }
             CAXSI_LAUNCH_CHECK(p);
         }
@@ -997,7 +1017,8 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
         {
             CAXSI_PROF(p, "tc_gemm_fwd_3xtf32", s);
             CAXSI_CUDA_TRY(tc_gemm(0, 256, d.R, T->B, d.Q, raw_hi ? f : T->f_hi, T->f_lo, T->Qp, T->S_hi, T->S_lo,
-                                   T->Qp, T->tab, T->Bp, p->err_flag + 1, p->num_sms, s, kband_of(p, 0)));
+                                   T->Qp, T->tab, T->Bp, p->err_flag + 1, p->num_sms, s, kband_of(p, 0), nullptr,
+                                   nullptr, 1));
         }
         CAXSI_LAUNCH_CHECK(p);
     } else if (p->gemm_engine == 0) {
@@ -1168,7 +1189,8 @@ caxsi_status table_forward_batch(caxsi_plan *p, int nb, const int32_t *ranges, c
         {
             CAXSI_PROF(p, "tc_gemm_fwd_3xtf32", s);
             CAXSI_CUDA_TRY(tc_gemm(0, 256, bs.rows, T->B, d.Q, bs.f_hi, bs.f_lo, T->Qp, T->S_hi, T->S_lo, T->Qp,
-                                   bs.tab, T->Bp, p->err_flag + 1, p->num_sms, s, kband_of(p, 0)));
+                                   bs.tab, T->Bp, p->err_flag + 1, p->num_sms, s, kband_of(p, 0), nullptr, nullptr,
+                                   1));
         }
         CAXSI_LAUNCH_CHECK(p);
         {
