@@ -1086,9 +1086,10 @@ k_adj_sym(SymAdjArgs A, const float *__restrict__ w, OutT *__restrict__ Vtab) {
         int j = 0;
         if (lane == 0) j = atomicAdd(&next_item, 1);
         j = __shfl_sync(0xffffffffu, j, 0);
-        const int64_t k = blockIdx.x + (int64_t)j * gridDim.x;
-        if (k >= nitems) break;
-        const int sg = (int)(k / A.R2), s = (int)(k - (int64_t)sg * A.R2);
+        // (32-bit: nitems + gridDim.x < 2^32)
+        const unsigned k = blockIdx.x + (unsigned)j * gridDim.x;
+        if (k >= (unsigned)nitems) break;
+        const int sg = (int)(k / (unsigned)A.R2), s = (int)(k - (unsigned)sg * (unsigned)A.R2);
         const uint32_t qr = A.seg[(int64_t)s * A.nseg + sg];
         const int qa = (int)(qr & 0xffffu), qe = (int)(qr >> 16);
         const int tlo = sg * A.L;
