@@ -744,11 +744,15 @@ __global__ void k_sym_build(PairArgs A, TabArgs T, int R2, int nrec, uint32_t *_
 }
 
 // Forward over the symmetric records: a block takes a chunk of voxel pairs;
-// the two W rows of each pair arrive by TMA bulk copies, double-buffered one
-// pair ahead, and the next pair's records are prefetched into L2 meanwhile; each
-// record adds its 8 pairs' contributions to its 4 pixels (owned by the record
-// within the pair: no conflicts, no atomics).  A thread loads SYM_U records
-// before it uses the first, so that their loads overlap.
+// the two W rows of each pair arrive by TMA bulk copies into a ring of NB
+// buffers, and the next pair's records are prefetched into L2; each record adds
+// its 8 pairs' contributions to its 4 pixels.  A thread takes the same record
+// slots r of every pair, so it alone updates their pixels: the warps need no
+// block barrier between pairs and drift apart by up to NB - 1 pairs.  A warp
+// that is done with a pair counts itself on the pair's buffer; the last one
+// issues the copy of pair s + NB into it, the first one prefetches the records
+// of pair s + 2.  A thread loads SYM_U records before it uses the first, so that
+// their loads overlap.
 // WT: the element type of the knot rows (float, or bf16 for the bf16 path).
 constexpr int SYM_U = 4;
 // Four bf16 record weights, widened exactly to FP32.
@@ -760,21 +764,30 @@ __device__ __forceinline__ float4 bf16x4_to_f4(uint2 u) {
 __device__ __forceinline__ float wval(const float *w, int t) { return w[t]; }
 __device__ __forceinline__ float wval(const __nv_bfloat16 *w, int t) { return __bfloat162float(w[t]); }
 
+// W row buffers of k_fwd_sym: 2 for FP32 rows, 4 for bf16 rows (the same bytes).
+template <typename WT> struct FwdSymRing { static constexpr int NB = sizeof(WT) == 4 ? 2 : 4; };
+
 template <typename WT>
 __global__ void __launch_bounds__(RT, 1)
 k_fwd_sym(SymArgs S, const WT *__restrict__ Wtab, float *__restrict__ part, int *err) {
+    constexpr int NB = FwdSymRing<WT>::NB;
+    constexpr int NW = RT / 32;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int npix_al = (S.npix + 3) & ~3;
     float *g_s = reinterpret_cast<float *>(smem_raw);
-    WT *wb = reinterpret_cast<WT *>(g_s + npix_al);             // [2 buffers][2 rows][Bp]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(wb + 4 * S.Bp);
-    const int tid = threadIdx.x;
+    WT *wb = reinterpret_cast<WT *>(g_s + npix_al);             // [NB buffers][2 rows][Bp]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(wb + 2 * NB * S.Bp);   // [NB] rows landed
+    int *done = reinterpret_cast<int *>(bar + NB);                       // [NB] warps done with the buffer
+    int *issued = done + NB;                                             // [NB] last pair copied into it
+    __shared__ int failed;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int s0 = blockIdx.x * S.vc, s1 = min(s0 + S.vc, S.R2);
     if (s0 >= s1) return;   // block-uniform
     const uint32_t row_bytes = (uint32_t)S.Bp * (uint32_t)sizeof(WT);
     auto issue = [&](int s, int buf) {
         const int i = s / S.J2, jq = s - i * S.J2;
         const int64_t v = (int64_t)i * S.J + jq, vp = (int64_t)i * S.J + (S.J - 1 - jq);
+        issued[buf] = s;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&bar[buf], 2u * row_bytes);
         bulk_g2s(wb + (2 * buf) * S.Bp, Wtab + v * S.Bp, row_bytes, &bar[buf]);
@@ -788,24 +801,24 @@ k_fwd_sym(SymArgs S, const WT *__restrict__ Wtab, float *__restrict__ part, int 
     };
     for (int p = tid; p < S.npix; p += RT) g_s[p] = 0.f;
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        failed = 0;
+        for (int b = 0; b < NB; ++b) {
+            mbar_init(&bar[b], 1);
+            done[b] = 0;
+            issued[b] = -1;
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        issue(s0, 0);
+        for (int k = 0; k < NB && s0 + k < s1; ++k) issue(s0 + k, k);
     }
+    if (tid == 32 && s0 + 1 < s1) prefetch(s0 + 1);
     __syncthreads();
-    bool ok = true;
-    uint32_t ph0 = 0u, ph1 = 0u;
     for (int s = s0; s < s1; ++s) {
-        const int buf = (s - s0) & 1;
-        if (tid == 0 && s + 1 < s1) issue(s + 1, buf ^ 1);   // its buffer was last read by pair s - 1
-        if (tid == 32 && s + 1 < s1) prefetch(s + 1);
-        const int late = mbar_wait(&bar[buf], buf ? ph1 : ph0) ? 0 : 1;
-        if (__syncthreads_or(late)) {
-            ok = false;
+        const int k = s - s0, buf = k % NB;
+        // warp-uniform: a warp goes on only if every lane saw the rows land
+        if (!__all_sync(0xffffffffu, mbar_wait(&bar[buf], (uint32_t)(k / NB) & 1u))) {
+            failed = 1;
             break;
         }
-        if (buf) ph1 ^= 1u; else ph0 ^= 1u;
         const WT *Wv = wb + (2 * buf) * S.Bp, *Wp = Wv + S.Bp;
         const int64_t base = (int64_t)s * S.nrec;
         for (int r0 = tid; r0 < S.nrec; r0 += SYM_U * RT) {
@@ -841,13 +854,27 @@ k_fwd_sym(SymArgs S, const WT *__restrict__ Wtab, float *__restrict__ part, int 
                 g_s[mm * S.N + nn] += ((bt & 8u) ? xap : 0.f) + ((bt & 32u) ? xbv : 0.f);
             }
         }
-        __syncthreads();
+        // this warp is done with the buffer (its reads of the rows are complete)
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            const int old = atomicAdd(&done[buf], 1);
+            if (old == 0 && s + 2 < s1) prefetch(s + 2);
+            if (old == NW - 1) {   // the last warp: the buffer is free for pair s + NB
+                __threadfence_block();
+                done[buf] = 0;
+                if (s + NB < s1) issue(s + NB, buf);
+            }
+        }
     }
-    if (!ok) {
+    __syncthreads();
+    if (failed) {
+        // a copy that did not land in time: record it, and wait (bounded) for every
+        // copy still in flight before the block's shared memory goes away
         if (tid == 0) {
             atomicExch(err, 1);
-            mbar_wait(&bar[0], ph0);
-            mbar_wait(&bar[1], ph1);
+            for (int b = 0; b < NB; ++b)
+                if (issued[b] >= 0) mbar_wait(&bar[b], (uint32_t)((issued[b] - s0) / NB) & 1u);
         }
         return;
     }
@@ -1440,7 +1467,9 @@ __global__ void k_adj_sub(SubArgs A, const float *__restrict__ w, float *__restr
     if (ql) *reinterpret_cast<float4 *>(out + (int64_t)v * A.Q + 4 * lane) = acc;
 }
 
-size_t fwd_sym_smem(int npix, int Bp) { return (size_t)((npix + 3) & ~3) * 4 + 4 * (size_t)Bp * 4 + 16; }
+// the partial image, 4 rows of FP32 (2 buffers) or 8 of bf16 (4 buffers), the
+// buffers' barriers and counters
+size_t fwd_sym_smem(int npix, int Bp) { return (size_t)((npix + 3) & ~3) * 4 + 4 * (size_t)Bp * 4 + 64; }
 
 size_t fwd_rec_smem(int npix, int Bp) {
     return (size_t)((npix + 3) & ~3) * 4 + 2 * (size_t)Bp * 4 + 16;
