@@ -405,7 +405,6 @@ void free_table(TablePath *T) {
         cudaFree(T->nband[k]);
     }
     cudaFree(T->f_hi);
-    cudaFree(T->f_lo);
     if (T->blas) cublasDestroy(T->blas);
     cudaFree(T->blas_ws);
     cudaFree(T->S16[0]);
@@ -423,7 +422,6 @@ void free_table(TablePath *T) {
     cudaFree(bs.obj_items);
     cudaFree(bs.tab);
     cudaFree(bs.f_hi);
-    cudaFree(bs.f_lo);
     cudaFree(bs.fpk);
     cudaFree(bs.part);
     delete T;
@@ -648,6 +646,8 @@ __global__ void k_pad_convert(const float *__restrict__ x, int64_t rows, int Q, 
         reinterpret_cast<__nv_bfloat16 *>(y)[i] = __float2bfloat16_rn(v);
     } else if (kind == 2) {
         reinterpret_cast<__half *>(y)[i] = __float2half_rn(v);
+    } else if (kind == 4) {   // the padded FP32 copy (split on chip by the contraction)
+        reinterpret_cast<float *>(y)[i] = v;
     } else {
         float h, lo;
         if (kind == 3) tf32_split_trunc(v, h, lo);
@@ -655,26 +655,6 @@ __global__ void k_pad_convert(const float *__restrict__ x, int64_t rows, int Q, 
         reinterpret_cast<float *>(y)[i] = h;
         ylo[i] = lo;
     }
-}
-
-// lo = x - (x with its low 13 mantissa bits cleared), n elements (n % 4 == 0,
-// 16-byte aligned): the remainder of the TF32 value a tensor core reads from x.
-__global__ void k_trunc_lo4(const float4 *__restrict__ x, int64_t n4, float4 *__restrict__ lo) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n4) return;
-    const float4 v = x[i];
-    float4 l;
-    l.x = v.x - __uint_as_float(__float_as_uint(v.x) & 0xffffe000u);
-    l.y = v.y - __uint_as_float(__float_as_uint(v.y) & 0xffffe000u);
-    l.z = v.z - __uint_as_float(__float_as_uint(v.z) & 0xffffe000u);
-    l.w = v.w - __uint_as_float(__float_as_uint(v.w) & 0xffffe000u);
-    lo[i] = l;
-}
-
-cudaError_t trunc_remainder(const float *x, int64_t n, float *lo, cudaStream_t s) {
-    k_trunc_lo4<<<(unsigned)ceil_div64(n / 4, 256), 256, 0, s>>>(reinterpret_cast<const float4 *>(x), n / 4,
-                                                                  reinterpret_cast<float4 *>(lo));
-    return cudaGetLastError();
 }
 
 cudaError_t pad_convert(const float *x, int64_t rows, int Q, int Qp, int kind, void *y, float *ylo,
@@ -755,7 +735,7 @@ caxsi_status blas_setup(caxsi_plan *p, TablePath *T) {
     if (cudaMalloc(&T->S_hi, nSb * 4) != cudaSuccess || cudaMalloc(&T->S_lo, nSb * 4) != cudaSuccess ||
         cudaMalloc(&T->St_hi, nSt32 * 4) != cudaSuccess || cudaMalloc(&T->St_lo, nSt32 * 4) != cudaSuccess ||
         cudaMalloc(&T->St16[0], nSt16 * 2) != cudaSuccess || cudaMalloc(&T->St16[1], nSt16 * 2) != cudaSuccess ||
-        cudaMalloc(&T->f_hi, nf * 4) != cudaSuccess || cudaMalloc(&T->f_lo, nf * 4) != cudaSuccess)
+        cudaMalloc(&T->f_hi, nf * 4) != cudaSuccess)
         return CAXSI_ERR_OOM;
     if (cudaMemset(T->St_hi, 0, nSt32 * 4) != cudaSuccess || cudaMemset(T->St_lo, 0, nSt32 * 4) != cudaSuccess ||
         cudaMemset(T->St16[0], 0, nSt16 * 2) != cudaSuccess || cudaMemset(T->St16[1], 0, nSt16 * 2) != cudaSuccess)
@@ -766,7 +746,7 @@ caxsi_status blas_setup(caxsi_plan *p, TablePath *T) {
     k_transpose_S<<<(unsigned)ceil_div64((int64_t)d.Q * T->B, 256), 256>>>(
         T->S, T->B, d.Q, T->St_hi, T->St_lo, (__nv_bfloat16 *)T->St16[0], (__half *)T->St16[1]);
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return CAXSI_ERR_CUDA;
-    p->table_bytes += 2 * nS * 4 + nSt32 * 8 + nSt16 * 4 + 2 * nf * 4;
+    p->table_bytes += 2 * nS * 4 + nSt32 * 8 + nSt16 * 4 + nf * 4;
     // the q band of each knot's row of S~ (first and last nonzero), and the GEMMs'
     // band tables from it
     std::vector<float> hS((size_t)T->B * d.Q);
@@ -795,19 +775,16 @@ caxsi_status blas_setup(caxsi_plan *p, TablePath *T) {
     return CAXSI_OK;
 }
 
-// Row-mapped TF32 split of the forward input: packed row r takes source row
-// rowmap[r] of x (the batched operators' packing), padded to Qp.
-__global__ void k_pack_split(const float *__restrict__ x, const int64_t *__restrict__ rowmap, int64_t rows, int Q,
-                             int Qp, float *__restrict__ hi, float *__restrict__ lo) {
+// Row-mapped copy of the forward input: packed row r takes source row rowmap[r]
+// of x (the batched operators' packing), padded to Qp (the contraction splits it
+// into TF32 parts on chip).
+__global__ void k_pack_rows(const float *__restrict__ x, const int64_t *__restrict__ rowmap, int64_t rows, int Q,
+                             int Qp, float *__restrict__ y) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= rows * Qp) return;
     const int64_t r = i / Qp;
     const int l = (int)(i - r * Qp);
-    const float v = l < Q ? x[rowmap[r] * Q + l] : 0.f;
-    float h, w;
-    tf32_split_trunc(v, h, w);
-    hi[i] = h;
-    lo[i] = w;
+    y[i] = l < Q ? x[rowmap[r] * Q + l] : 0.f;
 }
 
 // Packed adjoint rows back to each object's [R][Q] block (rows outside an
@@ -894,16 +871,14 @@ caxsi_status batch_layout(caxsi_plan *p, TablePath *T, int nb, const int32_t *ra
         cudaFree(bs.rowmap);
         cudaFree(bs.tab);
         cudaFree(bs.f_hi);
-        cudaFree(bs.f_lo);
         cudaFree(bs.fpk);
         bs.rowmap = nullptr;
-        bs.tab = bs.f_hi = bs.f_lo = bs.fpk = nullptr;
+        bs.tab = bs.f_hi = bs.fpk = nullptr;
         bs.rows_cap = 0;
         const size_t r = (size_t)(rows > 0 ? rows : 1);
         CAXSI_CUDA_TRY(cudaMalloc(&bs.rowmap, r * sizeof(int64_t)));
         CAXSI_CUDA_TRY(cudaMalloc(&bs.tab, r * T->Bp * sizeof(float)));
         CAXSI_CUDA_TRY(cudaMalloc(&bs.f_hi, r * T->Qp * sizeof(float)));
-        CAXSI_CUDA_TRY(cudaMalloc(&bs.f_lo, r * T->Qp * sizeof(float)));
         CAXSI_CUDA_TRY(cudaMalloc(&bs.fpk, r * d.Q * sizeof(float)));
         bs.rows_cap = rows;
     }
@@ -991,32 +966,28 @@ caxsi_status table_forward(caxsi_plan *p, const float *f, float *g_out, int path
             const int64_t r0 = h ? r1 : 0, nr = h ? d.R - r1 : r1;
             if (h) CAXSI_CUDA_TRY(cudaStreamWaitEvent(s, pipe->in_ready, 0));
             {
-                CAXSI_PROF(p, "split_tf32", s);
-                CAXSI_CUDA_TRY(trunc_remainder(f + r0 * d.Q, nr * d.Q, T->f_lo + r0 * d.Q, s));
-            }
-            CAXSI_LAUNCH_CHECK(p);
-            {
                 CAXSI_PROF(p, "tc_gemm_fwd_3xtf32", s);
-                CAXSI_CUDA_TRY(tc_gemm(0, 256, (int)nr, T->B, d.Q, f + r0 * d.Q, T->f_lo + r0 * d.Q, T->Qp, T->S_hi,
-                                       T->S_lo, T->Qp, T->tab + r0 * T->Bp, T->Bp, p->err_flag + 1, p->num_sms, s,
+                CAXSI_CUDA_TRY(tc_gemm(4, 256, (int)nr, T->B, d.Q, f + r0 * d.Q, nullptr, T->Qp, T->S_hi, T->S_lo,
+                                       T->Qp, T->tab + r0 * T->Bp, T->Bp, p->err_flag + 1, p->num_sms, s,
                                        kband_of(p, 0), nullptr, nullptr, 1));
             }
             CAXSI_LAUNCH_CHECK(p);
         }
     } else if (p->gemm_engine == 0 && path == CAXSI_PATH_TABLE_FP32) {
-        // Wtab[r][t] = sum_l f[r][l] S~[t][l] by the tcgen05 GEMM, 3xTF32.  With
-        // unpadded aligned rows f itself is the high part (the tensor core reads
-        // FP32 as TF32 by dropping the low 13 mantissa bits) and only the
-        // remainder is written; otherwise both parts go to padded copies.
-        {
-            CAXSI_PROF(p, "split_tf32", s);
-            if (raw_hi) CAXSI_CUDA_TRY(trunc_remainder(f, (int64_t)d.R * d.Q, T->f_lo, s));
-            else CAXSI_CUDA_TRY(pad_convert(f, d.R, d.Q, T->Qp, 3, T->f_hi, T->f_lo, s));
+        // Wtab[r][t] = sum_l f[r][l] S~[t][l] by the tcgen05 GEMM, 3xTF32, the TF32
+        // split of f made on chip (the tensor core reads FP32 as TF32 by dropping
+        // the low 13 mantissa bits; converter warps write the remainder).  Rows that
+        // are not 16-byte multiples or not aligned go through a padded copy first.
+        if (!raw_hi) {
+            {
+                CAXSI_PROF(p, "pad_f", s);
+                CAXSI_CUDA_TRY(pad_convert(f, d.R, d.Q, T->Qp, 4, T->f_hi, nullptr, s));
+            }
+            CAXSI_LAUNCH_CHECK(p);
         }
-        CAXSI_LAUNCH_CHECK(p);
         {
             CAXSI_PROF(p, "tc_gemm_fwd_3xtf32", s);
-            CAXSI_CUDA_TRY(tc_gemm(0, 256, d.R, T->B, d.Q, raw_hi ? f : T->f_hi, T->f_lo, T->Qp, T->S_hi, T->S_lo,
+            CAXSI_CUDA_TRY(tc_gemm(4, 256, d.R, T->B, d.Q, raw_hi ? f : T->f_hi, nullptr, T->Qp, T->S_hi, T->S_lo,
                                    T->Qp, T->tab, T->Bp, p->err_flag + 1, p->num_sms, s, kband_of(p, 0), nullptr,
                                    nullptr, 1));
         }
@@ -1181,14 +1152,14 @@ caxsi_status table_forward_batch(caxsi_plan *p, int nb, const int32_t *ranges, c
     const int64_t npix = (int64_t)d.M * d.N;
     if (bs.rows > 0) {
         {
-            CAXSI_PROF(p, "split_tf32", s);
-            k_pack_split<<<(unsigned)ceil_div64(bs.rows * T->Qp, 256), 256, 0, s>>>(f, bs.rowmap, bs.rows, d.Q,
-                                                                                 T->Qp, bs.f_hi, bs.f_lo);
+            CAXSI_PROF(p, "pack_rows", s);
+            k_pack_rows<<<(unsigned)ceil_div64(bs.rows * T->Qp, 256), 256, 0, s>>>(f, bs.rowmap, bs.rows, d.Q,
+                                                                                 T->Qp, bs.f_hi);
         }
         CAXSI_LAUNCH_CHECK(p);
         {
             CAXSI_PROF(p, "tc_gemm_fwd_3xtf32", s);
-            CAXSI_CUDA_TRY(tc_gemm(0, 256, bs.rows, T->B, d.Q, bs.f_hi, bs.f_lo, T->Qp, T->S_hi, T->S_lo, T->Qp,
+            CAXSI_CUDA_TRY(tc_gemm(4, 256, bs.rows, T->B, d.Q, bs.f_hi, nullptr, T->Qp, T->S_hi, T->S_lo, T->Qp,
                                    bs.tab, T->Bp, p->err_flag + 1, p->num_sms, s, kband_of(p, 0), nullptr, nullptr,
                                    1));
         }

@@ -29,7 +29,7 @@ struct BatchState {
     int items_cap = 0, nb_cap = 0;
     int64_t rows_cap = 0, part_cap = 0;
     float *tab = nullptr;          // [rows][Bp] W / V rows
-    float *f_hi = nullptr, *f_lo = nullptr;   // [rows][Qp]
+    float *f_hi = nullptr;         // [rows][Qp] packed forward input rows
     float *fpk = nullptr;          // [rows][Q] adjoint output rows
     float *part = nullptr;         // [n_items][M*N] forward partial images
 };
@@ -109,7 +109,7 @@ struct TablePath {
     float *S_hi = nullptr, *S_lo = nullptr;     // [B][Qp]
     float *St_hi = nullptr, *St_lo = nullptr;   // [Q][Bp]
     void *St16[2] = {nullptr, nullptr};         // [Q][Bp] bf16 / fp16
-    float *f_hi = nullptr, *f_lo = nullptr;     // [R][Qp] per-call split of the forward input
+    float *f_hi = nullptr;                      // [R][Qp] padded copy of the forward input (rows not 16-byte multiples)
     // Band tables of S~ for those GEMMs (device): per n-tile of the forward the
     // q k-blocks to keep, per K-chunk of the adjoint the q quarters to keep;
     // [0] for the TF32 operands, [1] for the 16-bit ones.

@@ -12,8 +12,12 @@
 // with A given once in FP32: the tile as loaded is its own high part (the tensor
 // core reads an FP32 operand as TF32 by dropping the low 13 mantissa bits) and
 // four converter warps write the exact remainder x - hi(x) next to it (half the
-// A traffic; the products with A_hi start before the remainder is written).  KIND 1 / 2 = single-pass bf16 / fp16 operands with
-// FP32 accumulation.
+// A traffic; the products with A_hi start before the remainder is written), and
+// B_hi, B_lo side by side so that A_hi [B_hi | B_lo] is one instruction (bn = 128).
+// KIND 4 = the on-chip A split with the three products of KIND 0 in KIND 0's
+// order (bn = 256, two converter warps; the MMAs of a stage wait for its
+// remainder), so that no separate pass splits A and the sums are those of KIND 0.  KIND 1 / 2 = single-pass
+// bf16 / fp16 operands with FP32 accumulation.
 //
 // Structure (one CTA per SM, persistent over 128 x BN output tiles):
 //   warp 0      TMA producer: 2-D tensor loads (128-byte swizzle) of the A and B
@@ -122,7 +126,7 @@ __device__ __forceinline__ uint64_t sw128_desc(const void *p) {
 }
 template <int KIND>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    if (KIND == 0) {
+    if (KIND == 0 || KIND == 3 || KIND == 4) {   // TF32 operands
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
                 d_tmem),
@@ -178,15 +182,16 @@ __global__ void __launch_bounds__(NT, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tA2,
           const __grid_constant__ CUtensorMap tB, const __grid_constant__ CUtensorMap tB2,
           const __grid_constant__ CUtensorMap tC, TcArgs a) {
-    constexpr bool X3 = KIND == 0 || KIND == 3;
-    constexpr bool SPLIT_A = KIND == 3;   // converter warps 10..13 split A in shared memory
+    constexpr bool X3 = KIND == 0 || KIND == 3 || KIND == 4;
+    constexpr bool SPLIT_A = KIND == 3 || KIND == 4;   // converter warps 10.. split A in shared memory
+    constexpr int NCONV = KIND == 3 ? 128 : 64;        // converter threads (kind 4: within 168 registers)
     constexpr uint32_t A_BYTES = 128 * 128;
     constexpr uint32_t B_BYTES = BN * 128;
     constexpr uint32_t STAGE = X3 ? 2 * (A_BYTES + B_BYTES) : (A_BYTES + B_BYTES);
     constexpr int KE = X3 ? 32 : 64;  // K elements per 128-byte row slice
     // kind 3 keeps B_hi and B_lo side by side in a stage, so that one N = 2 BN
     // instruction forms A_hi [B_hi | B_lo]: its accumulator is 2 BN columns wide
-    constexpr bool CAT = SPLIT_A;
+    constexpr bool CAT = KIND == 3;
     constexpr uint32_t ACC_COLS = CAT ? 2 * BN : BN;
     constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
     constexpr uint32_t B2_OFF = CAT ? A_BYTES + B_BYTES : 2 * A_BYTES + B_BYTES;   // B_lo in a stage
@@ -213,7 +218,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
         for (int s = 0; s < NS; ++s) {
             mb_init(&full[s], 1);
             mb_init(&empty[s], 1);
-            mb_init(&conv[s], 128);
+            mb_init(&conv[s], NCONV);
         }
         for (int b = 0; b < 2; ++b) {
             mb_init(&accf[b], 1);
@@ -294,6 +299,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                         const uint64_t da = sw128_desc(st), db = sw128_desc(st + A_BYTES) + boff;
                         const uint64_t dal = sw128_desc(st + A2_OFF);
                         const uint64_t dbl = sw128_desc(st + B2_OFF) + boff;
+                        if (SPLIT_A && !CAT) {
+                            // kind 4: A_lo first, so that the three products go in kind 0's
+                            // order (hi hi, hi lo, lo hi per K-step) and give its sums exactly
+                            if (!mb_wait(&conv[s], ph, abort)) { *abort = 1; ok = false; break; }
+                            fence_after();
+                        }
                         if (CAT) {
                             // A_hi x [B_hi | B_lo]: columns [0, BN) get A_hi B_hi, [BN, 2 BN) A_hi B_lo
 #pragma unroll
@@ -310,11 +321,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                                 mma<KIND>(d, da + adv, db + adv, idesc, acc);
                                 if (X3) {
                                     mma<KIND>(d, da + adv, dbl + adv, idesc, 1u);
-                                    if (!SPLIT_A) mma<KIND>(d, dal + adv, db + adv, idesc, 1u);
+                                    mma<KIND>(d, dal + adv, db + adv, idesc, 1u);
                                 }
                             }
                         }
-                        if (SPLIT_A) {
+                        if (CAT) {
                             // the A_lo x B_hi products once the converters have written A_lo
                             if (!mb_wait(&conv[s], ph, abort)) { *abort = 1; ok = false; break; }
                             fence_after();
@@ -351,7 +362,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtens
                 const float4 *hi = reinterpret_cast<const float4 *>(st);
                 float4 *lo = reinterpret_cast<float4 *>(st + A2_OFF);
 #pragma unroll
-                for (int e = ct; e < (int)(A_BYTES / 16); e += 128) {
+                for (int e = ct; e < (int)(A_BYTES / 16); e += NCONV) {
                     const float4 x = hi[e];
                     float4 l;
                     l.x = x.x - __uint_as_float(__float_as_uint(x.x) & 0xffffe000u);
@@ -547,8 +558,8 @@ bool make_map(CUtensorMap *m, const void *ptr, int elem_bytes, int64_t rows, int
 template <int BN, int KIND, int NS>
 cudaError_t launch_tc(const CUtensorMap &tA, const CUtensorMap &tA2, const CUtensorMap &tB,
                       const CUtensorMap &tB2, const CUtensorMap &tC, TcArgs a, int num_sms, cudaStream_t s) {
-    constexpr uint32_t STAGE = (KIND == 0 || KIND == 3 ? 2 : 1) * (128 * 128 + BN * 128);
-    constexpr int NT = KIND == 3 ? TCG_THREADS + 128 : TCG_THREADS;
+    constexpr uint32_t STAGE = (KIND == 0 || KIND == 3 || KIND == 4 ? 2 : 1) * (128 * 128 + BN * 128);
+    constexpr int NT = KIND == 3 ? TCG_THREADS + 128 : (KIND == 4 ? TCG_THREADS + 64 : TCG_THREADS);
     const size_t smem = 1024 + (size_t)NS * STAGE + 8 * TCG_STG + (3 * NS + 4) * 8 + 16;
     static_assert(1024 + NS * STAGE + 8 * TCG_STG + (3 * NS + 4) * 8 + 16 <= 232448, "shared memory");
     auto kfn = k_tc_gemm<BN, KIND, NS, NT>;
@@ -562,9 +573,9 @@ cudaError_t launch_tc(const CUtensorMap &tA, const CUtensorMap &tA2, const CUten
 }  // namespace
 
 // C[M][N] (row stride ldc) = A[M][K] (row stride lda) * B[N][K]^T (row stride ldb).
-// kind 0: A = (A_hi, A_lo), B = (B_hi, B_lo) FP32 arrays (3xTF32); kind 3: A in
-// FP32 (split on chip, A2 ignored), B = (B_hi, B_lo); kind 1 / 2: A, B bf16 / fp16
-// (A2, B2 ignored).  bn = 256 or 128.  Row strides in
+// kind 0: A = (A_hi, A_lo), B = (B_hi, B_lo) FP32 arrays (3xTF32); kind 3 (bn =
+// 128) and kind 4 (bn = 256): A in FP32 (split on chip, A2 ignored), B = (B_hi,
+// B_lo); kind 1 / 2: A, B bf16 / fp16 (A2, B2 ignored).  bn = 256 or 128.  Row strides in
 // elements must make 16-byte multiples; base pointers 16-byte aligned.  With C16
 // non-null the result is written there as bf16 (round to nearest), row stride
 // ldc elements, and C is not used.
@@ -572,7 +583,7 @@ cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const 
                     const void *B, const void *B2, int64_t ldb, float *C, int64_t ldc, int *err,
                     int num_sms, cudaStream_t s, const int2 *kband, const int2 *nband, uint16_t *C16,
                     int b_blocked) {
-    const int eb = (kind == 0 || kind == 3) ? 4 : 2;
+    const int eb = (kind == 0 || kind == 3 || kind == 4) ? 4 : 2;
     if (kband && nband) return cudaErrorInvalidValue;              // one kind of band at a time
     if (nband && (N + bn - 1) / bn != 1) return cudaErrorInvalidValue;   // quarters of the only n-tile
     const int ke = 128 / eb, nk = (K * eb + 127) / 128;
@@ -585,7 +596,7 @@ cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const 
     if (kind == 0) {
         if (!make_map(&tA2, A2, eb, M, K, lda, 128) || !make_map(&tB2, B2, eb, brows, bcols, bld, bn))
             return cudaErrorInvalidValue;
-    } else if (kind == 3) {
+    } else if (kind == 3 || kind == 4) {
         tA2 = tA;
         if (!make_map(&tB2, B2, eb, brows, bcols, bld, bn)) return cudaErrorInvalidValue;
     } else {
@@ -620,13 +631,15 @@ cudaError_t tc_gemm(int kind, int bn, int M, int N, int K, const void *A, const 
     a.kband = kband;
     a.nband = nband;
     if (bn == 256) {
-        if (kind == 3) return cudaErrorInvalidValue;   // the on-chip A split is built for bn = 128
+        if (kind == 3) return cudaErrorInvalidValue;   // the concatenated-B form is built for bn = 128
         if (kind == 0) return launch_tc<256, 0, 2>(tA, tA2, tB, tB2, tC, a, num_sms, s);
+        if (kind == 4) return launch_tc<256, 4, 2>(tA, tA2, tB, tB2, tC, a, num_sms, s);
         if (kind == 1) return launch_tc<256, 1, 4>(tA, tA2, tB, tB2, tC, a, num_sms, s);
         return launch_tc<256, 2, 4>(tA, tA2, tB, tB2, tC, a, num_sms, s);
     }
     if (kind == 0) return launch_tc<128, 0, 3>(tA, tA2, tB, tB2, tC, a, num_sms, s);
     if (kind == 3) return launch_tc<128, 3, 3>(tA, tA2, tB, tB2, tC, a, num_sms, s);
+    if (kind == 4) return cudaErrorInvalidValue;   // built for bn = 256
     if (kind == 1) return launch_tc<128, 1, 6>(tA, tA2, tB, tB2, tC, a, num_sms, s);
     return launch_tc<128, 2, 6>(tA, tA2, tB, tB2, tC, a, num_sms, s);
 }
